@@ -1,0 +1,320 @@
+"""Benchmark of the image-source RIR + convolution hot path on GB300.
+
+One step = one pass of the whole path over one batch: RIRs of 1024 shoebox
+rooms (8-mic array, lattice order 15, 81-tap Hann-windowed-sinc fractional
+delays, 8192 samples at 16 kHz), then the convolution of each room's 1 s
+white-Gaussian source with its 8 RIRs, then Gaussian noise at a per-room SNR
+drawn from U[0, 30] dB.  Inputs are synthetic (the paper's recordings are not
+available); shapes follow the paper's dataset generation (arXiv 2104.13347,
+Sec. II.A, III.A).
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
+on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("image-source taps/s and mic-samples/s at ≤1e-5 rel-L2; "
+          "served p50/p99 latency")
+N_ROOMS, N_MICS, ORDER, LH, FS, TS = 1024, 8, 15, 8192, 16000.0, 16000
+WORKLOAD = (f"{N_ROOMS} rooms U[3,10]x[3,8]x[2.5,4] m, beta U[0.5,0.95], {N_MICS}-mic 5 cm "
+            f"circle, order {ORDER}, 81-tap Hann sinc, RIR {LH} @ 16 kHz; 1 s sources, "
+            "SNR U[0,30] dB")
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+class Clocks:
+    """Samples nvidia-smi clocks and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            with open(self.path) as f:
+                for line in f:
+                    p = [x.strip() for x in line.split(",")]
+                    if len(p) >= 9 and p[1].replace(".", "").isdigit():
+                        rows.append(p)
+        except OSError:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except OSError:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]),
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+    return ws, rank
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_sample(rooms, srcs, n_rir_rooms=6, n_conv_rooms=1):
+    """Times the oracle (as it stands) on a bounded sample of the workload:
+    the RIRs of n_rir_rooms rooms and the convolutions of n_conv_rooms rooms.
+    Returns step-equivalent taps/s for the sampled rooms."""
+    import oracle
+    threads = oracle.max_threads()
+    t0 = time.perf_counter()
+    hs, st = oracle.rir_batch(rooms[:n_rir_rooms], n_threads=threads)
+    t_rir = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.convolve_batch(hs[:n_conv_rooms], [s.astype(np.float64) for s in srcs[:n_conv_rooms]],
+                          n_threads=threads)
+    t_conv = (time.perf_counter() - t0) * n_rir_rooms / n_conv_rooms
+    taps = int(st[:, 2].sum())
+    mic_samples = n_rir_rooms * N_MICS * (TS + LH - 1)
+    return {"value": taps / (t_rir + t_conv), "unit": "taps/s", "cores": threads,
+            "kind": "oracle",
+            "sample": (f"RIRs of {n_rir_rooms} rooms x {N_MICS} mics of the workload "
+                       f"({t_rir:.1f} s) + convolutions of {n_conv_rooms} room(s) scaled to "
+                       f"{n_rir_rooms} ({t_conv:.1f} s)"),
+            "mic_samples_per_s": mic_samples / (t_rir + t_conv),
+            "seconds": t_rir + t_conv}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    from paper_2104_13347_gb300 import workloads as wl
+    rooms = wl.room_batch(N_ROOMS, seed=1002)
+    srcs = wl.sources(rooms[:8], 1.0, seed=1003)
+    times, last = [], None
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        last = cpu_sample(rooms, srcs, n_rir_rooms=1, n_conv_rooms=1)
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    line = {"metric": METRIC, "value": last["value"], "unit": "taps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * statistics.median(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD, "rooms_per_step": 1,
+                       "note": "FP64 CPU oracle, one room's RIRs and convolutions per step"},
+            "cpu_baseline": {k: last[k] for k in ("value", "unit", "cores", "kind", "sample")},
+            "e2e": {"value": last["value"], "unit": "taps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, ws, rank):
+    import torch
+    import paper_2104_13347_gb300 as ism
+    from paper_2104_13347_gb300 import workloads as wl
+
+    ism.load()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    seed = 1002 + 7919 * rank  # each rank its own batch (weak scaling)
+    rooms = wl.room_batch(N_ROOMS, seed=seed)
+    srcs = wl.sources(rooms, 1.0, seed=seed + 1)
+    snr = wl.snrs(N_ROOMS, seed=seed + 2)
+    n_rirs, hl = ism.rir_batch_size(rooms)
+    jobs, ylen = ism.conv_jobs([N_MICS] * N_ROOMS, [LH] * N_ROOMS, [TS] * N_ROOMS, snr_db=snr,
+                               noise_ids=np.arange(N_ROOMS) + rank * N_ROOMS)
+    precision = ism.BF16X3 if args.precision == "bf16x3" else ism.F32
+    stream = torch.cuda.current_stream()
+    src_host = torch.from_numpy(np.concatenate(srcs)).pin_memory()
+    src = src_host.to(dev)
+    h = torch.empty(hl, device=dev)
+    y = torch.empty(ylen, device=dev)
+    stats = torch.zeros(2 * n_rirs, dtype=torch.int64, device=dev)
+    arr, keep = ism.make_rooms(rooms)  # descriptors built once (host)
+
+    ism.rir_batch(rooms, h=h, stats=stats, window=args.window)
+    torch.cuda.synchronize()
+    taps = int(stats.view(-1, 2)[:, 1].sum().item())
+    mic_samples = N_ROOMS * N_MICS * (TS + LH - 1)
+
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    rir_ms, conv_ms, noise_ms = [], [], []
+
+    def step(record=False):
+        if record:
+            ev[0].record(stream)
+        ism.rir_batch(rooms, h=h, window=args.window)
+        if record:
+            ev[1].record(stream)
+        ism.convolve_batch(jobs, h, src, y, seed=12345, precision=precision)
+        if record:
+            ev[2].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier(ws)
+    torch.cuda.synchronize()
+    clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with clocks:
+        start.record(stream)
+        for _ in range(args.steps):
+            step(record=True)
+            torch.cuda.synchronize()
+            rir_ms.append(ev[0].elapsed_time(ev[1]))
+            conv_ms.append(ev[1].elapsed_time(ev[2]))
+        end.record(stream)
+        torch.cuda.synchronize()
+    barrier(ws)
+    torch.cuda.synchronize()
+    total_ms = max_over_ranks(start.elapsed_time(end), ws)
+    ms_step = total_ms / args.steps
+    clk = clocks.summary()
+
+    # end to end through the public API with host buffers: pinned source in,
+    # noisy microphone signals out, both copies inside the timed region
+    y_host = torch.empty(ylen, dtype=torch.float32).pin_memory()
+    e_start, e_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    e_start.record(stream)
+    for _ in range(e2e_steps):
+        src.copy_(src_host, non_blocking=True)
+        ism.rir_batch(rooms, h=h, window=args.window)
+        ism.convolve_batch(jobs, h, src, y, seed=12345, precision=precision)
+        y_host.copy_(y, non_blocking=True)
+    e_end.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(e_start.elapsed_time(e_end), ws) / e2e_steps
+
+    pk, pk_kind = peaks()
+    sm_mhz = pk.get("sm_max_mhz", 2070.0)
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    # K1 is bound by the reciprocal (MUFU) pipe: 16 results per clock per SM,
+    # one reciprocal per tap.
+    peak_taps = 16.0 * n_sm * sm_mhz * 1e6
+    rir_med = statistics.median(rir_ms)
+    achieved = taps / (rir_med * 1e-3)
+    line = {
+        "metric": METRIC, "value": ws * taps / (ms_step * 1e-3), "unit": "taps/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if precision == ism.F32 else "bf16x3+f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "rooms": N_ROOMS, "mics": N_MICS, "order": ORDER,
+                   "rir_len": LH, "src_len": TS, "n_taps": 81, "window": args.window or 1024,
+                   "precision": args.precision, "parallelism": f"replicas x{ws}",
+                   "l2": "inputs larger than L2 (h 268 MB, y 793 MB per step)"},
+        "secondary": {"mic_samples_per_s": ws * mic_samples / (ms_step * 1e-3),
+                      "taps_per_step": taps, "mic_samples_per_step": mic_samples,
+                      "stage_ms": {"rir": rir_med, "conv_noise": statistics.median(conv_ms)}},
+        "roofline": {"bound": "alu", "kernel": "k_ism_taps", "achieved": achieved / 1e9,
+                     "peak": peak_taps / 1e9, "unit": "Gtap/s", "frac": achieved / peak_taps,
+                     "traffic": None,
+                     "peak_note": f"16 MUFU rcp/clk/SM x {n_sm} SMs x {sm_mhz:.0f} MHz "
+                                  f"({pk_kind} max clock)"},
+        "e2e": {"value": ws * taps / (e2e_ms * 1e-3), "unit": "taps/s",
+                "h2d_bytes_per_step": int(src_host.numel() * 4),
+                "d2h_bytes_per_step": int(ylen * 4), "ms_per_step": e2e_ms},
+        "gpu_launches": args.steps * (1 + 1 + 2),
+        "clocks": clk,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cb = cpu_sample(rooms, srcs)
+        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="f32", choices=["f32", "bf16x3"])
+    ap.add_argument("--window", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    ws, rank = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

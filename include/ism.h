@@ -1,0 +1,251 @@
+/*
+ * ism.h -- C ABI of the GB300 image-source RIR and convolution library
+ * (libism.so).
+ *
+ * The library computes, on one GPU, the dataset-generation path of
+ * arXiv 2104.13347, Sec. II.A: shoebox room impulse responses from the
+ * image-source method with fractional delays, then the batch convolution of
+ * source signals with those RIRs into multichannel microphone pressure, with
+ * the additive Gaussian noise at a chosen SNR of Sec. III.A.
+ *
+ * Conventions shared by every entry point:
+ *  - Plain C types only.  Pointers named *_dev are CUDA device pointers
+ *    (e.g. from a torch tensor); everything else is host memory.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Batch calls only enqueue work: they return once the work is
+ *    queued, and outputs are valid after the stream reaches that point.
+ *  - The caller owns every buffer it passes.  Host arrays may be freed once
+ *    the call returns.  Device outputs must not be read or freed before the
+ *    stream has passed the call.
+ *  - Every call returns an ism_status.  On error nothing has been launched,
+ *    and ism_last_error_string() (thread-local) says why.  No C++ exception
+ *    crosses this boundary.
+ *  - Lengths and offsets are counted in elements, not bytes.
+ */
+#ifndef ISM_H
+#define ISM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum ism_status {
+    ISM_OK = 0,
+    ISM_PENDING = 1,             /* serve: result not ready yet */
+    ISM_ERR_INVALID_ARG = 2,     /* validation failed; nothing launched */
+    ISM_ERR_OUT_OF_MEMORY = 3,   /* device scratch or serve pool exhausted */
+    ISM_ERR_BUSY = 4,            /* serve: cannot admit the request now */
+    ISM_ERR_TIMEOUT = 5,         /* serve: wait deadline passed */
+    ISM_ERR_CUDA = 6,            /* a CUDA runtime call failed */
+    ISM_ERR_INTERNAL = 7,        /* a kernel reported an internal error */
+    ISM_ERR_UNKNOWN_TICKET = 8   /* serve: ticket never issued or released */
+} ism_status;
+
+/* Fractional-delay filter.
+ *  ISM_FD_HANN_SINC: n_taps = 2H+1 (odd) taps j = -H..H at k0 + j, where
+ *    k0 = rint(tau), f = tau - k0, tap = sinc(j - f) * 0.5 (1 + cos(pi (j-f)/(H+1))).
+ *  ISM_FD_LAGRANGE: the paper's 7th-order Lagrange filter (Sec. II.A),
+ *    n_taps = P+1 (even) taps j = 0..P at floor(tau) - (P-1)/2 + j with
+ *    coefficients prod_{i != j} (D - i)/(j - i), D = tau - floor(tau) + (P-1)/2. */
+typedef enum ism_fd_kind { ISM_FD_HANN_SINC = 0, ISM_FD_LAGRANGE = 1 } ism_fd_kind;
+
+/* Arithmetic of the convolution.
+ *  ISM_F32: FP32 direct convolution on the CUDA cores.
+ *  ISM_BF16X3: tensor-core convolution with each operand split into
+ *    bf16 hi + lo parts, the cross products accumulated in FP32. */
+typedef enum ism_precision { ISM_F32 = 0, ISM_BF16X3 = 1 } ism_precision;
+
+/* One shoebox room, following the problem statement of Sec. II.A.
+ * dims    room size Lx, Ly, Lz in metres; the room is [0,Lx]x[0,Ly]x[0,Lz].
+ * beta    pressure reflection coefficient of each wall, in [0, 1], ordered
+ *         x=0, x=Lx, y=0, y=Ly, z=0, z=Lz.  An image reaching the mic after
+ *         a reflections on one wall is damped by beta^a (0^0 = 1).
+ * src     source position (metres), strictly inside the room.
+ * mics    host array of 3*n_mics doubles (x,y,z per mic), strictly inside
+ *         the room and not on the source.
+ * order   lattice order N >= 0: images (u,v,w,l,m,n), u,v,w in {0,1},
+ *         l,m,n in [-N, N], 8 (2N+1)^3 in all.
+ * fs, c   sampling rate (Hz) and speed of sound (m/s), both > 0.
+ * n_taps  fractional-delay filter length (see ism_fd_kind).
+ * rir_len RIR length Lh >= 1 in samples; taps outside [0, Lh) are dropped. */
+typedef struct ism_room {
+    double dims[3];
+    double beta[6];
+    double src[3];
+    const double *mics;
+    int32_t n_mics;
+    int32_t order;
+    double fs;
+    double c;
+    int32_t n_taps;
+    int32_t fd_kind;
+    int64_t rir_len;
+} ism_room;
+
+/* Options of ism_rir_batch_ex (zero-initialise for defaults). */
+typedef struct ism_rir_opts {
+    int32_t window;      /* output window per work item, samples; 0 = tuned */
+    int32_t per_room;    /* 1 = one plain launch per room (the unbatched path) */
+    int64_t *stats_dev;  /* optional device int64[2 * n_rirs]: per RIR, the
+                            images with a tap in [0, Lh) and the taps that
+                            landed in [0, Lh); accumulated (not overwritten),
+                            so zero it first */
+} ism_rir_opts;
+
+/* ism_rir_batch -- RIRs of a batch of rooms (Sec. II.A: image sources,
+ * per-image delay split, wall dampings over spherical spreading, fractional
+ * delay taps accumulated into h).
+ *
+ * rooms      host array of n_rooms rooms (n_rooms >= 0; 0 is a no-op).
+ * h_dev      device float output; RIR j (rooms in order, mics in order
+ *            within a room) occupies h_dev[h_offsets[j] .. + rir_len).
+ * h_offsets  host int64 array with one offset per RIR, or NULL for the
+ *            packed layout (each room's mics back to back, rooms back to
+ *            back).  Ranges must not overlap.
+ * Every output sample of every RIR is written (zeros where no tap lands).
+ * The image delay tau = d fs / c is split with the same FP64 rounding rule
+ * as the definition (ties to even), so integer delays and window counts are
+ * exact; taps are accumulated in FP32.
+ * Errors: ISM_ERR_INVALID_ARG for a point outside the room, beta outside
+ * [0,1], a tap count of the wrong parity for the filter, fs/c <= 0, order
+ * < 0 or > 200, rir_len < 1, n_mics < 1, or a NULL pointer; ISM_ERR_CUDA if
+ * a launch or scratch allocation fails. */
+int ism_rir_batch(const ism_room *rooms, int64_t n_rooms, float *h_dev,
+                  const int64_t *h_offsets, void *stream);
+
+/* As ism_rir_batch, with options (NULL = defaults). */
+int ism_rir_batch_ex(const ism_room *rooms, int64_t n_rooms, float *h_dev,
+                     const int64_t *h_offsets, const ism_rir_opts *opts, void *stream);
+
+/* Number of RIRs (sum of n_mics) and packed h length of a batch, for sizing
+ * buffers; host only. */
+int ism_rir_batch_size(const ism_room *rooms, int64_t n_rooms, int64_t *n_rirs,
+                       int64_t *h_len);
+
+/* One room of a convolution batch (Sec. II.A, "batch convolutions" of the
+ * RIRs with the source signals; Sec. III.A noise).
+ * n_mics      RIRs of the room, stored back to back in h_dev starting at
+ *             h_offset, each rir_len long.
+ * src_offset  the room's source signal, src_len samples, in src_dev.
+ * y_offset    output start; mic m writes y_dev[y_offset + m*(src_len +
+ *             rir_len - 1) ...], the full linear convolution.
+ * snr_db      noise level: each mic gets Gaussian noise of variance
+ *             mean(y^2 over all of the room's mics and samples) / 10^(snr/10).
+ *             NaN = no noise.
+ * noise_id    identifies the room's noise streams (with the call's seed):
+ *             the same (seed, noise_id) gives the same noise in any batch. */
+typedef struct ism_conv_job {
+    int32_t n_mics;
+    int32_t reserved;
+    int64_t rir_len;
+    int64_t src_len;
+    int64_t h_offset;
+    int64_t src_offset;
+    int64_t y_offset;
+    float snr_db;
+    int32_t reserved2;
+    uint64_t noise_id;
+} ism_conv_job;
+
+/* ism_convolve_batch -- y = s * h for every mic of every job, plus noise.
+ * jobs       host array of n_jobs jobs.
+ * h_dev      device float RIRs; src_dev device float sources; y_dev device
+ *            float outputs (must not overlap the inputs).
+ * seed       noise seed (SplitMix64 counters, Box--Muller).
+ * precision  ISM_F32 or ISM_BF16X3.
+ * Errors: ISM_ERR_INVALID_ARG (bad lengths, NULL pointers, unknown
+ * precision), ISM_ERR_CUDA, ISM_ERR_OUT_OF_MEMORY (scratch). */
+int ism_convolve_batch(const ism_conv_job *jobs, int64_t n_jobs, const float *h_dev,
+                       const float *src_dev, float *y_dev, uint64_t seed,
+                       int32_t precision, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Serving: continuous batching of RIR + convolution requests.
+ * Requests of uneven sizes arrive at any time; a background thread admits
+ * them while device memory (max_hbm_bytes) and slots allow, packs the
+ * admitted ones into ragged batches, and runs them on its streams so that
+ * batches overlap on the GPU.  Results stay on the device until released.
+ * Each request's result is the same alone or mixed with others, up to
+ * floating-point rounding of its own reduction order, which does not depend
+ * on the mix.
+ * ------------------------------------------------------------------------ */
+typedef struct ism_server ism_server;
+
+typedef struct ism_serve_config {
+    int64_t max_hbm_bytes;   /* device bytes the server may hold (0 = 8 GiB) */
+    int32_t max_batch;       /* requests per launch batch (0 = 64) */
+    int32_t n_streams;       /* concurrent batches in flight (0 = 2) */
+    int32_t precision;       /* ISM_F32 or ISM_BF16X3 */
+    int32_t max_queue;       /* waiting requests before submit says BUSY (0 = 4096) */
+    uint64_t seed;           /* noise seed */
+    int32_t device;          /* CUDA device ordinal */
+    int32_t reserved;
+} ism_serve_config;
+
+typedef struct ism_request {
+    ism_room room;
+    const float *src_host;   /* source signal, src_len floats; copied at submit */
+    int64_t src_len;
+    float snr_db;            /* NaN = no noise */
+    int32_t reserved;
+} ism_request;
+
+typedef struct ism_result {
+    const float *h_dev;      /* n_mics x rir_len, library-owned until release */
+    const float *y_dev;      /* n_mics x y_len, library-owned until release */
+    int32_t n_mics;
+    int32_t reserved;
+    int64_t rir_len;
+    int64_t y_len;
+    double queue_s;          /* submit -> launch */
+    double latency_s;        /* submit -> result ready on the device */
+} ism_result;
+
+typedef struct ism_serve_stats {
+    int64_t submitted, completed, rejected_busy, batches;
+    int64_t queued, in_flight;
+    int64_t bytes_in_use, bytes_peak;
+    int64_t taps;            /* image-source taps that landed in the RIRs */
+    int64_t mic_samples;     /* convolution outputs written */
+} ism_serve_stats;
+
+/* Creates a server on config->device.  Errors: INVALID_ARG, CUDA. */
+int ism_serve_create(const ism_serve_config *config, ism_server **out);
+
+/* Validates and enqueues a request; returns its ticket.  ISM_ERR_BUSY if
+ * the queue is full or the request alone needs more than max_hbm_bytes;
+ * ISM_ERR_INVALID_ARG for an invalid room or source. */
+int ism_serve_submit(ism_server *server, const ism_request *request, uint64_t *ticket);
+
+/* ISM_OK and the result if ready, ISM_PENDING if not yet,
+ * ISM_ERR_UNKNOWN_TICKET if the ticket was never issued or is released,
+ * ISM_ERR_CUDA / ISM_ERR_INTERNAL if the request's batch failed. */
+int ism_serve_poll(ism_server *server, uint64_t ticket, ism_result *out);
+
+/* As poll, blocking up to timeout_s seconds (ISM_ERR_TIMEOUT after). */
+int ism_serve_wait(ism_server *server, uint64_t ticket, double timeout_s, ism_result *out);
+
+/* Frees a finished request's device memory.  ISM_ERR_UNKNOWN_TICKET for an
+ * unknown ticket, ISM_PENDING if it is still running (not released). */
+int ism_serve_release(ism_server *server, uint64_t ticket);
+
+int ism_serve_stats_get(ism_server *server, ism_serve_stats *out);
+
+/* Stops the serving thread after in-flight batches finish and frees all
+ * server memory; outstanding results become invalid. */
+int ism_serve_destroy(ism_server *server);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char *ism_last_error_string(void);
+
+/* Library version string. */
+const char *ism_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ISM_H */

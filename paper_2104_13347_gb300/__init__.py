@@ -1,0 +1,17 @@
+"""GB300-native image-source RIR synthesis and multichannel convolution.
+
+The dataset-generation hot path of arXiv 2104.13347 (Sec. II.A): shoebox
+room impulse responses from the image-source method with fractional delays,
+then batch convolution of source signals with the RIRs into microphone
+pressure, with additive noise at a chosen SNR (Sec. III.A).  The compute runs
+in libism.so (hand-written CUDA for sm_103a) behind the C ABI of
+include/ism.h; this package is its Python binding.
+
+    import paper_2104_13347_gb300 as ism
+    h = ism.rir_batch(rooms)            # float32 CUDA tensor, packed RIRs
+"""
+from ._lib import (BF16X3, F32, FD_HANN_SINC, FD_LAGRANGE, IsmError, check, conv_jobs,  # noqa
+                   convolve_batch, last_error, load, make_rooms, rir_batch, rir_batch_size)
+
+__all__ = ["load", "rir_batch", "rir_batch_size", "convolve_batch", "conv_jobs", "IsmError",
+           "F32", "BF16X3", "FD_HANN_SINC", "FD_LAGRANGE", "last_error", "check", "make_rooms"]

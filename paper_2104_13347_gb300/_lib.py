@@ -1,0 +1,211 @@
+"""ctypes binding of libism.so (include/ism.h).
+
+Argument marshalling only: every step of the RIR and convolution path runs
+in the library's CUDA kernels.  torch supplies device memory and streams.
+If libism.so is missing or cannot be loaded this module raises; there is no
+fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libism.so")
+
+ISM_OK, ISM_PENDING = 0, 1
+ISM_ERR_INVALID_ARG, ISM_ERR_OUT_OF_MEMORY, ISM_ERR_BUSY = 2, 3, 4
+ISM_ERR_TIMEOUT, ISM_ERR_CUDA, ISM_ERR_INTERNAL, ISM_ERR_UNKNOWN_TICKET = 5, 6, 7, 8
+FD_HANN_SINC, FD_LAGRANGE = 0, 1
+F32, BF16X3 = 0, 1
+
+c_i32, c_i64, c_u64, c_f32, c_f64, c_vp = (ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64,
+                                           ctypes.c_float, ctypes.c_double, ctypes.c_void_p)
+
+
+class Room(ctypes.Structure):
+    _fields_ = [("dims", c_f64 * 3), ("beta", c_f64 * 6), ("src", c_f64 * 3), ("mics", c_vp),
+                ("n_mics", c_i32), ("order", c_i32), ("fs", c_f64), ("c", c_f64),
+                ("n_taps", c_i32), ("fd_kind", c_i32), ("rir_len", c_i64)]
+
+
+class RirOpts(ctypes.Structure):
+    _fields_ = [("window", c_i32), ("per_room", c_i32), ("stats_dev", c_vp)]
+
+
+class ConvJob(ctypes.Structure):
+    _fields_ = [("n_mics", c_i32), ("reserved", c_i32), ("rir_len", c_i64), ("src_len", c_i64),
+                ("h_offset", c_i64), ("src_offset", c_i64), ("y_offset", c_i64),
+                ("snr_db", c_f32), ("reserved2", c_i32), ("noise_id", c_u64)]
+
+
+class ServeConfig(ctypes.Structure):
+    _fields_ = [("max_hbm_bytes", c_i64), ("max_batch", c_i32), ("n_streams", c_i32),
+                ("precision", c_i32), ("max_queue", c_i32), ("seed", c_u64), ("device", c_i32),
+                ("reserved", c_i32)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("room", Room), ("src_host", c_vp), ("src_len", c_i64), ("snr_db", c_f32),
+                ("reserved", c_i32)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("h_dev", c_vp), ("y_dev", c_vp), ("n_mics", c_i32), ("reserved", c_i32),
+                ("rir_len", c_i64), ("y_len", c_i64), ("queue_s", c_f64), ("latency_s", c_f64)]
+
+
+class ServeStats(ctypes.Structure):
+    _fields_ = [(n, c_i64) for n in ("submitted", "completed", "rejected_busy", "batches",
+                                     "queued", "in_flight", "bytes_in_use", "bytes_peak", "taps",
+                                     "mic_samples")]
+
+
+# every symbol include/ism.h declares, with its ctypes signature
+SIGNATURES = {
+    "ism_rir_batch": (c_i32, [c_vp, c_i64, c_vp, c_vp, c_vp]),
+    "ism_rir_batch_ex": (c_i32, [c_vp, c_i64, c_vp, c_vp, c_vp, c_vp]),
+    "ism_rir_batch_size": (c_i32, [c_vp, c_i64, c_vp, c_vp]),
+    "ism_convolve_batch": (c_i32, [c_vp, c_i64, c_vp, c_vp, c_vp, c_u64, c_i32, c_vp]),
+    "ism_serve_create": (c_i32, [c_vp, c_vp]),
+    "ism_serve_submit": (c_i32, [c_vp, c_vp, c_vp]),
+    "ism_serve_poll": (c_i32, [c_vp, c_u64, c_vp]),
+    "ism_serve_wait": (c_i32, [c_vp, c_u64, c_f64, c_vp]),
+    "ism_serve_release": (c_i32, [c_vp, c_u64]),
+    "ism_serve_stats_get": (c_i32, [c_vp, c_vp]),
+    "ism_serve_destroy": (c_i32, [c_vp]),
+    "ism_last_error_string": (ctypes.c_char_p, []),
+    "ism_version": (ctypes.c_char_p, []),
+}
+
+_lib = None
+_lock = threading.Lock()
+
+
+class IsmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"ism status {status}: {msg}")
+        self.status = status
+
+
+def load(path: str = LIB_PATH):
+    """Loads libism.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with "
+                               "`python -m paper_2104_13347_gb300.build` (needs nvcc)")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def last_error() -> str:
+    return load().ism_last_error_string().decode()
+
+
+def check(status: int):
+    if status != ISM_OK:
+        raise IsmError(status, last_error())
+    return status
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def make_rooms(rooms):
+    """Room dicts (dims, beta, src, mics (M,3), fs, c, order, n_taps,
+    fd_kind, rir_len) -> (ctypes array, arrays kept alive)."""
+    arr = (Room * len(rooms))()
+    keep = []
+    for i, r in enumerate(rooms):
+        mics = np.ascontiguousarray(np.asarray(r["mics"], np.float64).reshape(-1, 3))
+        keep.append(mics)
+        R = arr[i]
+        R.dims[:] = [float(x) for x in r["dims"]]
+        R.beta[:] = [float(x) for x in r["beta"]]
+        R.src[:] = [float(x) for x in r["src"]]
+        R.mics = mics.ctypes.data
+        R.n_mics = mics.shape[0]
+        R.order = int(r["order"])
+        R.fs = float(r["fs"])
+        R.c = float(r["c"])
+        R.n_taps = int(r.get("n_taps", 81))
+        R.fd_kind = int(r.get("fd_kind", FD_HANN_SINC))
+        R.rir_len = int(r["rir_len"])
+    return arr, keep
+
+
+def rir_batch_size(rooms):
+    arr, keep = make_rooms(rooms)
+    nr, hl = c_i64(), c_i64()
+    check(load().ism_rir_batch_size(arr, len(rooms), ctypes.byref(nr), ctypes.byref(hl)))
+    return nr.value, hl.value
+
+
+def rir_batch(rooms, h=None, h_offsets=None, window=0, per_room=False, stats=None, stream=None):
+    """ism_rir_batch_ex: RIRs of the rooms into h (a float32 CUDA tensor;
+    allocated packed if None).  stats: optional int64 CUDA tensor (2 per
+    RIR), accumulated.  Returns h."""
+    import torch
+    lib = load()
+    arr, keep = make_rooms(rooms)
+    if h is None:
+        _, hl = rir_batch_size(rooms)
+        h = torch.empty(hl, dtype=torch.float32, device="cuda")
+    assert h.dtype == torch.float32 and h.is_cuda and h.is_contiguous()
+    offs = None
+    if h_offsets is not None:
+        offs = np.ascontiguousarray(h_offsets, np.int64)
+        keep.append(offs)
+    opts = RirOpts(int(window), int(bool(per_room)), stats.data_ptr() if stats is not None else None)
+    check(lib.ism_rir_batch_ex(arr, len(rooms), c_vp(h.data_ptr()),
+                               offs.ctypes.data if offs is not None else None,
+                               ctypes.byref(opts), _stream_ptr(stream)))
+    return h
+
+
+def conv_jobs(rooms_mics, rir_lens, src_lens, snr_db=None, noise_ids=None, h_offsets=None,
+              src_offsets=None, y_offsets=None):
+    """Builds the ism_conv_job array for a packed batch: room i has
+    rooms_mics[i] RIRs of rir_lens[i] samples and a source of src_lens[i]
+    samples; outputs are packed (mic-major within a room).  Returns
+    (jobs ctypes array, packed y length)."""
+    n = len(rooms_mics)
+    jobs = (ConvJob * n)()
+    ho = so = yo = 0
+    for i in range(n):
+        M, L, T = int(rooms_mics[i]), int(rir_lens[i]), int(src_lens[i])
+        J = jobs[i]
+        J.n_mics, J.rir_len, J.src_len = M, L, T
+        J.h_offset = ho if h_offsets is None else int(h_offsets[i])
+        J.src_offset = so if src_offsets is None else int(src_offsets[i])
+        J.y_offset = yo if y_offsets is None else int(y_offsets[i])
+        J.snr_db = math.nan if snr_db is None else float(snr_db[i])
+        J.noise_id = i if noise_ids is None else int(noise_ids[i])
+        ho += M * L
+        so += T
+        yo += M * (T + L - 1)
+    return jobs, yo
+
+
+def convolve_batch(jobs, h, src, y, seed=0, precision=F32, stream=None):
+    """ism_convolve_batch over a ConvJob array (see conv_jobs)."""
+    check(load().ism_convolve_batch(jobs, len(jobs), c_vp(h.data_ptr()), c_vp(src.data_ptr()),
+                                    c_vp(y.data_ptr()), c_u64(seed), int(precision),
+                                    _stream_ptr(stream)))
+    return y

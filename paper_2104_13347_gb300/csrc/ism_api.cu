@@ -1,0 +1,375 @@
+// ism_api.cu -- C ABI entry points: validation, job tables, scratch and
+// staging, and dispatch to the kernels (see include/ism.h).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "ism_internal.h"
+
+namespace ism {
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_err;
+
+void set_error(const std::string &msg) { g_err = msg; }
+int fail(int status, const std::string &msg) {
+    g_err = msg;
+    return status;
+}
+int cuda_fail(cudaError_t e, const char *what) {
+    g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    return ISM_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------------------
+// device info, scratch pool, pinned staging
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int kMaxDev = 64;
+std::mutex g_mu;
+int g_sms[kMaxDev];
+cudaMemPool_t g_pool[kMaxDev];
+bool g_pool_ok[kMaxDev];
+
+struct Stage {
+    int dev;
+    void *ptr;
+    size_t size;
+    cudaEvent_t ev;
+    bool used;
+};
+std::vector<Stage> g_stage;
+
+int cur_device(int *d) {
+    cudaError_t e = cudaGetDevice(d);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (*d < 0 || *d >= kMaxDev) return fail(ISM_ERR_INTERNAL, "device ordinal out of range");
+    return ISM_OK;
+}
+}  // namespace
+
+int device_sm_count() {
+    int d = 0;
+    if (cur_device(&d)) return 1;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_sms[d]) cudaDeviceGetAttribute(&g_sms[d], cudaDevAttrMultiProcessorCount, d);
+    return g_sms[d] > 0 ? g_sms[d] : 1;
+}
+
+int scratch_alloc(void **p, size_t bytes, cudaStream_t stream) {
+    int d = 0;
+    if (int st = cur_device(&d)) return st;
+    cudaMemPool_t pool;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        if (!g_pool_ok[d]) {
+            cudaMemPoolProps props;
+            memset(&props, 0, sizeof(props));
+            props.allocType = cudaMemAllocationTypePinned;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = d;
+            cudaError_t e = cudaMemPoolCreate(&g_pool[d], &props);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMemPoolCreate");
+            uint64_t thr = UINT64_MAX;
+            cudaMemPoolSetAttribute(g_pool[d], cudaMemPoolAttrReleaseThreshold, &thr);
+            g_pool_ok[d] = true;
+        }
+        pool = g_pool[d];
+    }
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMallocFromPoolAsync(p, bytes, pool, stream);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return fail(ISM_ERR_OUT_OF_MEMORY, "device scratch allocation failed");
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocFromPoolAsync");
+    return ISM_OK;
+}
+
+void scratch_free(void *p, cudaStream_t stream) {
+    if (p) cudaFreeAsync(p, stream);
+}
+
+int upload_async(void *dev_dst, const void *host_src, size_t bytes, cudaStream_t stream) {
+    if (bytes == 0) return ISM_OK;
+    int d = 0;
+    if (int st = cur_device(&d)) return st;
+    std::lock_guard<std::mutex> lk(g_mu);
+    Stage *slot = nullptr;
+    for (auto &s : g_stage) {
+        if (s.dev != d || s.size < bytes) continue;
+        if (s.used && cudaEventQuery(s.ev) != cudaSuccess) continue;
+        slot = &s;
+        break;
+    }
+    if (!slot) {
+        Stage s{d, nullptr, std::max<size_t>(bytes, 1 << 16), nullptr, false};
+        cudaError_t e = cudaHostAlloc(&s.ptr, s.size, cudaHostAllocDefault);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaHostAlloc(staging)");
+        e = cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            cudaFreeHost(s.ptr);
+            return cuda_fail(e, "cudaEventCreate(staging)");
+        }
+        g_stage.push_back(s);
+        slot = &g_stage.back();
+    }
+    cudaGetLastError();  // clear a not-ready status left by the queries
+    memcpy(slot->ptr, host_src, bytes);
+    cudaError_t e = cudaMemcpyAsync(dev_dst, slot->ptr, bytes, cudaMemcpyHostToDevice, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(upload)");
+    e = cudaEventRecord(slot->ev, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord(staging)");
+    slot->used = true;
+    return ISM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// validation
+// ---------------------------------------------------------------------------
+static bool inside(const double *p, const double *dims) {
+    for (int a = 0; a < 3; ++a)
+        if (!(p[a] > 0.0 && p[a] < dims[a])) return false;
+    return true;
+}
+
+int validate_room(const ism_room &r, int64_t idx) {
+    auto bad = [&](const std::string &why) {
+        return fail(ISM_ERR_INVALID_ARG, "room " + std::to_string(idx) + ": " + why);
+    };
+    for (int a = 0; a < 3; ++a)
+        if (!(r.dims[a] > 0.0) || !isfinite(r.dims[a])) return bad("dims must be finite and > 0");
+    for (int w = 0; w < 6; ++w)
+        if (!(r.beta[w] >= 0.0 && r.beta[w] <= 1.0)) return bad("beta must lie in [0, 1]");
+    if (!inside(r.src, r.dims)) return bad("source not strictly inside the room");
+    if (r.n_mics < 1) return bad("n_mics must be >= 1");
+    if (!r.mics) return bad("mics is NULL");
+    for (int m = 0; m < r.n_mics; ++m) {
+        const double *p = r.mics + 3 * m;
+        if (!inside(p, r.dims)) return bad("mic " + std::to_string(m) + " not strictly inside");
+        const double dx = p[0] - r.src[0], dy = p[1] - r.src[1], dz = p[2] - r.src[2];
+        if (dx * dx + dy * dy + dz * dz < 1e-12) return bad("mic coincides with the source");
+    }
+    if (!(r.fs > 0.0) || !isfinite(r.fs)) return bad("fs must be > 0");
+    if (!(r.c > 0.0) || !isfinite(r.c)) return bad("c must be > 0");
+    if (r.order < 0 || r.order > 200) return bad("order must lie in [0, 200]");
+    if (r.rir_len < 1 || r.rir_len > (int64_t)1 << 30) return bad("rir_len must lie in [1, 2^30]");
+    if (r.fd_kind == ISM_FD_HANN_SINC) {
+        if (r.n_taps < 1 || r.n_taps % 2 == 0 || r.n_taps > 255)
+            return bad("Hann-sinc n_taps must be odd and in [1, 255]");
+    } else if (r.fd_kind == ISM_FD_LAGRANGE) {
+        if (r.n_taps < 2 || r.n_taps % 2 != 0 || r.n_taps > 32)
+            return bad("Lagrange n_taps must be even and in [2, 32]");
+    } else {
+        return bad("unknown fd_kind");
+    }
+    // largest delay must stay representable in the FP32 integer part
+    double reach = 0.0;
+    for (int a = 0; a < 3; ++a) reach += pow((2.0 * r.order + 1.0) * r.dims[a] * 2.0, 2.0);
+    if (sqrt(reach) * r.fs / r.c > 8.0e6) return bad("lattice delays exceed 8e6 samples");
+    return ISM_OK;
+}
+
+}  // namespace ism
+
+using namespace ism;
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char *ism_last_error_string(void) { return g_err.c_str(); }
+
+const char *ism_version(void) { return "ism-gb300 0.1 (sm_103a)"; }
+
+int ism_rir_batch_size(const ism_room *rooms, int64_t n_rooms, int64_t *n_rirs, int64_t *h_len) {
+    if (n_rooms < 0 || (n_rooms > 0 && !rooms)) return fail(ISM_ERR_INVALID_ARG, "bad rooms");
+    int64_t nr = 0, hl = 0;
+    for (int64_t i = 0; i < n_rooms; ++i) {
+        if (rooms[i].n_mics < 1 || rooms[i].rir_len < 1)
+            return fail(ISM_ERR_INVALID_ARG, "room " + std::to_string(i) + ": bad size");
+        nr += rooms[i].n_mics;
+        hl += (int64_t)rooms[i].n_mics * rooms[i].rir_len;
+    }
+    if (n_rirs) *n_rirs = nr;
+    if (h_len) *h_len = hl;
+    return ISM_OK;
+}
+
+int ism_rir_batch_ex(const ism_room *rooms, int64_t n_rooms, float *h_dev,
+                     const int64_t *h_offsets, const ism_rir_opts *opts, void *stream_v) {
+    set_error("");
+    if (n_rooms < 0) return fail(ISM_ERR_INVALID_ARG, "n_rooms < 0");
+    if (n_rooms == 0) return ISM_OK;
+    if (!rooms || !h_dev) return fail(ISM_ERR_INVALID_ARG, "NULL rooms or h_dev");
+    cudaStream_t stream = (cudaStream_t)stream_v;
+    ism_rir_opts o;
+    memset(&o, 0, sizeof(o));
+    if (opts) o = *opts;
+    const int W = o.window > 0 ? o.window : 1024;
+    if (W % 32 != 0 || W < 32 || W > 8192)
+        return fail(ISM_ERR_INVALID_ARG, "window must be a multiple of 32 in [32, 8192]");
+
+    // jobs, one per RIR; grouped by filter kind (one launch per kind)
+    std::vector<RirJob> jobs[2];
+    std::vector<int64_t> room_of[2];
+    int max_order[2] = {0, 0}, max_taps[2] = {1, 1}, wmax[2] = {0, 0};
+    int64_t j = 0, packed = 0;
+    for (int64_t r = 0; r < n_rooms; ++r) {
+        const ism_room &R = rooms[r];
+        if (int st = validate_room(R, r)) return st;
+        const int kind = R.fd_kind;
+        for (int m = 0; m < R.n_mics; ++m, ++j) {
+            RirJob J;
+            memset(&J, 0, sizeof(J));
+            for (int a = 0; a < 3; ++a) {
+                J.src[a] = R.src[a];
+                J.mic[a] = R.mics[3 * m + a];
+                J.dims[a] = R.dims[a];
+            }
+            J.q = R.fs / R.c;
+            for (int w = 0; w < 6; ++w) J.beta[w] = (float)R.beta[w];
+            J.order = R.order;
+            J.n_taps = R.n_taps;
+            J.fd_kind = kind;
+            J.rir_len = R.rir_len;
+            J.n_windows = (int32_t)((R.rir_len + W - 1) / W);
+            J.h_offset = h_offsets ? h_offsets[j] : packed;
+            J.stat_index = j;
+            packed += R.rir_len;
+            if (J.h_offset < 0) return fail(ISM_ERR_INVALID_ARG, "negative h offset");
+            jobs[kind].push_back(J);
+            room_of[kind].push_back(r);
+            max_order[kind] = std::max(max_order[kind], R.order);
+            max_taps[kind] = std::max(max_taps[kind], R.n_taps);
+            wmax[kind] = std::max(wmax[kind], J.n_windows);
+        }
+    }
+    const int64_t n_rirs = j;
+    if (n_rirs > 0x3fffffff) return fail(ISM_ERR_INVALID_ARG, "too many RIRs");
+
+    for (int kind = 0; kind < 2; ++kind) {
+        auto &jv = jobs[kind];
+        if (jv.empty()) continue;
+        const size_t smem = rir_smem_bytes(W, max_order[kind], max_taps[kind]);
+        if (smem > 227 * 1024)
+            return fail(ISM_ERR_INVALID_ARG, "window/order/taps need too much shared memory");
+        const size_t jb = jv.size() * sizeof(RirJob);
+        void *scr = nullptr;
+        if (int st = scratch_alloc(&scr, jb + 256, stream)) return st;
+        RirJob *d_jobs = (RirJob *)scr;
+        unsigned int *d_counter = (unsigned int *)((char *)scr + jb);
+        long long *d_stats = (long long *)o.stats_dev;
+        int st = upload_async(d_jobs, jv.data(), jb, stream);
+        cudaError_t e = cudaSuccess;
+        if (!st) {
+            if (o.per_room) {
+                // The unbatched path: one launch per room, each over that
+                // room's RIRs only.
+                size_t b = 0;
+                while (!st && b < jv.size()) {
+                    size_t e2 = b + 1;
+                    while (e2 < jv.size() && room_of[kind][e2] == room_of[kind][b]) ++e2;
+                    int wm = 0;
+                    for (size_t k = b; k < e2; ++k) wm = std::max(wm, jv[k].n_windows);
+                    e = cudaMemsetAsync(d_counter, 0, sizeof(unsigned int), stream);
+                    if (e != cudaSuccess) { st = cuda_fail(e, "cudaMemsetAsync(counter)"); break; }
+                    RirLaunch L{d_jobs + b, (int)(e2 - b), wm, W, max_order[kind], max_taps[kind],
+                                kind, h_dev, d_stats, d_counter, nullptr, 0};
+                    st = launch_rir(L, stream);
+                    b = e2;
+                }
+            } else {
+                e = cudaMemsetAsync(d_counter, 0, sizeof(unsigned int), stream);
+                if (e != cudaSuccess) st = cuda_fail(e, "cudaMemsetAsync(counter)");
+                RirLaunch L{d_jobs, (int)jv.size(), wmax[kind], W, max_order[kind],
+                            max_taps[kind], kind, h_dev, d_stats, d_counter, nullptr, 0};
+                if (!st) st = launch_rir(L, stream);
+            }
+        }
+        scratch_free(scr, stream);
+        if (st) return st;
+    }
+    return ISM_OK;
+}
+
+int ism_rir_batch(const ism_room *rooms, int64_t n_rooms, float *h_dev, const int64_t *h_offsets,
+                  void *stream) {
+    return ism_rir_batch_ex(rooms, n_rooms, h_dev, h_offsets, nullptr, stream);
+}
+
+int ism_convolve_batch(const ism_conv_job *jobs, int64_t n_jobs, const float *h_dev,
+                       const float *src_dev, float *y_dev, uint64_t seed, int32_t precision,
+                       void *stream_v) {
+    set_error("");
+    if (n_jobs < 0) return fail(ISM_ERR_INVALID_ARG, "n_jobs < 0");
+    if (n_jobs == 0) return ISM_OK;
+    if (!jobs || !h_dev || !src_dev || !y_dev) return fail(ISM_ERR_INVALID_ARG, "NULL pointer");
+    if (precision != ISM_F32 && precision != ISM_BF16X3)
+        return fail(ISM_ERR_INVALID_ARG, "unknown precision");
+    if (n_jobs > 0x7fffffff) return fail(ISM_ERR_INVALID_ARG, "too many jobs");
+    cudaStream_t stream = (cudaStream_t)stream_v;
+    std::vector<ConvJob> cj(n_jobs);
+    bool any_noise = false;
+    int64_t max_elems = 0;
+    for (int64_t i = 0; i < n_jobs; ++i) {
+        const ism_conv_job &J = jobs[i];
+        if (J.n_mics < 1 || J.rir_len < 1 || J.src_len < 1 || J.h_offset < 0 ||
+            J.src_offset < 0 || J.y_offset < 0)
+            return fail(ISM_ERR_INVALID_ARG, "job " + std::to_string(i) + ": bad sizes/offsets");
+        ConvJob &c = cj[i];
+        memset(&c, 0, sizeof(c));
+        c.rir_len = J.rir_len;
+        c.src_len = J.src_len;
+        c.h_offset = J.h_offset;
+        c.src_offset = J.src_offset;
+        c.y_offset = J.y_offset;
+        c.y_len = J.src_len + J.rir_len - 1;
+        c.noise_id = J.noise_id;
+        c.n_mics = J.n_mics;
+        c.snr_db = J.snr_db;
+        if (!isnan(J.snr_db)) {
+            if (!isfinite(J.snr_db))
+                return fail(ISM_ERR_INVALID_ARG, "job " + std::to_string(i) + ": snr must be finite or NaN");
+            any_noise = true;
+        }
+        max_elems = std::max(max_elems, (int64_t)J.n_mics * c.y_len);
+    }
+    const int n_part = any_noise ? noise_partials_per_job(max_elems) : 0;
+    const size_t jb = cj.size() * sizeof(ConvJob);
+    const size_t pb = (size_t)n_part * n_jobs * sizeof(double);
+    void *scr = nullptr;
+    if (int st = scratch_alloc(&scr, jb + 256 + pb, stream)) return st;
+    ConvLaunch L;
+    memset(&L, 0, sizeof(L));
+    L.jobs_dev = (const ConvJob *)scr;
+    L.jobs_host = cj.data();
+    L.n_jobs = (int)n_jobs;
+    L.h_dev = h_dev;
+    L.src_dev = src_dev;
+    L.y_dev = y_dev;
+    L.precision = precision;
+    L.seed = seed;
+    L.any_noise = any_noise;
+    L.noise_partials_dev = (double *)((char *)scr + jb + 256);
+    L.n_partials_per_job = n_part;
+    int st = upload_async(scr, cj.data(), jb, stream);
+    if (!st) {
+        if (precision == ISM_BF16X3) st = launch_conv_bf16x3(L, stream);
+        else st = launch_conv_f32(L, stream);
+    }
+    if (!st) st = launch_noise(L, stream);
+    scratch_free(scr, stream);
+    return st;
+}
+
+}  // extern "C"

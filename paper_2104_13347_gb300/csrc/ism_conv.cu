@@ -1,0 +1,215 @@
+// ism_conv.cu -- K2b (FP32 direct convolution) and the noise epilogue.
+//
+// Convolution (arXiv 2104.13347, Sec. II.A: the dataset is built by batch
+// convolutions of the RIRs with source signals): for every mic m of a room,
+//   y_m[t] = sum_k h_m[k] s[t - k],  t in [0, Ts + Lh - 1).
+// Noise (Sec. III.A: Gaussian noise at a drawn SNR):
+//   y_m[t] += sigma z,  sigma^2 = mean(y^2 over the room's mics and samples)
+//   / 10^(snr/10), z from SplitMix64 counters and Box--Muller.
+//
+// K2b layout: one CTA per (room, group of 8 mics, tile of 2048 outputs);
+// each thread owns 8 consecutive outputs of all 8 mics (64 accumulators),
+// the source window and 8 RIR chunks are staged in shared memory, and the
+// tap loop runs 8 taps at a time from 16 source values held in registers,
+// so the inner loop is FFMAs fed by broadcast / 128-bit shared loads.  RIR
+// chunks whose products all hit zero source samples are skipped.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "ism_internal.h"
+
+namespace ism {
+namespace {
+
+constexpr int CT = 256;          // threads per CTA
+constexpr int OPT = 8;           // outputs per thread
+constexpr int TT = CT * OPT;     // outputs per tile (2048)
+constexpr int MG = 8;            // mics per CTA
+constexpr int KC = 256;          // taps per shared-memory chunk
+
+struct Tile {
+    int job;
+    int mic0;
+    int64_t t0;
+};
+
+__global__ void __launch_bounds__(CT, 2)
+k_conv_f32(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles,
+           const float *__restrict__ h, const float *__restrict__ src, float *__restrict__ y) {
+    __shared__ __align__(16) float s_src[TT + KC + 16];
+    __shared__ __align__(16) float s_h[MG][KC];
+    const Tile tl = tiles[blockIdx.x];
+    const ConvJob J = jobs[tl.job];
+    const int tid = threadIdx.x;
+    const int64_t t0 = tl.t0;
+    const int64_t Lh = J.rir_len, Ts = J.src_len;
+    const int nm = min(MG, J.n_mics - tl.mic0);
+    const float *hb = h + J.h_offset + (int64_t)tl.mic0 * Lh;
+    const float *sb = src + J.src_offset;
+
+    float acc[MG][OPT];
+#pragma unroll
+    for (int m = 0; m < MG; ++m)
+#pragma unroll
+        for (int i = 0; i < OPT; ++i) acc[m][i] = 0.f;
+
+    for (int64_t k0 = 0; k0 < Lh; k0 += KC) {
+        // source indices used by this chunk: t - k for t in [t0, t0+TT),
+        // k in [k0, k0+KC)
+        const int64_t lo = t0 - k0 - KC + 1, hi = t0 + TT - 1 - k0;
+        if (hi < 0 || lo >= Ts) continue;  // all products vanish
+        __syncthreads();
+        // s_src[i] = s[t0 - k0 - KC + i - 8 + 8] for i in [0, TT + KC + 16):
+        // index i holds s[t0 - k0 - KC - 8 + i]
+        for (int i = tid; i < TT + KC + 16; i += CT) {
+            const int64_t g = t0 - k0 - KC - 8 + i;
+            s_src[i] = (g >= 0 && g < Ts) ? sb[g] : 0.f;
+        }
+        for (int i = tid; i < MG * KC; i += CT) {
+            const int m = i / KC, kk = i - m * KC;
+            const int64_t k = k0 + kk;
+            s_h[m][kk] = (m < nm && k < Lh) ? hb[(int64_t)m * Lh + k] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 1
+        for (int kk = 0; kk < KC; kk += 8) {
+            // output t0 + 8 tid + i, tap k0 + kk + jj needs
+            // s[t0 + 8 tid + i - k0 - kk - jj] = s_src[8 tid + i - kk - jj + KC + 8]
+            const int base = 8 * tid - kk + KC + 8;  // multiple of 8
+            float sv[16];
+            const float4 *p4 = reinterpret_cast<const float4 *>(s_src + base - 8);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const float4 q = p4[v];
+                sv[4 * v] = q.x; sv[4 * v + 1] = q.y; sv[4 * v + 2] = q.z; sv[4 * v + 3] = q.w;
+            }
+            // sv[x] = s_src[base - 8 + x]; value for (i, jj) is sv[8 + i - jj]
+#pragma unroll
+            for (int m = 0; m < MG; ++m) {
+                const float4 ha = *reinterpret_cast<const float4 *>(&s_h[m][kk]);
+                const float4 hb4 = *reinterpret_cast<const float4 *>(&s_h[m][kk + 4]);
+                const float hv[8] = {ha.x, ha.y, ha.z, ha.w, hb4.x, hb4.y, hb4.z, hb4.w};
+#pragma unroll
+                for (int jj = 0; jj < 8; ++jj)
+#pragma unroll
+                    for (int i = 0; i < OPT; ++i) acc[m][i] = fmaf(hv[jj], sv[8 + i - jj], acc[m][i]);
+            }
+        }
+    }
+    const int64_t ylen = J.y_len;
+    float *yb = y + J.y_offset + (int64_t)tl.mic0 * ylen;
+#pragma unroll
+    for (int m = 0; m < MG; ++m) {
+        if (m < nm) {
+#pragma unroll
+            for (int i = 0; i < OPT; ++i) {
+                const int64_t t = t0 + 8 * tid + i;
+                if (t < ylen) yb[(int64_t)m * ylen + t] = acc[m][i];
+            }
+        }
+    }
+}
+
+// Noise, pass 1: partial sums of y^2 per (room, chunk), FP64, fixed order.
+constexpr int NCH = 65536;  // elements per partial
+__global__ void __launch_bounds__(256)
+k_sumsq(const ConvJob *__restrict__ jobs, const float *__restrict__ y, double *__restrict__ part,
+        int n_part) {
+    const ConvJob J = jobs[blockIdx.y];
+    const int64_t n = (int64_t)J.n_mics * J.y_len;
+    const int64_t b = (int64_t)blockIdx.x * NCH;
+    double acc = 0.0;
+    if (b < n) {
+        const float *yb = y + J.y_offset;
+        const int64_t e = min(b + NCH, n);
+        for (int64_t i = b + threadIdx.x; i < e; i += 256) {
+            const double v = yb[i];
+            acc += v * v;
+        }
+    }
+    __shared__ double s[256];
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[(int64_t)blockIdx.y * n_part + blockIdx.x] = s[0];
+}
+
+// Noise, pass 2: sigma from the partials (fixed order), then
+// y += sigma * z with z = sqrt(-2 ln u1) cos(2 pi u2) and u1, u2 the 24-bit
+// uniforms of SplitMix64 outputs 2t, 2t+1 of the (room, mic) stream.
+__global__ void __launch_bounds__(256)
+k_noise(const ConvJob *__restrict__ jobs, float *__restrict__ y, const double *__restrict__ part,
+        int n_part, uint64_t seed) {
+    const ConvJob J = jobs[blockIdx.y];
+    if (isnan(J.snr_db)) return;
+    const int64_t n = (int64_t)J.n_mics * J.y_len;
+    const int64_t b = (int64_t)blockIdx.x * NCH;
+    if (b >= n) return;
+    __shared__ float s_sigma;
+    if (threadIdx.x == 0) {
+        double p = 0.0;
+        for (int i = 0; i < n_part; ++i) p += part[(int64_t)blockIdx.y * n_part + i];
+        p /= (double)n;
+        s_sigma = (float)sqrt(p / pow(10.0, (double)J.snr_db / 10.0));
+    }
+    __syncthreads();
+    const float sigma = s_sigma;
+    float *yb = y + J.y_offset;
+    const int64_t e = min(b + NCH, n);
+    for (int64_t i = b + threadIdx.x; i < e; i += 256) {
+        const uint64_t m = (uint64_t)(i / J.y_len);
+        const uint64_t t = (uint64_t)(i - (int64_t)m * J.y_len);
+        const uint64_t key = sm64_out(seed, J.noise_id * 65536ull + m);
+        const uint64_t b1 = sm64_out(key, 2 * t), b2 = sm64_out(key, 2 * t + 1);
+        const float u1 = ((float)(b1 >> 40) + 0.5f) * (1.0f / 16777216.0f);
+        const float u2 = (float)(b2 >> 40) * (1.0f / 16777216.0f);
+        const float z = sqrtf(-2.f * logf(u1)) * cospif(2.f * u2);
+        yb[i] += sigma * z;
+    }
+}
+
+}  // namespace
+
+int launch_conv_f32(const ConvLaunch &L, cudaStream_t stream) {
+    std::vector<Tile> tiles;
+    for (int j = 0; j < L.n_jobs; ++j) {
+        const ConvJob &J = L.jobs_host[j];
+        for (int m0 = 0; m0 < J.n_mics; m0 += MG)
+            for (int64_t t0 = 0; t0 < J.y_len; t0 += TT) tiles.push_back(Tile{j, m0, t0});
+    }
+    if (tiles.empty()) return ISM_OK;
+    if (tiles.size() > 0x7fffffffULL) return fail(ISM_ERR_INVALID_ARG, "too many tiles");
+    void *d_tiles = nullptr;
+    int st = scratch_alloc(&d_tiles, tiles.size() * sizeof(Tile), stream);
+    if (st) return st;
+    st = upload_async(d_tiles, tiles.data(), tiles.size() * sizeof(Tile), stream);
+    if (st) { scratch_free(d_tiles, stream); return st; }
+    k_conv_f32<<<(unsigned)tiles.size(), CT, 0, stream>>>(L.jobs_dev, (const Tile *)d_tiles,
+                                                           L.h_dev, L.src_dev, L.y_dev);
+    cudaError_t e = cudaGetLastError();
+    scratch_free(d_tiles, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "launch k_conv_f32");
+    return ISM_OK;
+}
+
+int noise_partials_per_job(int64_t max_elems) { return (int)((max_elems + NCH - 1) / NCH); }
+
+int launch_noise(const ConvLaunch &L, cudaStream_t stream) {
+    if (!L.any_noise || L.n_jobs == 0) return ISM_OK;
+    dim3 grid(L.n_partials_per_job, L.n_jobs);
+    k_sumsq<<<grid, 256, 0, stream>>>(L.jobs_dev, L.y_dev, L.noise_partials_dev,
+                                      L.n_partials_per_job);
+    k_noise<<<grid, 256, 0, stream>>>(L.jobs_dev, L.y_dev, L.noise_partials_dev,
+                                      L.n_partials_per_job, L.seed);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "launch noise kernels");
+    return ISM_OK;
+}
+
+}  // namespace ism

@@ -1,0 +1,112 @@
+// ism_internal.h -- shared declarations of the CUDA library (not part of
+// the public ABI; include/ism.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/ism.h"
+
+namespace ism {
+
+// One RIR = (room, microphone) as the ISM kernel sees it.  FP64 geometry so
+// that the per-axis image offsets round exactly as the definition
+// (arXiv 2104.13347, Sec. II.A): offset = ((1-2p) s + (2q) L) - r.
+struct alignas(16) RirJob {
+    double src[3];
+    double mic[3];
+    double dims[3];
+    double q;           // fs / c, samples per metre (FP64, rounded once)
+    float beta[6];      // x0, x1, y0, y1, z0, z1
+    int32_t order;      // N
+    int32_t n_taps;
+    int32_t fd_kind;    // ISM_FD_HANN_SINC / ISM_FD_LAGRANGE
+    int32_t n_windows;  // ceil(rir_len / W)
+    int64_t rir_len;
+    int64_t h_offset;   // element offset of h[0] in the output buffer
+    int64_t stat_index; // RIR index in the caller's order (statistics slot)
+};
+
+// One room of a convolution batch on the device.
+struct alignas(16) ConvJob {
+    int64_t rir_len;
+    int64_t src_len;
+    int64_t h_offset;
+    int64_t src_offset;
+    int64_t y_offset;
+    int64_t y_len;       // src_len + rir_len - 1
+    uint64_t noise_id;   // identifies the room's noise streams (with the seed)
+    int32_t n_mics;
+    float snr_db;        // NaN = no noise
+};
+
+// Thread-local error message (ism_last_error_string).
+void set_error(const std::string &msg);
+int fail(int status, const std::string &msg);
+int cuda_fail(cudaError_t e, const char *what);
+
+// Pinned host staging for descriptor uploads.  Blocks are recycled once the
+// copy that read them has completed (an event per block), so uploads never
+// wait for earlier work on the stream.
+int upload_async(void *dev_dst, const void *host_src, size_t bytes, cudaStream_t stream);
+
+// Stream-ordered device scratch from the library's own memory pool (kept
+// cached between calls).
+int scratch_alloc(void **p, size_t bytes, cudaStream_t stream);
+void scratch_free(void *p, cudaStream_t stream);
+
+int device_sm_count();
+
+// K1: image-source taps.  jobs_dev has n_rirs jobs; every job's windows are
+// processed; wmax = max n_windows.  counter_dev: one zeroed uint32 work
+// counter.  max_order / max_taps size the shared memory and tap rows.
+struct RirLaunch {
+    const RirJob *jobs_dev;
+    int n_rirs;
+    int wmax;
+    int window;
+    int max_order;
+    int max_taps;
+    int fd_kind;          // all jobs of one launch share the filter kind
+    float *h_dev;
+    long long *stats_dev; // nullable
+    unsigned int *counter_dev;
+    int *err_dev;
+    int grid;             // 0 = persistent (SMs x blocks/SM)
+};
+int launch_rir(const RirLaunch &L, cudaStream_t stream);
+size_t rir_smem_bytes(int window, int max_order, int max_taps);
+
+// K2b / K2 / noise.
+struct ConvLaunch {
+    const ConvJob *jobs_dev;
+    const ConvJob *jobs_host;  // same table on the host (for grid sizing)
+    int n_jobs;
+    const float *h_dev;
+    const float *src_dev;
+    float *y_dev;
+    int precision;
+    uint64_t seed;
+    int any_noise;
+    double *noise_partials_dev;  // per job: partial sums of y^2 (scratch)
+    int n_partials_per_job;
+};
+int launch_conv_f32(const ConvLaunch &L, cudaStream_t stream);
+int launch_conv_bf16x3(const ConvLaunch &L, cudaStream_t stream);
+int noise_partials_per_job(int64_t max_elems);
+int launch_noise(const ConvLaunch &L, cudaStream_t stream);
+
+// SplitMix64 (Steele, Lea and Flood 2014): output i of the stream with
+// state x is mix(x + (i+1) * gamma).
+__host__ __device__ inline uint64_t sm64_mix(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+__host__ __device__ inline uint64_t sm64_out(uint64_t state, uint64_t i) {
+    return sm64_mix(state + (i + 1) * 0x9E3779B97F4A7C15ULL);
+}
+
+}  // namespace ism

@@ -1,0 +1,215 @@
+"""Host-side checks of the C ABI (no GPU needed).
+
+libism.so loads on a machine without a GPU, exports every function that
+include/ism.h declares, rejects invalid arguments before touching the
+device, and its serving layer reports (rather than hangs on) a device it
+cannot use: the failure is made on the host (a device ordinal that does not
+exist), never by faulting a GPU.
+"""
+import ctypes
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2104_13347_gb300 import _lib, build
+    build.build()
+    return _lib
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "ism.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(ism_\w+)\s*\(", text, flags=re.M)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert len(names) >= 13
+    so = ctypes.CDLL(lib.LIB_PATH)
+    for n in names:
+        assert hasattr(so, n), f"libism.so does not export {n}"
+    assert set(names) == set(lib.SIGNATURES), "binding signatures out of sync with ism.h"
+
+
+def test_version_and_error_string(lib):
+    L = lib.load()
+    assert b"sm_103a" in L.ism_version()
+    assert L.ism_last_error_string() is not None
+
+
+def good_room(**kw):
+    r = dict(dims=[5.0, 4.0, 3.0], beta=[0.8] * 6, src=[1.0, 1.0, 1.0],
+             mics=[[2.0, 2.0, 2.0]], fs=16000.0, c=343.0, order=3, n_taps=81, fd_kind=0,
+             rir_len=1024)
+    r.update(kw)
+    return r
+
+
+BAD = {
+    "source outside": dict(src=[6.0, 1.0, 1.0]),
+    "source on wall": dict(src=[0.0, 1.0, 1.0]),
+    "mic outside": dict(mics=[[2.0, 5.0, 1.0]]),
+    "mic on source": dict(mics=[[1.0, 1.0, 1.0]]),
+    "beta above 1": dict(beta=[0.8] * 5 + [1.2]),
+    "beta negative": dict(beta=[-0.1] + [0.8] * 5),
+    "even hann taps": dict(n_taps=80),
+    "odd lagrange taps": dict(fd_kind=1, n_taps=7),
+    "unknown filter": dict(fd_kind=5),
+    "fs zero": dict(fs=0.0),
+    "c negative": dict(c=-343.0),
+    "order negative": dict(order=-1),
+    "order too high": dict(order=201),
+    "empty rir": dict(rir_len=0),
+    "no mics": dict(mics=np.zeros((0, 3))),
+    "nan dims": dict(dims=[float("nan"), 4.0, 3.0]),
+}
+
+
+@pytest.mark.parametrize("case", sorted(BAD))
+def test_rir_batch_rejects_invalid_rooms(lib, case):
+    L = lib.load()
+    r = good_room(**BAD[case])
+    arr, keep = lib.make_rooms([r])
+    fake = ctypes.c_void_p(0x1000)  # never dereferenced: validation comes first
+    st = L.ism_rir_batch(arr, 1, fake, None, None)
+    assert st == lib.ISM_ERR_INVALID_ARG, (case, st, lib.last_error())
+    assert lib.last_error()
+
+
+def test_rir_batch_argument_errors(lib):
+    L = lib.load()
+    arr, keep = lib.make_rooms([good_room()])
+    assert L.ism_rir_batch(arr, -1, ctypes.c_void_p(0x1000), None, None) == lib.ISM_ERR_INVALID_ARG
+    assert L.ism_rir_batch(arr, 1, None, None, None) == lib.ISM_ERR_INVALID_ARG
+    assert L.ism_rir_batch(None, 0, None, None, None) == lib.ISM_OK  # empty batch: no-op
+    opts = lib.RirOpts(48, 0, None)  # window not a multiple of 32
+    assert L.ism_rir_batch_ex(arr, 1, ctypes.c_void_p(0x1000), None, ctypes.byref(opts),
+                              None) == lib.ISM_ERR_INVALID_ARG
+
+
+def test_rir_batch_size(lib):
+    rooms = [good_room(), good_room(mics=[[2, 2, 2], [3, 1, 1], [1, 3, 2]], rir_len=77)]
+    assert lib.rir_batch_size(rooms) == (4, 1024 + 3 * 77)
+
+
+def test_convolve_batch_argument_errors(lib):
+    L = lib.load()
+    jobs, _ = lib.conv_jobs([2], [100], [50])
+    p = ctypes.c_void_p(0x1000)
+    assert L.ism_convolve_batch(jobs, 1, p, p, p, 0, 7, None) == lib.ISM_ERR_INVALID_ARG
+    assert L.ism_convolve_batch(jobs, 1, None, p, p, 0, 0, None) == lib.ISM_ERR_INVALID_ARG
+    bad, _ = lib.conv_jobs([0], [100], [50])
+    assert L.ism_convolve_batch(bad, 1, p, p, p, 0, 0, None) == lib.ISM_ERR_INVALID_ARG
+    inf_snr, _ = lib.conv_jobs([1], [100], [50], snr_db=[float("inf")])
+    assert L.ism_convolve_batch(inf_snr, 1, p, p, p, 0, 0, None) == lib.ISM_ERR_INVALID_ARG
+    assert L.ism_convolve_batch(jobs, 0, p, p, p, 0, 0, None) == lib.ISM_OK
+
+
+# --------------------------------------------------------------------------
+# serving: host-side failure paths
+# --------------------------------------------------------------------------
+
+def make_request(lib, room, src):
+    arr, keep = lib.make_rooms([room])
+    rq = lib.Request()
+    rq.room = arr[0]
+    rq.src_host = src.ctypes.data
+    rq.src_len = len(src)
+    rq.snr_db = math.nan
+    return rq, keep
+
+
+def serve(lib, **kw):
+    cfg = lib.ServeConfig()
+    for k, v in kw.items():
+        setattr(cfg, k, v)
+    srv = ctypes.c_void_p()
+    st = lib.load().ism_serve_create(ctypes.byref(cfg), ctypes.byref(srv))
+    return st, srv
+
+
+def test_serve_config_validation(lib):
+    assert serve(lib, precision=9)[0] == lib.ISM_ERR_INVALID_ARG
+    assert serve(lib, n_streams=17)[0] == lib.ISM_ERR_INVALID_ARG
+    assert serve(lib, max_batch=-1)[0] == lib.ISM_ERR_INVALID_ARG
+
+
+def test_serve_unusable_device_fails_requests(lib):
+    """A device ordinal that does not exist: submits are accepted, the
+    serving thread cannot select the device, and every request reports
+    ISM_ERR_CUDA through wait/poll; nothing hangs."""
+    L = lib.load()
+    st, srv = serve(lib, device=97, max_queue=8)
+    assert st == lib.ISM_OK
+    src = np.ones(100, np.float32)
+    tickets = []
+    for _ in range(3):
+        rq, keep = make_request(lib, good_room(), src)
+        t = ctypes.c_uint64()
+        assert L.ism_serve_submit(srv, ctypes.byref(rq), ctypes.byref(t)) == lib.ISM_OK
+        tickets.append(t.value)
+    res = lib.Result()
+    for t in tickets:
+        st = L.ism_serve_wait(srv, t, 30.0, ctypes.byref(res))
+        assert st == lib.ISM_ERR_CUDA, (st, lib.last_error())
+        assert "device 97" in lib.last_error()
+        assert L.ism_serve_poll(srv, t, ctypes.byref(res)) == lib.ISM_ERR_CUDA
+        assert L.ism_serve_release(srv, t) == lib.ISM_OK
+        assert L.ism_serve_poll(srv, t, ctypes.byref(res)) == lib.ISM_ERR_UNKNOWN_TICKET
+        assert L.ism_serve_release(srv, t) == lib.ISM_ERR_UNKNOWN_TICKET
+    stats = lib.ServeStats()
+    assert L.ism_serve_stats_get(srv, ctypes.byref(stats)) == lib.ISM_OK
+    assert stats.submitted == 3 and stats.queued == 0
+    assert L.ism_serve_destroy(srv) == lib.ISM_OK
+
+
+def test_serve_admission_limits(lib):
+    """BUSY for a request larger than the memory budget and for more
+    outstanding (unreleased) requests than max_queue; INVALID_ARG for a bad
+    room or an empty source."""
+    L = lib.load()
+    st, srv = serve(lib, device=97, max_queue=2, max_hbm_bytes=1 << 20)
+    assert st == lib.ISM_OK
+    t = ctypes.c_uint64()
+    big = np.ones(400000, np.float32)  # > 1 MiB with outputs
+    rq, keep = make_request(lib, good_room(), big)
+    assert L.ism_serve_submit(srv, ctypes.byref(rq), ctypes.byref(t)) == lib.ISM_ERR_BUSY
+    small = np.ones(50, np.float32)
+    held = []
+    for _ in range(2):
+        rq, keep = make_request(lib, good_room(rir_len=64), small)
+        assert L.ism_serve_submit(srv, ctypes.byref(rq), ctypes.byref(t)) == lib.ISM_OK
+        held.append(t.value)
+    rq, keep = make_request(lib, good_room(rir_len=64), small)
+    assert L.ism_serve_submit(srv, ctypes.byref(rq), ctypes.byref(t)) == lib.ISM_ERR_BUSY
+    rq, keep = make_request(lib, good_room(src=[9.0, 1.0, 1.0]), small)
+    assert L.ism_serve_submit(srv, ctypes.byref(rq), ctypes.byref(t)) == lib.ISM_ERR_INVALID_ARG
+    rq, keep = make_request(lib, good_room(), small)
+    rq.src_len = 0
+    assert L.ism_serve_submit(srv, ctypes.byref(rq), ctypes.byref(t)) == lib.ISM_ERR_INVALID_ARG
+    res = lib.Result()
+    for h in held:
+        L.ism_serve_wait(srv, h, 30.0, ctypes.byref(res))
+        assert L.ism_serve_release(srv, h) == lib.ISM_OK
+    rq, keep = make_request(lib, good_room(rir_len=64), small)
+    assert L.ism_serve_submit(srv, ctypes.byref(rq), ctypes.byref(t)) == lib.ISM_OK
+    stats = lib.ServeStats()
+    L.ism_serve_stats_get(srv, ctypes.byref(stats))
+    assert stats.rejected_busy == 2
+    assert L.ism_serve_destroy(srv) == lib.ISM_OK
+
+
+def test_serve_wait_on_unknown_ticket(lib):
+    L = lib.load()
+    st, srv = serve(lib, device=97)
+    res = lib.Result()
+    assert L.ism_serve_wait(srv, 12345, 0.01, ctypes.byref(res)) == lib.ISM_ERR_UNKNOWN_TICKET
+    assert L.ism_serve_destroy(srv) == lib.ISM_OK

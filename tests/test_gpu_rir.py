@@ -1,0 +1,160 @@
+"""GPU parity of the image-source RIR kernel (K1) against the FP64 oracle.
+
+Bars (arXiv 2104.13347 Sec. II.A path): integer results -- image counts,
+contributing images, taps landing in the RIR, all decided by the integer
+part of each delay -- must equal the oracle's exactly; waveforms must be
+within 1e-5 relative L2 per RIR (FP32 tap accumulation against FP64).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2104_13347_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+def rel_l2(x, ref):
+    return float(np.linalg.norm(x - ref) / max(np.linalg.norm(ref), 1e-300))
+
+
+def gpu_rirs(ism, rooms, **kw):
+    import torch
+    n_rirs, _ = ism.rir_batch_size(rooms)
+    stats = torch.zeros(2 * n_rirs, dtype=torch.int64, device="cuda")
+    h = ism.rir_batch(rooms, stats=stats, **kw)
+    torch.cuda.synchronize()
+    h = h.cpu().numpy().astype(np.float64)
+    out, o = [], 0
+    for r in rooms:
+        M = np.asarray(r["mics"]).reshape(-1, 3).shape[0]
+        out.append(h[o:o + M * r["rir_len"]].reshape(M, r["rir_len"]))
+        o += M * r["rir_len"]
+    return out, stats.cpu().numpy().reshape(-1, 2)
+
+
+def check_rooms(ism, rooms, tol=TOL, **kw):
+    got, st = gpu_rirs(ism, rooms, **kw)
+    ref, ost = oracle.rir_batch(rooms)
+    j = 0
+    worst = 0.0
+    for g, r in zip(got, ref):
+        for m in range(g.shape[0]):
+            e = rel_l2(g[m], r[m])
+            worst = max(worst, e)
+            assert e <= tol, f"rir {j}: rel-L2 {e:.3e}"
+            j += 1
+    # contributing images and in-range taps: exact
+    np.testing.assert_array_equal(st[:, 0], ost[:, 1])
+    np.testing.assert_array_equal(st[:, 1], ost[:, 2])
+    return worst
+
+
+def test_single_room_order10(ism):
+    rooms = wl.single_room(seed=1001, order=10, rir_len=4096)
+    check_rooms(ism, rooms)
+
+
+def test_small_batch_ragged(ism):
+    """Several rooms, 1..11 mics, RIR lengths that are not multiples of the
+    window, orders 0..6, small windows so that each RIR spans many work
+    items and a ragged tail."""
+    rng = np.random.default_rng(11)
+    rooms = []
+    for i in range(7):
+        r = wl.room_batch(1, seed=100 + i, order=int(rng.integers(0, 7)),
+                          rir_len=int(rng.integers(50, 3000)), n_mics=int(rng.integers(1, 12)))[0]
+        rooms.append(r)
+    for W in (32, 256, 1024):
+        check_rooms(ism, rooms, window=W)
+
+
+def test_exact_integer_delay(ism):
+    """fs/c = 64 exactly and d = 1 m: h = delta[n-64] / (4 pi); every other
+    sample exactly zero, the peak within one FP32 rounding."""
+    room = dict(dims=[5, 4, 3], beta=[0.0] * 6, src=[2.0, 1.5, 1.5], mics=[[3.0, 1.5, 1.5]],
+                fs=16384.0, c=256.0, order=0, n_taps=81, fd_kind=0, rir_len=256)
+    (h,), st = gpu_rirs(ism, [room])
+    assert h[0, 64] == pytest.approx(1 / (4 * np.pi), rel=1.2e-7)
+    h[0, 64] = 0
+    assert not np.any(h)
+    # zero-gain images still land taps in range and are counted, as in the oracle
+    _, ost = oracle.rir_batch([room])
+    assert st[0, 0] == ost[0, 1] and st[0, 1] == ost[0, 2]
+
+
+def test_reciprocity(ism):
+    base = wl.room_batch(1, seed=7, order=5, rir_len=2048, n_mics=1)[0]
+    a = dict(base)
+    b = dict(base, src=base["mics"][0], mics=[base["src"]])
+    (ha,), _ = gpu_rirs(ism, [a])
+    (hb,), _ = gpu_rirs(ism, [b])
+    assert rel_l2(ha[0], hb[0]) < 1e-6
+
+
+def test_window_and_per_room_paths_agree(ism):
+    rooms = wl.room_batch(6, seed=12, order=6, rir_len=3000, n_mics=3)
+    a, _ = gpu_rirs(ism, rooms, window=512)
+    b, _ = gpu_rirs(ism, rooms, window=512, per_room=True)
+    c, _ = gpu_rirs(ism, rooms, window=128)
+    for x, y, z in zip(a, b, c):
+        np.testing.assert_array_equal(x, y)           # same items, same order
+        assert rel_l2(z, x) < 1e-6                    # different windows
+
+
+def test_lagrange_filter(ism):
+    rooms = wl.room_batch(3, seed=21, order=6, rir_len=2500, n_mics=2, n_taps=8,
+                          fd_kind=wl.FD_LAGRANGE)
+    check_rooms(ism, rooms)
+
+
+def test_mixed_filter_kinds_one_call(ism):
+    a = wl.room_batch(2, seed=31, order=4, rir_len=1500, n_mics=2)
+    b = wl.room_batch(2, seed=32, order=4, rir_len=1700, n_mics=3, n_taps=8,
+                      fd_kind=wl.FD_LAGRANGE)
+    check_rooms(ism, [a[0], b[0], a[1], b[1]])
+
+
+def test_short_filters_and_48k(ism):
+    rooms = []
+    for i, nt in enumerate((1, 3, 33, 65, 127)):
+        rooms += wl.room_batch(1, seed=40 + i, order=5, rir_len=2000, n_mics=2, n_taps=nt,
+                               fs=48000.0)
+    check_rooms(ism, rooms, window=256)
+
+
+def test_empty_batch_is_noop(ism):
+    import torch
+    h = torch.full((10,), 7.0, device="cuda")
+    ism.rir_batch([], h=h)
+    torch.cuda.synchronize()
+    assert torch.all(h == 7.0)
+
+
+def test_full_size_batch_sampled(ism):
+    """The 1024-room, order-15, 8-mic, 8192-sample batch in the benchmark's
+    launch configuration; a sample of RIRs checked against the oracle."""
+    import torch
+    rooms = wl.room_batch(1024, seed=1002)
+    n_rirs, hl = ism.rir_batch_size(rooms)
+    stats = torch.zeros(2 * n_rirs, dtype=torch.int64, device="cuda")
+    h = ism.rir_batch(rooms, stats=stats)
+    torch.cuda.synchronize()
+    h = h.view(n_rirs, 8192)
+    st = stats.view(n_rirs, 2).cpu().numpy()
+    rng = np.random.default_rng(5)
+    picks = sorted(rng.choice(n_rirs, 6, replace=False).tolist())
+    sub = []
+    for j in picks:
+        r = rooms[j // 8]
+        sub.append(dict(r, mics=np.asarray(r["mics"])[j % 8:j % 8 + 1]))
+    ref, ost = oracle.rir_batch(sub)
+    for k, j in enumerate(picks):
+        g = h[j].cpu().numpy().astype(np.float64)
+        assert rel_l2(g, ref[k][0]) <= TOL
+        assert st[j, 0] == ost[k, 1] and st[j, 1] == ost[k, 2]
+    assert np.all(np.isfinite(h.cpu().numpy()))
