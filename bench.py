@@ -186,12 +186,13 @@ def run_ours(args, ws, rank):
     ism.load()
     dev = torch.device("cuda", torch.cuda.current_device())
     seed = 1002 + 7919 * rank  # each rank its own batch (weak scaling)
-    rooms = wl.room_batch(N_ROOMS, seed=seed)
+    n_rooms = args.rooms
+    rooms = wl.room_batch(n_rooms, seed=seed)
     srcs = wl.sources(rooms, 1.0, seed=seed + 1)
-    snr = wl.snrs(N_ROOMS, seed=seed + 2)
+    snr = wl.snrs(n_rooms, seed=seed + 2)
     n_rirs, hl = ism.rir_batch_size(rooms)
-    jobs, ylen = ism.conv_jobs([N_MICS] * N_ROOMS, [LH] * N_ROOMS, [TS] * N_ROOMS, snr_db=snr,
-                               noise_ids=np.arange(N_ROOMS) + rank * N_ROOMS)
+    jobs, ylen = ism.conv_jobs([N_MICS] * n_rooms, [LH] * n_rooms, [TS] * n_rooms, snr_db=snr,
+                               noise_ids=np.arange(n_rooms) + rank * n_rooms)
     precision = ism.BF16X3 if args.precision == "bf16x3" else ism.F32
     stream = torch.cuda.current_stream()
     src_host = torch.from_numpy(np.concatenate(srcs)).pin_memory()
@@ -204,7 +205,7 @@ def run_ours(args, ws, rank):
     ism.rir_batch(rooms, h=h, stats=stats, window=args.window)
     torch.cuda.synchronize()
     taps = int(stats.view(-1, 2)[:, 1].sum().item())
-    mic_samples = N_ROOMS * N_MICS * (TS + LH - 1)
+    mic_samples = n_rooms * N_MICS * (TS + LH - 1)
 
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     rir_ms, conv_ms, noise_ms = [], [], []
@@ -271,7 +272,8 @@ def run_ours(args, ws, rank):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if precision == ism.F32 else "bf16x3+f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "rooms": N_ROOMS, "mics": N_MICS, "order": ORDER,
+        "config": {"workload": WORKLOAD if n_rooms == N_ROOMS else
+                   WORKLOAD.replace(f"{N_ROOMS} rooms", f"{n_rooms} rooms"), "rooms": n_rooms, "mics": N_MICS, "order": ORDER,
                    "rir_len": LH, "src_len": TS, "n_taps": 81, "window": args.window or 1024,
                    "precision": args.precision, "parallelism": f"replicas x{ws}",
                    "l2": "inputs larger than L2 (h 268 MB, y 793 MB per step)"},
@@ -305,6 +307,8 @@ def main():
     ap.add_argument("--precision", default="f32", choices=["f32", "bf16x3"])
     ap.add_argument("--window", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--rooms", type=int, default=N_ROOMS,
+                    help="rooms per step (smaller only for profiling captures)")
     args = ap.parse_args()
     ws, rank = dist_setup()
     if args.impl == "reference":

@@ -119,8 +119,8 @@ __host__ __device__ inline Layout make_layout(int window, int max_order, int max
 // with A = -a sin(pi f) / (2 pi) for the Hann-sinc filter, or v = (a, D)
 // for the Lagrange filter.
 
-// Delay split of one image (Sec. II.A: "keep the precision of the time
-// delays").  Returns the integer part k (rint, ties to even, for Hann;
+// Delay split of one image (Sec. II.A: the delay of every image must keep
+// its sub-sample precision).  Returns the integer part k (rint, ties to even, for Hann;
 // floor for Lagrange) and the fraction in FP32, plus d (FP32).
 template <int KIND>
 __device__ __forceinline__ void delay_split(const Tables &T, int TE, int ix, int iy, int iz,
