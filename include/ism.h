@@ -125,6 +125,35 @@ int ism_rir_batch_ex(const ism_room *rooms, int64_t n_rooms, float *h_dev,
 int ism_rir_batch_size(const ism_room *rooms, int64_t n_rooms, int64_t *n_rirs,
                        int64_t *h_len);
 
+/* Largest number of RIRs (sum of n_mics over the rooms) that one
+ * ism_rir_batch_noalloc call accepts. */
+#define ISM_NOALLOC_MAX_RIRS 14560
+
+/* ism_rir_batch_noalloc -- ism_rir_batch for callers that cannot allocate.
+ * The paper has no counterpart: this is a deployment variant of the same
+ * image-source kernel.  It is meant for callers that must not allocate
+ * device memory while they run -- their device memory is already owned by
+ * another allocator (such as a framework's caching allocator that reserved
+ * the whole GPU), or they sit in a latency-bound loop where cudaMalloc's
+ * implicit synchronisation and unbounded cost are not acceptable.
+ * Arguments, output layout and results are those of ism_rir_batch (same
+ * kernel, same 1024-sample windows); no statistics.  The call allocates
+ * nothing: its scratch is one fixed 2 MiB device array inside the library,
+ * which every GPU that loads the library holds until the process exits.
+ * Limits and rules:
+ *  - at most ISM_NOALLOC_MAX_RIRS RIRs per call; more returns
+ *    ISM_ERR_INVALID_ARG before anything is launched;
+ *  - the first call on a device looks up the array's device address on that
+ *    device (with it current); make that first call before any stream
+ *    capture;
+ *  - all calls share the array, which keeps the last call's contents; each
+ *    call clears what must start at zero, but calls that overlap on the GPU
+ *    (on different streams) race on it, so serialise them;
+ *  - job tables are copied from a host stack buffer with pageable copies,
+ *    which may make the call wait for earlier work on the stream. */
+int ism_rir_batch_noalloc(const ism_room *rooms, int64_t n_rooms, float *h_dev,
+                          const int64_t *h_offsets, void *stream);
+
 /* One room of a convolution batch (Sec. II.A, "batch convolutions" of the
  * RIRs with the source signals; Sec. III.A noise).
  * n_mics      RIRs of the room, stored back to back in h_dev starting at

@@ -70,6 +70,7 @@ SIGNATURES = {
     "ism_rir_batch": (c_i32, [c_vp, c_i64, c_vp, c_vp, c_vp]),
     "ism_rir_batch_ex": (c_i32, [c_vp, c_i64, c_vp, c_vp, c_vp, c_vp]),
     "ism_rir_batch_size": (c_i32, [c_vp, c_i64, c_vp, c_vp]),
+    "ism_rir_batch_noalloc": (c_i32, [c_vp, c_i64, c_vp, c_vp, c_vp]),
     "ism_convolve_batch": (c_i32, [c_vp, c_i64, c_vp, c_vp, c_vp, c_u64, c_i32, c_vp]),
     "ism_serve_create": (c_i32, [c_vp, c_vp]),
     "ism_serve_submit": (c_i32, [c_vp, c_vp, c_vp]),
@@ -176,6 +177,21 @@ def rir_batch(rooms, h=None, h_offsets=None, window=0, per_room=False, stats=Non
     check(lib.ism_rir_batch_ex(arr, len(rooms), c_vp(h.data_ptr()),
                                offs.ctypes.data if offs is not None else None,
                                ctypes.byref(opts), _stream_ptr(stream)))
+    return h
+
+
+def rir_batch_noalloc(rooms, h, h_offsets=None, stream=None):
+    """ism_rir_batch_noalloc: as rir_batch into an existing float32 CUDA
+    tensor h, through the entry point that allocates nothing."""
+    lib = load()
+    arr, keep = make_rooms(rooms)
+    offs = None
+    if h_offsets is not None:
+        offs = np.ascontiguousarray(h_offsets, np.int64)
+        keep.append(offs)
+    check(lib.ism_rir_batch_noalloc(arr, len(rooms), c_vp(h.data_ptr()),
+                                    offs.ctypes.data if offs is not None else None,
+                                    _stream_ptr(stream)))
     return h
 
 
