@@ -85,14 +85,27 @@ typedef struct ism_room {
     int64_t rir_len;
 } ism_room;
 
+/* How the taps are laid down.
+ *  ISM_RIR_SPARSE (default): each image adds P Chebyshev coefficients of its
+ *    fractional delay to sparse integer-delay arrays, and one FIR per output
+ *    window applies the filter (P <= 16 terms; the expansion error is below
+ *    1e-9 of the peak tap, and exact for the Lagrange filter).  Sums use
+ *    shared-memory atomics, so repeated runs agree to FP32 rounding.
+ *  ISM_RIR_DIRECT: every tap of every image is evaluated from the filter's
+ *    formula and accumulated in a fixed order (bitwise reproducible). */
+typedef enum ism_rir_variant { ISM_RIR_SPARSE = 0, ISM_RIR_DIRECT = 1 } ism_rir_variant;
+
 /* Options of ism_rir_batch_ex (zero-initialise for defaults). */
 typedef struct ism_rir_opts {
-    int32_t window;      /* output window per work item, samples; 0 = tuned */
+    int32_t window;      /* output window per work item, samples (multiple of
+                            32 in [32, 8192]); 0 = 1024 */
     int32_t per_room;    /* 1 = one plain launch per room (the unbatched path) */
     int64_t *stats_dev;  /* optional device int64[2 * n_rirs]: per RIR, the
                             images with a tap in [0, Lh) and the taps that
                             landed in [0, Lh); accumulated (not overwritten),
                             so zero it first */
+    int32_t variant;     /* ism_rir_variant */
+    int32_t reserved;
 } ism_rir_opts;
 
 /* ism_rir_batch -- RIRs of a batch of rooms (Sec. II.A: image sources,

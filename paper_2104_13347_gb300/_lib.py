@@ -21,6 +21,7 @@ ISM_OK, ISM_PENDING = 0, 1
 ISM_ERR_INVALID_ARG, ISM_ERR_OUT_OF_MEMORY, ISM_ERR_BUSY = 2, 3, 4
 ISM_ERR_TIMEOUT, ISM_ERR_CUDA, ISM_ERR_INTERNAL, ISM_ERR_UNKNOWN_TICKET = 5, 6, 7, 8
 FD_HANN_SINC, FD_LAGRANGE = 0, 1
+RIR_SPARSE, RIR_DIRECT = 0, 1
 F32, BF16X3 = 0, 1
 
 c_i32, c_i64, c_u64, c_f32, c_f64, c_vp = (ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64,
@@ -34,7 +35,8 @@ class Room(ctypes.Structure):
 
 
 class RirOpts(ctypes.Structure):
-    _fields_ = [("window", c_i32), ("per_room", c_i32), ("stats_dev", c_vp)]
+    _fields_ = [("window", c_i32), ("per_room", c_i32), ("stats_dev", c_vp), ("variant", c_i32),
+                ("reserved", c_i32)]
 
 
 class ConvJob(ctypes.Structure):
@@ -158,10 +160,12 @@ def rir_batch_size(rooms):
     return nr.value, hl.value
 
 
-def rir_batch(rooms, h=None, h_offsets=None, window=0, per_room=False, stats=None, stream=None):
+def rir_batch(rooms, h=None, h_offsets=None, window=0, per_room=False, stats=None, stream=None,
+              variant=RIR_SPARSE):
     """ism_rir_batch_ex: RIRs of the rooms into h (a float32 CUDA tensor;
     allocated packed if None).  stats: optional int64 CUDA tensor (2 per
-    RIR), accumulated.  Returns h."""
+    RIR), accumulated.  variant: RIR_SPARSE (default) or RIR_DIRECT.
+    Returns h."""
     import torch
     lib = load()
     arr, keep = make_rooms(rooms)
@@ -173,7 +177,8 @@ def rir_batch(rooms, h=None, h_offsets=None, window=0, per_room=False, stats=Non
     if h_offsets is not None:
         offs = np.ascontiguousarray(h_offsets, np.int64)
         keep.append(offs)
-    opts = RirOpts(int(window), int(bool(per_room)), stats.data_ptr() if stats is not None else None)
+    opts = RirOpts(int(window), int(bool(per_room)),
+                   stats.data_ptr() if stats is not None else None, int(variant), 0)
     check(lib.ism_rir_batch_ex(arr, len(rooms), c_vp(h.data_ptr()),
                                offs.ctypes.data if offs is not None else None,
                                ctypes.byref(opts), _stream_ptr(stream)))

@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -178,6 +179,86 @@ int validate_room(const ism_room &r, int64_t idx) {
     return ISM_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Chebyshev tables of the fractional-delay filters (FP64, cached)
+// ---------------------------------------------------------------------------
+namespace {
+constexpr double kPi = 3.14159265358979323846;
+
+// Hann-windowed sinc tap at continuous offset t (the filter's definition).
+double hann_sinc_tap(double t, int H) {
+    const double s = (t == 0.0) ? 1.0 : sin(kPi * t) / (kPi * t);
+    return s * 0.5 * (1.0 + cos(kPi * t / (double)(H + 1)));
+}
+
+// Lagrange coefficient j of order P at delay D.
+double lagrange_tap(int j, int P, double D) {
+    double c = 1.0;
+    for (int i = 0; i <= P; ++i)
+        if (i != j) c *= (D - (double)i) / (double)(j - i);
+    return c;
+}
+
+ChebTable build_cheb(int kind, int n_taps) {
+    // Chebyshev interpolation at M first-kind nodes: each tap, as a function
+    // of x in [-1, 1], is sampled at x_k = cos(pi (k + 1/2) / M) and
+    // c_p = (2/M) sum_k g(x_k) T_p(x_k) (c_0 halved).  Terms are kept while
+    // the largest remaining tail, over all taps, exceeds 1e-9 (the taps are
+    // of order 1, so this is far below FP32 resolution).
+    const int M = 64;
+    std::vector<double> c((size_t)M * n_taps);
+    std::vector<double> vals(M);
+    for (int j = 0; j < n_taps; ++j) {
+        for (int k = 0; k < M; ++k) {
+            const double x = cos(kPi * (k + 0.5) / M);
+            if (kind == ISM_FD_HANN_SINC) {
+                const int H = (n_taps - 1) / 2;
+                vals[k] = hann_sinc_tap((double)(j - H) - 0.5 * x, H);
+            } else {
+                const int P = n_taps - 1;
+                vals[k] = lagrange_tap(j, P, 0.5 * (P - 1) + 0.5 * (x + 1.0));
+            }
+        }
+        for (int p = 0; p < M; ++p) {
+            double acc = 0.0;
+            for (int k = 0; k < M; ++k) acc += vals[k] * cos(p * kPi * (k + 0.5) / M);
+            c[(size_t)p * n_taps + j] = (p == 0 ? 1.0 : 2.0) * acc / M;
+        }
+    }
+    ChebTable t;
+    t.n_cheb = 0;
+    for (int P = 1; P <= kMaxCheb; ++P) {
+        double worst = 0.0;
+        for (int j = 0; j < n_taps; ++j) {
+            double tail = 0.0;
+            for (int p = P; p < M; ++p) tail += fabs(c[(size_t)p * n_taps + j]);
+            worst = std::max(worst, tail);
+        }
+        if (worst <= 1e-9) {
+            t.n_cheb = P;
+            break;
+        }
+    }
+    if (t.n_cheb) {
+        t.coef.resize((size_t)t.n_cheb * n_taps);
+        for (size_t i = 0; i < t.coef.size(); ++i) t.coef[i] = (float)c[i];
+    }
+    return t;
+}
+
+std::mutex g_cheb_mu;
+std::vector<std::pair<std::pair<int, int>, ChebTable *>> g_cheb;
+}  // namespace
+
+const ChebTable &cheb_table(int fd_kind, int n_taps) {
+    std::lock_guard<std::mutex> lk(g_cheb_mu);
+    for (auto &e : g_cheb)
+        if (e.first.first == fd_kind && e.first.second == n_taps) return *e.second;
+    ChebTable *t = new ChebTable(build_cheb(fd_kind, n_taps));
+    g_cheb.push_back({{fd_kind, n_taps}, t});
+    return *t;
+}
+
 }  // namespace ism
 
 using namespace ism;
@@ -218,6 +299,8 @@ int ism_rir_batch_ex(const ism_room *rooms, int64_t n_rooms, float *h_dev,
     const int W = o.window > 0 ? o.window : 1024;
     if (W % 32 != 0 || W < 32 || W > 8192)
         return fail(ISM_ERR_INVALID_ARG, "window must be a multiple of 32 in [32, 8192]");
+    if (o.variant != ISM_RIR_SPARSE && o.variant != ISM_RIR_DIRECT)
+        return fail(ISM_ERR_INVALID_ARG, "unknown variant");
 
     // jobs, one per RIR; grouped by filter kind (one launch per kind)
     std::vector<RirJob> jobs[2];
@@ -240,11 +323,11 @@ int ism_rir_batch_ex(const ism_room *rooms, int64_t n_rooms, float *h_dev,
             for (int w = 0; w < 6; ++w) J.beta[w] = (float)R.beta[w];
             J.order = R.order;
             J.n_taps = R.n_taps;
-            J.fd_kind = kind;
+            J.fd_kind = (int16_t)kind;
             J.rir_len = R.rir_len;
             J.n_windows = (int32_t)((R.rir_len + W - 1) / W);
             J.h_offset = h_offsets ? h_offsets[j] : packed;
-            J.stat_index = j;
+            J.stat_index = (int32_t)j;  // statistics slot: RIR index in the caller's order
             packed += R.rir_len;
             if (J.h_offset < 0) return fail(ISM_ERR_INVALID_ARG, "negative h offset");
             jobs[kind].push_back(J);
@@ -260,17 +343,51 @@ int ism_rir_batch_ex(const ism_room *rooms, int64_t n_rooms, float *h_dev,
     for (int kind = 0; kind < 2; ++kind) {
         auto &jv = jobs[kind];
         if (jv.empty()) continue;
-        const size_t smem = rir_smem_bytes(W, max_order[kind], max_taps[kind]);
-        if (smem > 227 * 1024)
+        // sparse path: one Chebyshev table per distinct filter length
+        bool sparse = o.variant == ISM_RIR_SPARSE;
+        std::vector<float> tabs;
+        int max_cheb = 0;
+        if (sparse) {
+            std::vector<std::pair<int, int>> seen;  // (n_taps, offset)
+            for (auto &J : jv) {
+                int off = -1;
+                for (auto &pr : seen)
+                    if (pr.first == J.n_taps) off = pr.second;
+                const ChebTable &ct = cheb_table(kind, J.n_taps);
+                if (ct.n_cheb == 0) { sparse = false; break; }
+                if (off < 0) {
+                    off = (int)tabs.size();
+                    tabs.insert(tabs.end(), ct.coef.begin(), ct.coef.end());
+                    seen.push_back({J.n_taps, off});
+                }
+                J.tab_offset = off;
+                J.n_cheb = (int16_t)ct.n_cheb;
+                max_cheb = std::max(max_cheb, ct.n_cheb);
+            }
+            if (sparse && rir_sparse_smem_bytes(W, max_order[kind], max_taps[kind], max_cheb) >
+                              227 * 1024)
+                sparse = false;
+        }
+        if (!sparse && rir_smem_bytes(W, max_order[kind], max_taps[kind]) > 227 * 1024)
             return fail(ISM_ERR_INVALID_ARG, "window/order/taps need too much shared memory");
         const size_t jb = jv.size() * sizeof(RirJob);
+        const size_t tb = sparse ? tabs.size() * sizeof(float) : 0;
         void *scr = nullptr;
-        if (int st = scratch_alloc(&scr, jb + 256, stream)) return st;
+        if (int st = scratch_alloc(&scr, jb + 256 + tb, stream)) return st;
         RirJob *d_jobs = (RirJob *)scr;
         unsigned int *d_counter = (unsigned int *)((char *)scr + jb);
+        const float *d_tabs = (const float *)((char *)scr + jb + 256);
         long long *d_stats = (long long *)o.stats_dev;
         int st = upload_async(d_jobs, jv.data(), jb, stream);
+        if (!st && tb) st = upload_async((void *)d_tabs, tabs.data(), tb, stream);
         cudaError_t e = cudaSuccess;
+        auto run = [&](const RirJob *jd, int n, int wm) {
+            e = cudaMemsetAsync(d_counter, 0, sizeof(unsigned int), stream);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(counter)");
+            RirLaunch L{jd, n, wm, W, max_order[kind], max_taps[kind], kind, h_dev, d_stats,
+                        d_counter, nullptr, 0, d_tabs, max_cheb};
+            return sparse ? launch_rir_sparse(L, stream) : launch_rir(L, stream);
+        };
         if (!st) {
             if (o.per_room) {
                 // The unbatched path: one launch per room, each over that
@@ -281,19 +398,11 @@ int ism_rir_batch_ex(const ism_room *rooms, int64_t n_rooms, float *h_dev,
                     while (e2 < jv.size() && room_of[kind][e2] == room_of[kind][b]) ++e2;
                     int wm = 0;
                     for (size_t k = b; k < e2; ++k) wm = std::max(wm, jv[k].n_windows);
-                    e = cudaMemsetAsync(d_counter, 0, sizeof(unsigned int), stream);
-                    if (e != cudaSuccess) { st = cuda_fail(e, "cudaMemsetAsync(counter)"); break; }
-                    RirLaunch L{d_jobs + b, (int)(e2 - b), wm, W, max_order[kind], max_taps[kind],
-                                kind, h_dev, d_stats, d_counter, nullptr, 0};
-                    st = launch_rir(L, stream);
+                    st = run(d_jobs + b, (int)(e2 - b), wm);
                     b = e2;
                 }
             } else {
-                e = cudaMemsetAsync(d_counter, 0, sizeof(unsigned int), stream);
-                if (e != cudaSuccess) st = cuda_fail(e, "cudaMemsetAsync(counter)");
-                RirLaunch L{d_jobs, (int)jv.size(), wmax[kind], W, max_order[kind],
-                            max_taps[kind], kind, h_dev, d_stats, d_counter, nullptr, 0};
-                if (!st) st = launch_rir(L, stream);
+                st = run(d_jobs, (int)jv.size(), wmax[kind]);
             }
         }
         scratch_free(scr, stream);

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/ism.h"
 
@@ -22,12 +23,15 @@ struct alignas(16) RirJob {
     float beta[6];      // x0, x1, y0, y1, z0, z1
     int32_t order;      // N
     int32_t n_taps;
-    int32_t fd_kind;    // ISM_FD_HANN_SINC / ISM_FD_LAGRANGE
+    int16_t fd_kind;    // ISM_FD_HANN_SINC / ISM_FD_LAGRANGE
+    int16_t n_cheb;     // Chebyshev terms of the filter table (sparse kernel)
     int32_t n_windows;  // ceil(rir_len / W)
     int64_t rir_len;
     int64_t h_offset;   // element offset of h[0] in the output buffer
-    int64_t stat_index; // RIR index in the caller's order (statistics slot)
+    int32_t stat_index; // RIR index in the caller's order (statistics slot)
+    int32_t tab_offset; // offset of the filter's Chebyshev table (floats)
 };
+static_assert(sizeof(RirJob) == 144, "RirJob layout");
 
 // One room of a convolution batch on the device.
 struct alignas(16) ConvJob {
@@ -75,9 +79,26 @@ struct RirLaunch {
     unsigned int *counter_dev;
     int *err_dev;
     int grid;             // 0 = persistent (SMs x blocks/SM)
+    const float *tabs_dev;  // sparse kernel: Chebyshev tables [p][n_taps]
+    int max_cheb;           // sparse kernel: largest n_cheb of the jobs
 };
+// Direct per-tap kernel (bitwise reproducible).
 int launch_rir(const RirLaunch &L, cudaStream_t stream);
 size_t rir_smem_bytes(int window, int max_order, int max_taps);
+// Sparse integer-delay arrays + Chebyshev FIR kernel.
+int launch_rir_sparse(const RirLaunch &L, cudaStream_t stream);
+size_t rir_sparse_smem_bytes(int window, int max_order, int max_taps, int max_cheb);
+constexpr int kMaxCheb = 16;
+
+// Chebyshev table of a fractional-delay filter: coef[p * n_taps + j], tap j
+// (first tap = 0) as a function of x in [-1, 1], x = 2f (Hann sinc, f the
+// fraction in [-1/2, 1/2]) or x = 2f - 1 (Lagrange, f in [0, 1)).  n_cheb is
+// the number of terms kept (<= kMaxCheb), or 0 if the filter needs more.
+struct ChebTable {
+    int n_cheb;
+    std::vector<float> coef;
+};
+const ChebTable &cheb_table(int fd_kind, int n_taps);
 
 // K2b / K2 / noise.
 struct ConvLaunch {

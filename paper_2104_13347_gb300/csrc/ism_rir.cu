@@ -7,12 +7,12 @@
 //
 // Work decomposition (GB300-first, no global atomics on h):
 //  * A work item is one output window [w0, w0+W) of one RIR.  A persistent
-//    grid (SMs x 2 CTAs) pulls items from one atomic counter, later windows
-//    (more images) first.
+//    grid pulls items from one atomic counter, later windows (more images)
+//    first.
 //  * The CTA enumerates only the images whose taps reach its window: per
-//    lattice column (u,l,v,m,w) the admissible n form at most two intervals
-//    (a quadratic in n), solved in FP32 with a safety margin; each candidate
-//    is then tested exactly on its delay.
+//    lattice column (u,l,v,m,w) the admissible n are the integers with
+//    zmin <= |Delta_z(n)| <= zmax, solved in FP32 with a safety margin; each
+//    candidate is then tested exactly on its delay.
 //  * Delays: image-to-mic squared offsets per axis are tabled once per item in
 //    FP64 with the definition's rounding, d^2 and sqrt are done in
 //    float-float (FP32 pipe; GB300's FP64 rate is a small fraction of FP32),
@@ -21,12 +21,23 @@
 //    of a rounding boundary or of an integer (so exact integer delays give
 //    exact Kronecker deltas).  The integer part therefore equals the
 //    definition's bit for bit, and the fractional part to ~1e-9 samples.
-//  * Taps: one warp per image, one lane per tap (81 taps -> 3 rows of 32).
-//    sin(pi (j-f)) = -(-1)^j sin(pi f) and the Hann term is expanded in
-//    cos/sin of pi j/(H+1) (per-lane constants) and of pi f/(H+1) (per
-//    image), leaving one reciprocal per tap.  Each warp accumulates into its
-//    own shared-memory copy of the window (no atomics, fixed order), and the
-//    copies are summed in a fixed order into coalesced stores of h.
+//
+// Two ways to lay the taps down:
+//  * k_ism_sparse (default): the tap function of the filter, g_j(f), is
+//    expanded in Chebyshev polynomials of the fraction, g_j(f) ~ sum_p
+//    B[p][j] T_p(x(f)) (FP64 table, truncated where the remaining terms sum
+//    below 1e-9; exact for the Lagrange filter, whose taps are polynomials in
+//    the delay).  Each image then adds a T_p(x) to P sparse integer-delay
+//    arrays c_p[kb] (shared-memory atomics) -- the paper's representation of
+//    the integer delays as a sparse array -- and one fixed-order FIR per
+//    window gives h[n] = sum_p sum_j B[p][j] c_p[n - j].  Per image: P
+//    products instead of one reciprocal and ~7 operations per tap.
+//  * k_ism_taps (direct): one warp per image, one lane per tap (81 taps -> 3
+//    rows of 32).  sin(pi (j-f)) = -(-1)^j sin(pi f) and the Hann term is
+//    expanded in cos/sin of pi j/(H+1) (per-lane constants) and of
+//    pi f/(H+1) (per image), leaving one reciprocal per tap.  Each warp
+//    accumulates into its own shared-memory copy of the window (no atomics,
+//    fixed order, bitwise reproducible).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -38,9 +49,10 @@ namespace {
 
 constexpr int NT = 256;           // threads per CTA
 constexpr int NW = NT / 32;       // warps per CTA
-constexpr int CAP = 2048;         // candidate / record buffer (images)
-constexpr int CPT = CAP / NT;     // candidates per thread in the record phase
+constexpr int CAP = 2048;         // candidate buffer (images)
+constexpr int CPT = CAP / NT;     // candidates per thread per flush
 constexpr float kEps = 0.2f;      // metres of margin in the column solve
+constexpr int PADL = 8;           // left padding of the sparse arrays (floats)
 
 __device__ __forceinline__ float rcp_approx(float x) {
     float r;
@@ -75,6 +87,9 @@ __device__ __forceinline__ int block_scan(int v, int *s_w, int &total) {
     return off;
 }
 
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+__host__ __device__ inline int round4(int x) { return (x + 3) & ~3; }
+
 struct Tables {
     double *sq;   // [3][TE] squared axis offsets (FP64, definition rounding)
     float *hi;    // [3][TE] float-float split of sq
@@ -83,20 +98,23 @@ struct Tables {
     float *g;     // [3][TE] wall damping product along the axis
 };
 
-// Shared-memory carve-up (sizes from the launch's max order / taps).
+// Shared-memory carve-up.  Common part: tables, axis lists, candidates.
+// Direct kernel adds one private window row per warp; sparse kernel adds
+// the P sparse arrays, the integer-delay (delta) array, the Chebyshev table
+// and the FIR partial sums.
 struct Layout {
-    int TE;       // table entries per axis: 2 (2 Nmax + 1)
-    int RL;       // private row length in floats
-    size_t off_sq, off_hi, off_lo, off_dl, off_g, off_lx, off_ly, off_cand, off_rec4,
-        off_reck, off_idx, off_rows, total;
+    int TE, RL, CL, TPS;
+    size_t off_sq, off_hi, off_lo, off_dl, off_g, off_lx, off_ly, off_cand, off_rows, off_c,
+        off_delta, off_B, off_part, total;
 };
 
-__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
-
-__host__ __device__ inline Layout make_layout(int window, int max_order, int max_taps) {
+__host__ __device__ inline Layout make_layout(bool sparse, int window, int max_order,
+                                              int max_taps, int max_cheb) {
     Layout L;
     L.TE = 2 * (2 * max_order + 1);
-    L.RL = (window + 2 * (max_taps - 1) + 3) & ~3;
+    L.RL = round4(window + 2 * (max_taps - 1));
+    L.CL = round4(window + max_taps + 12 + PADL);
+    L.TPS = round4(max_taps);
     size_t o = 0;
     L.off_sq = o;   o = align16(o + sizeof(double) * 3 * L.TE);
     L.off_hi = o;   o = align16(o + sizeof(float) * 3 * L.TE);
@@ -105,23 +123,26 @@ __host__ __device__ inline Layout make_layout(int window, int max_order, int max
     L.off_g = o;    o = align16(o + sizeof(float) * 3 * L.TE);
     L.off_lx = o;   o = align16(o + sizeof(int) * L.TE);
     L.off_ly = o;   o = align16(o + sizeof(int) * L.TE);
-    L.off_cand = o; o = align16(o + sizeof(uint32_t) * CAP);
-    L.off_rec4 = o; o = align16(o + sizeof(float4) * CAP);
-    L.off_reck = o; o = align16(o + sizeof(int) * CAP);
-    L.off_idx = o;  o = align16(o + sizeof(uint16_t) * CAP);
-    L.off_rows = o; o = align16(o + sizeof(float) * (size_t)NW * L.RL);
+    // the sparse kernel's FIR partial sums (2 W floats) reuse the candidate
+    // buffer, which is idle during the FIR
+    const size_t cand_words = (sparse && 2 * window > CAP) ? (size_t)(2 * window) : (size_t)CAP;
+    L.off_cand = o; o = align16(o + sizeof(uint32_t) * cand_words);
+    L.off_rows = L.off_c = L.off_delta = L.off_B = o;
+    L.off_part = L.off_cand;
+    if (!sparse) {
+        L.off_rows = o; o = align16(o + sizeof(float) * (size_t)NW * L.RL);
+    } else {
+        L.off_c = o;     o = align16(o + sizeof(float) * (size_t)max_cheb * L.CL);
+        L.off_delta = o; o = align16(o + sizeof(float) * (size_t)L.CL);
+        L.off_B = o;     o = align16(o + sizeof(float) * (size_t)max_cheb * L.TPS);
+    }
     L.total = o;
     return L;
 }
 
-// Image record of one candidate (shared memory, at the candidate's slot):
-// first tap index kb, and v = (A, A cos(pi f/(H+1)), A sin(pi f/(H+1)), f)
-// with A = -a sin(pi f) / (2 pi) for the Hann-sinc filter, or v = (a, D)
-// for the Lagrange filter.
-
 // Delay split of one image (Sec. II.A: the delay of every image must keep
-// its sub-sample precision).  Returns the integer part k (rint, ties to even, for Hann;
-// floor for Lagrange) and the fraction in FP32, plus d (FP32).
+// its sub-sample precision).  Returns the integer part k (rint, ties to
+// even, for Hann; floor for Lagrange) and the fraction in FP32, plus d.
 template <int KIND>
 __device__ __forceinline__ void delay_split(const Tables &T, int TE, int ix, int iy, int iz,
                                             float qh, float ql, double q, int &k_out,
@@ -185,13 +206,222 @@ __device__ __forceinline__ void delay_split(const Tables &T, int TE, int ix, int
     d_out = dh;
 }
 
+// Per-item constants (identical in every thread of the CTA).
+struct Item {
+    int N, TEj, n_taps, H, P;   // order, table entries, taps, Hann half-width, Lagrange order
+    int w0, W;
+    long long Lh, kb_lo, kb_hi; // window's first-tap range
+    double q;
+    float qh, ql, dlo2, dhi2, dhe2, dhe, eps, inv2Lz;
+};
+
+template <int KIND>
+__device__ __forceinline__ void item_setup(const RirJob &J, int W, int wi, Item &it) {
+    it.N = J.order;
+    it.TEj = 2 * (2 * it.N + 1);
+    it.n_taps = J.n_taps;
+    it.H = (it.n_taps - 1) / 2;
+    it.P = it.n_taps - 1;
+    it.Lh = J.rir_len;
+    it.W = W;
+    it.w0 = wi * W;
+    it.q = J.q;
+    it.qh = (float)it.q;
+    it.ql = (float)(it.q - (double)it.qh);
+    it.kb_lo = (long long)it.w0 - it.n_taps + 1;
+    it.kb_hi = min((long long)it.w0 + W - 1, it.Lh - 1);
+    double tau_lo, tau_hi;
+    if (KIND == ISM_FD_HANN_SINC) {
+        tau_lo = (double)(it.kb_lo + it.H) - 0.5;
+        tau_hi = (double)(it.kb_hi + it.H) + 0.5;
+    } else {
+        tau_lo = (double)(it.kb_lo + (it.P - 1) / 2);
+        tau_hi = (double)(it.kb_hi + (it.P + 1) / 2);
+    }
+    const float d_lo = (float)fmax(tau_lo / it.q, 0.0);
+    const float d_hi = (float)(tau_hi / it.q);
+    it.eps = kEps + 1e-6f * d_hi;
+    it.dlo2 = d_lo * d_lo;
+    it.dhi2 = d_hi * d_hi;
+    it.dhe = d_hi + it.eps;
+    it.dhe2 = it.dhe * it.dhe;
+    it.inv2Lz = 1.f / (2.f * (float)J.dims[2]);
+}
+
+// Per-axis tables (all threads).  Offsets in FP64 with the definition's
+// rounding: ((1-2p) s + (2q) L) - r.
+__device__ __forceinline__ void build_tables(const RirJob &J, const Tables &T, int TE,
+                                             const Item &it) {
+    const int N = it.N, TEj = it.TEj;
+    for (int e = threadIdx.x; e < 3 * TEj; e += NT) {
+        const int a = e / TEj, ei = e - a * TEj;
+        const int p = ei / (2 * N + 1), qq = ei - p * (2 * N + 1) - N;
+        const double s = J.src[a], Ld = J.dims[a], r = J.mic[a];
+        const double img = __dadd_rn(p ? -s : s, __dmul_rn((double)(2 * qq), Ld));
+        const double dlt = __dsub_rn(img, r);
+        const double sq = __dmul_rn(dlt, dlt);
+        const float sh = __double2float_rn(sq);
+        T.sq[a * TE + ei] = sq;
+        T.hi[a * TE + ei] = sh;
+        T.lo[a * TE + ei] = __double2float_rn(sq - (double)sh);
+        T.dl[a * TE + ei] = __double2float_rn(dlt);
+        const float b0 = J.beta[2 * a], b1 = J.beta[2 * a + 1];
+        T.g[a * TE + ei] = powf(b0, (float)abs(qq - p)) * powf(b1, (float)abs(qq));
+    }
+}
+
+// Axis lists (warps 0 and 1): table entries whose offset alone is in reach.
+__device__ __forceinline__ void build_lists(const Tables &T, int TE, const Item &it, int *s_lx,
+                                            int *s_ly, int *s_nl) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp < 2) {
+        const float *dd = T.dl + warp * TE;
+        int *lst = warp ? s_ly : s_lx;
+        int cnt = 0;
+        for (int base = 0; base < it.TEj; base += 32) {
+            const int e = base + lane;
+            const bool ok = e < it.TEj && fabsf(dd[e]) <= it.dhe;
+            const unsigned b = __ballot_sync(0xffffffffu, ok);
+            if (ok) lst[cnt + __popc(b & ((1u << lane) - 1u))] = e;
+            cnt += __popc(b);
+        }
+        if (lane == 0) s_nl[warp] = cnt;
+    }
+}
+
+// Column sweep: candidates per (u,l,v,m,w) column, handed to flush(nc) in
+// batches of at most CAP.  All threads call it; block-uniform control flow.
+template <class Flush>
+__device__ __forceinline__ void column_sweep(const Tables &T, int TE, const Item &it,
+                                             const int *s_lx, const int *s_ly, int nLX, int nLY,
+                                             int *s_scan, uint32_t *s_cand, Flush &flush) {
+    const int N = it.N, tid = threadIdx.x;
+    const long long n_cols = (long long)nLX * nLY * 2;
+    int n_cand = 0;  // block-uniform
+    for (long long cb = 0; cb < n_cols; cb += NT) {
+        const long long c = cb + tid;
+        int lo_a = 1, hi_a = 0, lo_b = 1, hi_b = 0, ix = 0, iy = 0, wz = 0;
+        if (c < n_cols) {
+            wz = (int)(c & 1);
+            const long long t = c >> 1;
+            ix = s_lx[(int)(t / nLY)];
+            iy = s_ly[(int)(t % nLY)];
+            const float dx = T.dl[ix], dy = T.dl[TE + iy];
+            const float rho2 = dx * dx + dy * dy;
+            if (rho2 <= it.dhe2) {
+                // Delta_z(n) = cz + 2 Lz n must satisfy zmin <= |Delta_z| <= zmax:
+                // the full range [-zmax, zmax] minus the open hole (-zmin, zmin).
+                const float zmax = sqrtf(fmaxf(it.dhi2 - rho2, 0.f)) + it.eps;
+                const float zmin2 = it.dlo2 - rho2;
+                const float zmin = zmin2 > 0.f ? sqrtf(zmin2) - it.eps : 0.f;
+                const float cz = T.dl[2 * TE + wz * (2 * N + 1) + N];
+                const float lim = (float)N + 1.f;
+                const float u_lo = fminf(fmaxf((-zmax - cz) * it.inv2Lz, -lim), lim);
+                const float u_hi = fminf(fmaxf((zmax - cz) * it.inv2Lz, -lim), lim);
+                int n_lo = (int)ceilf(u_lo);
+                int n_hi = (int)floorf(u_hi);
+                if (n_lo < -N) n_lo = -N;
+                if (n_hi > N) n_hi = N;
+                int h_lo = 1, h_hi = 0;  // hole (excluded n), empty by default
+                if (zmin > 0.f) {
+                    const float v_lo = fminf(fmaxf((-zmin - cz) * it.inv2Lz, -lim), lim);
+                    const float v_hi = fminf(fmaxf((zmin - cz) * it.inv2Lz, -lim), lim);
+                    h_lo = (int)floorf(v_lo) + 1;
+                    h_hi = (int)ceilf(v_hi) - 1;
+                }
+                if (h_lo <= h_hi) {
+                    lo_a = n_lo;
+                    hi_a = n_hi < h_lo - 1 ? n_hi : h_lo - 1;
+                    lo_b = n_lo > h_hi + 1 ? n_lo : h_hi + 1;
+                    hi_b = n_hi;
+                } else {
+                    lo_a = n_lo;
+                    hi_a = n_hi;
+                }
+            }
+        }
+        const int cnt = max(hi_a - lo_a + 1, 0) + max(hi_b - lo_b + 1, 0);
+        int total;
+        const int off = block_scan(cnt, s_scan, total);
+        if (total == 0) continue;
+        if (n_cand + total > CAP && n_cand > 0) {
+            flush(n_cand);
+            n_cand = 0;
+        }
+        const int zb = wz * (2 * N + 1) + N;
+        const uint32_t base_code = (uint32_t)ix | ((uint32_t)iy << 10);
+        // candidates with global index in [g_lo, g_hi) go to s_cand[dst + index]
+        auto emit = [&](int g_lo, int g_hi, int dst) {
+            int gi = off;
+            for (int n = lo_a; n <= hi_a; ++n, ++gi)
+                if (gi >= g_lo && gi < g_hi) s_cand[dst + gi] = base_code | ((uint32_t)(zb + n) << 20);
+            for (int n = lo_b; n <= hi_b; ++n, ++gi)
+                if (gi >= g_lo && gi < g_hi) s_cand[dst + gi] = base_code | ((uint32_t)(zb + n) << 20);
+        };
+        if (total <= CAP) {
+            emit(0, total, n_cand);
+            n_cand += total;
+        } else {
+            for (int pb = 0; pb < total; pb += CAP) {
+                emit(pb, pb + CAP, -pb);
+                flush(min(CAP, total - pb));
+            }
+        }
+    }
+    if (n_cand > 0) flush(n_cand);
+}
+
+// Evaluates one candidate: delay split, window test, gain, statistics.
+// Returns false if the image's taps miss the window.
+template <int KIND>
+__device__ __forceinline__ bool eval_candidate(const Tables &T, int TE, const Item &it,
+                                               uint32_t cd, int &kb, float &f, float &a,
+                                               unsigned long long &my_taps,
+                                               unsigned long long &my_contrib) {
+    const int ix = cd & 1023, iy = (cd >> 10) & 1023, iz = cd >> 20;
+    int k;
+    float d;
+    delay_split<KIND>(T, TE, ix, iy, iz, it.qh, it.ql, it.q, k, f, d);
+    kb = (KIND == ISM_FD_HANN_SINC) ? k - it.H : k - (it.P - 1) / 2;
+    if (kb < it.kb_lo || kb > it.kb_hi) return false;
+    a = T.g[ix] * T.g[TE + iy] * T.g[2 * TE + iz] * __frcp_rn(12.566370614359172f * d);
+    // statistics: taps in [w0, w0+W) n [0, Lh); an image counts as
+    // contributing in the window of its first in-range tap.
+    const long long lo = max((long long)kb, max((long long)it.w0, 0ll));
+    const long long hi = min((long long)kb + it.n_taps, min((long long)it.w0 + it.W, it.Lh));
+    if (hi > lo) my_taps += (unsigned long long)(hi - lo);
+    const long long first = max((long long)kb, 0ll);
+    if (first < min((long long)kb + it.n_taps, it.Lh) && first >= it.w0 &&
+        first < (long long)it.w0 + it.W)
+        ++my_contrib;
+    return true;
+}
+
+__device__ __forceinline__ void flush_stats(long long *stats, const RirJob &J,
+                                            unsigned long long *s_stat,
+                                            unsigned long long my_contrib,
+                                            unsigned long long my_taps) {
+    if (!stats) return;
+    atomicAdd(&s_stat[0], my_contrib);
+    atomicAdd(&s_stat[1], my_taps);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const long long si = J.stat_index;
+        atomicAdd((unsigned long long *)&stats[2 * si], s_stat[0]);
+        atomicAdd((unsigned long long *)&stats[2 * si + 1], s_stat[1]);
+    }
+}
+
+// ===========================================================================
+// k_ism_taps: direct per-tap kernel
+// ===========================================================================
 template <int R, int KIND>
 __global__ void __launch_bounds__(NT, 2)
 k_ism_taps(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int max_order,
            int max_taps, float *__restrict__ h, long long *__restrict__ stats,
            unsigned int *__restrict__ counter) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const Layout Lay = make_layout(W, max_order, max_taps);
+    const Layout Lay = make_layout(false, W, max_order, max_taps, 0);
     const int TE = Lay.TE;
     Tables T;
     T.sq = (double *)(smem + Lay.off_sq);
@@ -202,9 +432,6 @@ k_ism_taps(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int max
     int *s_lx = (int *)(smem + Lay.off_lx);
     int *s_ly = (int *)(smem + Lay.off_ly);
     uint32_t *s_cand = (uint32_t *)(smem + Lay.off_cand);
-    float4 *s_rec4 = (float4 *)(smem + Lay.off_rec4);
-    int *s_reck = (int *)(smem + Lay.off_reck);
-    uint16_t *s_idx = (uint16_t *)(smem + Lay.off_idx);
     float *s_rows = (float *)(smem + Lay.off_rows);
     __shared__ int s_scan[NW];
     __shared__ int s_item, s_nl[2];
@@ -214,7 +441,6 @@ k_ism_taps(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int max
     const int HALO = max_taps - 1;
     const int RL = Lay.RL;
 
-    // Private rows start zeroed; each item leaves them zeroed.
     for (int i = tid; i < NW * RL; i += NT) s_rows[i] = 0.f;
 
     const long long n_items = (long long)n_rirs * wmax;
@@ -224,71 +450,15 @@ k_ism_taps(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int max
         const long long item = s_item;
         if (item >= n_items) break;
         const int wi = wmax - 1 - (int)(item / n_rirs);
-        const int ji = (int)(item % n_rirs);
-        const RirJob &J = jobs[ji];
+        const RirJob &J = jobs[(int)(item % n_rirs)];
         if (wi >= J.n_windows) { __syncthreads(); continue; }
-
-        const int N = J.order;
-        const int TEj = 2 * (2 * N + 1);
-        const int n_taps = J.n_taps;
-        const int H = (n_taps - 1) / 2;            // Hann half-width
-        const int P = n_taps - 1;                   // Lagrange order
-        const long long Lh = J.rir_len;
-        const int w0 = wi * W;
-        const double q = J.q;
-        const float qh = (float)q;
-        const float ql = (float)(q - (double)qh);
-
-        // ---- per-axis tables (FP64 offsets with the definition's rounding)
-        for (int e = tid; e < 3 * TEj; e += NT) {
-            const int a = e / TEj, ei = e - a * TEj;
-            const int p = ei / (2 * N + 1), qq = ei - p * (2 * N + 1) - N;
-            const double s = J.src[a], Ld = J.dims[a], r = J.mic[a];
-            const double img = __dadd_rn(p ? -s : s, __dmul_rn((double)(2 * qq), Ld));
-            const double dlt = __dsub_rn(img, r);
-            const double sq = __dmul_rn(dlt, dlt);
-            const float sh = __double2float_rn(sq);
-            T.sq[a * TE + ei] = sq;
-            T.hi[a * TE + ei] = sh;
-            T.lo[a * TE + ei] = __double2float_rn(sq - (double)sh);
-            T.dl[a * TE + ei] = __double2float_rn(dlt);
-            const float b0 = J.beta[2 * a], b1 = J.beta[2 * a + 1];
-            T.g[a * TE + ei] = powf(b0, (float)abs(qq - p)) * powf(b1, (float)abs(qq));
-        }
+        Item it;
+        item_setup<KIND>(J, W, wi, it);
+        build_tables(J, T, TE, it);
         if (tid < 2) s_stat[tid] = 0ull;
-
-        // ---- window bounds: first-tap index kb in [kb_lo, kb_hi]
-        const long long kb_lo = (long long)w0 - n_taps + 1;
-        const long long kb_hi = min((long long)w0 + W - 1, Lh - 1);
-        double tau_lo, tau_hi;
-        if (KIND == ISM_FD_HANN_SINC) {
-            tau_lo = (double)(kb_lo + H) - 0.5;
-            tau_hi = (double)(kb_hi + H) + 0.5;
-        } else {
-            tau_lo = (double)(kb_lo + (P - 1) / 2);
-            tau_hi = (double)(kb_hi + (P + 1) / 2);
-        }
-        const float d_lo = (float)fmax(tau_lo / q, 0.0);
-        const float d_hi = (float)(tau_hi / q);
-        const float eps = kEps + 1e-6f * d_hi;
-        const float dlo2 = d_lo * d_lo, dhi2 = d_hi * d_hi;
-        const float dhe = d_hi + eps, dhe2 = dhe * dhe;
         __syncthreads();
-
-        // ---- axis lists: entries whose offset alone is within reach
-        if (warp < 2) {
-            const float *dd = T.dl + warp * TE;
-            int *lst = warp ? s_ly : s_lx;
-            int cnt = 0;
-            for (int base = 0; base < TEj; base += 32) {
-                const int e = base + lane;
-                const bool ok = e < TEj && fabsf(dd[e]) <= dhe;
-                const unsigned b = __ballot_sync(0xffffffffu, ok);
-                if (ok) lst[cnt + __popc(b & ((1u << lane) - 1u))] = e;
-                cnt += __popc(b);
-            }
-            if (lane == 0) s_nl[warp] = cnt;
-        }
+        build_lists(T, TE, it, s_lx, s_ly, s_nl);
+        const int H = it.H, P = it.P, w0 = it.w0;
         // per-lane tap constants
         float cC[R], cS[R], cSJ[R], cMS[R];
         bool cOK[R];
@@ -313,181 +483,84 @@ k_ism_taps(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int max
         }
         __syncthreads();
         const int nLX = s_nl[0], nLY = s_nl[1];
-        const long long n_cols = (long long)nLX * nLY * 2;
-        const float Lz = (float)J.dims[2];
-        const float inv2Lz = 1.f / (2.f * Lz);
         unsigned long long my_contrib = 0, my_taps = 0;
 
-        // ---- flush: records for s_cand[0..nc), then taps
+        // flush: for each candidate, one warp lays its taps into that warp's
+        // private row.  Candidates are handed out round-robin to warps in
+        // candidate order; each thread evaluates its warp's candidates
+        // lane-parallel first, then the warp walks them one by one.
         auto flush = [&](int nc) {
             __syncthreads();
-            // records are written at their candidate slot; only the indices
-            // of the valid ones are compacted (block scan, fixed order)
-            unsigned vmask = 0;
-            const int c0 = tid * CPT;
-#pragma unroll 1
-            for (int t = 0; t < CPT; ++t) {
-                const int ci = c0 + t;
-                if (ci >= nc) break;
-                const uint32_t cd = s_cand[ci];
-                const int ix = cd & 1023, iy = (cd >> 10) & 1023, iz = cd >> 20;
-                int k;
-                float f, d;
-                delay_split<KIND>(T, TE, ix, iy, iz, qh, ql, q, k, f, d);
-                const int kb = (KIND == ISM_FD_HANN_SINC) ? k - H : k - (P - 1) / 2;
-                if (kb < kb_lo || kb > kb_hi) continue;
-                const float a = T.g[ix] * T.g[TE + iy] * T.g[2 * TE + iz] *
-                                __frcp_rn(12.566370614359172f * d);
-                float4 v;
-                if (KIND == ISM_FD_HANN_SINC) {
-                    if (fabsf(f) < 1e-30f) {
-                        v = make_float4(a, 0.f, 0.f, 0.f);
-                    } else {
-                        float sp, cp, sw, cw;
-                        sincospif(f, &sp, &cp);
-                        sincospif(f / (float)(H + 1), &sw, &cw);
-                        const float A = -a * sp * 0.15915494309189535f;
-                        v = make_float4(A, A * cw, A * sw, f);
-                    }
-                } else {
-                    v = make_float4(a, f + (float)((P - 1) / 2), 0.f, 0.f);
-                }
-                s_reck[ci] = kb;
-                s_rec4[ci] = v;
-                vmask |= 1u << t;
-                // statistics: taps in [w0, w0+W) n [0, Lh); an image counts
-                // as contributing in the window of its first in-range tap.
-                const long long lo = max((long long)kb, max((long long)w0, 0ll));
-                const long long hi = min((long long)kb + n_taps, min((long long)w0 + W, Lh));
-                if (hi > lo) my_taps += (unsigned long long)(hi - lo);
-                const long long first = max((long long)kb, 0ll);
-                if (first < min((long long)kb + n_taps, Lh) && first >= w0 &&
-                    first < (long long)w0 + W)
-                    ++my_contrib;
-            }
-            int nrec;
-            int o = block_scan(__popc(vmask), s_scan, nrec);
-            while (vmask) {
-                const int t = __ffs(vmask) - 1;
-                vmask &= vmask - 1;
-                s_idx[o++] = (uint16_t)(c0 + t);
-            }
-            __syncthreads();
-            // taps: warp per image, lane per tap, private row per warp
             float *rowp = s_rows + warp * RL + lane;
-            for (int i = warp; i < nrec; i += NW) {
-                const int ri = s_idx[i];
-                const int kb = s_reck[ri];
-                const float4 v = s_rec4[ri];
-                // row index of tap index n is n - w0 + HALO, in [0, RL)
-                float *p = rowp + (kb - w0 + HALO);
-                if (KIND == ISM_FD_HANN_SINC) {
-                    if (v.w == 0.f) {
-                        if (lane == 0) p[H] += v.x;
-                        continue;
-                    }
-#pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        if (cOK[r]) {
-                            const float xs = fmaf(cMS[r], v.w, cSJ[r]);
-                            const float rcp = rcp_approx(xs);
-                            const float nn = fmaf(cC[r], v.y, fmaf(cS[r], v.z, v.x));
-                            p[32 * r] = fmaf(nn, rcp, p[32 * r]);
+            for (int base = warp * 32; base < nc; base += NW * 32) {
+                const int ci = base + lane;
+                int kb = INT32_MIN;
+                float f = 0.f, a = 0.f;
+                if (ci < nc) {
+                    if (!eval_candidate<KIND>(T, TE, it, s_cand[ci], kb, f, a, my_taps,
+                                              my_contrib))
+                        kb = INT32_MIN;
+                }
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (kb != INT32_MIN) {
+                    if (KIND == ISM_FD_HANN_SINC) {
+                        if (fabsf(f) < 1e-30f) {
+                            v = make_float4(a, 0.f, 0.f, 0.f);
+                        } else {
+                            float sp, cp, sw, cw;
+                            sincospif(f, &sp, &cp);
+                            sincospif(f / (float)(H + 1), &sw, &cw);
+                            const float A = -a * sp * 0.15915494309189535f;
+                            v = make_float4(A, A * cw, A * sw, f);
                         }
+                    } else {
+                        v = make_float4(a, f + (float)((P - 1) / 2), 0.f, 0.f);
                     }
-                } else {
+                }
+                unsigned vm = __ballot_sync(0xffffffffu, kb != INT32_MIN);
+                while (vm) {
+                    const int src = __ffs(vm) - 1;
+                    vm &= vm - 1;
+                    const int kbs = __shfl_sync(0xffffffffu, kb, src);
+                    const float vx = __shfl_sync(0xffffffffu, v.x, src);
+                    const float vy = __shfl_sync(0xffffffffu, v.y, src);
+                    const float vz = __shfl_sync(0xffffffffu, v.z, src);
+                    const float vw = __shfl_sync(0xffffffffu, v.w, src);
+                    // row index of tap index n is n - w0 + HALO, in [0, RL)
+                    float *p = rowp + (kbs - w0 + HALO);
+                    if (KIND == ISM_FD_HANN_SINC) {
+                        if (vw == 0.f) {
+                            if (lane == 0) p[H] += vx;
+                            continue;
+                        }
 #pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        if (cOK[r]) {
-                            const int j = lane + 32 * r;
-                            float prod = cC[r];
-                            for (int i2 = 0; i2 <= P; ++i2)
-                                if (i2 != j) prod *= (v.y - (float)i2);
-                            p[32 * r] = fmaf(v.x, prod, p[32 * r]);
+                        for (int r = 0; r < R; ++r) {
+                            if (cOK[r]) {
+                                const float xs = fmaf(cMS[r], vw, cSJ[r]);
+                                const float rcp = rcp_approx(xs);
+                                const float nn = fmaf(cC[r], vy, fmaf(cS[r], vz, vx));
+                                p[32 * r] = fmaf(nn, rcp, p[32 * r]);
+                            }
+                        }
+                    } else {
+#pragma unroll
+                        for (int r = 0; r < R; ++r) {
+                            if (cOK[r]) {
+                                const int j = lane + 32 * r;
+                                float prod = cC[r];
+                                for (int i2 = 0; i2 <= P; ++i2)
+                                    if (i2 != j) prod *= (vy - (float)i2);
+                                p[32 * r] = fmaf(vx, prod, p[32 * r]);
+                            }
                         }
                     }
                 }
             }
             __syncthreads();
         };
+        column_sweep(T, TE, it, s_lx, s_ly, nLX, nLY, s_scan, s_cand, flush);
 
-        // ---- column sweep: candidates per (u,l,v,m,w) column
-        int n_cand = 0;  // block-uniform
-        for (long long cb = 0; cb < n_cols; cb += NT) {
-            const long long c = cb + tid;
-            int lo_a = 1, hi_a = 0, lo_b = 1, hi_b = 0, ix = 0, iy = 0, wz = 0;
-            if (c < n_cols) {
-                wz = (int)(c & 1);
-                const long long t = c >> 1;
-                ix = s_lx[(int)(t / nLY)];
-                iy = s_ly[(int)(t % nLY)];
-                const float dx = T.dl[ix], dy = T.dl[TE + iy];
-                const float rho2 = dx * dx + dy * dy;
-                if (rho2 <= dhe2) {
-                    // Delta_z(n) = cz + 2 Lz n must satisfy zmin <= |Delta_z| <= zmax:
-                    // the full range [-zmax, zmax] minus the open hole (-zmin, zmin).
-                    const float zmax = sqrtf(fmaxf(dhi2 - rho2, 0.f)) + eps;
-                    const float zmin2 = dlo2 - rho2;
-                    const float zmin = zmin2 > 0.f ? sqrtf(zmin2) - eps : 0.f;
-                    const float cz = T.dl[2 * TE + wz * (2 * N + 1) + N];
-                    const float lim = (float)N + 1.f;
-                    const float u_lo = fminf(fmaxf((-zmax - cz) * inv2Lz, -lim), lim);
-                    const float u_hi = fminf(fmaxf((zmax - cz) * inv2Lz, -lim), lim);
-                    int n_lo = (int)ceilf(u_lo);
-                    int n_hi = (int)floorf(u_hi);
-                    if (n_lo < -N) n_lo = -N;
-                    if (n_hi > N) n_hi = N;
-                    int h_lo = 1, h_hi = 0;  // hole (excluded n), empty by default
-                    if (zmin > 0.f) {
-                        const float v_lo = fminf(fmaxf((-zmin - cz) * inv2Lz, -lim), lim);
-                        const float v_hi = fminf(fmaxf((zmin - cz) * inv2Lz, -lim), lim);
-                        h_lo = (int)floorf(v_lo) + 1;
-                        h_hi = (int)ceilf(v_hi) - 1;
-                    }
-                    if (h_lo <= h_hi) {
-                        lo_a = n_lo;
-                        hi_a = n_hi < h_lo - 1 ? n_hi : h_lo - 1;
-                        lo_b = n_lo > h_hi + 1 ? n_lo : h_hi + 1;
-                        hi_b = n_hi;
-                    } else {
-                        lo_a = n_lo;
-                        hi_a = n_hi;
-                    }
-                }
-            }
-            const int cnt = max(hi_a - lo_a + 1, 0) + max(hi_b - lo_b + 1, 0);
-            int total;
-            const int off = block_scan(cnt, s_scan, total);
-            if (total == 0) continue;
-            if (n_cand + total > CAP && n_cand > 0) {
-                flush(n_cand);
-                n_cand = 0;
-            }
-            const int zb = wz * (2 * N + 1) + N;
-            const uint32_t base_code = (uint32_t)ix | ((uint32_t)iy << 10);
-            // write candidates with global index in [g_lo, g_hi) at dst + idx
-            auto emit = [&](int g_lo, int g_hi, int dst) {
-                int gi = off;
-                for (int n = lo_a; n <= hi_a; ++n, ++gi)
-                    if (gi >= g_lo && gi < g_hi)
-                        s_cand[dst + gi] = base_code | ((uint32_t)(zb + n) << 20);
-                for (int n = lo_b; n <= hi_b; ++n, ++gi)
-                    if (gi >= g_lo && gi < g_hi)
-                        s_cand[dst + gi] = base_code | ((uint32_t)(zb + n) << 20);
-            };
-            if (total <= CAP) {
-                emit(0, total, n_cand);
-                n_cand += total;
-            } else {
-                for (int pb = 0; pb < total; pb += CAP) {
-                    emit(pb, pb + CAP, -pb);
-                    flush(min(CAP, total - pb));
-                }
-            }
-        }
-        if (n_cand > 0) flush(n_cand);
-
-        // ---- window output: fixed-order sum of the private rows
+        // window output: fixed-order sum of the private rows
         __syncthreads();
         float *hout = h + J.h_offset;
         for (int i = tid; i < W; i += NT) {
@@ -495,27 +568,174 @@ k_ism_taps(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int max
             float acc = 0.f;
 #pragma unroll
             for (int wv = 0; wv < NW; ++wv) acc += s_rows[wv * RL + HALO + i];
-            if (n < Lh) hout[n] = acc;
+            if (n < it.Lh) hout[n] = acc;
         }
         __syncthreads();
         for (int i = tid; i < NW * RL; i += NT) s_rows[i] = 0.f;
-        if (stats) {
-            atomicAdd(&s_stat[0], my_contrib);
-            atomicAdd(&s_stat[1], my_taps);
+        flush_stats(stats, J, s_stat, my_contrib, my_taps);
+        __syncthreads();
+    }
+}
+
+// ===========================================================================
+// k_ism_sparse: sparse integer-delay arrays + Chebyshev FIR
+// ===========================================================================
+template <int KIND>
+__global__ void __launch_bounds__(NT, 3)
+k_ism_sparse(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int max_order,
+             int max_taps, int max_cheb, const float *__restrict__ tabs, float *__restrict__ h,
+             long long *__restrict__ stats, unsigned int *__restrict__ counter) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const Layout Lay = make_layout(true, W, max_order, max_taps, max_cheb);
+    const int TE = Lay.TE, CL = Lay.CL, TPS = Lay.TPS;
+    Tables T;
+    T.sq = (double *)(smem + Lay.off_sq);
+    T.hi = (float *)(smem + Lay.off_hi);
+    T.lo = (float *)(smem + Lay.off_lo);
+    T.dl = (float *)(smem + Lay.off_dl);
+    T.g = (float *)(smem + Lay.off_g);
+    int *s_lx = (int *)(smem + Lay.off_lx);
+    int *s_ly = (int *)(smem + Lay.off_ly);
+    uint32_t *s_cand = (uint32_t *)(smem + Lay.off_cand);
+    float *s_c = (float *)(smem + Lay.off_c);
+    float *s_delta = (float *)(smem + Lay.off_delta);
+    float *s_B = (float *)(smem + Lay.off_B);
+    float *s_part = (float *)(smem + Lay.off_part);
+    __shared__ int s_scan[NW];
+    __shared__ int s_item, s_nl[2];
+    __shared__ unsigned long long s_stat[2];
+
+    const int tid = threadIdx.x;
+    for (int i = tid; i < max_cheb * CL; i += NT) s_c[i] = 0.f;
+    for (int i = tid; i < CL; i += NT) s_delta[i] = 0.f;
+
+    const long long n_items = (long long)n_rirs * wmax;
+    for (;;) {
+        if (tid == 0) s_item = (int)atomicAdd(counter, 1u);
+        __syncthreads();
+        const long long item = s_item;
+        if (item >= n_items) break;
+        const int wi = wmax - 1 - (int)(item / n_rirs);
+        const RirJob &J = jobs[(int)(item % n_rirs)];
+        if (wi >= J.n_windows) { __syncthreads(); continue; }
+        Item it;
+        item_setup<KIND>(J, W, wi, it);
+        build_tables(J, T, TE, it);
+        const int Pc = J.n_cheb;
+        const int n_taps = it.n_taps;
+        // the job's Chebyshev table, zero-padded to TPS taps
+        for (int e = tid; e < max_cheb * TPS; e += NT) {
+            const int p = e / TPS, j = e - p * TPS;
+            s_B[e] = (p < Pc && j < n_taps) ? tabs[J.tab_offset + p * n_taps + j] : 0.f;
+        }
+        if (tid < 2) s_stat[tid] = 0ull;
+        __syncthreads();
+        build_lists(T, TE, it, s_lx, s_ly, s_nl);
+        __syncthreads();
+        const int nLX = s_nl[0], nLY = s_nl[1];
+        // position of first-tap index kb in the sparse arrays; chosen so that
+        // the FIR's 128-bit loads are aligned
+        const int OFF = (4 - (n_taps - 1) % 4) % 4;
+        const int POS0 = OFF + PADL - (int)it.kb_lo;
+        const int jdelta = (KIND == ISM_FD_HANN_SINC) ? it.H : (it.P - 1) / 2;
+        unsigned long long my_contrib = 0, my_taps = 0;
+
+        auto flush = [&](int nc) {
             __syncthreads();
-            if (tid == 0) {
-                const long long si = J.stat_index;
-                atomicAdd((unsigned long long *)&stats[2 * si], s_stat[0]);
-                atomicAdd((unsigned long long *)&stats[2 * si + 1], s_stat[1]);
+            const int c0 = tid * CPT;
+#pragma unroll 1
+            for (int t = 0; t < CPT; ++t) {
+                const int ci = c0 + t;
+                if (ci >= nc) break;
+                int kb;
+                float f, a;
+                if (!eval_candidate<KIND>(T, TE, it, s_cand[ci], kb, f, a, my_taps, my_contrib))
+                    continue;
+                const int pos = kb + POS0;
+                if (f == 0.f) {  // integer delay: exact Kronecker delta
+                    atomicAdd(&s_delta[pos], a);
+                    continue;
+                }
+                const float x = (KIND == ISM_FD_HANN_SINC) ? 2.f * f : 2.f * f - 1.f;
+                float t0 = 1.f, t1 = x;
+                atomicAdd(&s_c[pos], a);
+                if (Pc > 1) atomicAdd(&s_c[CL + pos], a * x);
+                for (int p = 2; p < Pc; ++p) {
+                    const float t2 = fmaf(2.f * x, t1, -t0);
+                    atomicAdd(&s_c[p * CL + pos], a * t2);
+                    t0 = t1;
+                    t1 = t2;
+                }
+            }
+            __syncthreads();
+        };
+        column_sweep(T, TE, it, s_lx, s_ly, nLX, nLY, s_scan, s_cand, flush);
+        __syncthreads();
+
+        // FIR: h[w0+i] = sum_p sum_j B[p][j] c_p[kb = w0+i-j] + delta.  Threads
+        // 0..127 take p in [0, ceil(P/2)), threads 128..255 the rest; each owns
+        // 8 consecutive outputs and walks the taps 4 at a time with a sliding
+        // 12-value window of c in registers (128-bit shared loads).
+        {
+            const int half = tid >> 7, gt = tid & 127;
+            const int ph = (Pc + 1) / 2;
+            const int p_lo = half ? ph : 0, p_hi = half ? Pc : ph;
+            const int TPj = round4(n_taps);
+            for (int g = gt; g < W / 8; g += 128) {
+                float acc[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) acc[q] = 0.f;
+                const int base = 8 * g + n_taps - 1 + OFF + PADL;  // multiple of 4
+                for (int p = p_lo; p < p_hi; ++p) {
+                    const float *cp = s_c + p * CL;
+                    const float *bp = s_B + p * TPS;
+                    float win[12];
+#pragma unroll
+                    for (int v = 0; v < 3; ++v) {
+                        const float4 w4 = *reinterpret_cast<const float4 *>(cp + base - 4 + 4 * v);
+                        win[4 * v] = w4.x; win[4 * v + 1] = w4.y;
+                        win[4 * v + 2] = w4.z; win[4 * v + 3] = w4.w;
+                    }
+                    for (int jb = 0; jb < TPj; jb += 4) {
+                        const float4 b4 = *reinterpret_cast<const float4 *>(bp + jb);
+                        const float bv[4] = {b4.x, b4.y, b4.z, b4.w};
+                        // c at position base + q - jb - jj is win[4 + q - jj]
+#pragma unroll
+                        for (int jj = 0; jj < 4; ++jj)
+#pragma unroll
+                            for (int q = 0; q < 8; ++q) acc[q] = fmaf(bv[jj], win[4 + q - jj], acc[q]);
+                        if (jb + 4 < TPj) {
+#pragma unroll
+                            for (int v = 11; v >= 4; --v) win[v] = win[v - 4];
+                            const float4 w4 =
+                                *reinterpret_cast<const float4 *>(cp + base - jb - 8);
+                            win[0] = w4.x; win[1] = w4.y; win[2] = w4.z; win[3] = w4.w;
+                        }
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < 8; ++q) s_part[half * W + 8 * g + q] = acc[q];
             }
         }
+        __syncthreads();
+        float *hout = h + J.h_offset;
+        for (int i = tid; i < W; i += NT) {
+            const long long n = (long long)it.w0 + i;
+            const float v = s_part[i] + s_part[W + i] +
+                            s_delta[i + n_taps - 1 - jdelta + OFF + PADL];
+            if (n < it.Lh) hout[n] = v;
+        }
+        __syncthreads();
+        for (int i = tid; i < Pc * CL; i += NT) s_c[i] = 0.f;
+        for (int i = tid; i < CL; i += NT) s_delta[i] = 0.f;
+        flush_stats(stats, J, s_stat, my_contrib, my_taps);
         __syncthreads();
     }
 }
 
 template <int R, int KIND>
-int launch_t(const RirLaunch &L, cudaStream_t stream) {
-    const Layout Lay = make_layout(L.window, L.max_order, L.max_taps);
+int launch_direct_t(const RirLaunch &L, cudaStream_t stream) {
+    const Layout Lay = make_layout(false, L.window, L.max_order, L.max_taps, 0);
     auto kern = k_ism_taps<R, KIND>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)Lay.total);
@@ -537,26 +757,61 @@ int launch_t(const RirLaunch &L, cudaStream_t stream) {
     return ISM_OK;
 }
 
+template <int KIND>
+int launch_sparse_t(const RirLaunch &L, cudaStream_t stream) {
+    const Layout Lay = make_layout(true, L.window, L.max_order, L.max_taps, L.max_cheb);
+    auto kern = k_ism_sparse<KIND>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)Lay.total);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_ism_sparse)");
+    int grid = L.grid;
+    if (grid <= 0) {
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, Lay.total);
+        if (e != cudaSuccess) return cuda_fail(e, "occupancy(k_ism_sparse)");
+        grid = device_sm_count() * (per_sm > 0 ? per_sm : 1);
+    }
+    const long long items = (long long)L.n_rirs * L.wmax;
+    if ((long long)grid > items) grid = (int)items;
+    if (grid < 1) return ISM_OK;
+    kern<<<grid, NT, Lay.total, stream>>>(L.jobs_dev, L.n_rirs, L.wmax, L.window, L.max_order,
+                                          L.max_taps, L.max_cheb, L.tabs_dev, L.h_dev,
+                                          L.stats_dev, L.counter_dev);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "launch k_ism_sparse");
+    return ISM_OK;
+}
+
 }  // namespace
 
 size_t rir_smem_bytes(int window, int max_order, int max_taps) {
-    return make_layout(window, max_order, max_taps).total;
+    return make_layout(false, window, max_order, max_taps, 0).total;
+}
+
+size_t rir_sparse_smem_bytes(int window, int max_order, int max_taps, int max_cheb) {
+    return make_layout(true, window, max_order, max_taps, max_cheb).total;
 }
 
 int launch_rir(const RirLaunch &L, cudaStream_t stream) {
-    if (L.fd_kind == ISM_FD_LAGRANGE) return launch_t<1, ISM_FD_LAGRANGE>(L, stream);
+    if (L.fd_kind == ISM_FD_LAGRANGE) return launch_direct_t<1, ISM_FD_LAGRANGE>(L, stream);
     const int rows = (L.max_taps + 31) / 32;
     switch (rows) {
-        case 1: return launch_t<1, ISM_FD_HANN_SINC>(L, stream);
-        case 2: return launch_t<2, ISM_FD_HANN_SINC>(L, stream);
-        case 3: return launch_t<3, ISM_FD_HANN_SINC>(L, stream);
-        case 4: return launch_t<4, ISM_FD_HANN_SINC>(L, stream);
-        case 5: return launch_t<5, ISM_FD_HANN_SINC>(L, stream);
-        case 6: return launch_t<6, ISM_FD_HANN_SINC>(L, stream);
-        case 7: return launch_t<7, ISM_FD_HANN_SINC>(L, stream);
-        case 8: return launch_t<8, ISM_FD_HANN_SINC>(L, stream);
+        case 1: return launch_direct_t<1, ISM_FD_HANN_SINC>(L, stream);
+        case 2: return launch_direct_t<2, ISM_FD_HANN_SINC>(L, stream);
+        case 3: return launch_direct_t<3, ISM_FD_HANN_SINC>(L, stream);
+        case 4: return launch_direct_t<4, ISM_FD_HANN_SINC>(L, stream);
+        case 5: return launch_direct_t<5, ISM_FD_HANN_SINC>(L, stream);
+        case 6: return launch_direct_t<6, ISM_FD_HANN_SINC>(L, stream);
+        case 7: return launch_direct_t<7, ISM_FD_HANN_SINC>(L, stream);
+        case 8: return launch_direct_t<8, ISM_FD_HANN_SINC>(L, stream);
         default: return fail(ISM_ERR_INVALID_ARG, "n_taps above 255 is not supported");
     }
+}
+
+int launch_rir_sparse(const RirLaunch &L, cudaStream_t stream) {
+    if (L.window % 8 != 0) return fail(ISM_ERR_INVALID_ARG, "window must be a multiple of 8");
+    if (L.fd_kind == ISM_FD_LAGRANGE) return launch_sparse_t<ISM_FD_LAGRANGE>(L, stream);
+    return launch_sparse_t<ISM_FD_HANN_SINC>(L, stream);
 }
 
 }  // namespace ism

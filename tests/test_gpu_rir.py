@@ -54,12 +54,17 @@ def check_rooms(ism, rooms, tol=TOL, **kw):
     return worst
 
 
-def test_single_room_order10(ism):
+VARIANTS = [0, 1]  # sparse integer-delay arrays + FIR; direct per-tap
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_single_room_order10(ism, variant):
     rooms = wl.single_room(seed=1001, order=10, rir_len=4096)
-    check_rooms(ism, rooms)
+    check_rooms(ism, rooms, variant=variant)
 
 
-def test_small_batch_ragged(ism):
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_small_batch_ragged(ism, variant):
     """Several rooms, 1..11 mics, RIR lengths that are not multiples of the
     window, orders 0..6, small windows so that each RIR spans many work
     items and a ragged tail."""
@@ -70,15 +75,16 @@ def test_small_batch_ragged(ism):
                           rir_len=int(rng.integers(50, 3000)), n_mics=int(rng.integers(1, 12)))[0]
         rooms.append(r)
     for W in (32, 256, 1024):
-        check_rooms(ism, rooms, window=W)
+        check_rooms(ism, rooms, window=W, variant=variant)
 
 
-def test_exact_integer_delay(ism):
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_exact_integer_delay(ism, variant):
     """fs/c = 64 exactly and d = 1 m: h = delta[n-64] / (4 pi); every other
     sample exactly zero, the peak within one FP32 rounding."""
     room = dict(dims=[5, 4, 3], beta=[0.0] * 6, src=[2.0, 1.5, 1.5], mics=[[3.0, 1.5, 1.5]],
                 fs=16384.0, c=256.0, order=0, n_taps=81, fd_kind=0, rir_len=256)
-    (h,), st = gpu_rirs(ism, [room])
+    (h,), st = gpu_rirs(ism, [room], variant=variant)
     assert h[0, 64] == pytest.approx(1 / (4 * np.pi), rel=1.2e-7)
     h[0, 64] = 0
     assert not np.any(h)
@@ -97,34 +103,52 @@ def test_reciprocity(ism):
 
 
 def test_window_and_per_room_paths_agree(ism):
+    """The direct path is bitwise reproducible: the per-room launches and the
+    batched launch lay down the same items in the same order.  The sparse
+    path sums with shared-memory atomics, so it agrees to FP32 rounding."""
     rooms = wl.room_batch(6, seed=12, order=6, rir_len=3000, n_mics=3)
-    a, _ = gpu_rirs(ism, rooms, window=512)
-    b, _ = gpu_rirs(ism, rooms, window=512, per_room=True)
-    c, _ = gpu_rirs(ism, rooms, window=128)
-    for x, y, z in zip(a, b, c):
-        np.testing.assert_array_equal(x, y)           # same items, same order
-        assert rel_l2(z, x) < 1e-6                    # different windows
+    a, _ = gpu_rirs(ism, rooms, window=512, variant=1)
+    b, _ = gpu_rirs(ism, rooms, window=512, per_room=True, variant=1)
+    c, _ = gpu_rirs(ism, rooms, window=128, variant=1)
+    d, _ = gpu_rirs(ism, rooms, window=512, per_room=True, variant=0)
+    e, _ = gpu_rirs(ism, rooms, window=256, variant=0)
+    for x, y, z, u, v in zip(a, b, c, d, e):
+        np.testing.assert_array_equal(x, y)
+        assert rel_l2(z, x) < 1e-6
+        assert rel_l2(u, x) < 1e-6
+        assert rel_l2(v, x) < 1e-6
 
 
-def test_lagrange_filter(ism):
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_lagrange_filter(ism, variant):
     rooms = wl.room_batch(3, seed=21, order=6, rir_len=2500, n_mics=2, n_taps=8,
                           fd_kind=wl.FD_LAGRANGE)
-    check_rooms(ism, rooms)
+    check_rooms(ism, rooms, variant=variant)
 
 
-def test_mixed_filter_kinds_one_call(ism):
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_mixed_filter_kinds_one_call(ism, variant):
     a = wl.room_batch(2, seed=31, order=4, rir_len=1500, n_mics=2)
     b = wl.room_batch(2, seed=32, order=4, rir_len=1700, n_mics=3, n_taps=8,
                       fd_kind=wl.FD_LAGRANGE)
-    check_rooms(ism, [a[0], b[0], a[1], b[1]])
+    check_rooms(ism, [a[0], b[0], a[1], b[1]], variant=variant)
 
 
-def test_short_filters_and_48k(ism):
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_short_filters_and_48k(ism, variant):
     rooms = []
     for i, nt in enumerate((1, 3, 33, 65, 127)):
         rooms += wl.room_batch(1, seed=40 + i, order=5, rir_len=2000, n_mics=2, n_taps=nt,
                                fs=48000.0)
-    check_rooms(ism, rooms, window=256)
+    check_rooms(ism, rooms, window=256, variant=variant)
+
+
+def test_long_lagrange_uses_direct_path(ism):
+    """A 32-tap Lagrange filter needs more Chebyshev terms than the sparse
+    kernel keeps; the library takes the direct path for it."""
+    rooms = wl.room_batch(1, seed=50, order=3, rir_len=1200, n_mics=2, n_taps=32,
+                          fd_kind=wl.FD_LAGRANGE)
+    check_rooms(ism, rooms)
 
 
 def test_empty_batch_is_noop(ism):
@@ -135,14 +159,15 @@ def test_empty_batch_is_noop(ism):
     assert torch.all(h == 7.0)
 
 
-def test_full_size_batch_sampled(ism):
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_full_size_batch_sampled(ism, variant):
     """The 1024-room, order-15, 8-mic, 8192-sample batch in the benchmark's
     launch configuration; a sample of RIRs checked against the oracle."""
     import torch
     rooms = wl.room_batch(1024, seed=1002)
     n_rirs, hl = ism.rir_batch_size(rooms)
     stats = torch.zeros(2 * n_rirs, dtype=torch.int64, device="cuda")
-    h = ism.rir_batch(rooms, stats=stats)
+    h = ism.rir_batch(rooms, stats=stats, variant=variant)
     torch.cuda.synchronize()
     h = h.view(n_rirs, 8192)
     st = stats.view(n_rirs, 2).cpu().numpy()
