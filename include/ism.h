@@ -138,6 +138,14 @@ int ism_rir_batch_ex(const ism_room *rooms, int64_t n_rooms, float *h_dev,
 int ism_rir_batch_size(const ism_room *rooms, int64_t n_rooms, int64_t *n_rirs,
                        int64_t *h_len);
 
+/* Number of Chebyshev terms P the sparse path uses for a filter (host only,
+ * no device work): *n_terms = P in [1, 16], or 0 when the filter needs more
+ * terms and ism_rir_batch takes the direct path for it.  The per-output FIR
+ * of the sparse path costs P * n_taps multiply-adds.
+ * Errors: ISM_ERR_INVALID_ARG for an unknown filter, a tap count of the
+ * wrong parity, or a NULL pointer. */
+int ism_rir_filter_terms(int32_t fd_kind, int32_t n_taps, int32_t *n_terms);
+
 /* Largest number of RIRs (sum of n_mics over the rooms) that one
  * ism_rir_batch_noalloc call accepts. */
 #define ISM_NOALLOC_MAX_RIRS 14560

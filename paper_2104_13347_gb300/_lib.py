@@ -73,6 +73,7 @@ SIGNATURES = {
     "ism_rir_batch_ex": (c_i32, [c_vp, c_i64, c_vp, c_vp, c_vp, c_vp]),
     "ism_rir_batch_size": (c_i32, [c_vp, c_i64, c_vp, c_vp]),
     "ism_rir_batch_noalloc": (c_i32, [c_vp, c_i64, c_vp, c_vp, c_vp]),
+    "ism_rir_filter_terms": (c_i32, [c_i32, c_i32, c_vp]),
     "ism_convolve_batch": (c_i32, [c_vp, c_i64, c_vp, c_vp, c_vp, c_u64, c_i32, c_vp]),
     "ism_serve_create": (c_i32, [c_vp, c_vp]),
     "ism_serve_submit": (c_i32, [c_vp, c_vp, c_vp]),
@@ -160,17 +161,36 @@ def rir_batch_size(rooms):
     return nr.value, hl.value
 
 
+def rir_filter_terms(fd_kind, n_taps):
+    """Chebyshev terms P the sparse path uses for a filter (0 = direct path)."""
+    n = c_i32()
+    check(load().ism_rir_filter_terms(int(fd_kind), int(n_taps), ctypes.byref(n)))
+    return n.value
+
+
+class PreparedRooms:
+    """Rooms marshalled once into the C layout (reuse across calls)."""
+
+    def __init__(self, rooms):
+        self.arr, self.keep = make_rooms(rooms)
+        self.n = len(rooms)
+        self.n_rirs, self.h_len = rir_batch_size(rooms)
+
+
 def rir_batch(rooms, h=None, h_offsets=None, window=0, per_room=False, stats=None, stream=None,
               variant=RIR_SPARSE):
-    """ism_rir_batch_ex: RIRs of the rooms into h (a float32 CUDA tensor;
-    allocated packed if None).  stats: optional int64 CUDA tensor (2 per
-    RIR), accumulated.  variant: RIR_SPARSE (default) or RIR_DIRECT.
-    Returns h."""
+    """ism_rir_batch_ex: RIRs of the rooms (room dicts or PreparedRooms) into
+    h (a float32 CUDA tensor; allocated packed if None).  stats: optional
+    int64 CUDA tensor (2 per RIR), accumulated.  variant: RIR_SPARSE
+    (default) or RIR_DIRECT.  Returns h."""
     import torch
     lib = load()
-    arr, keep = make_rooms(rooms)
+    if isinstance(rooms, PreparedRooms):
+        arr, keep = rooms.arr, [rooms.keep]
+    else:
+        arr, keep = make_rooms(rooms)
     if h is None:
-        _, hl = rir_batch_size(rooms)
+        hl = rooms.h_len if isinstance(rooms, PreparedRooms) else rir_batch_size(rooms)[1]
         h = torch.empty(hl, dtype=torch.float32, device="cuda")
     assert h.dtype == torch.float32 and h.is_cuda and h.is_contiguous()
     offs = None
@@ -179,7 +199,7 @@ def rir_batch(rooms, h=None, h_offsets=None, window=0, per_room=False, stats=Non
         keep.append(offs)
     opts = RirOpts(int(window), int(bool(per_room)),
                    stats.data_ptr() if stats is not None else None, int(variant), 0)
-    check(lib.ism_rir_batch_ex(arr, len(rooms), c_vp(h.data_ptr()),
+    check(lib.ism_rir_batch_ex(arr, len(arr), c_vp(h.data_ptr()),
                                offs.ctypes.data if offs is not None else None,
                                ctypes.byref(opts), _stream_ptr(stream)))
     return h

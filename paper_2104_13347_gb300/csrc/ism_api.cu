@@ -411,6 +411,22 @@ int ism_rir_batch_ex(const ism_room *rooms, int64_t n_rooms, float *h_dev,
     return ISM_OK;
 }
 
+int ism_rir_filter_terms(int32_t fd_kind, int32_t n_taps, int32_t *n_terms) {
+    set_error("");
+    if (!n_terms) return fail(ISM_ERR_INVALID_ARG, "NULL n_terms");
+    if (fd_kind == ISM_FD_HANN_SINC) {
+        if (n_taps < 1 || n_taps % 2 == 0 || n_taps > 255)
+            return fail(ISM_ERR_INVALID_ARG, "Hann-sinc n_taps must be odd and in [1, 255]");
+    } else if (fd_kind == ISM_FD_LAGRANGE) {
+        if (n_taps < 2 || n_taps % 2 != 0 || n_taps > 32)
+            return fail(ISM_ERR_INVALID_ARG, "Lagrange n_taps must be even and in [2, 32]");
+    } else {
+        return fail(ISM_ERR_INVALID_ARG, "unknown fd_kind");
+    }
+    *n_terms = cheb_table(fd_kind, n_taps).n_cheb;
+    return ISM_OK;
+}
+
 int ism_rir_batch(const ism_room *rooms, int64_t n_rooms, float *h_dev, const int64_t *h_offsets,
                   void *stream) {
     return ism_rir_batch_ex(rooms, n_rooms, h_dev, h_offsets, nullptr, stream);

@@ -642,11 +642,9 @@ k_ism_sparse(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int m
 
         auto flush = [&](int nc) {
             __syncthreads();
-            const int c0 = tid * CPT;
+            // strided: every thread gets work even when the buffer is short
 #pragma unroll 1
-            for (int t = 0; t < CPT; ++t) {
-                const int ci = c0 + t;
-                if (ci >= nc) break;
+            for (int ci = tid; ci < nc; ci += NT) {
                 int kb;
                 float f, a;
                 if (!eval_candidate<KIND>(T, TE, it, s_cand[ci], kb, f, a, my_taps, my_contrib))

@@ -143,12 +143,13 @@ def test_short_filters_and_48k(ism, variant):
     check_rooms(ism, rooms, window=256, variant=variant)
 
 
-def test_long_lagrange_uses_direct_path(ism):
-    """A 32-tap Lagrange filter needs more Chebyshev terms than the sparse
-    kernel keeps; the library takes the direct path for it."""
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_long_lagrange_filter(ism, variant):
+    """A 32-tap (order 31) Lagrange filter: its taps over one sample of
+    delay are smooth enough that the sparse path keeps ~10 Chebyshev terms."""
     rooms = wl.room_batch(1, seed=50, order=3, rir_len=1200, n_mics=2, n_taps=32,
                           fd_kind=wl.FD_LAGRANGE)
-    check_rooms(ism, rooms)
+    check_rooms(ism, rooms, variant=variant)
 
 
 def test_empty_batch_is_noop(ism):
