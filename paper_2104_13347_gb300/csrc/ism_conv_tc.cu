@@ -1,8 +1,373 @@
-// ism_conv_tc.cu -- K2: split-BF16 tensor-core convolution (in progress).
+// ism_conv_tc.cu -- K2: the convolution y_m = s * h_m on the tcgen05 tensor
+// cores, in split BF16 (each FP32 operand as bf16 hi + lo, FP32 accumulate).
+//
+// Convolution (arXiv 2104.13347, Sec. II.A: the dataset is built by batch
+// convolution of the RIRs with source signals), for every mic m of a room:
+//   y_m[t] = sum_k h_m[k] s[t - k],  t in [0, Ts + Lh - 1).
+//
+// Block-Toeplitz GEMM.  A tile of 2048 outputs t = T0 + 8n + p (n < 256
+// columns, p < 8 phases) of 8 mics is one GEMM D (128 x 256) = A (128 x K) B
+// (K x 256) over the RIR taps:
+//   B[k][n] = s[c + k + 8n],  c = T0 - Lh + 1      (source, forward)
+//   A[(q,m,p)][k] = part_q(h_m[Lh - 1 + p - k])    (RIR, reversed, phase p)
+// so that D[(q,m,p)][n] = sum_k A B accumulates, over q in {hi, lo},
+// y_m[T0 + 8n + p] (each row's j = Lh-1+p-k runs over the whole RIR).
+// B is a Toeplitz matrix whose rows shift by 8 elements = 16 bytes, so it is
+// read straight from a linear copy of the source in shared memory through a
+// no-swizzle K-major descriptor with leading-dimension offset 16 B and
+// stride offset 128 B (core matrices overlap); A is materialised per chunk
+// of 64 taps (8 phases x 8 mics x hi/lo = 128 rows, 16 KB).  Per chunk the
+// MMA issuer runs 4 K-steps x {B_hi, B_lo} = 8 MMAs of 128 x 256 x 16 into
+// one TMEM accumulator, so the result holds all four products hi/lo x hi/lo.
+// Chunks whose source window is all zero padding are skipped.
+//
+// Warp roles (160 threads): warps 0-3 produce the pipeline stages (A rows and
+// the chunk's source window, split to bf16 in registers, FP32 inputs read
+// straight from global memory) and run the epilogue; warp 4 allocates TMEM
+// and one of its lanes issues the MMAs.  Stages hand over through mbarriers
+// (full: 128 producer arrivals; empty: tcgen05.commit).  Every wait is
+// bounded: on timeout the kernel records an error, stops issuing, waits
+// (bounded) for its own MMAs, frees TMEM and returns.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
 #include "ism_internal.h"
 
 namespace ism {
-int launch_conv_bf16x3(const ConvLaunch &, cudaStream_t) {
-    return fail(ISM_ERR_INVALID_ARG, "ISM_BF16X3 is not built into this library yet");
+
+__device__ int g_conv_tc_error;  // set to 1 by a timed-out wait
+
+namespace {
+
+constexpr int KC = 64;                 // RIR taps per chunk
+constexpr int NN = 256;                // GEMM N: time groups of 8
+constexpr int TT = 8 * NN;             // outputs per tile (2048)
+constexpr int MG = 8;                  // mics per tile
+constexpr int NS = 4;                  // pipeline stages
+constexpr int BW = 2112;               // source window per chunk (>= KC + 8 (NN-1), x8)
+constexpr int A_BYTES = 8 * 16 * 128;  // 8 k-groups x 16 row groups x 8 rows x 16 B
+constexpr int STAGE = A_BYTES + 2 * BW * 2;
+constexpr int NPROD = 128;             // producer threads (warps 0-3)
+constexpr int NTHR = 160;
+constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s bound on any mbarrier wait
+
+struct Tile {
+    int job;
+    int mic0;
+    int64_t t0;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
 }
+
+// tcgen05 shared-memory matrix descriptor: start address, leading and
+// stride byte offsets (16-byte units), descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t make_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFF) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= 1ull << 46;
+    return d;
+}
+
+// Instruction descriptor, kind::f16: D f32, A and B bf16, both K-major,
+// N = 256, M = 128.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NN >> 3) << 17) |
+                            ((128u >> 4) << 24);
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Waits for the given phase parity of an mbarrier, at most kWaitNs.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    const unsigned long long t0 = global_ns();
+    while (true) {
+        uint32_t ok;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            "selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (global_ns() - t0 > kWaitNs) break;
+    }
+    atomicExch(&g_conv_tc_error, 1);
+    return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo_k, float hi_k) {
+    // element with the lower k at the lower address (low half)
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo_k, hi_k);
+    return *reinterpret_cast<const uint32_t *>(&v);
+}
+
+__device__ __forceinline__ float bf16_round(float x) {
+    return __bfloat162float(__float2bfloat16_rn(x));
+}
+
+__global__ void __launch_bounds__(NTHR, 2)
+k_conv_tc(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles,
+          const float *__restrict__ h, const float *__restrict__ src, float *__restrict__ y) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar_full[NS], bar_empty[NS], bar_done;
+    __shared__ uint32_t s_tmem;
+    __shared__ volatile int s_abort;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const Tile tl = tiles[blockIdx.x];
+    const ConvJob J = jobs[tl.job];
+    const int64_t Lh = J.rir_len, Ts = J.src_len, T0 = tl.t0;
+    const int nm = min(MG, J.n_mics - tl.mic0);
+    const float *hb = h + J.h_offset + (int64_t)tl.mic0 * Lh;
+    const float *sb = src + J.src_offset;
+    const int64_t c0 = T0 - Lh + 1;                    // source index of B[0][0] at k = 0
+    const int n_chunks = (int)((Lh + 7 + KC - 1) / KC);
+    // a chunk is skipped when its whole source window is zero padding
+    auto live = [&](int ch) {
+        const int64_t lo = c0 + (int64_t)ch * KC, hi = lo + KC - 1 + 8 * (NN - 1);
+        return hi >= 0 && lo < Ts;
+    };
+
+    if (tid == 0) {
+        for (int s = 0; s < NS; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_full[s])),
+                         "r"(NPROD));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_empty[s])),
+                         "r"(1));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_done)), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+        s_abort = 0;
+    }
+    if (warp == 4) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&s_tmem)),
+                     "r"(256));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = s_tmem;
+
+    int n_live = 0;
+    for (int ch = 0; ch < n_chunks; ++ch) n_live += live(ch);
+
+    if (warp < 4) {
+        // ------------------------------------------------------------------
+        // producers
+        // ------------------------------------------------------------------
+        const int q = tid >> 6;                 // 0 = hi rows, 1 = lo rows
+        const int item = tid & 63, m = item >> 3, kg = item & 7;
+        int i = 0;  // live-chunk counter
+        for (int ch = 0; ch < n_chunks; ++ch) {
+            if (!live(ch)) continue;
+            const int s = i % NS, u = i / NS;
+            if (u > 0 && !mbar_wait(smem_u32(&bar_empty[s]), (u - 1) & 1)) {
+                s_abort = 1;
+                break;
+            }
+            if (s_abort) break;
+            unsigned char *st = smem + (size_t)s * STAGE;
+            const int64_t k0 = (int64_t)ch * KC;
+            // A: rows (q, m, p), k-group kg: element (p, kr) = part_q(v[p - kr + 7]),
+            // v[i] = h_m[Lh - 8 - k0 - 8 kg + i]
+            {
+                float v[15];
+                const int64_t base = Lh - 8 - k0 - 8 * kg;
+#pragma unroll
+                for (int e = 0; e < 15; ++e) {
+                    const int64_t idx = base + e;
+                    float x = 0.f;
+                    if (m < nm && idx >= 0 && idx < Lh) x = __ldg(hb + (int64_t)m * Lh + idx);
+                    const float xh = bf16_round(x);
+                    v[e] = q ? x - xh : xh;
+                }
+                unsigned char *dst = st + kg * 2048 + (8 * q + m) * 128;
+#pragma unroll
+                for (int p = 0; p < 8; ++p) {
+                    uint4 row;
+                    row.x = pack_bf16(v[p + 7], v[p + 6]);
+                    row.y = pack_bf16(v[p + 5], v[p + 4]);
+                    row.z = pack_bf16(v[p + 3], v[p + 2]);
+                    row.w = pack_bf16(v[p + 1], v[p + 0]);
+                    *reinterpret_cast<uint4 *>(dst + p * 16) = row;
+                }
+            }
+            // B: the chunk's source window, s[c0 + k0 + e], split hi / lo
+            {
+                uint32_t *bh = reinterpret_cast<uint32_t *>(st + A_BYTES);
+                uint32_t *bl = reinterpret_cast<uint32_t *>(st + A_BYTES + BW * 2);
+                const int64_t sbase = c0 + k0;
+                for (int e2 = tid; e2 < BW / 2; e2 += NPROD) {
+                    const int64_t i0 = sbase + 2 * e2;
+                    const float x0 = (i0 >= 0 && i0 < Ts) ? __ldg(sb + i0) : 0.f;
+                    const float x1 = (i0 + 1 >= 0 && i0 + 1 < Ts) ? __ldg(sb + i0 + 1) : 0.f;
+                    const float h0 = bf16_round(x0), h1 = bf16_round(x1);
+                    bh[e2] = pack_bf16(h0, h1);
+                    bl[e2] = pack_bf16(x0 - h0, x1 - h1);
+                }
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(smem_u32(&bar_full[s]));
+            ++i;
+        }
+    } else if (lane == 0) {
+        // ------------------------------------------------------------------
+        // MMA issuer
+        // ------------------------------------------------------------------
+        int i = 0;
+        uint32_t acc = 0;
+        for (int ch = 0; ch < n_chunks; ++ch) {
+            if (!live(ch)) continue;
+            const int s = i % NS, u = i / NS;
+            if (!mbar_wait(smem_u32(&bar_full[s]), u & 1)) {
+                s_abort = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t a0 = smem_u32(smem + (size_t)s * STAGE);
+            const uint32_t bh0 = a0 + A_BYTES, bl0 = bh0 + BW * 2;
+#pragma unroll
+            for (int kk = 0; kk < KC / 16; ++kk) {
+                const uint64_t ad = make_desc(a0 + kk * 2 * 2048, 2048, 128);
+                const uint64_t bhd = make_desc(bh0 + kk * 32, 16, 128);
+                const uint64_t bld = make_desc(bl0 + kk * 32, 16, 128);
+                asm volatile(
+                    "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                    "l"(ad), "l"(bhd), "r"(kIdesc), "r"(acc));
+                acc = 1;
+                asm volatile(
+                    "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                    "l"(ad), "l"(bld), "r"(kIdesc), "r"(acc));
+            }
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    smem_u32(&bar_empty[s])));
+            ++i;
+        }
+        // all issued MMAs done -> bar_done
+        asm volatile(
+            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_u32(&bar_done)));
+    }
+
+    // ----------------------------------------------------------------------
+    // epilogue (warps 0-3): TMEM lane quadrant w = rows 32w .. 32w+31 =
+    // (q = w/2, m = 4 (w%2) + lane/8, p = lane%8).  The lo half (warps 2, 3)
+    // goes through shared memory (the stage buffers are idle by then).
+    // ----------------------------------------------------------------------
+    bool ok = true;
+    if (warp < 4) ok = mbar_wait(smem_u32(&bar_done), 0);
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    __syncthreads();
+    ok = ok && !s_abort && n_live > 0;
+    float *lo_buf = reinterpret_cast<float *>(smem);  // [64 rows][256 cols]
+    if (warp >= 2 && warp < 4 && ok) {
+        const int row = (warp - 2) * 32 + lane;
+        for (int cb = 0; cb < NN; cb += 32) {
+            uint32_t r[32];
+            const uint32_t addr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+                "%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                  "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+                  "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]),
+                  "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+                  "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+                  "=r"(r[30]), "=r"(r[31])
+                : "r"(addr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+            for (int j = 0; j < 32; ++j) lo_buf[row * NN + cb + j] = __uint_as_float(r[j]);
+        }
+    }
+    __syncthreads();
+    if (warp < 2) {
+        const int row = warp * 32 + lane;           // (m, p) within the hi half
+        const int m = row >> 3, p = row & 7;
+        const int64_t ylen = J.y_len;
+        float *ym = y + J.y_offset + (int64_t)(tl.mic0 + m) * ylen;
+        for (int cb = 0; cb < NN; cb += 32) {
+            uint32_t r[32];
+            if (ok) {
+                const uint32_t addr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb;
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,"
+                    "%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,"
+                    "%31}, [%32];"
+                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                      "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+                      "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+                      "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                      "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]),
+                      "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                    : "r"(addr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;");
+            } else {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) r[j] = 0u;
+            }
+            if (m < nm) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int64_t t = T0 + 8 * (cb + j) + p;
+                    const float v = __uint_as_float(r[j]) + (ok ? lo_buf[row * NN + cb + j] : 0.f);
+                    if (t < ylen) ym[t] = v;
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 4) {
+        __syncwarp();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
+    }
+}
+
+}  // namespace
+
+int launch_conv_bf16x3(const ConvLaunch &L, cudaStream_t stream) {
+    std::vector<Tile> tiles;
+    for (int j = 0; j < L.n_jobs; ++j) {
+        const ConvJob &J = L.jobs_host[j];
+        for (int m0 = 0; m0 < J.n_mics; m0 += MG)
+            for (int64_t t0 = 0; t0 < J.y_len; t0 += TT) tiles.push_back(Tile{j, m0, t0});
+    }
+    if (tiles.empty()) return ISM_OK;
+    if (tiles.size() > 0x7fffffffULL) return fail(ISM_ERR_INVALID_ARG, "too many tiles");
+    const size_t smem = (size_t)NS * STAGE;
+    cudaError_t e = cudaFuncSetAttribute(k_conv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_conv_tc)");
+    void *d_tiles = nullptr;
+    int st = scratch_alloc(&d_tiles, tiles.size() * sizeof(Tile), stream);
+    if (st) return st;
+    st = upload_async(d_tiles, tiles.data(), tiles.size() * sizeof(Tile), stream);
+    if (st) { scratch_free(d_tiles, stream); return st; }
+    k_conv_tc<<<(unsigned)tiles.size(), NTHR, smem, stream>>>(L.jobs_dev, (const Tile *)d_tiles,
+                                                               L.h_dev, L.src_dev, L.y_dev);
+    e = cudaGetLastError();
+    scratch_free(d_tiles, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "launch k_conv_tc");
+    return ISM_OK;
+}
+
 }  // namespace ism

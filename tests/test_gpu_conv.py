@@ -53,7 +53,7 @@ def ragged_case(seed=3):
     return hs, ss
 
 
-@pytest.mark.parametrize("precision", [0])
+@pytest.mark.parametrize("precision", [0, 1])
 def test_conv_ragged_parity(ism, precision):
     hs, ss = ragged_case()
     got = run_conv(ism, hs, ss, precision)
@@ -63,6 +63,33 @@ def test_conv_ragged_parity(ism, precision):
         assert g.shape == r.shape
         for m in range(g.shape[0]):
             assert rel_l2(g[m], r[m]) <= TOL[precision]
+
+
+def test_conv_delta_rir_bf16x3(ism):
+    """A delta RIR is exact in bf16 (lo = 0), so the split path returns the
+    source to the split's representation error (2^-16 relative)."""
+    rng = np.random.default_rng(8)
+    s = rng.standard_normal(3000).astype(np.float32)
+    h = np.zeros((2, 700), np.float32)
+    h[0, 0] = 1.0
+    h[1, 613] = 1.0
+    (y,) = run_conv(ism, [h], [s], 1)
+    np.testing.assert_allclose(y[0, :3000], s, rtol=2e-5, atol=0)
+    assert not np.any(y[0, 3000:])
+    np.testing.assert_allclose(y[1, 613:3613], s, rtol=2e-5, atol=0)
+    assert not np.any(y[1, :613])
+
+
+def test_conv_long_rir_and_many_mics(ism):
+    """RIR longer than a tile and 11 mics (two mic groups), both paths."""
+    rng = np.random.default_rng(12)
+    hs = [(rng.standard_normal((11, 5000)) * np.exp(-np.arange(5000) / 1500)).astype(np.float32)]
+    ss = [rng.standard_normal(2500).astype(np.float32)]
+    ref = oracle.convolve_batch([hs[0].astype(np.float64)], [ss[0].astype(np.float64)])[0]
+    for precision in (0, 1):
+        (y,) = run_conv(ism, hs, ss, precision)
+        for m in range(11):
+            assert rel_l2(y[m], ref[m]) <= TOL[precision]
 
 
 def test_conv_delta_rir_exact(ism):
@@ -107,7 +134,8 @@ def test_noise_same_in_any_batch(ism):
     np.testing.assert_array_equal(full[3], part[1])
 
 
-def test_full_size_conv_sampled(ism):
+@pytest.mark.parametrize("precision", [0, 1])
+def test_full_size_conv_sampled(ism, precision):
     """1024 rooms x 8 mics, 8192-sample RIRs, 1 s sources at 16 kHz, in the
     benchmark's launch configuration; sampled outputs against the oracle."""
     import torch
@@ -117,7 +145,7 @@ def test_full_size_conv_sampled(ism):
     jobs, ylen = ism.conv_jobs([8] * 1024, [8192] * 1024, [len(s) for s in srcs])
     scat = torch.from_numpy(np.concatenate(srcs)).cuda()
     y = torch.empty(ylen, device="cuda")
-    ism.convolve_batch(jobs, h, scat, y, precision=0)
+    ism.convolve_batch(jobs, h, scat, y, precision=precision)
     torch.cuda.synchronize()
     T = 16000 + 8192 - 1
     y = y.view(1024, 8, T)
@@ -129,5 +157,5 @@ def test_full_size_conv_sampled(ism):
         ref = oracle.convolve_at(hv[r, m].cpu().numpy().astype(np.float64),
                                  srcs[r].astype(np.float64), ts)
         got = y[r, m].cpu().numpy().astype(np.float64)[ts]
-        assert rel_l2(got, ref) <= TOL[0]
+        assert rel_l2(got, ref) <= TOL[precision]
     assert torch.isfinite(y).all()
