@@ -89,7 +89,8 @@ typedef struct ism_room {
  *  ISM_RIR_SPARSE (default): each image adds P Chebyshev coefficients of its
  *    fractional delay to sparse integer-delay arrays, and one FIR per output
  *    window applies the filter (P <= 16 terms; the expansion error is below
- *    1e-9 of the peak tap, and exact for the Lagrange filter).  Sums use
+ *    5e-8 of the peak tap -- under FP32 resolution -- and zero for the 8-tap
+ *    Lagrange filter).  Sums use
  *    shared-memory atomics, so repeated runs agree to FP32 rounding.
  *  ISM_RIR_DIRECT: every tap of every image is evaluated from the filter's
  *    formula and accumulated in a fixed order (bitwise reproducible). */

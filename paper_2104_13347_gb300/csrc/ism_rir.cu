@@ -26,8 +26,9 @@
 //  * k_ism_sparse (default): the tap function of the filter, g_j(f), is
 //    expanded in Chebyshev polynomials of the fraction, g_j(f) ~ sum_p
 //    B[p][j] T_p(x(f)) (FP64 table, truncated where the remaining terms sum
-//    below 1e-9; exact for the Lagrange filter, whose taps are polynomials in
-//    the delay).  Each image then adds a T_p(x) to P sparse integer-delay
+//    below 5e-8 of the peak tap, under FP32 resolution; exact for the
+//    8-tap Lagrange filter, whose taps are degree-7 polynomials in the
+//    delay).  Each image then adds a T_p(x) to P sparse integer-delay
 //    arrays c_p[kb] (shared-memory atomics) -- the paper's representation of
 //    the integer delays as a sparse array -- and one fixed-order FIR per
 //    window gives h[n] = sum_p sum_j B[p][j] c_p[n - j].  Per image: P
@@ -92,10 +93,9 @@ __host__ __device__ inline int round4(int x) { return (x + 3) & ~3; }
 
 struct Tables {
     double *sq;   // [3][TE] squared axis offsets (FP64, definition rounding)
-    float *hi;    // [3][TE] float-float split of sq
-    float *lo;
+    float4 *hlg;  // [3][TE] (hi, lo, g, -): float-float split of sq and the
+                  // wall damping product along the axis, one 128-bit load
     float *dl;    // [3][TE] axis offset, FP32
-    float *g;     // [3][TE] wall damping product along the axis
 };
 
 // Shared-memory carve-up.  Common part: tables, axis lists, candidates.
@@ -104,7 +104,7 @@ struct Tables {
 // and the FIR partial sums.
 struct Layout {
     int TE, RL, CL, TPS;
-    size_t off_sq, off_hi, off_lo, off_dl, off_g, off_lx, off_ly, off_cand, off_rows, off_c,
+    size_t off_sq, off_hlg, off_dl, off_lx, off_ly, off_cand, off_rows, off_c,
         off_delta, off_B, off_part, total;
 };
 
@@ -117,10 +117,8 @@ __host__ __device__ inline Layout make_layout(bool sparse, int window, int max_o
     L.TPS = round4(max_taps);
     size_t o = 0;
     L.off_sq = o;   o = align16(o + sizeof(double) * 3 * L.TE);
-    L.off_hi = o;   o = align16(o + sizeof(float) * 3 * L.TE);
-    L.off_lo = o;   o = align16(o + sizeof(float) * 3 * L.TE);
+    L.off_hlg = o;  o = align16(o + sizeof(float4) * 3 * L.TE);
     L.off_dl = o;   o = align16(o + sizeof(float) * 3 * L.TE);
-    L.off_g = o;    o = align16(o + sizeof(float) * 3 * L.TE);
     L.off_lx = o;   o = align16(o + sizeof(int) * L.TE);
     L.off_ly = o;   o = align16(o + sizeof(int) * L.TE);
     // the sparse kernel's FIR partial sums (2 W floats) reuse the candidate
@@ -146,10 +144,10 @@ __host__ __device__ inline Layout make_layout(bool sparse, int window, int max_o
 template <int KIND>
 __device__ __forceinline__ void delay_split(const Tables &T, int TE, int ix, int iy, int iz,
                                             float qh, float ql, double q, int &k_out,
-                                            float &f_out, float &d_out) {
-    const float xh = T.hi[ix], xl = T.lo[ix];
-    const float yh = T.hi[TE + iy], yl = T.lo[TE + iy];
-    const float zh = T.hi[2 * TE + iz], zl = T.lo[2 * TE + iz];
+                                            float &f_out, float &d_out, float &g_out) {
+    const float4 X = T.hlg[ix], Y = T.hlg[TE + iy], Z = T.hlg[2 * TE + iz];
+    const float xh = X.x, xl = X.y, yh = Y.x, yl = Y.y, zh = Z.x, zl = Z.y;
+    g_out = X.z * Y.z * Z.z;
     // d^2 = x + y + z in float-float (two-sum with renormalisation).
     float s1 = __fadd_rn(xh, yh);
     float bb = __fsub_rn(s1, xh);
@@ -211,6 +209,7 @@ struct Item {
     int N, TEj, n_taps, H, P;   // order, table entries, taps, Hann half-width, Lagrange order
     int w0, W;
     long long Lh, kb_lo, kb_hi; // window's first-tap range
+    int kb_lo32, kb_hi32, Lh32, wend;  // 32-bit copies; wend = min(w0 + W, Lh)
     double q;
     float qh, ql, dlo2, dhi2, dhe2, dhe, eps, inv2Lz;
 };
@@ -230,6 +229,10 @@ __device__ __forceinline__ void item_setup(const RirJob &J, int W, int wi, Item 
     it.ql = (float)(it.q - (double)it.qh);
     it.kb_lo = (long long)it.w0 - it.n_taps + 1;
     it.kb_hi = min((long long)it.w0 + W - 1, it.Lh - 1);
+    it.kb_lo32 = (int)it.kb_lo;
+    it.kb_hi32 = (int)it.kb_hi;
+    it.Lh32 = (int)it.Lh;
+    it.wend = (int)min((long long)it.w0 + W, it.Lh);
     double tau_lo, tau_hi;
     if (KIND == ISM_FD_HANN_SINC) {
         tau_lo = (double)(it.kb_lo + it.H) - 0.5;
@@ -262,11 +265,11 @@ __device__ __forceinline__ void build_tables(const RirJob &J, const Tables &T, i
         const double sq = __dmul_rn(dlt, dlt);
         const float sh = __double2float_rn(sq);
         T.sq[a * TE + ei] = sq;
-        T.hi[a * TE + ei] = sh;
-        T.lo[a * TE + ei] = __double2float_rn(sq - (double)sh);
         T.dl[a * TE + ei] = __double2float_rn(dlt);
         const float b0 = J.beta[2 * a], b1 = J.beta[2 * a + 1];
-        T.g[a * TE + ei] = powf(b0, (float)abs(qq - p)) * powf(b1, (float)abs(qq));
+        T.hlg[a * TE + ei] = make_float4(sh, __double2float_rn(sq - (double)sh),
+                                         powf(b0, (float)abs(qq - p)) * powf(b1, (float)abs(qq)),
+                                         0.f);
     }
 }
 
@@ -289,6 +292,75 @@ __device__ __forceinline__ void build_lists(const Tables &T, int TE, const Item 
     }
 }
 
+// Column solve: for column c = ((u,l), (v,m), w) of the axis lists, the
+// admissible n (|Delta_z(n)| in [zmin, zmax]) as up to two intervals
+// [lo_a, hi_a], [lo_b, hi_b]; empty intervals have lo > hi.
+struct Col {
+    int lo_a, hi_a, lo_b, hi_b, ix, iy, wz;
+    __device__ __forceinline__ int count() const {
+        return max(hi_a - lo_a + 1, 0) + max(hi_b - lo_b + 1, 0);
+    }
+};
+
+__device__ __forceinline__ Col column_solve(const Tables &T, int TE, const Item &it,
+                                            const int *s_lx, const int *s_ly, int nLY,
+                                            long long c, long long n_cols) {
+    const int N = it.N;
+    Col r{1, 0, 1, 0, 0, 0, 0};
+    if (c >= n_cols) return r;
+    r.wz = (int)(c & 1);
+    const long long t = c >> 1;
+    r.ix = s_lx[(int)(t / nLY)];
+    r.iy = s_ly[(int)(t % nLY)];
+    const float dx = T.dl[r.ix], dy = T.dl[TE + r.iy];
+    const float rho2 = dx * dx + dy * dy;
+    if (rho2 > it.dhe2) return r;
+    // Delta_z(n) = cz + 2 Lz n must satisfy zmin <= |Delta_z| <= zmax:
+    // the full range [-zmax, zmax] minus the open hole (-zmin, zmin).
+    const float zmax = sqrtf(fmaxf(it.dhi2 - rho2, 0.f)) + it.eps;
+    const float zmin2 = it.dlo2 - rho2;
+    const float zmin = zmin2 > 0.f ? sqrtf(zmin2) - it.eps : 0.f;
+    const float cz = T.dl[2 * TE + r.wz * (2 * N + 1) + N];
+    const float lim = (float)N + 1.f;
+    const float u_lo = fminf(fmaxf((-zmax - cz) * it.inv2Lz, -lim), lim);
+    const float u_hi = fminf(fmaxf((zmax - cz) * it.inv2Lz, -lim), lim);
+    int n_lo = (int)ceilf(u_lo);
+    int n_hi = (int)floorf(u_hi);
+    if (n_lo < -N) n_lo = -N;
+    if (n_hi > N) n_hi = N;
+    int h_lo = 1, h_hi = 0;  // hole (excluded n), empty by default
+    if (zmin > 0.f) {
+        const float v_lo = fminf(fmaxf((-zmin - cz) * it.inv2Lz, -lim), lim);
+        const float v_hi = fminf(fmaxf((zmin - cz) * it.inv2Lz, -lim), lim);
+        h_lo = (int)floorf(v_lo) + 1;
+        h_hi = (int)ceilf(v_hi) - 1;
+    }
+    if (h_lo <= h_hi) {
+        r.lo_a = n_lo;
+        r.hi_a = n_hi < h_lo - 1 ? n_hi : h_lo - 1;
+        r.lo_b = n_lo > h_hi + 1 ? n_lo : h_hi + 1;
+        r.hi_b = n_hi;
+    } else {
+        r.lo_a = n_lo;
+        r.hi_a = n_hi;
+    }
+    return r;
+}
+
+// Writes the candidates of column col whose warp- or block-level index
+// (first index off) lies in [g_lo, g_hi), candidate index i going to
+// dst[(base + i) & mask].
+__device__ __forceinline__ void column_emit(const Col &col, int N, int off, int g_lo, int g_hi,
+                                            uint32_t *dst, int base, int mask) {
+    const int zb = col.wz * (2 * N + 1) + N;
+    const uint32_t code = (uint32_t)col.ix | ((uint32_t)col.iy << 10);
+    int gi = off;
+    for (int n = col.lo_a; n <= col.hi_a; ++n, ++gi)
+        if (gi >= g_lo && gi < g_hi) dst[(base + gi) & mask] = code | ((uint32_t)(zb + n) << 20);
+    for (int n = col.lo_b; n <= col.hi_b; ++n, ++gi)
+        if (gi >= g_lo && gi < g_hi) dst[(base + gi) & mask] = code | ((uint32_t)(zb + n) << 20);
+}
+
 // Column sweep: candidates per (u,l,v,m,w) column, handed to flush(nc) in
 // batches of at most CAP.  All threads call it; block-uniform control flow.
 template <class Flush>
@@ -300,75 +372,71 @@ __device__ __forceinline__ void column_sweep(const Tables &T, int TE, const Item
     int n_cand = 0;  // block-uniform
     for (long long cb = 0; cb < n_cols; cb += NT) {
         const long long c = cb + tid;
-        int lo_a = 1, hi_a = 0, lo_b = 1, hi_b = 0, ix = 0, iy = 0, wz = 0;
-        if (c < n_cols) {
-            wz = (int)(c & 1);
-            const long long t = c >> 1;
-            ix = s_lx[(int)(t / nLY)];
-            iy = s_ly[(int)(t % nLY)];
-            const float dx = T.dl[ix], dy = T.dl[TE + iy];
-            const float rho2 = dx * dx + dy * dy;
-            if (rho2 <= it.dhe2) {
-                // Delta_z(n) = cz + 2 Lz n must satisfy zmin <= |Delta_z| <= zmax:
-                // the full range [-zmax, zmax] minus the open hole (-zmin, zmin).
-                const float zmax = sqrtf(fmaxf(it.dhi2 - rho2, 0.f)) + it.eps;
-                const float zmin2 = it.dlo2 - rho2;
-                const float zmin = zmin2 > 0.f ? sqrtf(zmin2) - it.eps : 0.f;
-                const float cz = T.dl[2 * TE + wz * (2 * N + 1) + N];
-                const float lim = (float)N + 1.f;
-                const float u_lo = fminf(fmaxf((-zmax - cz) * it.inv2Lz, -lim), lim);
-                const float u_hi = fminf(fmaxf((zmax - cz) * it.inv2Lz, -lim), lim);
-                int n_lo = (int)ceilf(u_lo);
-                int n_hi = (int)floorf(u_hi);
-                if (n_lo < -N) n_lo = -N;
-                if (n_hi > N) n_hi = N;
-                int h_lo = 1, h_hi = 0;  // hole (excluded n), empty by default
-                if (zmin > 0.f) {
-                    const float v_lo = fminf(fmaxf((-zmin - cz) * it.inv2Lz, -lim), lim);
-                    const float v_hi = fminf(fmaxf((zmin - cz) * it.inv2Lz, -lim), lim);
-                    h_lo = (int)floorf(v_lo) + 1;
-                    h_hi = (int)ceilf(v_hi) - 1;
-                }
-                if (h_lo <= h_hi) {
-                    lo_a = n_lo;
-                    hi_a = n_hi < h_lo - 1 ? n_hi : h_lo - 1;
-                    lo_b = n_lo > h_hi + 1 ? n_lo : h_hi + 1;
-                    hi_b = n_hi;
-                } else {
-                    lo_a = n_lo;
-                    hi_a = n_hi;
-                }
-            }
-        }
-        const int cnt = max(hi_a - lo_a + 1, 0) + max(hi_b - lo_b + 1, 0);
+        const Col col = column_solve(T, TE, it, s_lx, s_ly, nLY, c, n_cols);
         int total;
-        const int off = block_scan(cnt, s_scan, total);
+        const int off = block_scan(col.count(), s_scan, total);
         if (total == 0) continue;
         if (n_cand + total > CAP && n_cand > 0) {
             flush(n_cand);
             n_cand = 0;
         }
-        const int zb = wz * (2 * N + 1) + N;
-        const uint32_t base_code = (uint32_t)ix | ((uint32_t)iy << 10);
-        // candidates with global index in [g_lo, g_hi) go to s_cand[dst + index]
-        auto emit = [&](int g_lo, int g_hi, int dst) {
-            int gi = off;
-            for (int n = lo_a; n <= hi_a; ++n, ++gi)
-                if (gi >= g_lo && gi < g_hi) s_cand[dst + gi] = base_code | ((uint32_t)(zb + n) << 20);
-            for (int n = lo_b; n <= hi_b; ++n, ++gi)
-                if (gi >= g_lo && gi < g_hi) s_cand[dst + gi] = base_code | ((uint32_t)(zb + n) << 20);
-        };
         if (total <= CAP) {
-            emit(0, total, n_cand);
+            column_emit(col, N, off, 0, total, s_cand, n_cand, 0x7fffffff);
             n_cand += total;
         } else {
             for (int pb = 0; pb < total; pb += CAP) {
-                emit(pb, pb + CAP, -pb);
+                column_emit(col, N, off, pb, pb + CAP, s_cand, -pb, 0x7fffffff);
                 flush(min(CAP, total - pb));
             }
         }
     }
     if (n_cand > 0) flush(n_cand);
+}
+
+// Warp-independent column sweep: warp w takes column batches w, w + NW,
+// ... (32 columns each, one per lane), appends their candidates to its own
+// ring buffer (WCAP slots) and hands them to proc(code, valid) 32 at a time,
+// one per lane.  No block-wide barrier is involved.
+constexpr int WCAP = CAP / NW;  // 256 slots per warp
+
+template <class Proc>
+__device__ __forceinline__ void warp_sweep(const Tables &T, int TE, const Item &it,
+                                           const int *s_lx, const int *s_ly, int nLX, int nLY,
+                                           uint32_t *ring, Proc &proc) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long n_cols = (long long)nLX * nLY * 2;
+    int head = 0, tail = 0;  // warp-uniform ring positions
+    for (long long cb = (long long)warp * 32; cb < n_cols; cb += NT) {
+        const Col col = column_solve(T, TE, it, s_lx, s_ly, nLY, cb + lane, n_cols);
+        const int cnt = col.count();
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        const int off = incl - cnt;
+        for (int g = 0; g < total;) {
+            const int take = min(WCAP - (tail - head), total - g);
+            column_emit(col, it.N, off, g, g + take, ring, tail - g, WCAP - 1);
+            __syncwarp();
+            tail += take;
+            g += take;
+            while (tail - head >= 32) {
+                const uint32_t cd = ring[(head + lane) & (WCAP - 1)];
+                head += 32;
+                proc(cd, true);
+            }
+            __syncwarp();
+        }
+    }
+    if (tail > head) {
+        const bool v = lane < tail - head;
+        const uint32_t cd = v ? ring[(head + lane) & (WCAP - 1)] : 0u;
+        proc(cd, v);
+    }
+    __syncwarp();
 }
 
 // Evaluates one candidate: delay split, window test, gain, statistics.
@@ -380,19 +448,19 @@ __device__ __forceinline__ bool eval_candidate(const Tables &T, int TE, const It
                                                unsigned long long &my_contrib) {
     const int ix = cd & 1023, iy = (cd >> 10) & 1023, iz = cd >> 20;
     int k;
-    float d;
-    delay_split<KIND>(T, TE, ix, iy, iz, it.qh, it.ql, it.q, k, f, d);
+    float d, g;
+    delay_split<KIND>(T, TE, ix, iy, iz, it.qh, it.ql, it.q, k, f, d, g);
     kb = (KIND == ISM_FD_HANN_SINC) ? k - it.H : k - (it.P - 1) / 2;
-    if (kb < it.kb_lo || kb > it.kb_hi) return false;
-    a = T.g[ix] * T.g[TE + iy] * T.g[2 * TE + iz] * __frcp_rn(12.566370614359172f * d);
+    if (kb < it.kb_lo32 || kb > it.kb_hi32) return false;
+    a = g * __frcp_rn(12.566370614359172f * d);
     // statistics: taps in [w0, w0+W) n [0, Lh); an image counts as
-    // contributing in the window of its first in-range tap.
-    const long long lo = max((long long)kb, max((long long)it.w0, 0ll));
-    const long long hi = min((long long)kb + it.n_taps, min((long long)it.w0 + it.W, it.Lh));
-    if (hi > lo) my_taps += (unsigned long long)(hi - lo);
-    const long long first = max((long long)kb, 0ll);
-    if (first < min((long long)kb + it.n_taps, it.Lh) && first >= it.w0 &&
-        first < (long long)it.w0 + it.W)
+    // contributing in the window of its first in-range tap.  All indices
+    // here fit in 32 bits (Lh <= 2^30).
+    const int lo = max(kb, max(it.w0, 0));
+    const int hi = min(kb + it.n_taps, it.wend);
+    if (hi > lo) my_taps += (unsigned)(hi - lo);
+    const int first = max(kb, 0);
+    if (first < min(kb + it.n_taps, it.Lh32) && first >= it.w0 && first < it.w0 + it.W)
         ++my_contrib;
     return true;
 }
@@ -425,10 +493,8 @@ k_ism_taps(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int max
     const int TE = Lay.TE;
     Tables T;
     T.sq = (double *)(smem + Lay.off_sq);
-    T.hi = (float *)(smem + Lay.off_hi);
-    T.lo = (float *)(smem + Lay.off_lo);
+    T.hlg = (float4 *)(smem + Lay.off_hlg);
     T.dl = (float *)(smem + Lay.off_dl);
-    T.g = (float *)(smem + Lay.off_g);
     int *s_lx = (int *)(smem + Lay.off_lx);
     int *s_ly = (int *)(smem + Lay.off_ly);
     uint32_t *s_cand = (uint32_t *)(smem + Lay.off_cand);
@@ -590,10 +656,8 @@ k_ism_sparse(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int m
     const int TE = Lay.TE, CL = Lay.CL, TPS = Lay.TPS;
     Tables T;
     T.sq = (double *)(smem + Lay.off_sq);
-    T.hi = (float *)(smem + Lay.off_hi);
-    T.lo = (float *)(smem + Lay.off_lo);
+    T.hlg = (float4 *)(smem + Lay.off_hlg);
     T.dl = (float *)(smem + Lay.off_dl);
-    T.g = (float *)(smem + Lay.off_g);
     int *s_lx = (int *)(smem + Lay.off_lx);
     int *s_ly = (int *)(smem + Lay.off_ly);
     uint32_t *s_cand = (uint32_t *)(smem + Lay.off_cand);
@@ -640,34 +704,28 @@ k_ism_sparse(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int m
         const int jdelta = (KIND == ISM_FD_HANN_SINC) ? it.H : (it.P - 1) / 2;
         unsigned long long my_contrib = 0, my_taps = 0;
 
-        auto flush = [&](int nc) {
-            __syncthreads();
-            // strided: every thread gets work even when the buffer is short
-#pragma unroll 1
-            for (int ci = tid; ci < nc; ci += NT) {
-                int kb;
-                float f, a;
-                if (!eval_candidate<KIND>(T, TE, it, s_cand[ci], kb, f, a, my_taps, my_contrib))
-                    continue;
-                const int pos = kb + POS0;
-                if (f == 0.f) {  // integer delay: exact Kronecker delta
-                    atomicAdd(&s_delta[pos], a);
-                    continue;
-                }
-                const float x = (KIND == ISM_FD_HANN_SINC) ? 2.f * f : 2.f * f - 1.f;
-                float t0 = 1.f, t1 = x;
-                atomicAdd(&s_c[pos], a);
-                if (Pc > 1) atomicAdd(&s_c[CL + pos], a * x);
-                for (int p = 2; p < Pc; ++p) {
-                    const float t2 = fmaf(2.f * x, t1, -t0);
-                    atomicAdd(&s_c[p * CL + pos], a * t2);
-                    t0 = t1;
-                    t1 = t2;
-                }
+        auto proc = [&](uint32_t cd, bool valid) {
+            int kb;
+            float f, a;
+            if (!valid || !eval_candidate<KIND>(T, TE, it, cd, kb, f, a, my_taps, my_contrib))
+                return;
+            const int pos = kb + POS0;
+            if (f == 0.f) {  // integer delay: exact Kronecker delta
+                atomicAdd(&s_delta[pos], a);
+                return;
             }
-            __syncthreads();
+            const float x = (KIND == ISM_FD_HANN_SINC) ? 2.f * f : 2.f * f - 1.f;
+            float t0 = 1.f, t1 = x;
+            atomicAdd(&s_c[pos], a);
+            if (Pc > 1) atomicAdd(&s_c[CL + pos], a * x);
+            for (int p = 2; p < Pc; ++p) {
+                const float t2 = fmaf(2.f * x, t1, -t0);
+                atomicAdd(&s_c[p * CL + pos], a * t2);
+                t0 = t1;
+                t1 = t2;
+            }
         };
-        column_sweep(T, TE, it, s_lx, s_ly, nLX, nLY, s_scan, s_cand, flush);
+        warp_sweep(T, TE, it, s_lx, s_ly, nLX, nLY, s_cand + (tid >> 5) * WCAP, proc);
         __syncthreads();
 
         // FIR: h[w0+i] = sum_p sum_j B[p][j] c_p[kb = w0+i-j] + delta.  Threads
