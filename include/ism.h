@@ -219,9 +219,9 @@ int ism_convolve_batch(const ism_conv_job *jobs, int64_t n_jobs, const float *h_
  * them while device memory (max_hbm_bytes) and slots allow, packs the
  * admitted ones into ragged batches, and runs them on its streams so that
  * batches overlap on the GPU.  Results stay on the device until released.
- * Each request's result is the same alone or mixed with others, up to
- * floating-point rounding of its own reduction order, which does not depend
- * on the mix.
+ * Each request's work items (RIR windows, convolution tiles, noise streams
+ * keyed by its noise_id) are the same alone or mixed with others; the RIR
+ * sums use shared-memory atomics, so results agree to FP32 rounding.
  * ------------------------------------------------------------------------ */
 typedef struct ism_server ism_server;
 
@@ -242,6 +242,8 @@ typedef struct ism_request {
     int64_t src_len;
     float snr_db;            /* NaN = no noise */
     int32_t reserved;
+    uint64_t noise_id;       /* noise streams of the request (with the server
+                                seed); 0 = use the ticket */
 } ism_request;
 
 typedef struct ism_result {
@@ -278,6 +280,14 @@ int ism_serve_poll(ism_server *server, uint64_t ticket, ism_result *out);
 
 /* As poll, blocking up to timeout_s seconds (ISM_ERR_TIMEOUT after). */
 int ism_serve_wait(ism_server *server, uint64_t ticket, double timeout_s, ism_result *out);
+
+/* Copies a finished request's RIRs (n_mics x rir_len) and microphone
+ * signals (n_mics x y_len), mic-major, into caller buffers h_out / y_out
+ * (device or host memory; either may be NULL), enqueued on `stream`; read
+ * them once the stream has passed the copy.  Same status codes as poll
+ * (ISM_PENDING if not finished yet). */
+int ism_serve_copy(ism_server *server, uint64_t ticket, float *h_out, float *y_out,
+                   void *stream);
 
 /* Frees a finished request's device memory.  ISM_ERR_UNKNOWN_TICKET for an
  * unknown ticket, ISM_PENDING if it is still running (not released). */

@@ -13,8 +13,8 @@ include/ism.h; this package is its Python binding.
 from ._lib import (BF16X3, F32, FD_HANN_SINC, FD_LAGRANGE, RIR_DIRECT, RIR_SPARSE, IsmError,  # noqa
                    PreparedRooms, check, conv_jobs, convolve_batch, last_error, load, make_rooms,
                    rir_batch,
-                   rir_batch_noalloc, rir_batch_size, rir_filter_terms)
+                   rir_batch_noalloc, rir_batch_size, rir_filter_terms, Server)
 
 __all__ = ["load", "rir_batch", "rir_batch_size", "rir_batch_noalloc", "convolve_batch",
            "conv_jobs", "IsmError", "F32", "BF16X3", "FD_HANN_SINC", "FD_LAGRANGE", "RIR_SPARSE",
-           "RIR_DIRECT", "last_error", "check", "make_rooms", "PreparedRooms", "rir_filter_terms"]
+           "RIR_DIRECT", "last_error", "check", "make_rooms", "PreparedRooms", "rir_filter_terms", "Server"]

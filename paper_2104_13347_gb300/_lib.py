@@ -53,7 +53,7 @@ class ServeConfig(ctypes.Structure):
 
 class Request(ctypes.Structure):
     _fields_ = [("room", Room), ("src_host", c_vp), ("src_len", c_i64), ("snr_db", c_f32),
-                ("reserved", c_i32)]
+                ("reserved", c_i32), ("noise_id", c_u64)]
 
 
 class Result(ctypes.Structure):
@@ -80,6 +80,7 @@ SIGNATURES = {
     "ism_serve_poll": (c_i32, [c_vp, c_u64, c_vp]),
     "ism_serve_wait": (c_i32, [c_vp, c_u64, c_f64, c_vp]),
     "ism_serve_release": (c_i32, [c_vp, c_u64]),
+    "ism_serve_copy": (c_i32, [c_vp, c_u64, c_vp, c_vp, c_vp]),
     "ism_serve_stats_get": (c_i32, [c_vp, c_vp]),
     "ism_serve_destroy": (c_i32, [c_vp]),
     "ism_last_error_string": (ctypes.c_char_p, []),
@@ -250,3 +251,72 @@ def convolve_batch(jobs, h, src, y, seed=0, precision=F32, stream=None):
                                     c_vp(y.data_ptr()), c_u64(seed), int(precision),
                                     _stream_ptr(stream)))
     return y
+
+
+class Server:
+    """ism_serve_*: continuous-batching server (argument marshalling only)."""
+
+    def __init__(self, max_hbm_bytes=0, max_batch=0, n_streams=0, precision=F32, max_queue=0,
+                 seed=0, device=None):
+        import torch
+        self._lib = load()
+        if device is None:
+            device = torch.cuda.current_device() if torch.cuda.is_available() else 0
+        cfg = ServeConfig(int(max_hbm_bytes), int(max_batch), int(n_streams), int(precision),
+                          int(max_queue), int(seed), int(device), 0)
+        self._h = c_vp()
+        check(self._lib.ism_serve_create(ctypes.byref(cfg), ctypes.byref(self._h)))
+
+    def submit(self, room, src, snr_db=math.nan, noise_id=0):
+        """Submits one room dict and its float32 source; returns the ticket
+        (raises IsmError with status ISM_ERR_BUSY when not admitted)."""
+        arr, keep = make_rooms([room])
+        src = np.ascontiguousarray(src, np.float32)
+        rq = Request()
+        rq.room = arr[0]
+        rq.src_host = src.ctypes.data
+        rq.src_len = len(src)
+        rq.snr_db = float(snr_db)
+        rq.noise_id = int(noise_id)
+        t = c_u64()
+        check(self._lib.ism_serve_submit(self._h, ctypes.byref(rq), ctypes.byref(t)))
+        return t.value
+
+    def poll(self, ticket):
+        res = Result()
+        st = self._lib.ism_serve_poll(self._h, c_u64(ticket), ctypes.byref(res))
+        if st == ISM_PENDING:
+            return None
+        check(st)
+        return res
+
+    def wait(self, ticket, timeout_s=60.0):
+        res = Result()
+        check(self._lib.ism_serve_wait(self._h, c_u64(ticket), float(timeout_s),
+                                       ctypes.byref(res)))
+        return res
+
+    def copy(self, ticket, h_out=None, y_out=None, stream=None):
+        check(self._lib.ism_serve_copy(self._h, c_u64(ticket),
+                                       c_vp(h_out.data_ptr()) if h_out is not None else None,
+                                       c_vp(y_out.data_ptr()) if y_out is not None else None,
+                                       _stream_ptr(stream)))
+
+    def release(self, ticket):
+        check(self._lib.ism_serve_release(self._h, c_u64(ticket)))
+
+    def stats(self):
+        s = ServeStats()
+        check(self._lib.ism_serve_stats_get(self._h, ctypes.byref(s)))
+        return {n: getattr(s, n) for n, _ in ServeStats._fields_}
+
+    def close(self):
+        if self._h:
+            check(self._lib.ism_serve_destroy(self._h))
+            self._h = c_vp()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

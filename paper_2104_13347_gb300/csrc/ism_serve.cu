@@ -11,8 +11,9 @@
 //  * completion: an event per batch, polled with cudaEventQuery (never a
 //    blocking wait), marks the batch's requests done and records latency.
 // Every request's RIR windows, convolution tiles and noise streams (keyed
-// by its ticket) are computed the same way whatever else is in its batch, so
-// a result is the same alone or in any mix.  The device is selected lazily
+// by its noise id, or its ticket) are the same work items whatever else is
+// in its batch, so a result is the same alone or in any mix up to FP32
+// rounding (the RIR sums use shared-memory atomics).  The device is selected lazily
 // by the thread: if it cannot be used, requests fail with ISM_ERR_CUDA and a
 // message, which poll/wait report.
 #include <cuda_runtime.h>
@@ -55,6 +56,7 @@ struct Req {
     float *src_pinned = nullptr;
     int64_t src_len = 0;
     float snr_db = NAN;
+    uint64_t noise_id = 0;
     int64_t bytes = 0;
     State state = QUEUED;
     bool released = false;
@@ -216,7 +218,7 @@ void ism_server::launch(std::vector<std::shared_ptr<Req>> &take) {
             j.src_offset = r->src_off;
             j.y_offset = r->y_off;
             j.snr_db = r->snr_db;
-            j.noise_id = r->ticket;
+            j.noise_id = r->noise_id ? r->noise_id : r->ticket;
             jobs.push_back(j);
         }
         ism_rir_opts o;
@@ -391,6 +393,7 @@ int ism_serve_submit(ism_server *s, const ism_request *rq, uint64_t *ticket) {
     r->room.mics = nullptr;
     r->src_len = rq->src_len;
     r->snr_db = rq->snr_db;
+    r->noise_id = rq->noise_id;
     r->bytes = bytes;
     {
         std::lock_guard<std::mutex> lk(s->mu);
@@ -468,6 +471,28 @@ int ism_serve_wait(ism_server *s, uint64_t ticket, double timeout_s, ism_result 
             return fail(ISM_ERR_TIMEOUT, "wait deadline passed");
         }
     }
+}
+
+int ism_serve_copy(ism_server *s, uint64_t ticket, float *h_out, float *y_out, void *stream) {
+    if (!s) return fail(ISM_ERR_INVALID_ARG, "NULL server");
+    ism_result r;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        auto it = s->reqs.find(ticket);
+        if (it == s->reqs.end()) return fail(ISM_ERR_UNKNOWN_TICKET, "unknown ticket");
+        const int st = fill_result(*it->second, &r);
+        if (st != ISM_OK) return st;
+    }
+    cudaStream_t cs = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    if (h_out)
+        e = cudaMemcpyAsync(h_out, r.h_dev, sizeof(float) * r.n_mics * r.rir_len, cudaMemcpyDefault,
+                            cs);
+    if (e == cudaSuccess && y_out)
+        e = cudaMemcpyAsync(y_out, r.y_dev, sizeof(float) * r.n_mics * r.y_len, cudaMemcpyDefault,
+                            cs);
+    if (e != cudaSuccess) return cuda_fail(e, "ism_serve_copy");
+    return ISM_OK;
 }
 
 int ism_serve_release(ism_server *s, uint64_t ticket) {

@@ -1,0 +1,123 @@
+"""GPU tests of the continuous-batching server (ism_serve_*).
+
+Requests of uneven sizes are submitted while others are on the GPU; each
+result must match the batch entry points on the same inputs, be the same
+alone and in the mix (to FP32 rounding: the RIR sums use shared-memory
+atomics), and match the FP64 oracle at the path's bars (arXiv 2104.13347
+Sec. II.A RIR + convolution, Sec. III.A noise).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2104_13347_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+def rel_l2(x, ref):
+    return float(np.linalg.norm(x - ref) / max(np.linalg.norm(ref), 1e-300))
+
+
+def requests(n, seed):
+    """Small mixed requests: 1-9 mics, RIRs 300-5000 samples, sources of
+    500-6000 samples, orders 2-6, some with noise."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        room = wl.room_batch(1, seed=seed * 1000 + i, order=int(rng.integers(2, 7)),
+                             rir_len=int(rng.integers(300, 5000)),
+                             n_mics=int(rng.integers(1, 10)))[0]
+        src = rng.standard_normal(int(rng.integers(500, 6000))).astype(np.float32)
+        snr = float(rng.uniform(0, 30)) if i % 3 == 0 else math.nan
+        out.append((room, src, snr, 7000 + i))
+    return out
+
+
+def fetch(ism, srv, ticket, room, src):
+    import torch
+    res = srv.wait(ticket, 60.0)
+    M, L, T = res.n_mics, res.rir_len, res.y_len
+    assert M == len(room["mics"]) and L == room["rir_len"] and T == len(src) + L - 1
+    h = torch.empty(M * L, device="cuda")
+    y = torch.empty(M * T, device="cuda")
+    srv.copy(ticket, h, y)
+    torch.cuda.synchronize()
+    return (h.cpu().numpy().reshape(M, L).astype(np.float64),
+            y.cpu().numpy().reshape(M, T).astype(np.float64), res)
+
+
+def direct(ism, room, src, snr, noise_id, seed, precision):
+    """The same request through the batch entry points."""
+    import torch
+    h = ism.rir_batch([room])
+    jobs, ylen = ism.conv_jobs([len(room["mics"])], [room["rir_len"]], [len(src)],
+                               snr_db=[snr], noise_ids=[noise_id])
+    y = torch.empty(ylen, device="cuda")
+    ism.convolve_batch(jobs, h, torch.from_numpy(src).cuda(), y, seed=seed,
+                       precision=precision)
+    torch.cuda.synchronize()
+    M, L = len(room["mics"]), room["rir_len"]
+    return (h.cpu().numpy().reshape(M, L).astype(np.float64),
+            y.cpu().numpy().reshape(M, -1).astype(np.float64))
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_serve_mix_matches_batch_api_and_alone(ism, precision):
+    reqs = requests(24, seed=3)
+    seed = 99
+    with ism.Server(precision=precision, seed=seed, max_batch=8, n_streams=3) as srv:
+        tickets = [srv.submit(r, s, snr, nid) for r, s, snr, nid in reqs]
+        mixed = [fetch(ism, srv, t, r, s) for t, (r, s, _, _) in zip(tickets, reqs)]
+        st = srv.stats()
+        assert st["completed"] == len(reqs) and st["batches"] >= 2
+        for t in tickets:
+            srv.release(t)
+    # alone: a fresh server per request
+    for k in (0, 5, 17):
+        r, s, snr, nid = reqs[k]
+        with ism.Server(precision=precision, seed=seed) as srv:
+            t = srv.submit(r, s, snr, nid)
+            h1, y1, _ = fetch(ism, srv, t, r, s)
+        h0, y0, _ = mixed[k]
+        assert rel_l2(h0, h1) < 1e-6
+        assert rel_l2(y0, y1) < 1e-5
+    # batch entry points on the same inputs
+    for k in (1, 6, 12):
+        r, s, snr, nid = reqs[k]
+        hd, yd = direct(ism, r, s, snr, nid, seed, precision)
+        assert rel_l2(mixed[k][0], hd) < 1e-6
+        assert rel_l2(mixed[k][1], yd) < 1e-5
+
+
+def test_serve_parity_with_oracle(ism):
+    reqs = requests(4, seed=5)
+    with ism.Server(precision=0) as srv:
+        tickets = [srv.submit(r, s) for r, s, _, _ in reqs]  # no noise
+        for t, (r, s, _, _) in zip(tickets, reqs):
+            h, y, res = fetch(ism, srv, t, r, s)
+            href, _ = oracle.rir_batch([r])
+            yref = oracle.convolve_batch([href[0]], [s.astype(np.float64)])[0]
+            for m in range(h.shape[0]):
+                assert rel_l2(h[m], href[0][m]) <= 1e-5
+                assert rel_l2(y[m], yref[m]) <= 1e-5
+            assert res.latency_s >= res.queue_s >= 0
+            srv.release(t)
+
+
+def test_serve_hbm_admission_queues_requests(ism):
+    """A device budget that holds only a couple of requests at a time: all
+    requests still complete, the budget is never exceeded."""
+    reqs = requests(12, seed=7)
+    budget = 3 << 20
+    with ism.Server(max_hbm_bytes=budget, max_batch=4, n_streams=2) as srv:
+        tickets = [srv.submit(r, s) for r, s, _, _ in reqs]
+        for t, (r, s, _, _) in zip(tickets, reqs):
+            fetch(ism, srv, t, r, s)
+            srv.release(t)  # frees memory so queued requests can be admitted
+        st = srv.stats()
+        assert st["completed"] == len(reqs)
+        assert 0 < st["bytes_peak"] <= budget
+        assert st["taps"] > 0 and st["mic_samples"] > 0
