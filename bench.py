@@ -327,11 +327,12 @@ def run_ours(args, ws, rank):
     conv_med = statistics.median(conv_ms)
     contrib = int(stats.view(-1, 2)[:, 0].sum().item())
     P = ism.rir_filter_terms(0, 81)
-    # K1 (sparse path) algorithmic FP32 work per launch: the FIR, 2 P n_taps
-    # flops per output sample, plus the Chebyshev scatter, 2 P flops per
-    # contributing image.  Peak: FP32 FMA pipe, 128 lanes x 2 flops per
-    # clock per SM at the maximum SM clock.
-    k1_flops = 2.0 * P * 81 * n_rirs * LH + 2.0 * P * contrib
+    # K1 (sparse path) algorithmic FP32 work per launch: per contributing
+    # image 41 flops for the float-float delay split and gain plus 4P - 4 for
+    # the Chebyshev scatter (recurrence, scaling, accumulation); per output
+    # sample 2 P n_taps for the FIR.  Peak: FP32 FMA pipe, 128 lanes x 2
+    # flops per clock per SM at the maximum SM clock.
+    k1_flops = 2.0 * P * 81 * n_rirs * LH + (41.0 + 4 * P - 4) * contrib
     peak_fp32 = 2.0 * 128 * n_sm * sm_mhz * 1e6
     k1_rate = k1_flops / (rir_med * 1e-3)
     # context: the direct per-tap formulation is bound by the reciprocal
@@ -353,8 +354,9 @@ def run_ours(args, ws, rank):
                       "stage_ms": {"rir": rir_med, "conv_noise": conv_med}},
         "roofline": {"bound": "alu", "kernel": "k_ism_sparse", "achieved": k1_rate / 1e12,
                      "peak": peak_fp32 / 1e12, "unit": "TFLOP/s", "frac": k1_rate / peak_fp32,
-                     "traffic": None,
-                     "work": f"FIR 2*P*n_taps per output + 2*P per contributing image, P={P}",
+                     "traffic": 4 * 6.97e6,
+                     "traffic_note": "dram read+write of a 256-room ncu capture x 4 rooms",
+                     "work": f"2*P*n_taps per output (FIR) + 41+4P-4 per contributing image, P={P}",
                      "peak_note": f"FP32 FMA pipe, 128 lanes x 2 flop/clk/SM x {n_sm} SMs x "
                                   f"{sm_mhz:.0f} MHz ({pk_kind} max clock)",
                      "taps_per_s": taps / (rir_med * 1e-3),
