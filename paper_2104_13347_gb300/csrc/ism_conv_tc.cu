@@ -21,10 +21,16 @@
 // one TMEM accumulator, so the result holds all four products hi/lo x hi/lo.
 // Chunks whose source window is all zero padding are skipped.
 //
-// Warp roles (160 threads): warps 0-3 produce the pipeline stages (A rows and
-// the chunk's source window, split to bf16 in registers, FP32 inputs read
-// straight from global memory) and run the epilogue; warp 4 allocates TMEM
-// and one of its lanes issues the MMAs.  Stages hand over through mbarriers
+// The tile's whole source window is converted to bf16 hi/lo once at the
+// start when it fits in shared memory (RIRs up to ~9k samples); longer RIRs
+// convert each chunk's 2112-sample window into its pipeline stage instead.
+// The raw RIR values of each chunk are staged with cp.async (double
+// buffered, zero-filled outside the RIR) and each producer thread builds one
+// 16-byte row (one row group, one phase) per k-group, so a warp's 128-bit
+// stores cover 512 contiguous bytes.
+//
+// Warp roles (160 threads): warps 0-3 produce the pipeline stages and run
+// the epilogue; warp 4 allocates TMEM and one of its lanes issues the MMAs.  Stages hand over through mbarriers
 // (full: 128 producer arrivals; empty: tcgen05.commit).  Every wait is
 // bounded: on timeout the kernel records an error, stops issuing, waits
 // (bounded) for its own MMAs, frees TMEM and returns.
@@ -32,6 +38,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "ism_internal.h"
@@ -118,7 +125,59 @@ __device__ __forceinline__ float bf16_round(float x) {
     return __bfloat162float(__float2bfloat16_rn(x));
 }
 
-__global__ void __launch_bounds__(NTHR, 2)
+constexpr int STG_FLOATS = 8 * 72;     // raw RIR staging per chunk: 8 mics x 72 values
+
+__device__ __forceinline__ void cp_async4(uint32_t dst, const float *src, bool ok) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src),
+                 "r"(ok ? 4 : 0)
+                 : "memory");
+}
+
+// OR of pred over the 128 producer threads (named barrier 1); also a barrier.
+__device__ __forceinline__ bool producers_any(bool pred) {
+    uint32_t r;
+    asm volatile(
+        "{\n.reg .pred p, q;\nsetp.ne.u32 p, %1, 0;\nbar.red.or.pred q, 1, 128, p;\n"
+        "selp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(r)
+        : "r"((uint32_t)pred)
+        : "memory");
+    return r != 0;
+}
+
+__device__ __forceinline__ void producers_sync() {
+    asm volatile("bar.sync 1, 128;" ::: "memory");
+}
+
+// Shared-memory layout.  whole_b: NS A stages (16 KB each), RIR staging,
+// then the tile's source window (bf16 hi, bf16 lo; bl elements each).
+// Otherwise NS stages of (A, window hi, window lo), then RIR staging.
+struct TcLayout {
+    size_t a_stride, stg, bhi, blo, total;
+    int bl;
+};
+
+__host__ __device__ inline TcLayout tc_layout(bool whole_b, int n_chunks) {
+    TcLayout L;
+    if (whole_b) {
+        L.bl = (n_chunks * KC + 8 * (NN - 1) + 8 + 7) & ~7;
+        L.a_stride = A_BYTES;
+        L.stg = (size_t)NS * A_BYTES;
+        L.bhi = L.stg + STG_FLOATS * 2 * 4;
+        L.blo = L.bhi + (size_t)L.bl * 2;
+        L.total = L.blo + (size_t)L.bl * 2;
+    } else {
+        L.bl = BW;
+        L.a_stride = STAGE;
+        L.stg = (size_t)NS * STAGE;
+        L.bhi = L.blo = 0;  // per stage, after A
+        L.total = L.stg + STG_FLOATS * 2 * 4;
+    }
+    return L;
+}
+
+template <bool WHOLE_B>
+__global__ void __launch_bounds__(NTHR, 1)
 k_conv_tc(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles,
           const float *__restrict__ h, const float *__restrict__ src, float *__restrict__ y) {
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -135,11 +194,14 @@ k_conv_tc(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles,
     const float *sb = src + J.src_offset;
     const int64_t c0 = T0 - Lh + 1;                    // source index of B[0][0] at k = 0
     const int n_chunks = (int)((Lh + 7 + KC - 1) / KC);
-    // a chunk is skipped when its whole source window is zero padding
-    auto live = [&](int ch) {
-        const int64_t lo = c0 + (int64_t)ch * KC, hi = lo + KC - 1 + 8 * (NN - 1);
-        return hi >= 0 && lo < Ts;
-    };
+    const TcLayout Lay = tc_layout(WHOLE_B, n_chunks);
+    // live chunks (source window not all zero padding) form one range
+    int64_t lo_c = -c0 - (KC - 1 + 8 * (NN - 1));
+    lo_c = lo_c <= 0 ? 0 : (lo_c + KC - 1) / KC;
+    int64_t hi_c = Ts - 1 - c0;
+    hi_c = hi_c < 0 ? -1 : hi_c / KC;
+    const int ch_lo = (int)lo_c, ch_hi = (int)min(hi_c, (int64_t)n_chunks - 1);
+    const int n_live = ch_hi >= ch_lo ? ch_hi - ch_lo + 1 : 0;
 
     if (tid == 0) {
         for (int s = 0; s < NS; ++s) {
@@ -152,6 +214,20 @@ k_conv_tc(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles,
         asm volatile("fence.mbarrier_init.release.cluster;");
         s_abort = 0;
     }
+    if (WHOLE_B && n_live > 0) {
+        // the tile's source window s[c0 + e], e in [0, bl), as bf16 hi / lo
+        uint32_t *bh = reinterpret_cast<uint32_t *>(smem + Lay.bhi);
+        uint32_t *bl = reinterpret_cast<uint32_t *>(smem + Lay.blo);
+        for (int e2 = tid; e2 < Lay.bl / 2; e2 += NTHR) {
+            const int64_t i0 = c0 + 2 * e2;
+            const float x0 = (i0 >= 0 && i0 < Ts) ? __ldg(sb + i0) : 0.f;
+            const float x1 = (i0 + 1 >= 0 && i0 + 1 < Ts) ? __ldg(sb + i0 + 1) : 0.f;
+            const float h0 = bf16_round(x0), h1 = bf16_round(x1);
+            bh[e2] = pack_bf16(h0, h1);
+            bl[e2] = pack_bf16(x0 - h0, x1 - h1);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
     if (warp == 4) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&s_tmem)),
@@ -163,55 +239,61 @@ k_conv_tc(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles,
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = s_tmem;
 
-    int n_live = 0;
-    for (int ch = 0; ch < n_chunks; ++ch) n_live += live(ch);
-
     if (warp < 4) {
         // ------------------------------------------------------------------
-        // producers
+        // producers: thread = (row group g = (q, m), phase p)
         // ------------------------------------------------------------------
-        const int q = tid >> 6;                 // 0 = hi rows, 1 = lo rows
-        const int item = tid & 63, m = item >> 3, kg = item & 7;
-        int i = 0;  // live-chunk counter
-        for (int ch = 0; ch < n_chunks; ++ch) {
-            if (!live(ch)) continue;
-            const int s = i % NS, u = i / NS;
-            if (u > 0 && !mbar_wait(smem_u32(&bar_empty[s]), (u - 1) & 1)) {
+        const int g = tid >> 3, q = g >> 3, m = g & 7, p = tid & 7;
+        float *stg = reinterpret_cast<float *>(smem + Lay.stg);
+        const uint32_t stg_u32 = smem_u32(stg);
+        auto stage_rir = [&](int ch, int buf) {
+            // stg[buf][mm][e] = h_mm[Lh - 64 - 64 ch + e], e in [0, 72)
+            const int64_t start = Lh - 64 - (int64_t)ch * KC;
+            for (int e = tid; e < STG_FLOATS; e += NPROD) {
+                const int mm = e / 72, ee = e - mm * 72;
+                const int64_t idx = start + ee;
+                const bool ok = mm < nm && idx >= 0 && idx < Lh;
+                cp_async4(stg_u32 + 4u * (uint32_t)(buf * STG_FLOATS + e),
+                          ok ? hb + (int64_t)mm * Lh + idx : hb, ok);
+            }
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        };
+        if (n_live > 0) stage_rir(ch_lo, 0);
+        if (n_live > 1) stage_rir(ch_lo + 1, 1);
+        else asm volatile("cp.async.commit_group;" ::: "memory");
+        for (int i = 0; i < n_live; ++i) {
+            const int ch = ch_lo + i, s = i % NS, u = i / NS, buf = i & 1;
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+            const bool ok = (u == 0) || mbar_wait(smem_u32(&bar_empty[s]), (u - 1) & 1);
+            if (producers_any(!ok || s_abort)) {  // uniform decision, also a barrier
                 s_abort = 1;
                 break;
             }
-            if (s_abort) break;
-            unsigned char *st = smem + (size_t)s * STAGE;
-            const int64_t k0 = (int64_t)ch * KC;
-            // A: rows (q, m, p), k-group kg: element (p, kr) = part_q(v[p - kr + 7]),
-            // v[i] = h_m[Lh - 8 - k0 - 8 kg + i]
-            {
-                float v[15];
-                const int64_t base = Lh - 8 - k0 - 8 * kg;
+            unsigned char *st = smem + (size_t)s * Lay.a_stride;
+            // A rows (q, m, p) for each k-group kg: element kr is
+            // part_q(h_m[Lh - 1 + p - 64 ch - 8 kg - kr]) = part_q(stg[63 + p - 8 kg - kr])
+            const float *sv = stg + buf * STG_FLOATS + m * 72 + 63 + p;
 #pragma unroll
-                for (int e = 0; e < 15; ++e) {
-                    const int64_t idx = base + e;
-                    float x = 0.f;
-                    if (m < nm && idx >= 0 && idx < Lh) x = __ldg(hb + (int64_t)m * Lh + idx);
+            for (int kg = 0; kg < 8; ++kg) {
+                float v[8];
+#pragma unroll
+                for (int kr = 0; kr < 8; ++kr) {
+                    const float x = sv[-8 * kg - kr];
                     const float xh = bf16_round(x);
-                    v[e] = q ? x - xh : xh;
+                    v[kr] = q ? x - xh : xh;
                 }
-                unsigned char *dst = st + kg * 2048 + (8 * q + m) * 128;
-#pragma unroll
-                for (int p = 0; p < 8; ++p) {
-                    uint4 row;
-                    row.x = pack_bf16(v[p + 7], v[p + 6]);
-                    row.y = pack_bf16(v[p + 5], v[p + 4]);
-                    row.z = pack_bf16(v[p + 3], v[p + 2]);
-                    row.w = pack_bf16(v[p + 1], v[p + 0]);
-                    *reinterpret_cast<uint4 *>(dst + p * 16) = row;
-                }
+                uint4 row;
+                row.x = pack_bf16(v[0], v[1]);
+                row.y = pack_bf16(v[2], v[3]);
+                row.z = pack_bf16(v[4], v[5]);
+                row.w = pack_bf16(v[6], v[7]);
+                *reinterpret_cast<uint4 *>(st + kg * 2048 + g * 128 + p * 16) = row;
             }
-            // B: the chunk's source window, s[c0 + k0 + e], split hi / lo
-            {
+            if (!WHOLE_B) {
+                // the chunk's source window, s[c0 + 64 ch + e], split hi / lo
                 uint32_t *bh = reinterpret_cast<uint32_t *>(st + A_BYTES);
                 uint32_t *bl = reinterpret_cast<uint32_t *>(st + A_BYTES + BW * 2);
-                const int64_t sbase = c0 + k0;
+                const int64_t sbase = c0 + (int64_t)ch * KC;
                 for (int e2 = tid; e2 < BW / 2; e2 += NPROD) {
                     const int64_t i0 = sbase + 2 * e2;
                     const float x0 = (i0 >= 0 && i0 < Ts) ? __ldg(sb + i0) : 0.f;
@@ -223,24 +305,32 @@ k_conv_tc(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles,
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             mbar_arrive(smem_u32(&bar_full[s]));
-            ++i;
+            producers_sync();  // every producer is done with stg[buf]
+            if (i + 2 < n_live) stage_rir(ch + 2, buf);
+            else asm volatile("cp.async.commit_group;" ::: "memory");
         }
+        asm volatile("cp.async.wait_all;" ::: "memory");
     } else if (lane == 0) {
         // ------------------------------------------------------------------
         // MMA issuer
         // ------------------------------------------------------------------
-        int i = 0;
         uint32_t acc = 0;
-        for (int ch = 0; ch < n_chunks; ++ch) {
-            if (!live(ch)) continue;
-            const int s = i % NS, u = i / NS;
+        for (int i = 0; i < n_live; ++i) {
+            const int ch = ch_lo + i, s = i % NS, u = i / NS;
             if (!mbar_wait(smem_u32(&bar_full[s]), u & 1)) {
                 s_abort = 1;
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;");
-            const uint32_t a0 = smem_u32(smem + (size_t)s * STAGE);
-            const uint32_t bh0 = a0 + A_BYTES, bl0 = bh0 + BW * 2;
+            const uint32_t a0 = smem_u32(smem + (size_t)s * Lay.a_stride);
+            uint32_t bh0, bl0;
+            if (WHOLE_B) {
+                bh0 = smem_u32(smem + Lay.bhi) + 2u * (uint32_t)(ch * KC);
+                bl0 = smem_u32(smem + Lay.blo) + 2u * (uint32_t)(ch * KC);
+            } else {
+                bh0 = a0 + A_BYTES;
+                bl0 = bh0 + BW * 2;
+            }
 #pragma unroll
             for (int kk = 0; kk < KC / 16; ++kk) {
                 const uint64_t ad = make_desc(a0 + kk * 2 * 2048, 2048, 128);
@@ -259,7 +349,6 @@ k_conv_tc(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles,
             asm volatile(
                 "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                     smem_u32(&bar_empty[s])));
-            ++i;
         }
         // all issued MMAs done -> bar_done
         asm volatile(
@@ -345,26 +434,46 @@ k_conv_tc(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles,
 }  // namespace
 
 int launch_conv_bf16x3(const ConvLaunch &L, cudaStream_t stream) {
-    std::vector<Tile> tiles;
+    // one launch per layout: tiles whose whole source window fits in shared
+    // memory, and the rest (long RIRs) with per-chunk windows
+    std::vector<Tile> tiles[2];
+    int max_chunks = 0;
     for (int j = 0; j < L.n_jobs; ++j) {
         const ConvJob &J = L.jobs_host[j];
+        const int n_chunks = (int)((J.rir_len + 7 + KC - 1) / KC);
+        const bool whole = tc_layout(true, n_chunks).total <= 227 * 1024;
+        if (whole) max_chunks = std::max(max_chunks, n_chunks);
         for (int m0 = 0; m0 < J.n_mics; m0 += MG)
-            for (int64_t t0 = 0; t0 < J.y_len; t0 += TT) tiles.push_back(Tile{j, m0, t0});
+            for (int64_t t0 = 0; t0 < J.y_len; t0 += TT) tiles[whole].push_back(Tile{j, m0, t0});
     }
-    if (tiles.empty()) return ISM_OK;
-    if (tiles.size() > 0x7fffffffULL) return fail(ISM_ERR_INVALID_ARG, "too many tiles");
-    const size_t smem = (size_t)NS * STAGE;
-    cudaError_t e = cudaFuncSetAttribute(k_conv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_conv_tc)");
+    const size_t n_tiles = tiles[0].size() + tiles[1].size();
+    if (n_tiles == 0) return ISM_OK;
+    if (n_tiles > 0x7fffffffULL) return fail(ISM_ERR_INVALID_ARG, "too many tiles");
     void *d_tiles = nullptr;
-    int st = scratch_alloc(&d_tiles, tiles.size() * sizeof(Tile), stream);
+    int st = scratch_alloc(&d_tiles, n_tiles * sizeof(Tile), stream);
     if (st) return st;
-    st = upload_async(d_tiles, tiles.data(), tiles.size() * sizeof(Tile), stream);
+    std::vector<Tile> all(tiles[1]);
+    all.insert(all.end(), tiles[0].begin(), tiles[0].end());
+    st = upload_async(d_tiles, all.data(), n_tiles * sizeof(Tile), stream);
     if (st) { scratch_free(d_tiles, stream); return st; }
-    k_conv_tc<<<(unsigned)tiles.size(), NTHR, smem, stream>>>(L.jobs_dev, (const Tile *)d_tiles,
-                                                               L.h_dev, L.src_dev, L.y_dev);
-    e = cudaGetLastError();
+    cudaError_t e = cudaSuccess;
+    if (!tiles[1].empty()) {
+        const size_t smem = tc_layout(true, max_chunks).total;
+        e = cudaFuncSetAttribute(k_conv_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e == cudaSuccess)
+            k_conv_tc<true><<<(unsigned)tiles[1].size(), NTHR, smem, stream>>>(
+                L.jobs_dev, (const Tile *)d_tiles, L.h_dev, L.src_dev, L.y_dev);
+    }
+    if (e == cudaSuccess && !tiles[0].empty()) {
+        const size_t smem = tc_layout(false, 0).total;
+        e = cudaFuncSetAttribute(k_conv_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e == cudaSuccess)
+            k_conv_tc<false><<<(unsigned)tiles[0].size(), NTHR, smem, stream>>>(
+                L.jobs_dev, (const Tile *)d_tiles + tiles[1].size(), L.h_dev, L.src_dev, L.y_dev);
+    }
+    if (e == cudaSuccess) e = cudaGetLastError();
     scratch_free(d_tiles, stream);
     if (e != cudaSuccess) return cuda_fail(e, "launch k_conv_tc");
     return ISM_OK;
