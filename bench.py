@@ -120,13 +120,21 @@ def barrier(ws):
 
 
 def max_over_ranks(x, ws):
+    """Largest value over ranks (the job's time is its slowest rank's)."""
     if ws == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def rank_seed(rank):
+    """Each rank generates its own batch of rooms (weak scaling: the units
+    are independent rooms, so ranks share no data and exchange nothing)."""
+    return 1002 + 7919 * rank
 
 
 def cpu_sample(rooms, srcs, n_rir_rooms=6, n_conv_rooms=1):
@@ -247,7 +255,7 @@ def run_ours(args, ws, rank):
 
     ism.load()
     dev = torch.device("cuda", torch.cuda.current_device())
-    seed = 1002 + 7919 * rank  # each rank its own batch (weak scaling)
+    seed = rank_seed(rank)
     n_rooms = args.rooms
     rooms = wl.room_batch(n_rooms, seed=seed)
     srcs = wl.sources(rooms, 1.0, seed=seed + 1)
