@@ -357,8 +357,14 @@ int ism_rir_batch_ex(const ism_room *rooms, int64_t n_rooms, float *h_dev,
                 const ChebTable &ct = cheb_table(kind, J.n_taps);
                 if (ct.n_cheb == 0) { sparse = false; break; }
                 if (off < 0) {
+                    // rows padded with zeros to a multiple of 4 taps (the
+                    // kernel reads them as 16-byte vectors)
                     off = (int)tabs.size();
-                    tabs.insert(tabs.end(), ct.coef.begin(), ct.coef.end());
+                    const int tp = (J.n_taps + 3) & ~3;
+                    tabs.resize(tabs.size() + (size_t)ct.n_cheb * tp, 0.f);
+                    for (int p = 0; p < ct.n_cheb; ++p)
+                        for (int jj = 0; jj < J.n_taps; ++jj)
+                            tabs[off + (size_t)p * tp + jj] = ct.coef[(size_t)p * J.n_taps + jj];
                     seen.push_back({J.n_taps, off});
                 }
                 J.tab_offset = off;

@@ -29,7 +29,8 @@ struct alignas(16) RirJob {
     int64_t rir_len;
     int64_t h_offset;   // element offset of h[0] in the output buffer
     int32_t stat_index; // RIR index in the caller's order (statistics slot)
-    int32_t tab_offset; // offset of the filter's Chebyshev table (floats)
+    int32_t tab_offset; // offset of the filter's Chebyshev table (floats; P rows of
+                        // round4(n_taps) taps, zero-padded)
 };
 static_assert(sizeof(RirJob) == 144, "RirJob layout");
 

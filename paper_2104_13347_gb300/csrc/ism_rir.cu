@@ -51,7 +51,6 @@ namespace {
 constexpr int NT = 256;           // threads per CTA
 constexpr int NW = NT / 32;       // warps per CTA
 constexpr int CAP = 2048;         // candidate buffer (images)
-constexpr int CPT = CAP / NT;     // candidates per thread per flush
 constexpr float kEps = 0.2f;      // metres of margin in the column solve
 constexpr int PADL = 8;           // left padding of the sparse arrays (floats)
 
@@ -103,9 +102,9 @@ struct Tables {
 // the P sparse arrays, the integer-delay (delta) array, the Chebyshev table
 // and the FIR partial sums.
 struct Layout {
-    int TE, RL, CL, TPS;
+    int TE, RL, CL;
     size_t off_sq, off_hlg, off_dl, off_lx, off_ly, off_cand, off_rows, off_c,
-        off_delta, off_B, off_part, total;
+        off_delta, off_part, total;
 };
 
 __host__ __device__ inline Layout make_layout(bool sparse, int window, int max_order,
@@ -114,54 +113,50 @@ __host__ __device__ inline Layout make_layout(bool sparse, int window, int max_o
     L.TE = 2 * (2 * max_order + 1);
     L.RL = round4(window + 2 * (max_taps - 1));
     L.CL = round4(window + max_taps + 12 + PADL);
-    L.TPS = round4(max_taps);
     size_t o = 0;
     L.off_sq = o;   o = align16(o + sizeof(double) * 3 * L.TE);
     L.off_hlg = o;  o = align16(o + sizeof(float4) * 3 * L.TE);
     L.off_dl = o;   o = align16(o + sizeof(float) * 3 * L.TE);
     L.off_lx = o;   o = align16(o + sizeof(int) * L.TE);
     L.off_ly = o;   o = align16(o + sizeof(int) * L.TE);
-    // the sparse kernel's FIR partial sums (2 W floats) reuse the candidate
-    // buffer, which is idle during the FIR
-    const size_t cand_words = (sparse && 2 * window > CAP) ? (size_t)(2 * window) : (size_t)CAP;
+    // sparse kernel: the per-warp candidate stashes (32 records of 16 B) and,
+    // after the sweep, the FIR partial sums (W floats) share one buffer
+    size_t cand_words = CAP;
+    if (sparse) cand_words = (size_t)(window > NW * 32 * 4 ? window : NW * 32 * 4);
     L.off_cand = o; o = align16(o + sizeof(uint32_t) * cand_words);
-    L.off_rows = L.off_c = L.off_delta = L.off_B = o;
+    L.off_rows = L.off_c = L.off_delta = o;
     L.off_part = L.off_cand;
     if (!sparse) {
         L.off_rows = o; o = align16(o + sizeof(float) * (size_t)NW * L.RL);
     } else {
         L.off_c = o;     o = align16(o + sizeof(float) * (size_t)max_cheb * L.CL);
         L.off_delta = o; o = align16(o + sizeof(float) * (size_t)L.CL);
-        L.off_B = o;     o = align16(o + sizeof(float) * (size_t)max_cheb * L.TPS);
     }
     L.total = o;
     return L;
 }
 
+// Float-float sum (ah + al) + (bh + bl): two-sum of the high parts, the
+// low parts added to the error, renormalised.
+__device__ __forceinline__ void ff_add(float ah, float al, float bh, float bl, float &sh,
+                                       float &sl) {
+    const float s = __fadd_rn(ah, bh);
+    const float bb = __fsub_rn(s, ah);
+    float e = __fadd_rn(__fsub_rn(ah, __fsub_rn(s, bb)), __fsub_rn(bh, bb));
+    e = __fadd_rn(e, __fadd_rn(al, bl));
+    sh = __fadd_rn(s, e);
+    sl = __fsub_rn(e, __fsub_rn(sh, s));
+}
+
 // Delay split of one image (Sec. II.A: the delay of every image must keep
-// its sub-sample precision).  Returns the integer part k (rint, ties to
-// even, for Hann; floor for Lagrange) and the fraction in FP32, plus d.
+// its sub-sample precision) from d^2 = Dh + Dl in float-float.  Returns the
+// integer part k (rint, ties to even, for Hann; floor for Lagrange) and the
+// fraction in FP32, plus d.  sqx, sqy, sqz: the FP64 squared axis offsets,
+// read only on the exact path.
 template <int KIND>
-__device__ __forceinline__ void delay_split(const Tables &T, int TE, int ix, int iy, int iz,
-                                            float qh, float ql, double q, int &k_out,
-                                            float &f_out, float &d_out, float &g_out) {
-    const float4 X = T.hlg[ix], Y = T.hlg[TE + iy], Z = T.hlg[2 * TE + iz];
-    const float xh = X.x, xl = X.y, yh = Y.x, yl = Y.y, zh = Z.x, zl = Z.y;
-    g_out = X.z * Y.z * Z.z;
-    // d^2 = x + y + z in float-float (two-sum with renormalisation).
-    float s1 = __fadd_rn(xh, yh);
-    float bb = __fsub_rn(s1, xh);
-    float e1 = __fadd_rn(__fsub_rn(xh, __fsub_rn(s1, bb)), __fsub_rn(yh, bb));
-    e1 = __fadd_rn(e1, __fadd_rn(xl, yl));
-    float t1 = __fadd_rn(s1, e1);
-    e1 = __fsub_rn(e1, __fsub_rn(t1, s1));
-    s1 = t1;
-    float s2 = __fadd_rn(s1, zh);
-    bb = __fsub_rn(s2, s1);
-    float e2 = __fadd_rn(__fsub_rn(s1, __fsub_rn(s2, bb)), __fsub_rn(zh, bb));
-    e2 = __fadd_rn(e2, __fadd_rn(e1, zl));
-    const float Dh = __fadd_rn(s2, e2);
-    const float Dl = __fsub_rn(e2, __fsub_rn(Dh, s2));
+__device__ __forceinline__ void split_d2(float Dh, float Dl, const double *sqx, const double *sqy,
+                                         const double *sqz, float qh, float ql, double q,
+                                         int &k_out, float &f_out, float &d_out) {
     // sqrt: FP32 estimate plus one Newton correction in float-float.
     const float r = rsqrtf(Dh);
     const float s0 = __fmul_rn(Dh, r);
@@ -192,7 +187,7 @@ __device__ __forceinline__ void delay_split(const Tables &T, int TE, int ix, int
     }
     if (near) {
         // Exact path: the definition's FP64 operations in its order.
-        const double d2 = __dadd_rn(__dadd_rn(T.sq[ix], T.sq[TE + iy]), T.sq[2 * TE + iz]);
+        const double d2 = __dadd_rn(__dadd_rn(*sqx, *sqy), *sqz);
         const double d = __dsqrt_rn(d2);
         const double tau = __dmul_rn(d, q);
         const double kd = (KIND == ISM_FD_HANN_SINC) ? rint(tau) : floor(tau);
@@ -202,6 +197,21 @@ __device__ __forceinline__ void delay_split(const Tables &T, int TE, int ix, int
     k_out = (int)k;
     f_out = f;
     d_out = dh;
+}
+
+// Delay split of image (ix, iy, iz) from the tables; also returns the wall
+// damping product g.
+template <int KIND>
+__device__ __forceinline__ void delay_split(const Tables &T, int TE, int ix, int iy, int iz,
+                                            float qh, float ql, double q, int &k_out,
+                                            float &f_out, float &d_out, float &g_out) {
+    const float4 X = T.hlg[ix], Y = T.hlg[TE + iy], Z = T.hlg[2 * TE + iz];
+    g_out = X.z * Y.z * Z.z;
+    float s1, e1, Dh, Dl;
+    ff_add(X.x, X.y, Y.x, Y.y, s1, e1);
+    ff_add(s1, e1, Z.x, Z.y, Dh, Dl);
+    split_d2<KIND>(Dh, Dl, &T.sq[ix], &T.sq[TE + iy], &T.sq[2 * TE + iz], qh, ql, q, k_out, f_out,
+                   d_out);
 }
 
 // Per-item constants (identical in every thread of the CTA).
@@ -304,14 +314,20 @@ struct Col {
 
 __device__ __forceinline__ Col column_solve(const Tables &T, int TE, const Item &it,
                                             const int *s_lx, const int *s_ly, int nLY,
-                                            long long c, long long n_cols) {
+                                            int c, int n_cols) {
     const int N = it.N;
     Col r{1, 0, 1, 0, 0, 0, 0};
     if (c >= n_cols) return r;
-    r.wz = (int)(c & 1);
-    const long long t = c >> 1;
-    r.ix = s_lx[(int)(t / nLY)];
-    r.iy = s_ly[(int)(t % nLY)];
+    r.wz = c & 1;
+    // (x, y) list positions of column pair t = c / 2 (t < 2^20): quotient
+    // by an FP32 reciprocal, corrected to the exact integer division
+    const int t = c >> 1;
+    int xi = (int)((float)t * __frcp_rn((float)nLY));
+    int yi = t - xi * nLY;
+    if (yi < 0) { --xi; yi += nLY; }
+    else if (yi >= nLY) { ++xi; yi -= nLY; }
+    r.ix = s_lx[xi];
+    r.iy = s_ly[yi];
     const float dx = T.dl[r.ix], dy = T.dl[TE + r.iy];
     const float rho2 = dx * dx + dy * dy;
     if (rho2 > it.dhe2) return r;
@@ -368,10 +384,10 @@ __device__ __forceinline__ void column_sweep(const Tables &T, int TE, const Item
                                              const int *s_lx, const int *s_ly, int nLX, int nLY,
                                              int *s_scan, uint32_t *s_cand, Flush &flush) {
     const int N = it.N, tid = threadIdx.x;
-    const long long n_cols = (long long)nLX * nLY * 2;
+    const int n_cols = nLX * nLY * 2;
     int n_cand = 0;  // block-uniform
-    for (long long cb = 0; cb < n_cols; cb += NT) {
-        const long long c = cb + tid;
+    for (int cb = 0; cb < n_cols; cb += NT) {
+        const int c = cb + tid;
         const Col col = column_solve(T, TE, it, s_lx, s_ly, nLY, c, n_cols);
         int total;
         const int off = block_scan(col.count(), s_scan, total);
@@ -393,22 +409,36 @@ __device__ __forceinline__ void column_sweep(const Tables &T, int TE, const Item
     if (n_cand > 0) flush(n_cand);
 }
 
-// Warp-independent column sweep: warp w takes column batches w, w + NW,
-// ... (32 columns each, one per lane), appends their candidates to its own
-// ring buffer (WCAP slots) and hands them to proc(code, valid) 32 at a time,
-// one per lane.  No block-wide barrier is involved.
-constexpr int WCAP = CAP / NW;  // 256 slots per warp
-
+// Warp-independent column sweep with lane-per-candidate expansion.  Warp w
+// takes column batches w, w + NW, ... (32 columns each, one per lane).  Each
+// lane solves its column and, if the column has candidates, its float-float
+// rho^2 = x^2 + y^2 and damping product g_xy once.  A warp-wide scan of the
+// counts numbers the batch's candidates; candidate g goes to lane g mod 32,
+// which finds its column by binary search over the inclusive counts and
+// fetches the column's data with shuffles (two packed words and three
+// floats).  Batches are always 32 candidates wide: the last < 32 candidates
+// of a column batch wait in a per-warp stash of (rho_h, rho_l, g_xy, code)
+// records for the next one.  proc(rho_h, rho_l, g_xy, code, valid) gets one
+// candidate per lane; code = iz | ix << 12 | iy << 22 (iz: absolute index of
+// the z table entry).  No block-wide barrier is involved.
 template <class Proc>
-__device__ __forceinline__ void warp_sweep(const Tables &T, int TE, const Item &it,
-                                           const int *s_lx, const int *s_ly, int nLX, int nLY,
-                                           uint32_t *ring, Proc &proc) {
+__device__ __forceinline__ void warp_expand(const Tables &T, int TE, const Item &it,
+                                            const int *s_lx, const int *s_ly, int nLX, int nLY,
+                                            float4 *stash, Proc &proc) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const long long n_cols = (long long)nLX * nLY * 2;
-    int head = 0, tail = 0;  // warp-uniform ring positions
-    for (long long cb = (long long)warp * 32; cb < n_cols; cb += NT) {
+    const int n_cols = nLX * nLY * 2;  // <= 2 * 802^2
+    const int N = it.N;
+    int L = 0;  // warp-uniform stash count, < 32
+    for (int cb = warp * 32; cb < n_cols; cb += NT) {
         const Col col = column_solve(T, TE, it, s_lx, s_ly, nLY, cb + lane, n_cols);
-        const int cnt = col.count();
+        const int na = max(col.hi_a - col.lo_a + 1, 0), nb = max(col.hi_b - col.lo_b + 1, 0);
+        const int cnt = na + nb;
+        float Rh = 0.f, Rl = 0.f, gxy = 0.f;
+        if (cnt > 0) {
+            const float4 X = T.hlg[col.ix], Y = T.hlg[TE + col.iy];
+            ff_add(X.x, X.y, Y.x, Y.y, Rh, Rl);
+            gxy = X.z * Y.z;
+        }
         int incl = cnt;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -416,25 +446,61 @@ __device__ __forceinline__ void warp_sweep(const Tables &T, int TE, const Item &
             if (lane >= o) incl += y;
         }
         const int total = __shfl_sync(0xffffffffu, incl, 31);
-        const int off = incl - cnt;
-        for (int g = 0; g < total;) {
-            const int take = min(WCAP - (tail - head), total - g);
-            column_emit(col, it.N, off, g, g + take, ring, tail - g, WCAP - 1);
-            __syncwarp();
-            tail += take;
-            g += take;
-            while (tail - head >= 32) {
-                const uint32_t cd = ring[(head + lane) & (WCAP - 1)];
-                head += 32;
-                proc(cd, true);
+        if (total == 0) continue;
+        // packed column data: (iz base, ix, iy) and (first candidate index,
+        // size of interval a, hole between the intervals); all fields fit
+        // (iz < 3 TE <= 2406, ix, iy < 1024, total <= 32 (2N+1) < 2^14,
+        // na, gap <= 2N+1 <= 401)
+        const int zbase = 2 * TE + col.wz * (2 * N + 1) + N + col.lo_a;
+        const int gap = nb > 0 ? col.lo_b - (col.lo_a + na) : 0;
+        const uint32_t k1 = cnt > 0 ? ((uint32_t)zbase | ((uint32_t)col.ix << 12) |
+                                       ((uint32_t)col.iy << 22))
+                                    : 0u;
+        const uint32_t k2 = (uint32_t)(incl - cnt) | ((uint32_t)na << 14) | ((uint32_t)gap << 23);
+        auto fetch = [&](int g, float &rh, float &rl, float &gg, uint32_t &code) {
+            int c = 0;  // number of lanes whose inclusive count is <= g
+#pragma unroll
+            for (int st = 16; st >= 1; st >>= 1) {
+                const int v = __shfl_sync(0xffffffffu, incl, c + st - 1);
+                if (v <= g) c += st;
             }
+            const uint32_t a1 = __shfl_sync(0xffffffffu, k1, c);
+            const uint32_t a2 = __shfl_sync(0xffffffffu, k2, c);
+            rh = __shfl_sync(0xffffffffu, Rh, c);
+            rl = __shfl_sync(0xffffffffu, Rl, c);
+            gg = __shfl_sync(0xffffffffu, gxy, c);
+            const int r = g - (int)(a2 & 0x3fffu);
+            const int iz = (int)(a1 & 4095u) + r + (r >= (int)((a2 >> 14) & 511u) ? (int)(a2 >> 23) : 0);
+            code = (a1 & ~4095u) | (uint32_t)iz;
+        };
+        int pos = 0;
+        while (L + (total - pos) >= 32) {
+            float rh, rl, gg;
+            uint32_t code;
+            fetch(max(pos + lane - L, 0), rh, rl, gg, code);
+            if (lane < L) {
+                const float4 sv = stash[lane];
+                rh = sv.x; rl = sv.y; gg = sv.z; code = __float_as_uint(sv.w);
+            }
+            pos += 32 - L;
+            L = 0;
+            proc(rh, rl, gg, code, true);
+        }
+        const int rem = total - pos;
+        if (rem > 0) {
+            float rh, rl, gg;
+            uint32_t code;
+            fetch(min(pos + lane, total - 1), rh, rl, gg, code);
             __syncwarp();
+            if (lane < rem) stash[L + lane] = make_float4(rh, rl, gg, __uint_as_float(code));
+            __syncwarp();
+            L += rem;
         }
     }
-    if (tail > head) {
-        const bool v = lane < tail - head;
-        const uint32_t cd = v ? ring[(head + lane) & (WCAP - 1)] : 0u;
-        proc(cd, v);
+    if (L > 0) {
+        const bool v = lane < L;
+        const float4 sv = v ? stash[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+        proc(sv.x, sv.y, sv.z, __float_as_uint(sv.w), v);
     }
     __syncwarp();
 }
@@ -462,6 +528,35 @@ __device__ __forceinline__ bool eval_candidate(const Tables &T, int TE, const It
     const int first = max(kb, 0);
     if (first < min(kb + it.n_taps, it.Lh32) && first >= it.w0 && first < it.w0 + it.W)
         ++my_contrib;
+    return true;
+}
+
+// Evaluates one column-expanded candidate: delay split from the column's
+// rho^2 and the z table, window test, gain, statistics.  Returns false if
+// the image's taps miss the window.
+template <int KIND, bool STATS>
+__device__ __forceinline__ bool eval_expanded(const Tables &T, int TE, const Item &it, float Rh,
+                                              float Rl, float gxy, uint32_t code, int &kb,
+                                              float &f, float &a, unsigned &my_taps,
+                                              unsigned &my_contrib) {
+    const int iz = code & 4095u, ix = (code >> 12) & 1023u, iy = code >> 22;
+    const float4 Z = T.hlg[iz];
+    float Dh, Dl;
+    ff_add(Rh, Rl, Z.x, Z.y, Dh, Dl);
+    int k;
+    float d;
+    split_d2<KIND>(Dh, Dl, &T.sq[ix], &T.sq[TE + iy], &T.sq[iz], it.qh, it.ql, it.q, k, f, d);
+    kb = (KIND == ISM_FD_HANN_SINC) ? k - it.H : k - (it.P - 1) / 2;
+    if (kb < it.kb_lo32 || kb > it.kb_hi32) return false;
+    a = (gxy * Z.z) * __frcp_rn(12.566370614359172f * d);
+    if (STATS) {
+        const int lo = max(kb, max(it.w0, 0));
+        const int hi = min(kb + it.n_taps, it.wend);
+        if (hi > lo) my_taps += (unsigned)(hi - lo);
+        const int first = max(kb, 0);
+        if (first < min(kb + it.n_taps, it.Lh32) && first >= it.w0 && first < it.w0 + it.W)
+            ++my_contrib;
+    }
     return true;
 }
 
@@ -646,14 +741,14 @@ k_ism_taps(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int max
 // ===========================================================================
 // k_ism_sparse: sparse integer-delay arrays + Chebyshev FIR
 // ===========================================================================
-template <int KIND>
-__global__ void __launch_bounds__(NT, 3)
+template <int KIND, bool STATS>
+__global__ void __launch_bounds__(NT, 4)
 k_ism_sparse(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int max_order,
              int max_taps, int max_cheb, const float *__restrict__ tabs, float *__restrict__ h,
              long long *__restrict__ stats, unsigned int *__restrict__ counter) {
     extern __shared__ __align__(16) unsigned char smem[];
     const Layout Lay = make_layout(true, W, max_order, max_taps, max_cheb);
-    const int TE = Lay.TE, CL = Lay.CL, TPS = Lay.TPS;
+    const int TE = Lay.TE, CL = Lay.CL;
     Tables T;
     T.sq = (double *)(smem + Lay.off_sq);
     T.hlg = (float4 *)(smem + Lay.off_hlg);
@@ -663,9 +758,7 @@ k_ism_sparse(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int m
     uint32_t *s_cand = (uint32_t *)(smem + Lay.off_cand);
     float *s_c = (float *)(smem + Lay.off_c);
     float *s_delta = (float *)(smem + Lay.off_delta);
-    float *s_B = (float *)(smem + Lay.off_B);
     float *s_part = (float *)(smem + Lay.off_part);
-    __shared__ int s_scan[NW];
     __shared__ int s_item, s_nl[2];
     __shared__ unsigned long long s_stat[2];
 
@@ -687,11 +780,6 @@ k_ism_sparse(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int m
         build_tables(J, T, TE, it);
         const int Pc = J.n_cheb;
         const int n_taps = it.n_taps;
-        // the job's Chebyshev table, zero-padded to TPS taps
-        for (int e = tid; e < max_cheb * TPS; e += NT) {
-            const int p = e / TPS, j = e - p * TPS;
-            s_B[e] = (p < Pc && j < n_taps) ? tabs[J.tab_offset + p * n_taps + j] : 0.f;
-        }
         if (tid < 2) s_stat[tid] = 0ull;
         __syncthreads();
         build_lists(T, TE, it, s_lx, s_ly, s_nl);
@@ -702,12 +790,13 @@ k_ism_sparse(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int m
         const int OFF = (4 - (n_taps - 1) % 4) % 4;
         const int POS0 = OFF + PADL - (int)it.kb_lo;
         const int jdelta = (KIND == ISM_FD_HANN_SINC) ? it.H : (it.P - 1) / 2;
-        unsigned long long my_contrib = 0, my_taps = 0;
+        unsigned my_contrib = 0, my_taps = 0;
 
-        auto proc = [&](uint32_t cd, bool valid) {
+        auto proc = [&](float Rh, float Rl, float gxy, uint32_t code, bool valid) {
             int kb;
             float f, a;
-            if (!valid || !eval_candidate<KIND>(T, TE, it, cd, kb, f, a, my_taps, my_contrib))
+            if (!valid || !eval_expanded<KIND, STATS>(T, TE, it, Rh, Rl, gxy, code, kb, f, a,
+                                                      my_taps, my_contrib))
                 return;
             const int pos = kb + POS0;
             if (f == 0.f) {  // integer delay: exact Kronecker delta
@@ -725,60 +814,75 @@ k_ism_sparse(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int m
                 t1 = t2;
             }
         };
-        warp_sweep(T, TE, it, s_lx, s_ly, nLX, nLY, s_cand + (tid >> 5) * WCAP, proc);
+        warp_expand(T, TE, it, s_lx, s_ly, nLX, nLY,
+                    reinterpret_cast<float4 *>(s_cand) + (tid >> 5) * 32, proc);
         __syncthreads();
 
         // FIR: h[w0+i] = sum_p sum_j B[p][j] c_p[kb = w0+i-j] + delta.  Threads
         // 0..127 take p in [0, ceil(P/2)), threads 128..255 the rest; each owns
         // 8 consecutive outputs and walks the taps 4 at a time with a sliding
-        // 12-value window of c in registers (128-bit shared loads).
+        // 12-value window of c in registers (128-bit shared loads).  The
+        // table B (rows padded to a multiple of 4 taps with zeros) is read
+        // through the read-only cache; all lanes load the same words.
         {
             const int half = tid >> 7, gt = tid & 127;
             const int ph = (Pc + 1) / 2;
             const int p_lo = half ? ph : 0, p_hi = half ? Pc : ph;
             const int TPj = round4(n_taps);
-            for (int g = gt; g < W / 8; g += 128) {
+            const float *Bj = tabs + J.tab_offset;
+            for (int g0 = 0; g0 < W / 8; g0 += 128) {
+                const int g = g0 + gt;
                 float acc[8];
 #pragma unroll
                 for (int q = 0; q < 8; ++q) acc[q] = 0.f;
-                const int base = 8 * g + n_taps - 1 + OFF + PADL;  // multiple of 4
-                for (int p = p_lo; p < p_hi; ++p) {
-                    const float *cp = s_c + p * CL;
-                    const float *bp = s_B + p * TPS;
-                    float win[12];
+                if (g < W / 8) {
+                    const int base = 8 * g + n_taps - 1 + OFF + PADL;  // multiple of 4
+                    for (int p = p_lo; p < p_hi; ++p) {
+                        const float *cp = s_c + p * CL;
+                        const float4 *bp = reinterpret_cast<const float4 *>(Bj + p * TPj);
+                        float win[12];
 #pragma unroll
-                    for (int v = 0; v < 3; ++v) {
-                        const float4 w4 = *reinterpret_cast<const float4 *>(cp + base - 4 + 4 * v);
-                        win[4 * v] = w4.x; win[4 * v + 1] = w4.y;
-                        win[4 * v + 2] = w4.z; win[4 * v + 3] = w4.w;
-                    }
-                    for (int jb = 0; jb < TPj; jb += 4) {
-                        const float4 b4 = *reinterpret_cast<const float4 *>(bp + jb);
-                        const float bv[4] = {b4.x, b4.y, b4.z, b4.w};
-                        // c at position base + q - jb - jj is win[4 + q - jj]
-#pragma unroll
-                        for (int jj = 0; jj < 4; ++jj)
-#pragma unroll
-                            for (int q = 0; q < 8; ++q) acc[q] = fmaf(bv[jj], win[4 + q - jj], acc[q]);
-                        if (jb + 4 < TPj) {
-#pragma unroll
-                            for (int v = 11; v >= 4; --v) win[v] = win[v - 4];
+                        for (int v = 0; v < 3; ++v) {
                             const float4 w4 =
-                                *reinterpret_cast<const float4 *>(cp + base - jb - 8);
-                            win[0] = w4.x; win[1] = w4.y; win[2] = w4.z; win[3] = w4.w;
+                                *reinterpret_cast<const float4 *>(cp + base - 4 + 4 * v);
+                            win[4 * v] = w4.x; win[4 * v + 1] = w4.y;
+                            win[4 * v + 2] = w4.z; win[4 * v + 3] = w4.w;
+                        }
+                        for (int jb = 0; jb < TPj; jb += 4) {
+                            const float4 b4 = __ldg(bp + (jb >> 2));
+                            const float bv[4] = {b4.x, b4.y, b4.z, b4.w};
+                            // c at position base + q - jb - jj is win[4 + q - jj]
+#pragma unroll
+                            for (int jj = 0; jj < 4; ++jj)
+#pragma unroll
+                                for (int q = 0; q < 8; ++q)
+                                    acc[q] = fmaf(bv[jj], win[4 + q - jj], acc[q]);
+                            if (jb + 4 < TPj) {
+#pragma unroll
+                                for (int v = 11; v >= 4; --v) win[v] = win[v - 4];
+                                const float4 w4 =
+                                    *reinterpret_cast<const float4 *>(cp + base - jb - 8);
+                                win[0] = w4.x; win[1] = w4.y; win[2] = w4.z; win[3] = w4.w;
+                            }
                         }
                     }
-                }
+                    if (half) {
 #pragma unroll
-                for (int q = 0; q < 8; ++q) s_part[half * W + 8 * g + q] = acc[q];
+                        for (int q = 0; q < 8; ++q) s_part[8 * g + q] = acc[q];
+                    }
+                }
+                __syncthreads();
+                if (!half && g < W / 8) {
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) s_part[8 * g + q] += acc[q];
+                }
             }
         }
         __syncthreads();
         float *hout = h + J.h_offset;
         for (int i = tid; i < W; i += NT) {
             const long long n = (long long)it.w0 + i;
-            const float v = s_part[i] + s_part[W + i] +
-                            s_delta[i + n_taps - 1 - jdelta + OFF + PADL];
+            const float v = s_part[i] + s_delta[i + n_taps - 1 - jdelta + OFF + PADL];
             if (n < it.Lh) hout[n] = v;
         }
         __syncthreads();
@@ -813,10 +917,10 @@ int launch_direct_t(const RirLaunch &L, cudaStream_t stream) {
     return ISM_OK;
 }
 
-template <int KIND>
+template <int KIND, bool STATS>
 int launch_sparse_t(const RirLaunch &L, cudaStream_t stream) {
     const Layout Lay = make_layout(true, L.window, L.max_order, L.max_taps, L.max_cheb);
-    auto kern = k_ism_sparse<KIND>;
+    auto kern = k_ism_sparse<KIND, STATS>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)Lay.total);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_ism_sparse)");
@@ -866,8 +970,14 @@ int launch_rir(const RirLaunch &L, cudaStream_t stream) {
 
 int launch_rir_sparse(const RirLaunch &L, cudaStream_t stream) {
     if (L.window % 8 != 0) return fail(ISM_ERR_INVALID_ARG, "window must be a multiple of 8");
-    if (L.fd_kind == ISM_FD_LAGRANGE) return launch_sparse_t<ISM_FD_LAGRANGE>(L, stream);
-    return launch_sparse_t<ISM_FD_HANN_SINC>(L, stream);
+    if (L.max_cheb < 1 || L.max_cheb > kMaxCheb)
+        return fail(ISM_ERR_INVALID_ARG, "Chebyshev term count out of range");
+    const bool st = L.stats_dev != nullptr;  // statistics compiled out when not asked for
+    if (L.fd_kind == ISM_FD_LAGRANGE)
+        return st ? launch_sparse_t<ISM_FD_LAGRANGE, true>(L, stream)
+                  : launch_sparse_t<ISM_FD_LAGRANGE, false>(L, stream);
+    return st ? launch_sparse_t<ISM_FD_HANN_SINC, true>(L, stream)
+              : launch_sparse_t<ISM_FD_HANN_SINC, false>(L, stream);
 }
 
 }  // namespace ism
