@@ -741,6 +741,29 @@ k_ism_taps(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int max
 // ===========================================================================
 // k_ism_sparse: sparse integer-delay arrays + Chebyshev FIR
 // ===========================================================================
+// Fixed-point sparse arrays.  Per window, gains are scaled so that the
+// largest gain an image reaching the window can have, a_max = 1/(4 pi
+// d_floor) (d_floor: the window's first delay, or the direct path, which no
+// image undercuts for points inside the box; beta <= 1), maps to kFix0 =
+// 2^24.  Term p of an image is rounded to an int32 and added with a native
+// u32 shared-memory atomic: an FP32 shared atomic costs a load and a
+// compare-and-swap on this GPU, and shared-memory wavefronts bound this
+// kernel.  c_0 = sum of a >= |c_p| for every p (|T_p| <= 1), so while no c_0
+// entry (nor an integer-delay entry, also a sum of gains) passes kFixLimit
+// = 2^31 - 2^25, every array ends at its exact integer sum in int32 range
+// (wrap-around of intermediate sums cancels modulo 2^32).  The c_0 update
+// returns the old value; a sum past the limit flags the window, which is
+// redone at a 2^7 coarser scale (so the quantum stays near 2^-24 of the
+// largest sum).  The fourth attempt takes the scale at which n_bound images
+// at a_max stay below the limit: one delay bucket (one sample) holds at most
+// n_bound = 4 C (l / (2 Lz) + 1) images, C = (2 (2N+1))^2 lattice columns,
+// each meeting the bucket's spherical shell in at most two z-intervals of
+// length l <= sqrt(2 d t + t^2) per z-parity (t: the bucket's width in
+// metres, d: the window's largest distance).  Integer sums do not depend on
+// the order of the additions: the sparse path is bitwise reproducible.
+constexpr double kFix0 = 16777216.0;           // 2^24
+constexpr uint32_t kFixLimit = 0x7e000000u;    // 2^31 - 2^25
+
 template <int KIND, bool STATS>
 __global__ void __launch_bounds__(NT, 4)
 k_ism_sparse(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int max_order,
@@ -759,12 +782,15 @@ k_ism_sparse(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int m
     float *s_c = (float *)(smem + Lay.off_c);
     float *s_delta = (float *)(smem + Lay.off_delta);
     float *s_part = (float *)(smem + Lay.off_part);
-    __shared__ int s_item, s_nl[2];
+    __shared__ int s_item, s_nl[2], s_ovf;
     __shared__ unsigned long long s_stat[2];
 
     const int tid = threadIdx.x;
-    for (int i = tid; i < max_cheb * CL; i += NT) s_c[i] = 0.f;
-    for (int i = tid; i < CL; i += NT) s_delta[i] = 0.f;
+    uint32_t *s_cq = (uint32_t *)s_c;      // the same words before conversion
+    uint32_t *s_dq = (uint32_t *)s_delta;
+    for (int i = tid; i < max_cheb * CL; i += NT) s_cq[i] = 0u;
+    for (int i = tid; i < CL; i += NT) s_dq[i] = 0u;
+    if (tid == 0) s_ovf = 0;
 
     const long long n_items = (long long)n_rirs * wmax;
     for (;;) {
@@ -781,6 +807,7 @@ k_ism_sparse(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int m
         const int Pc = J.n_cheb;
         const int n_taps = it.n_taps;
         if (tid < 2) s_stat[tid] = 0ull;
+        if (tid == 0) s_ovf = 0;
         __syncthreads();
         build_lists(T, TE, it, s_lx, s_ly, s_nl);
         __syncthreads();
@@ -791,7 +818,27 @@ k_ism_sparse(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int m
         const int POS0 = OFF + PADL - (int)it.kb_lo;
         const int jdelta = (KIND == ISM_FD_HANN_SINC) ? it.H : (it.P - 1) / 2;
         unsigned my_contrib = 0, my_taps = 0;
-
+        // Fixed-point accumulation (see kFix0).  d_floor bounds from below
+        // the distance of every image whose taps reach this window.
+        double d_floor, n_bound;
+        {
+            const double dx = J.src[0] - J.mic[0], dy = J.src[1] - J.mic[1],
+                         dz = J.src[2] - J.mic[2];
+            const double d_dir = sqrt(dx * dx + dy * dy + dz * dz);
+            double tau_lo, tau_hi;
+            if (KIND == ISM_FD_HANN_SINC) {
+                tau_lo = (double)(it.kb_lo + it.H) - 0.5;
+                tau_hi = (double)(it.kb_hi + it.H) + 0.5;
+            } else {
+                tau_lo = (double)(it.kb_lo + (it.P - 1) / 2);
+                tau_hi = (double)(it.kb_hi + (it.P + 1) / 2);
+            }
+            d_floor = fmax(d_dir, tau_lo / it.q) * (1.0 - 1e-6);
+            const double tb = (1.0 + 1e-5) / it.q, dmax = tau_hi / it.q + tb;
+            const double ncol = 4.0 * (2 * it.N + 1) * (double)(2 * it.N + 1);
+            n_bound = 4.0 * ncol * (sqrt(2.0 * dmax * tb + tb * tb) / (2.0 * J.dims[2]) + 1.0);
+        }
+        float S = 0.f;
         auto proc = [&](float Rh, float Rl, float gxy, uint32_t code, bool valid) {
             int kb;
             float f, a;
@@ -799,23 +846,49 @@ k_ism_sparse(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int m
                                                       my_taps, my_contrib))
                 return;
             const int pos = kb + POS0;
-            if (f == 0.f) {  // integer delay: exact Kronecker delta
-                atomicAdd(&s_delta[pos], a);
-                return;
+            const float as = a * S;
+            const uint32_t q0 = __float2uint_rn(as);
+            uint32_t *c0 = (f == 0.f) ? s_dq : s_cq;  // integer delay: exact Kronecker delta
+            const uint32_t old = atomicAdd(&c0[pos], q0);
+            if (f != 0.f) {
+                const float x = (KIND == ISM_FD_HANN_SINC) ? 2.f * f : 2.f * f - 1.f;
+                float t0 = 1.f, t1 = x;
+                if (Pc > 1) atomicAdd(&s_cq[CL + pos], (uint32_t)__float2int_rn(as * x));
+                for (int p = 2; p < Pc; ++p) {
+                    const float t2 = fmaf(2.f * x, t1, -t0);
+                    atomicAdd(&s_cq[p * CL + pos], (uint32_t)__float2int_rn(as * t2));
+                    t0 = t1;
+                    t1 = t2;
+                }
             }
-            const float x = (KIND == ISM_FD_HANN_SINC) ? 2.f * f : 2.f * f - 1.f;
-            float t0 = 1.f, t1 = x;
-            atomicAdd(&s_c[pos], a);
-            if (Pc > 1) atomicAdd(&s_c[CL + pos], a * x);
-            for (int p = 2; p < Pc; ++p) {
-                const float t2 = fmaf(2.f * x, t1, -t0);
-                atomicAdd(&s_c[p * CL + pos], a * t2);
-                t0 = t1;
-                t1 = t2;
-            }
+            if (old + q0 > kFixLimit) s_ovf = 1;  // this window is redone at a coarser scale
         };
-        warp_expand(T, TE, it, s_lx, s_ly, nLX, nLY,
-                    reinterpret_cast<float4 *>(s_cand) + (tid >> 5) * 32, proc);
+        float invS = 0.f;
+        for (int attempt = 0;; ++attempt) {
+            // scale: a_max = 1 / (4 pi d_floor) maps to kFix0, then 2^7 less per
+            // retry; the fourth attempt takes the scale at which n_bound images
+            // at a_max cannot exceed the limit
+            double sc = kFix0 * 12.566370614359172 * d_floor;
+            if (attempt < 3) sc = ldexp(sc, -7 * attempt);
+            else sc = fmin(ldexp(sc, -21), 0.5 * (double)kFixLimit * 12.566370614359172 * d_floor / n_bound);
+            S = (float)sc;
+            invS = (float)(1.0 / sc);
+            my_contrib = 0;
+            my_taps = 0;
+            warp_expand(T, TE, it, s_lx, s_ly, nLX, nLY,
+                        reinterpret_cast<float4 *>(s_cand) + (tid >> 5) * 32, proc);
+            __syncthreads();
+            const int ovf = s_ovf;
+            if (!ovf || attempt >= 3) break;
+            __syncthreads();
+            if (tid == 0) s_ovf = 0;
+            for (int i = tid; i < Pc * CL; i += NT) s_cq[i] = 0u;
+            for (int i = tid; i < CL; i += NT) s_dq[i] = 0u;
+            __syncthreads();
+        }
+        // fixed point -> float, in place
+        for (int i = tid; i < Pc * CL; i += NT) s_c[i] = (float)(int)s_cq[i] * invS;
+        for (int i = tid; i < CL; i += NT) s_delta[i] = (float)s_dq[i] * invS;
         __syncthreads();
 
         // FIR: h[w0+i] = sum_p sum_j B[p][j] c_p[kb = w0+i-j] + delta.  Threads
