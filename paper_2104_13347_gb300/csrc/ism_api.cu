@@ -452,7 +452,7 @@ int ism_convolve_batch(const ism_conv_job *jobs, int64_t n_jobs, const float *h_
     cudaStream_t stream = (cudaStream_t)stream_v;
     std::vector<ConvJob> cj(n_jobs);
     bool any_noise = false;
-    int64_t max_elems = 0;
+    int64_t n_part = 0;
     for (int64_t i = 0; i < n_jobs; ++i) {
         const ism_conv_job &J = jobs[i];
         if (J.n_mics < 1 || J.rir_len < 1 || J.src_len < 1 || J.h_offset < 0 ||
@@ -474,11 +474,14 @@ int ism_convolve_batch(const ism_conv_job *jobs, int64_t n_jobs, const float *h_
                 return fail(ISM_ERR_INVALID_ARG, "job " + std::to_string(i) + ": snr must be finite or NaN");
             any_noise = true;
         }
-        max_elems = std::max(max_elems, (int64_t)J.n_mics * c.y_len);
+        const int64_t nt = (c.y_len + kConvTT - 1) / kConvTT;
+        if ((J.n_mics + (int64_t)kConvMG - 1) / kConvMG * nt > 0x3fffffff)
+            return fail(ISM_ERR_INVALID_ARG, "job " + std::to_string(i) + ": too many tiles");
+        c.part_offset = n_part;
+        n_part += conv_partials_per_job(J.n_mics, c.y_len);
     }
-    const int n_part = any_noise ? noise_partials_per_job(max_elems) : 0;
     const size_t jb = cj.size() * sizeof(ConvJob);
-    const size_t pb = (size_t)n_part * n_jobs * sizeof(double);
+    const size_t pb = any_noise ? (size_t)n_part * sizeof(double) : 0;
     void *scr = nullptr;
     if (int st = scratch_alloc(&scr, jb + 256 + pb, stream)) return st;
     ConvLaunch L;
@@ -492,8 +495,7 @@ int ism_convolve_batch(const ism_conv_job *jobs, int64_t n_jobs, const float *h_
     L.precision = precision;
     L.seed = seed;
     L.any_noise = any_noise;
-    L.noise_partials_dev = (double *)((char *)scr + jb + 256);
-    L.n_partials_per_job = n_part;
+    L.noise_partials_dev = any_noise ? (double *)((char *)scr + jb + 256) : nullptr;
     int st = upload_async(scr, cj.data(), jb, stream);
     if (!st) {
         if (precision == ISM_BF16X3) st = launch_conv_bf16x3(L, stream);

@@ -5,7 +5,9 @@
 //   y_m[t] = sum_k h_m[k] s[t - k],  t in [0, Ts + Lh - 1).
 // Noise (Sec. III.A: Gaussian noise at a drawn SNR):
 //   y_m[t] += sigma z,  sigma^2 = mean(y^2 over the room's mics and samples)
-//   / 10^(snr/10), z from SplitMix64 counters and Box--Muller.
+//   / 10^(snr/10), z from SplitMix64 counters and Box--Muller.  The sums of
+//   y^2 come from the convolution kernels' epilogues, one partial per tile
+//   (float-float per thread, FP64 across threads, fixed order).
 //
 // K2b layout: one CTA per (room, group of 8 mics, tile of 2048 outputs);
 // each thread owns 8 consecutive outputs of all 8 mics (64 accumulators),
@@ -17,6 +19,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "ism_internal.h"
@@ -29,6 +32,7 @@ constexpr int OPT = 8;           // outputs per thread
 constexpr int TT = CT * OPT;     // outputs per tile (2048)
 constexpr int MG = 8;            // mics per CTA
 constexpr int KC = 256;          // taps per shared-memory chunk
+static_assert(TT == kConvTT && MG == kConvMG, "tile shape of the noise partials");
 
 struct Tile {
     int job;
@@ -38,7 +42,8 @@ struct Tile {
 
 __global__ void __launch_bounds__(CT, 2)
 k_conv_f32(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles,
-           const float *__restrict__ h, const float *__restrict__ src, float *__restrict__ y) {
+           const float *__restrict__ h, const float *__restrict__ src, float *__restrict__ y,
+           double *__restrict__ part) {
     __shared__ __align__(16) float s_src[TT + KC + 16];
     __shared__ __align__(16) float s_h[MG][KC];
     const Tile tl = tiles[blockIdx.x];
@@ -101,60 +106,55 @@ k_conv_f32(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles,
     }
     const int64_t ylen = J.y_len;
     float *yb = y + J.y_offset + (int64_t)tl.mic0 * ylen;
+    float ss = 0.f, se = 0.f;  // float-float sum of y^2 (noise partial)
 #pragma unroll
     for (int m = 0; m < MG; ++m) {
         if (m < nm) {
 #pragma unroll
             for (int i = 0; i < OPT; ++i) {
                 const int64_t t = t0 + 8 * tid + i;
-                if (t < ylen) yb[(int64_t)m * ylen + t] = acc[m][i];
+                if (t < ylen) {
+                    const float v = acc[m][i];
+                    yb[(int64_t)m * ylen + t] = v;
+                    ff_accumulate_sq(v, ss, se);
+                }
             }
         }
     }
-}
-
-// Noise, pass 1: partial sums of y^2 per (room, chunk), FP64, fixed order.
-constexpr int NCH = 65536;  // elements per partial
-__global__ void __launch_bounds__(256)
-k_sumsq(const ConvJob *__restrict__ jobs, const float *__restrict__ y, double *__restrict__ part,
-        int n_part) {
-    const ConvJob J = jobs[blockIdx.y];
-    const int64_t n = (int64_t)J.n_mics * J.y_len;
-    const int64_t b = (int64_t)blockIdx.x * NCH;
-    double acc = 0.0;
-    if (b < n) {
-        const float *yb = y + J.y_offset;
-        const int64_t e = min(b + NCH, n);
-        for (int64_t i = b + threadIdx.x; i < e; i += 256) {
-            const double v = yb[i];
-            acc += v * v;
+    if (part) {  // uniform: noise partial of this tile, fixed order
+        __shared__ double s_red[CT / 32];
+        const double r = warp_sum_f64((double)ss + (double)se);
+        if ((tid & 31) == 0) s_red[tid >> 5] = r;
+        __syncthreads();
+        if (tid == 0) {
+            double t = 0.0;
+            for (int w = 0; w < CT / 32; ++w) t += s_red[w];
+            part[J.part_offset + conv_partial_slot(tl.mic0, t0, ylen)] = t;
         }
     }
-    __shared__ double s[256];
-    s[threadIdx.x] = acc;
-    __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-        if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) part[(int64_t)blockIdx.y * n_part + blockIdx.x] = s[0];
 }
 
-// Noise, pass 2: sigma from the partials (fixed order), then
+// Noise: sigma from the job's tile partials (fixed order), then
 // y += sigma * z with z = sqrt(-2 ln u1) cos(2 pi u2) and u1, u2 the 24-bit
-// uniforms of SplitMix64 outputs 2t, 2t+1 of the (room, mic) stream.
+// uniforms of SplitMix64 outputs 2t, 2t+1 of the (room, mic) stream.  Block
+// x of job y covers flat indices [x NCH, (x+1) NCH) of the job's (mic, t)
+// samples; each thread walks its samples with stride 256, carrying (mic, t)
+// and the mic's stream key instead of dividing per sample.
+constexpr int NCH = 65536;  // samples per block
 __global__ void __launch_bounds__(256)
 k_noise(const ConvJob *__restrict__ jobs, float *__restrict__ y, const double *__restrict__ part,
-        int n_part, uint64_t seed) {
+        uint64_t seed) {
     const ConvJob J = jobs[blockIdx.y];
     if (isnan(J.snr_db)) return;
-    const int64_t n = (int64_t)J.n_mics * J.y_len;
+    const int64_t ylen = J.y_len;
+    const int64_t n = (int64_t)J.n_mics * ylen;
     const int64_t b = (int64_t)blockIdx.x * NCH;
     if (b >= n) return;
     __shared__ float s_sigma;
     if (threadIdx.x == 0) {
+        const int np = conv_partials_per_job(J.n_mics, ylen);
         double p = 0.0;
-        for (int i = 0; i < n_part; ++i) p += part[(int64_t)blockIdx.y * n_part + i];
+        for (int i = 0; i < np; ++i) p += part[J.part_offset + i];
         p /= (double)n;
         s_sigma = (float)sqrt(p / pow(10.0, (double)J.snr_db / 10.0));
     }
@@ -162,15 +162,22 @@ k_noise(const ConvJob *__restrict__ jobs, float *__restrict__ y, const double *_
     const float sigma = s_sigma;
     float *yb = y + J.y_offset;
     const int64_t e = min(b + NCH, n);
-    for (int64_t i = b + threadIdx.x; i < e; i += 256) {
-        const uint64_t m = (uint64_t)(i / J.y_len);
-        const uint64_t t = (uint64_t)(i - (int64_t)m * J.y_len);
-        const uint64_t key = sm64_out(seed, J.noise_id * 65536ull + m);
-        const uint64_t b1 = sm64_out(key, 2 * t), b2 = sm64_out(key, 2 * t + 1);
+    int64_t i = b + threadIdx.x;
+    if (i >= e) return;
+    uint64_t m = (uint64_t)(i / ylen);
+    int64_t t = i - (int64_t)m * ylen;
+    uint64_t key = sm64_out(seed, J.noise_id * 65536ull + m);
+    for (; i < e; i += 256) {
+        const uint64_t b1 = sm64_out(key, 2 * (uint64_t)t), b2 = sm64_out(key, 2 * (uint64_t)t + 1);
         const float u1 = ((float)(b1 >> 40) + 0.5f) * (1.0f / 16777216.0f);
         const float u2 = (float)(b2 >> 40) * (1.0f / 16777216.0f);
         const float z = sqrtf(-2.f * logf(u1)) * cospif(2.f * u2);
         yb[i] += sigma * z;
+        t += 256;
+        if (t >= ylen) {
+            while (t >= ylen) { t -= ylen; ++m; }
+            key = sm64_out(seed, J.noise_id * 65536ull + m);
+        }
     }
 }
 
@@ -191,24 +198,34 @@ int launch_conv_f32(const ConvLaunch &L, cudaStream_t stream) {
     st = upload_async(d_tiles, tiles.data(), tiles.size() * sizeof(Tile), stream);
     if (st) { scratch_free(d_tiles, stream); return st; }
     k_conv_f32<<<(unsigned)tiles.size(), CT, 0, stream>>>(L.jobs_dev, (const Tile *)d_tiles,
-                                                           L.h_dev, L.src_dev, L.y_dev);
+                                                           L.h_dev, L.src_dev, L.y_dev,
+                                                           L.noise_partials_dev);
     cudaError_t e = cudaGetLastError();
     scratch_free(d_tiles, stream);
     if (e != cudaSuccess) return cuda_fail(e, "launch k_conv_f32");
     return ISM_OK;
 }
 
-int noise_partials_per_job(int64_t max_elems) { return (int)((max_elems + NCH - 1) / NCH); }
-
 int launch_noise(const ConvLaunch &L, cudaStream_t stream) {
     if (!L.any_noise || L.n_jobs == 0) return ISM_OK;
-    dim3 grid(L.n_partials_per_job, L.n_jobs);
-    k_sumsq<<<grid, 256, 0, stream>>>(L.jobs_dev, L.y_dev, L.noise_partials_dev,
-                                      L.n_partials_per_job);
-    k_noise<<<grid, 256, 0, stream>>>(L.jobs_dev, L.y_dev, L.noise_partials_dev,
-                                      L.n_partials_per_job, L.seed);
+    int64_t max_n = 0;
+    for (int j = 0; j < L.n_jobs; ++j)
+        max_n = std::max(max_n, (int64_t)L.jobs_host[j].n_mics * L.jobs_host[j].y_len);
+    const int64_t nb = (max_n + NCH - 1) / NCH;
+    if (nb > 0x7fffffff) return fail(ISM_ERR_INVALID_ARG, "job too large for the noise grid");
+    if (L.n_jobs > 65535) {
+        // grid.y limit: one launch per group of 65535 jobs
+        for (int j0 = 0; j0 < L.n_jobs; j0 += 65535) {
+            const int nj = std::min(65535, L.n_jobs - j0);
+            k_noise<<<dim3((unsigned)nb, nj), 256, 0, stream>>>(L.jobs_dev + j0, L.y_dev,
+                                                               L.noise_partials_dev, L.seed);
+        }
+    } else {
+        k_noise<<<dim3((unsigned)nb, L.n_jobs), 256, 0, stream>>>(L.jobs_dev, L.y_dev,
+                                                                 L.noise_partials_dev, L.seed);
+    }
     cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "launch noise kernels");
+    if (e != cudaSuccess) return cuda_fail(e, "launch k_noise");
     return ISM_OK;
 }
 

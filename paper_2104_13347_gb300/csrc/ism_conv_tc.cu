@@ -53,6 +53,7 @@ constexpr int KC = 64;                 // RIR taps per chunk
 constexpr int NN = 256;                // GEMM N: time groups of 8
 constexpr int TT = 8 * NN;             // outputs per tile (2048)
 constexpr int MG = 8;                  // mics per tile
+static_assert(TT == kConvTT && MG == kConvMG, "tile shape of the noise partials");
 constexpr int NS = 4;                  // pipeline stages
 constexpr int BW = 2112;               // source window per chunk (>= KC + 8 (NN-1), x8)
 constexpr int A_BYTES = 8 * 16 * 128;  // 8 k-groups x 16 row groups x 8 rows x 16 B
@@ -179,9 +180,11 @@ __host__ __device__ inline TcLayout tc_layout(bool whole_b, int n_chunks) {
 template <bool WHOLE_B>
 __global__ void __launch_bounds__(NTHR, 1)
 k_conv_tc(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles,
-          const float *__restrict__ h, const float *__restrict__ src, float *__restrict__ y) {
+          const float *__restrict__ h, const float *__restrict__ src, float *__restrict__ y,
+          double *__restrict__ part) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) uint64_t bar_full[NS], bar_empty[NS], bar_done;
+    __shared__ double s_red[2];
     __shared__ uint32_t s_tmem;
     __shared__ volatile int s_abort;
 
@@ -393,6 +396,7 @@ k_conv_tc(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles,
         const int m = row >> 3, p = row & 7;
         const int64_t ylen = J.y_len;
         float *ym = y + J.y_offset + (int64_t)(tl.mic0 + m) * ylen;
+        float ss = 0.f, se = 0.f;
         for (int cb = 0; cb < NN; cb += 32) {
             uint32_t r[32];
             if (ok) {
@@ -418,13 +422,22 @@ k_conv_tc(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles,
                 for (int j = 0; j < 32; ++j) {
                     const int64_t t = T0 + 8 * (cb + j) + p;
                     const float v = __uint_as_float(r[j]) + (ok ? lo_buf[row * NN + cb + j] : 0.f);
-                    if (t < ylen) ym[t] = v;
+                    if (t < ylen) {
+                        ym[t] = v;
+                        ff_accumulate_sq(v, ss, se);
+                    }
                 }
             }
         }
+        // noise partial: the tile's sum of y^2 (float-float per row, FP64
+        // across rows, fixed order)
+        const double r = warp_sum_f64((double)ss + (double)se);
+        if (lane == 0) s_red[warp] = r;
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
+    if (part && tid == 0)
+        part[J.part_offset + conv_partial_slot(tl.mic0, T0, J.y_len)] = s_red[0] + s_red[1];
     if (warp == 4) {
         __syncwarp();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
@@ -463,7 +476,8 @@ int launch_conv_bf16x3(const ConvLaunch &L, cudaStream_t stream) {
                                  (int)smem);
         if (e == cudaSuccess)
             k_conv_tc<true><<<(unsigned)tiles[1].size(), NTHR, smem, stream>>>(
-                L.jobs_dev, (const Tile *)d_tiles, L.h_dev, L.src_dev, L.y_dev);
+                L.jobs_dev, (const Tile *)d_tiles, L.h_dev, L.src_dev, L.y_dev,
+                L.noise_partials_dev);
     }
     if (e == cudaSuccess && !tiles[0].empty()) {
         const size_t smem = tc_layout(false, 0).total;
@@ -471,7 +485,8 @@ int launch_conv_bf16x3(const ConvLaunch &L, cudaStream_t stream) {
                                  (int)smem);
         if (e == cudaSuccess)
             k_conv_tc<false><<<(unsigned)tiles[0].size(), NTHR, smem, stream>>>(
-                L.jobs_dev, (const Tile *)d_tiles + tiles[1].size(), L.h_dev, L.src_dev, L.y_dev);
+                L.jobs_dev, (const Tile *)d_tiles + tiles[1].size(), L.h_dev, L.src_dev, L.y_dev,
+                L.noise_partials_dev);
     }
     if (e == cudaSuccess) e = cudaGetLastError();
     scratch_free(d_tiles, stream);

@@ -45,6 +45,7 @@ struct alignas(16) ConvJob {
     uint64_t noise_id;   // identifies the room's noise streams (with the seed)
     int32_t n_mics;
     float snr_db;        // NaN = no noise
+    int64_t part_offset; // first noise partial slot of the job
 };
 
 // Thread-local error message (ism_last_error_string).
@@ -112,13 +113,46 @@ struct ConvLaunch {
     int precision;
     uint64_t seed;
     int any_noise;
-    double *noise_partials_dev;  // per job: partial sums of y^2 (scratch)
-    int n_partials_per_job;
+    // sum of y^2 over the tile of mic group g and output block b of job j
+    // in slot part_offset(j) + g * ceil(y_len / kConvTT) + b, written by the
+    // convolution kernels when non-null (noise requested)
+    double *noise_partials_dev;
 };
+// Tile shape shared by both convolution kernels (and the noise partials).
+constexpr int kConvMG = 8;     // mics per tile
+constexpr int kConvTT = 2048;  // outputs per tile
+__host__ __device__ inline int conv_partials_per_job(int n_mics, int64_t y_len) {
+    return (int)((n_mics + kConvMG - 1) / kConvMG * ((y_len + kConvTT - 1) / kConvTT));
+}
+__host__ __device__ inline int conv_partial_slot(int mic0, int64_t t0, int64_t y_len) {
+    return (int)(mic0 / kConvMG * ((y_len + kConvTT - 1) / kConvTT) + t0 / kConvTT);
+}
 int launch_conv_f32(const ConvLaunch &L, cudaStream_t stream);
 int launch_conv_bf16x3(const ConvLaunch &L, cudaStream_t stream);
-int noise_partials_per_job(int64_t max_elems);
 int launch_noise(const ConvLaunch &L, cudaStream_t stream);
+
+#ifdef __CUDACC__
+// s + e += v^2 in float-float: the square's rounding error from an FMA, the
+// sum's from a two-sum (error-free transformations; the pair keeps ~2^-44
+// relative accuracy over thousands of terms).
+__device__ __forceinline__ void ff_accumulate_sq(float v, float &s, float &e) {
+    const float p = __fmul_rn(v, v);
+    const float pe = __fmaf_rn(v, v, -p);
+    const float t = __fadd_rn(s, p);
+    const float bb = __fsub_rn(t, s);
+    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bb)), __fsub_rn(p, bb));
+    e = __fadd_rn(e, __fadd_rn(err, pe));
+    s = t;
+}
+
+// Sum of x over the 32 lanes of a warp, FP64, fixed shuffle tree; valid in
+// lane 0.
+__device__ __forceinline__ double warp_sum_f64(double x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    return x;
+}
+#endif
 
 // SplitMix64 (Steele, Lea and Flood 2014): output i of the stream with
 // state x is mix(x + (i+1) * gamma).
