@@ -347,7 +347,7 @@ int ism_rir_batch_ex(const ism_room *rooms, int64_t n_rooms, float *h_dev,
         // sparse path: one Chebyshev table per distinct filter length
         bool sparse = o.variant == ISM_RIR_SPARSE;
         std::vector<float> tabs;
-        int max_cheb = 0;
+        int max_cheb = 0, min_cheb = kMaxCheb;
         if (sparse) {
             std::vector<std::pair<int, int>> seen;  // (n_taps, offset)
             for (auto &J : jv) {
@@ -370,6 +370,7 @@ int ism_rir_batch_ex(const ism_room *rooms, int64_t n_rooms, float *h_dev,
                 J.tab_offset = off;
                 J.n_cheb = (int16_t)ct.n_cheb;
                 max_cheb = std::max(max_cheb, ct.n_cheb);
+                min_cheb = std::min(min_cheb, ct.n_cheb);
             }
             if (sparse && rir_sparse_smem_bytes(W, max_order[kind], max_taps[kind], max_cheb) >
                               227 * 1024)
@@ -392,7 +393,7 @@ int ism_rir_batch_ex(const ism_room *rooms, int64_t n_rooms, float *h_dev,
             e = cudaMemsetAsync(d_counter, 0, sizeof(unsigned int), stream);
             if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(counter)");
             RirLaunch L{jd, n, wm, W, max_order[kind], max_taps[kind], kind, h_dev, d_stats,
-                        d_counter, nullptr, 0, d_tabs, max_cheb};
+                        d_counter, nullptr, 0, d_tabs, max_cheb, min_cheb};
             return sparse ? launch_rir_sparse(L, stream) : launch_rir(L, stream);
         };
         if (!st) {

@@ -83,6 +83,7 @@ struct RirLaunch {
     int grid;             // 0 = persistent (SMs x blocks/SM)
     const float *tabs_dev;  // sparse kernel: Chebyshev tables [p][n_taps]
     int max_cheb;           // sparse kernel: largest n_cheb of the jobs
+    int min_cheb;           // sparse kernel: smallest n_cheb of the jobs
 };
 // Direct per-tap kernel (bitwise reproducible).
 int launch_rir(const RirLaunch &L, cudaStream_t stream);

@@ -43,6 +43,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "ism_internal.h"
 
 namespace ism {
@@ -764,7 +766,9 @@ k_ism_taps(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int max
 constexpr double kFix0 = 16777216.0;           // 2^24
 constexpr uint32_t kFixLimit = 0x7e000000u;    // 2^31 - 2^25
 
-template <int KIND, bool STATS>
+// PFIX > 0: every job of the launch has PFIX Chebyshev terms (the term loop
+// is unrolled); 0: per-job count.
+template <int KIND, bool STATS, int PFIX>
 __global__ void __launch_bounds__(NT, 4)
 k_ism_sparse(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int max_order,
              int max_taps, int max_cheb, const float *__restrict__ tabs, float *__restrict__ h,
@@ -851,14 +855,30 @@ k_ism_sparse(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int m
             uint32_t *c0 = (f == 0.f) ? s_dq : s_cq;  // integer delay: exact Kronecker delta
             const uint32_t old = atomicAdd(&c0[pos], q0);
             if (f != 0.f) {
+                // u_p = a S T_p(x) by the Chebyshev recurrence on the scaled
+                // values, u_{p+1} = 2 x u_p - u_{p-1}: one FMA, one conversion
+                // and one atomic per term
                 const float x = (KIND == ISM_FD_HANN_SINC) ? 2.f * f : 2.f * f - 1.f;
-                float t0 = 1.f, t1 = x;
-                if (Pc > 1) atomicAdd(&s_cq[CL + pos], (uint32_t)__float2int_rn(as * x));
-                for (int p = 2; p < Pc; ++p) {
-                    const float t2 = fmaf(2.f * x, t1, -t0);
-                    atomicAdd(&s_cq[p * CL + pos], (uint32_t)__float2int_rn(as * t2));
-                    t0 = t1;
-                    t1 = t2;
+                const float x2 = 2.f * x;
+                uint32_t *cp = s_cq + pos;
+                float u0 = as, u1 = as * x;
+                if (PFIX > 0) {
+                    atomicAdd(cp + CL, (uint32_t)__float2int_rn(u1));
+#pragma unroll
+                    for (int p = 2; p < PFIX; ++p) {
+                        const float u2 = fmaf(x2, u1, -u0);
+                        atomicAdd(cp + p * CL, (uint32_t)__float2int_rn(u2));
+                        u0 = u1;
+                        u1 = u2;
+                    }
+                } else {
+                    if (Pc > 1) atomicAdd(cp + CL, (uint32_t)__float2int_rn(u1));
+                    for (int p = 2; p < Pc; ++p) {
+                        const float u2 = fmaf(x2, u1, -u0);
+                        atomicAdd(cp + p * CL, (uint32_t)__float2int_rn(u2));
+                        u0 = u1;
+                        u1 = u2;
+                    }
                 }
             }
             if (old + q0 > kFixLimit) s_ovf = 1;  // this window is redone at a coarser scale
@@ -913,31 +933,42 @@ k_ism_sparse(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int m
                     for (int p = p_lo; p < p_hi; ++p) {
                         const float *cp = s_c + p * CL;
                         const float4 *bp = reinterpret_cast<const float4 *>(Bj + p * TPj);
-                        float win[12];
+                        // 12-register window: at sub-step s (taps jb + 4s ..
+                        // jb + 4s + 3) logical value L = c[base - jb - 4s - 4 + L]
+                        // sits in R[(L - 4s) mod 12], so three sub-steps rotate it
+                        // in place without register moves
+                        float R[12];
 #pragma unroll
                         for (int v = 0; v < 3; ++v) {
                             const float4 w4 =
                                 *reinterpret_cast<const float4 *>(cp + base - 4 + 4 * v);
-                            win[4 * v] = w4.x; win[4 * v + 1] = w4.y;
-                            win[4 * v + 2] = w4.z; win[4 * v + 3] = w4.w;
+                            R[4 * v] = w4.x; R[4 * v + 1] = w4.y;
+                            R[4 * v + 2] = w4.z; R[4 * v + 3] = w4.w;
                         }
-                        for (int jb = 0; jb < TPj; jb += 4) {
-                            const float4 b4 = __ldg(bp + (jb >> 2));
+                        auto step = [&](int jb, auto sc) {
+                            constexpr int S = decltype(sc)::value;
+                            const float4 b4 = __ldg(bp + (jb >> 2) + S);
                             const float bv[4] = {b4.x, b4.y, b4.z, b4.w};
-                            // c at position base + q - jb - jj is win[4 + q - jj]
 #pragma unroll
                             for (int jj = 0; jj < 4; ++jj)
 #pragma unroll
                                 for (int q = 0; q < 8; ++q)
-                                    acc[q] = fmaf(bv[jj], win[4 + q - jj], acc[q]);
-                            if (jb + 4 < TPj) {
-#pragma unroll
-                                for (int v = 11; v >= 4; --v) win[v] = win[v - 4];
-                                const float4 w4 =
-                                    *reinterpret_cast<const float4 *>(cp + base - jb - 8);
-                                win[0] = w4.x; win[1] = w4.y; win[2] = w4.z; win[3] = w4.w;
+                                    acc[q] = fmaf(bv[jj], R[(4 + q - jj - 4 * S + 12) % 12], acc[q]);
+                            if (jb + 4 * S + 4 < TPj) {
+                                const float4 w4 = *reinterpret_cast<const float4 *>(
+                                    cp + base - jb - 4 * S - 8);
+                                constexpr int d = (12 - 4 * (S + 1) % 12) % 12;
+                                R[d] = w4.x; R[d + 1] = w4.y; R[d + 2] = w4.z; R[d + 3] = w4.w;
                             }
+                        };
+                        int jb = 0;
+                        for (; jb + 12 <= TPj; jb += 12) {
+                            step(jb, std::integral_constant<int, 0>{});
+                            step(jb, std::integral_constant<int, 1>{});
+                            step(jb, std::integral_constant<int, 2>{});
                         }
+                        if (jb < TPj) step(jb, std::integral_constant<int, 0>{});
+                        if (jb + 4 < TPj) step(jb, std::integral_constant<int, 1>{});
                     }
                     if (half) {
 #pragma unroll
@@ -990,10 +1021,10 @@ int launch_direct_t(const RirLaunch &L, cudaStream_t stream) {
     return ISM_OK;
 }
 
-template <int KIND, bool STATS>
+template <int KIND, bool STATS, int PFIX>
 int launch_sparse_t(const RirLaunch &L, cudaStream_t stream) {
     const Layout Lay = make_layout(true, L.window, L.max_order, L.max_taps, L.max_cheb);
-    auto kern = k_ism_sparse<KIND, STATS>;
+    auto kern = k_ism_sparse<KIND, STATS, PFIX>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)Lay.total);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_ism_sparse)");
@@ -1046,11 +1077,19 @@ int launch_rir_sparse(const RirLaunch &L, cudaStream_t stream) {
     if (L.max_cheb < 1 || L.max_cheb > kMaxCheb)
         return fail(ISM_ERR_INVALID_ARG, "Chebyshev term count out of range");
     const bool st = L.stats_dev != nullptr;  // statistics compiled out when not asked for
-    if (L.fd_kind == ISM_FD_LAGRANGE)
-        return st ? launch_sparse_t<ISM_FD_LAGRANGE, true>(L, stream)
-                  : launch_sparse_t<ISM_FD_LAGRANGE, false>(L, stream);
-    return st ? launch_sparse_t<ISM_FD_HANN_SINC, true>(L, stream)
-              : launch_sparse_t<ISM_FD_HANN_SINC, false>(L, stream);
+    const int pf = L.min_cheb == L.max_cheb ? L.max_cheb : 0;
+    if (L.fd_kind == ISM_FD_LAGRANGE) {
+        if (pf == 8)
+            return st ? launch_sparse_t<ISM_FD_LAGRANGE, true, 8>(L, stream)
+                      : launch_sparse_t<ISM_FD_LAGRANGE, false, 8>(L, stream);
+        return st ? launch_sparse_t<ISM_FD_LAGRANGE, true, 0>(L, stream)
+                  : launch_sparse_t<ISM_FD_LAGRANGE, false, 0>(L, stream);
+    }
+    if (pf == 9)
+        return st ? launch_sparse_t<ISM_FD_HANN_SINC, true, 9>(L, stream)
+                  : launch_sparse_t<ISM_FD_HANN_SINC, false, 9>(L, stream);
+    return st ? launch_sparse_t<ISM_FD_HANN_SINC, true, 0>(L, stream)
+              : launch_sparse_t<ISM_FD_HANN_SINC, false, 0>(L, stream);
 }
 
 }  // namespace ism
