@@ -127,6 +127,8 @@ __device__ __forceinline__ float bf16_round(float x) {
 }
 
 constexpr int STG_FLOATS = 8 * 72;     // raw RIR staging per chunk: 8 mics x 72 values
+constexpr int CV_WORDS = 2 * 8 * 36;   // one chunk's RIR as bf16 pairs: [hi/lo][mic][36 words]
+constexpr int CV_BYTES = CV_WORDS * 4;
 
 __device__ __forceinline__ void cp_async4(uint32_t dst, const float *src, bool ok) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src),
@@ -150,11 +152,14 @@ __device__ __forceinline__ void producers_sync() {
     asm volatile("bar.sync 1, 128;" ::: "memory");
 }
 
-// Shared-memory layout.  whole_b: NS A stages (16 KB each), RIR staging,
-// then the tile's source window (bf16 hi, bf16 lo; bl elements each).
-// Otherwise NS stages of (A, window hi, window lo), then RIR staging.
+// Shared-memory layout.  whole_b: NS A stages (16 KB each), RIR staging
+// (two raw chunks), the converted RIR (one chunk of bf16 hi / lo: the
+// barrier that opens each chunk orders every read of it before the next
+// conversion), then the tile's source window (bf16 hi, bf16 lo; bl elements
+// each).  Otherwise NS stages of (A, window hi, window lo), then the RIR
+// staging and conversion.
 struct TcLayout {
-    size_t a_stride, stg, bhi, blo, total;
+    size_t a_stride, stg, cv, bhi, blo, total;
     int bl;
 };
 
@@ -164,15 +169,17 @@ __host__ __device__ inline TcLayout tc_layout(bool whole_b, int n_chunks) {
         L.bl = (n_chunks * KC + 8 * (NN - 1) + 8 + 7) & ~7;
         L.a_stride = A_BYTES;
         L.stg = (size_t)NS * A_BYTES;
-        L.bhi = L.stg + STG_FLOATS * 2 * 4;
+        L.cv = L.stg + STG_FLOATS * 2 * 4;
+        L.bhi = L.cv + CV_BYTES;
         L.blo = L.bhi + (size_t)L.bl * 2;
         L.total = L.blo + (size_t)L.bl * 2;
     } else {
         L.bl = BW;
         L.a_stride = STAGE;
         L.stg = (size_t)NS * STAGE;
+        L.cv = L.stg + STG_FLOATS * 2 * 4;
         L.bhi = L.blo = 0;  // per stage, after A
-        L.total = L.stg + STG_FLOATS * 2 * 4;
+        L.total = L.cv + CV_BYTES;
     }
     return L;
 }
@@ -264,6 +271,8 @@ k_conv_tc(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles,
         if (n_live > 0) stage_rir(ch_lo, 0);
         if (n_live > 1) stage_rir(ch_lo + 1, 1);
         else asm volatile("cp.async.commit_group;" ::: "memory");
+        uint32_t *cvb = reinterpret_cast<uint32_t *>(smem + Lay.cv);
+        const uint32_t sel = (p & 1) ? 0x3254u : 0x1032u;  // see the row build below
         for (int i = 0; i < n_live; ++i) {
             const int ch = ch_lo + i, s = i % NS, u = i / NS, buf = i & 1;
             asm volatile("cp.async.wait_group 1;" ::: "memory");
@@ -272,28 +281,47 @@ k_conv_tc(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles,
                 s_abort = 1;
                 break;
             }
-            unsigned char *st = smem + (size_t)s * Lay.a_stride;
-            // A rows (q, m, p) for each k-group kg: element kr is
-            // part_q(h_m[Lh - 1 + p - 64 ch - 8 kg - kr]) = part_q(stg[63 + p - 8 kg - kr])
-            const float *sv = stg + buf * STG_FLOATS + m * 72 + 63 + p;
-#pragma unroll
-            for (int kg = 0; kg < 8; ++kg) {
-                float v[8];
-#pragma unroll
-                for (int kr = 0; kr < 8; ++kr) {
-                    const float x = sv[-8 * kg - kr];
-                    const float xh = bf16_round(x);
-                    v[kr] = q ? x - xh : xh;
+            // (1) the staged chunk as bf16 pairs, once per value:
+            // cv[q][mm][w] = (part_q(stg[mm][2w]), part_q(stg[mm][2w + 1]))
+            {
+                const float2 *sv2 = reinterpret_cast<const float2 *>(stg + buf * STG_FLOATS);
+                uint32_t *cv = cvb;
+                for (int w = tid; w < STG_FLOATS / 2; w += NPROD) {
+                    const float2 x = sv2[w];
+                    const float h0 = bf16_round(x.x), h1 = bf16_round(x.y);
+                    cv[w] = pack_bf16(h0, h1);
+                    cv[STG_FLOATS / 2 + w] = pack_bf16(x.x - h0, x.y - h1);
                 }
-                uint4 row;
-                row.x = pack_bf16(v[0], v[1]);
-                row.y = pack_bf16(v[2], v[3]);
-                row.z = pack_bf16(v[4], v[5]);
-                row.w = pack_bf16(v[6], v[7]);
-                *reinterpret_cast<uint4 *>(st + kg * 2048 + g * 128 + p * 16) = row;
+            }
+            producers_sync();  // conversions visible; stg[buf] free again
+            if (i + 2 < n_live) stage_rir(ch + 2, buf);
+            else asm volatile("cp.async.commit_group;" ::: "memory");
+            // (2) A rows (q, m, p) for each k-group kg: element kr is
+            // part_q(h_m[Lh - 1 + p - 64 ch - 8 kg - kr]) = part_q(stg[m][63 + p - 8 kg - kr]).
+            // With p = 2a + o and V[i] = cv[q][m][a + i], word j of row kg
+            // (elements kr = 2j, 2j + 1) is, for o = 1, the low half of
+            // V[32 - 4 kg - j] and the high half of V[31 - 4 kg - j]
+            // (byte_perm selector 0x3254); for o = 0, the two halves of
+            // V[31 - 4 kg - j] swapped (0x1032).
+            {
+                const uint32_t *cv = cvb + q * (STG_FLOATS / 2) + m * 36 + (p >> 1);
+                uint32_t V[33];
+#pragma unroll
+                for (int k = 0; k < 33; ++k) V[k] = cv[k];
+                unsigned char *st = smem + (size_t)s * Lay.a_stride;
+#pragma unroll
+                for (int kg = 0; kg < 8; ++kg) {
+                    uint4 row;
+                    row.x = __byte_perm(V[31 - 4 * kg], V[32 - 4 * kg], sel);
+                    row.y = __byte_perm(V[30 - 4 * kg], V[31 - 4 * kg], sel);
+                    row.z = __byte_perm(V[29 - 4 * kg], V[30 - 4 * kg], sel);
+                    row.w = __byte_perm(V[28 - 4 * kg], V[29 - 4 * kg], sel);
+                    *reinterpret_cast<uint4 *>(st + kg * 2048 + g * 128 + p * 16) = row;
+                }
             }
             if (!WHOLE_B) {
                 // the chunk's source window, s[c0 + 64 ch + e], split hi / lo
+                unsigned char *st = smem + (size_t)s * Lay.a_stride;
                 uint32_t *bh = reinterpret_cast<uint32_t *>(st + A_BYTES);
                 uint32_t *bl = reinterpret_cast<uint32_t *>(st + A_BYTES + BW * 2);
                 const int64_t sbase = c0 + (int64_t)ch * KC;
@@ -308,9 +336,6 @@ k_conv_tc(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles,
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             mbar_arrive(smem_u32(&bar_full[s]));
-            producers_sync();  // every producer is done with stg[buf]
-            if (i + 2 < n_live) stage_rir(ch + 2, buf);
-            else asm volatile("cp.async.commit_group;" ::: "memory");
         }
         asm volatile("cp.async.wait_all;" ::: "memory");
     } else if (lane == 0) {
