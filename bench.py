@@ -36,6 +36,30 @@ WORKLOAD = (f"{N_ROOMS} rooms U[3,10]x[3,8]x[2.5,4] m, beta U[0.5,0.95], {N_MICS
             "SNR U[0,30] dB")
 
 
+# K1 DRAM traffic per room from the ncu capture summarised in
+# profiles/k_ism_sparse_and_k_conv_tc_1024rooms.md (None when that capture
+# predates the current kernel), and the binding resources it measured.
+K1_TRAFFIC_PER_ROOM = None
+K1_TRAFFIC_NOTE = "no capture of the current kernel yet"
+K1_BINDING = None
+
+
+def k2_live_chunks(n_tiles, ts, lh, kc=64, nn=256):
+    """Live 64-tap chunks summed over the time tiles of one mic group (the
+    tensor-core kernel skips chunks whose source window is all padding)."""
+    n_chunks = (lh + 7 + kc - 1) // kc
+    tot = 0
+    for t in range(n_tiles):
+        c0 = t * 8 * nn - lh + 1
+        lo = -c0 - (kc - 1 + 8 * (nn - 1))
+        lo = 0 if lo <= 0 else (lo + kc - 1) // kc
+        hi = ts - 1 - c0
+        hi = -1 if hi < 0 else hi // kc
+        hi = min(hi, n_chunks - 1)
+        tot += max(hi - lo + 1, 0)
+    return tot
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -277,17 +301,17 @@ def run_ours(args, ws, rank):
     taps = int(stats.view(-1, 2)[:, 1].sum().item())
     mic_samples = n_rooms * N_MICS * (TS + LH - 1)
 
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-    rir_ms, conv_ms, noise_ms = [], [], []
+    # per-step stage events, read after the timed region (no host sync inside)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
 
-    def step(record=False):
-        if record:
+    def step(ev=None):
+        if ev:
             ev[0].record(stream)
         ism.rir_batch(prep, h=h, window=args.window)
-        if record:
+        if ev:
             ev[1].record(stream)
         ism.convolve_batch(jobs, h, src, y, seed=12345, precision=precision)
-        if record:
+        if ev:
             ev[2].record(stream)
 
     for _ in range(args.warmup):
@@ -299,13 +323,12 @@ def run_ours(args, ws, rank):
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with clocks:
         start.record(stream)
-        for _ in range(args.steps):
-            step(record=True)
-            torch.cuda.synchronize()
-            rir_ms.append(ev[0].elapsed_time(ev[1]))
-            conv_ms.append(ev[1].elapsed_time(ev[2]))
+        for i in range(args.steps):
+            step(evs[i])
         end.record(stream)
         torch.cuda.synchronize()
+    rir_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    conv_ms = [e[1].elapsed_time(e[2]) for e in evs]
     barrier(ws)
     torch.cuda.synchronize()
     total_ms = max_over_ranks(start.elapsed_time(end), ws)
@@ -336,16 +359,35 @@ def run_ours(args, ws, rank):
     contrib = int(stats.view(-1, 2)[:, 0].sum().item())
     P = ism.rir_filter_terms(0, 81)
     # K1 (sparse path) algorithmic FP32 work per launch: per contributing
-    # image 41 flops for the float-float delay split and gain plus 4P - 4 for
-    # the Chebyshev scatter (recurrence, scaling, accumulation); per output
+    # image 40 flops for the float-float delay split and the gain, and 2P - 1
+    # for the P Chebyshev terms (recurrence on the scaled gain); per output
     # sample 2 P n_taps for the FIR.  Peak: FP32 FMA pipe, 128 lanes x 2
     # flops per clock per SM at the maximum SM clock.
-    k1_flops = 2.0 * P * 81 * n_rirs * LH + (41.0 + 4 * P - 4) * contrib
+    k1_flops = 2.0 * P * 81 * n_rirs * LH + (40.0 + 2 * P - 1) * contrib
     peak_fp32 = 2.0 * 128 * n_sm * sm_mhz * 1e6
     k1_rate = k1_flops / (rir_med * 1e-3)
     # context: the direct per-tap formulation is bound by the reciprocal
     # (MUFU) pipe, 16 results per clock per SM, one per tap
     direct_bound = 16.0 * n_sm * sm_mhz * 1e6
+
+    # K2 alone (no noise), timed back to back: split-BF16 needs at least the
+    # three products hi.hi, hi.lo, lo.hi of 2 Ts Lh flops per mic; the kernel
+    # executes four (lo.lo too) on 8-tap column groups of 64-tap chunks
+    jobs_clean, _ = ism.conv_jobs([N_MICS] * n_rooms, [LH] * n_rooms, [TS] * n_rooms)
+    k2_ms = None
+    if precision == ism.BF16X3:
+        k2e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ism.convolve_batch(jobs_clean, h, src, y, precision=precision)
+        k2e[0].record(stream)
+        for _ in range(3):
+            ism.convolve_batch(jobs_clean, h, src, y, precision=precision)
+        k2e[1].record(stream)
+        torch.cuda.synchronize()
+        k2_ms = k2e[0].elapsed_time(k2e[1]) / 3
+    k2_alg = 3 * 2.0 * TS * LH * n_rooms * N_MICS
+    n_tiles_t = -(-(TS + LH - 1) // 2048)
+    k2_exec = 8 * 2.0 * 128 * 256 * 16 * k2_live_chunks(n_tiles_t, TS, LH) * n_rooms
+    bf16_peak = pk.get("bf16_tflops", 1900.0) * 1e12
     line = {
         "metric": METRIC, "value": ws * taps / (ms_step * 1e-3), "unit": "taps/s",
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
@@ -356,19 +398,30 @@ def run_ours(args, ws, rank):
                    WORKLOAD.replace(f"{N_ROOMS} rooms", f"{n_rooms} rooms"), "rooms": n_rooms, "mics": N_MICS, "order": ORDER,
                    "rir_len": LH, "src_len": TS, "n_taps": 81, "window": args.window or 1024,
                    "precision": args.precision, "parallelism": f"replicas x{ws}",
-                   "l2": "inputs larger than L2 (h 268 MB, y 793 MB per step)"},
+                   "l2": f"inputs larger than L2 (h {hl * 4 / 1e6:.0f} MB, y {ylen * 4 / 1e6:.0f} MB "
+                         "per step), no flush"},
         "secondary": {"mic_samples_per_s": ws * mic_samples / (ms_step * 1e-3),
                       "taps_per_step": taps, "mic_samples_per_step": mic_samples,
                       "stage_ms": {"rir": rir_med, "conv_noise": conv_med}},
         "roofline": {"bound": "alu", "kernel": "k_ism_sparse", "achieved": k1_rate / 1e12,
                      "peak": peak_fp32 / 1e12, "unit": "TFLOP/s", "frac": k1_rate / peak_fp32,
-                     "traffic": 4 * 6.97e6,
-                     "traffic_note": "dram read+write of a 256-room ncu capture x 4 rooms",
-                     "work": f"2*P*n_taps per output (FIR) + 41+4P-4 per contributing image, P={P}",
+                     "traffic": K1_TRAFFIC_PER_ROOM * n_rooms if K1_TRAFFIC_PER_ROOM else None,
+                     "traffic_note": K1_TRAFFIC_NOTE,
+                     "work": f"2*P*n_taps per output (FIR) + 40+2P-1 per contributing image, P={P}",
                      "peak_note": f"FP32 FMA pipe, 128 lanes x 2 flop/clk/SM x {n_sm} SMs x "
                                   f"{sm_mhz:.0f} MHz ({pk_kind} max clock)",
+                     "binding": K1_BINDING,
                      "taps_per_s": taps / (rir_med * 1e-3),
                      "direct_formulation_bound_taps_per_s": direct_bound},
+        "roofline_k2": None if k2_ms is None else {
+            "bound": "tensor", "kernel": "k_conv_tc", "achieved": k2_alg / (k2_ms * 1e-3) / 1e12,
+            "peak": bf16_peak / 1e12, "unit": "TFLOP/s",
+            "frac": k2_alg / (k2_ms * 1e-3) / bf16_peak,
+            "executed_tflops": k2_exec / (k2_ms * 1e-3) / 1e12,
+            "executed_frac": k2_exec / (k2_ms * 1e-3) / bf16_peak, "ms": k2_ms,
+            "work": "3 x 2 Ts Lh per mic (split-BF16 minimum); executed: 8 MMAs 128x256x16 "
+                    "per live 64-tap chunk per tile",
+            "peak_note": f"dense bf16, {pk_kind} burst (kernel timed alone)"},
         "e2e": {"value": ws * taps / (e2e_ms * 1e-3), "unit": "taps/s",
                 "h2d_bytes_per_step": int(src_host.numel() * 4),
                 "d2h_bytes_per_step": int(ylen * 4), "ms_per_step": e2e_ms},

@@ -394,7 +394,11 @@ k_conv_tc(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles,
     asm volatile("tcgen05.fence::after_thread_sync;");
     __syncthreads();
     ok = ok && !s_abort && n_live > 0;
-    float *lo_buf = reinterpret_cast<float *>(smem);  // [64 rows][256 cols]
+    // [64 rows][257]: the odd row stride puts a warp's 32 rows (one column)
+    // in 32 different banks
+    constexpr int LOS = NN + 1;
+    static_assert(64 * LOS * 4 <= NS * A_BYTES + STG_FLOATS * 2 * 4, "lo rows fit the idle stages");
+    float *lo_buf = reinterpret_cast<float *>(smem);
     if (warp >= 2 && warp < 4 && ok) {
         const int row = (warp - 2) * 32 + lane;
         for (int cb = 0; cb < NN; cb += 32) {
@@ -412,7 +416,7 @@ k_conv_tc(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles,
                 : "r"(addr));
             asm volatile("tcgen05.wait::ld.sync.aligned;");
 #pragma unroll
-            for (int j = 0; j < 32; ++j) lo_buf[row * NN + cb + j] = __uint_as_float(r[j]);
+            for (int j = 0; j < 32; ++j) lo_buf[row * LOS + cb + j] = __uint_as_float(r[j]);
         }
     }
     __syncthreads();
@@ -446,7 +450,7 @@ k_conv_tc(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles,
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
                     const int64_t t = T0 + 8 * (cb + j) + p;
-                    const float v = __uint_as_float(r[j]) + (ok ? lo_buf[row * NN + cb + j] : 0.f);
+                    const float v = __uint_as_float(r[j]) + (ok ? lo_buf[row * LOS + cb + j] : 0.f);
                     if (t < ylen) {
                         ym[t] = v;
                         ff_accumulate_sq(v, ss, se);
