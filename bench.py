@@ -425,7 +425,7 @@ def run_ours(args, ws, rank):
         "e2e": {"value": ws * taps / (e2e_ms * 1e-3), "unit": "taps/s",
                 "h2d_bytes_per_step": int(src_host.numel() * 4),
                 "d2h_bytes_per_step": int(ylen * 4), "ms_per_step": e2e_ms},
-        "gpu_launches": args.steps * 3,  # K1, convolution (noise partials fused), noise
+        "gpu_launches": args.steps * 4,  # K1 tables + K1, convolution (noise partials fused), noise
         "clocks": clk,
     }
     if args.serve_rate > 0:

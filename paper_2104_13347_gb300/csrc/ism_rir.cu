@@ -43,6 +43,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <type_traits>
 
 #include "ism_internal.h"
@@ -93,7 +94,7 @@ __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(
 __host__ __device__ inline int round4(int x) { return (x + 3) & ~3; }
 
 struct Tables {
-    double *sq;   // [3][TE] squared axis offsets (FP64, definition rounding)
+    const double *sq;  // [3][TE] squared axis offsets (FP64, definition rounding)
     float4 *hlg;  // [3][TE] (hi, lo, g, -): float-float split of sq and the
                   // wall damping product along the axis, one 128-bit load
     float *dl;    // [3][TE] axis offset, FP32
@@ -116,7 +117,9 @@ __host__ __device__ inline Layout make_layout(bool sparse, int window, int max_o
     L.RL = round4(window + 2 * (max_taps - 1));
     L.CL = round4(window + max_taps + 12 + PADL);
     size_t o = 0;
-    L.off_sq = o;   o = align16(o + sizeof(double) * 3 * L.TE);
+    // the sparse kernel reads the FP64 squares (exact path only) from the
+    // per-RIR tables in global memory
+    L.off_sq = o;   o = align16(o + (sparse ? 0 : sizeof(double) * 3 * L.TE));
     L.off_hlg = o;  o = align16(o + sizeof(float4) * 3 * L.TE);
     L.off_dl = o;   o = align16(o + sizeof(float) * 3 * L.TE);
     L.off_lx = o;   o = align16(o + sizeof(int) * L.TE);
@@ -263,25 +266,60 @@ __device__ __forceinline__ void item_setup(const RirJob &J, int W, int wi, Item 
     it.inv2Lz = 1.f / (2.f * (float)J.dims[2]);
 }
 
-// Per-axis tables (all threads).  Offsets in FP64 with the definition's
-// rounding: ((1-2p) s + (2q) L) - r.
-__device__ __forceinline__ void build_tables(const RirJob &J, const Tables &T, int TE,
-                                             const Item &it) {
+// One per-axis table entry: axis a, entry ei = p (2N+1) + (qq + N) of a
+// job.  Offset in FP64 with the definition's rounding,
+// ((1-2p) s + (2q) L) - r, its square (FP64, and split into two floats),
+// and the wall damping product along the axis.
+__device__ __forceinline__ void table_entry(const RirJob &J, int N, int a, int ei, double &sq,
+                                            float4 &hlg, float &dl) {
+    const int p = ei / (2 * N + 1), qq = ei - p * (2 * N + 1) - N;
+    const double s = J.src[a], Ld = J.dims[a], r = J.mic[a];
+    const double img = __dadd_rn(p ? -s : s, __dmul_rn((double)(2 * qq), Ld));
+    const double dlt = __dsub_rn(img, r);
+    sq = __dmul_rn(dlt, dlt);
+    const float sh = __double2float_rn(sq);
+    dl = __double2float_rn(dlt);
+    const float b0 = J.beta[2 * a], b1 = J.beta[2 * a + 1];
+    hlg = make_float4(sh, __double2float_rn(sq - (double)sh),
+                      powf(b0, (float)abs(qq - p)) * powf(b1, (float)abs(qq)), 0.f);
+}
+
+// Per-axis tables of one job (all NT threads of the direct kernel).
+__device__ __forceinline__ void build_tables(const RirJob &J, const Tables &T, double *sq_out,
+                                             int TE, const Item &it) {
     const int N = it.N, TEj = it.TEj;
     for (int e = threadIdx.x; e < 3 * TEj; e += NT) {
         const int a = e / TEj, ei = e - a * TEj;
-        const int p = ei / (2 * N + 1), qq = ei - p * (2 * N + 1) - N;
-        const double s = J.src[a], Ld = J.dims[a], r = J.mic[a];
-        const double img = __dadd_rn(p ? -s : s, __dmul_rn((double)(2 * qq), Ld));
-        const double dlt = __dsub_rn(img, r);
-        const double sq = __dmul_rn(dlt, dlt);
-        const float sh = __double2float_rn(sq);
-        T.sq[a * TE + ei] = sq;
-        T.dl[a * TE + ei] = __double2float_rn(dlt);
-        const float b0 = J.beta[2 * a], b1 = J.beta[2 * a + 1];
-        T.hlg[a * TE + ei] = make_float4(sh, __double2float_rn(sq - (double)sh),
-                                         powf(b0, (float)abs(qq - p)) * powf(b1, (float)abs(qq)),
-                                         0.f);
+        double sq;
+        float4 hlg;
+        float dl;
+        table_entry(J, N, a, ei, sq, hlg, dl);
+        sq_out[a * TE + ei] = sq;
+        T.dl[a * TE + ei] = dl;
+        T.hlg[a * TE + ei] = hlg;
+    }
+}
+
+// Per-RIR tables in global memory for the sparse kernel, computed once per
+// RIR instead of once per window (GB300's FP64 pipe is narrow): RIR j's
+// entry (a, ei) at j * 3 TE + a TE + ei.
+__global__ void __launch_bounds__(128)
+k_ism_tables(const RirJob *__restrict__ jobs, int n_rirs, int TE, double *__restrict__ g_sq,
+             float4 *__restrict__ g_hlg, float *__restrict__ g_dl) {
+    for (int j = blockIdx.x; j < n_rirs; j += gridDim.x) {
+        const RirJob &J = jobs[j];
+        const int N = J.order, TEj = 2 * (2 * N + 1);
+        const size_t base = (size_t)j * 3 * TE;
+        for (int e = threadIdx.x; e < 3 * TEj; e += blockDim.x) {
+            const int a = e / TEj, ei = e - a * TEj;
+            double sq;
+            float4 hlg;
+            float dl;
+            table_entry(J, N, a, ei, sq, hlg, dl);
+            g_sq[base + a * TE + ei] = sq;
+            g_hlg[base + a * TE + ei] = hlg;
+            g_dl[base + a * TE + ei] = dl;
+        }
     }
 }
 
@@ -589,7 +627,8 @@ k_ism_taps(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int max
     const Layout Lay = make_layout(false, W, max_order, max_taps, 0);
     const int TE = Lay.TE;
     Tables T;
-    T.sq = (double *)(smem + Lay.off_sq);
+    double *s_sq = (double *)(smem + Lay.off_sq);
+    T.sq = s_sq;
     T.hlg = (float4 *)(smem + Lay.off_hlg);
     T.dl = (float *)(smem + Lay.off_dl);
     int *s_lx = (int *)(smem + Lay.off_lx);
@@ -617,7 +656,7 @@ k_ism_taps(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int max
         if (wi >= J.n_windows) { __syncthreads(); continue; }
         Item it;
         item_setup<KIND>(J, W, wi, it);
-        build_tables(J, T, TE, it);
+        build_tables(J, T, s_sq, TE, it);
         if (tid < 2) s_stat[tid] = 0ull;
         __syncthreads();
         build_lists(T, TE, it, s_lx, s_ly, s_nl);
@@ -772,12 +811,14 @@ template <int KIND, bool STATS, int PFIX>
 __global__ void __launch_bounds__(NT, 4)
 k_ism_sparse(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int max_order,
              int max_taps, int max_cheb, const float *__restrict__ tabs, float *__restrict__ h,
-             long long *__restrict__ stats, unsigned int *__restrict__ counter) {
+             long long *__restrict__ stats, unsigned int *__restrict__ counter,
+             const double *__restrict__ g_sq, const float4 *__restrict__ g_hlg,
+             const float *__restrict__ g_dl) {
     extern __shared__ __align__(16) unsigned char smem[];
     const Layout Lay = make_layout(true, W, max_order, max_taps, max_cheb);
     const int TE = Lay.TE, CL = Lay.CL;
     Tables T;
-    T.sq = (double *)(smem + Lay.off_sq);
+    T.sq = nullptr;  // per item: the RIR's FP64 table in global memory (exact path only)
     T.hlg = (float4 *)(smem + Lay.off_hlg);
     T.dl = (float *)(smem + Lay.off_dl);
     int *s_lx = (int *)(smem + Lay.off_lx);
@@ -788,6 +829,8 @@ k_ism_sparse(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int m
     float *s_part = (float *)(smem + Lay.off_part);
     __shared__ int s_item, s_nl[2], s_ovf;
     __shared__ unsigned long long s_stat[2];
+    __shared__ Item s_it;
+    __shared__ float s_S[4], s_invS[4];
 
     const int tid = threadIdx.x;
     uint32_t *s_cq = (uint32_t *)s_c;      // the same words before conversion
@@ -803,16 +846,61 @@ k_ism_sparse(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int m
         const long long item = s_item;
         if (item >= n_items) break;
         const int wi = wmax - 1 - (int)(item / n_rirs);
-        const RirJob &J = jobs[(int)(item % n_rirs)];
+        const int jr = (int)(item % n_rirs);
+        const RirJob &J = jobs[jr];
         if (wi >= J.n_windows) { __syncthreads(); continue; }
-        Item it;
-        item_setup<KIND>(J, W, wi, it);
-        build_tables(J, T, TE, it);
+        {
+            // the RIR's tables, computed once per RIR by k_ism_tables
+            const int TEj = 2 * (2 * J.order + 1);
+            const size_t base = (size_t)jr * 3 * TE;
+            for (int e = tid; e < 3 * TEj; e += NT) {
+                const int a = e / TEj, ei = e - a * TEj;
+                T.hlg[a * TE + ei] = g_hlg[base + a * TE + ei];
+                T.dl[a * TE + ei] = g_dl[base + a * TE + ei];
+            }
+            T.sq = g_sq + base;
+        }
+        if (tid == 0) {
+            // per-window scalars, once (FP64 work kept off the other threads)
+            Item i0;
+            item_setup<KIND>(J, W, wi, i0);
+            s_it = i0;
+            // fixed-point scales (see kFix0): d_floor bounds from below the
+            // distance of every image whose taps reach this window
+            const double dx = J.src[0] - J.mic[0], dy = J.src[1] - J.mic[1],
+                         dz = J.src[2] - J.mic[2];
+            const double d_dir = sqrt(dx * dx + dy * dy + dz * dz);
+            double tau_lo, tau_hi;
+            if (KIND == ISM_FD_HANN_SINC) {
+                tau_lo = (double)(i0.kb_lo + i0.H) - 0.5;
+                tau_hi = (double)(i0.kb_hi + i0.H) + 0.5;
+            } else {
+                tau_lo = (double)(i0.kb_lo + (i0.P - 1) / 2);
+                tau_hi = (double)(i0.kb_hi + (i0.P + 1) / 2);
+            }
+            const double d_floor = fmax(d_dir, tau_lo / i0.q) * (1.0 - 1e-6);
+            const double tb = (1.0 + 1e-5) / i0.q, dmax = tau_hi / i0.q + tb;
+            const double ncol = 4.0 * (2 * i0.N + 1) * (double)(2 * i0.N + 1);
+            const double n_bound =
+                4.0 * ncol * (sqrt(2.0 * dmax * tb + tb * tb) / (2.0 * J.dims[2]) + 1.0);
+            // a_max = 1 / (4 pi d_floor) maps to kFix0, then 2^7 less per
+            // retry; the fourth attempt takes the scale at which n_bound
+            // images at a_max cannot exceed the limit
+            for (int at = 0; at < 4; ++at) {
+                double sc = kFix0 * 12.566370614359172 * d_floor;
+                if (at < 3) sc = ldexp(sc, -7 * at);
+                else sc = fmin(ldexp(sc, -21),
+                               0.5 * (double)kFixLimit * 12.566370614359172 * d_floor / n_bound);
+                s_S[at] = (float)sc;
+                s_invS[at] = (float)(1.0 / sc);
+            }
+            s_stat[0] = s_stat[1] = 0ull;
+            s_ovf = 0;
+        }
+        __syncthreads();
+        const Item it = s_it;
         const int Pc = J.n_cheb;
         const int n_taps = it.n_taps;
-        if (tid < 2) s_stat[tid] = 0ull;
-        if (tid == 0) s_ovf = 0;
-        __syncthreads();
         build_lists(T, TE, it, s_lx, s_ly, s_nl);
         __syncthreads();
         const int nLX = s_nl[0], nLY = s_nl[1];
@@ -822,26 +910,6 @@ k_ism_sparse(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int m
         const int POS0 = OFF + PADL - (int)it.kb_lo;
         const int jdelta = (KIND == ISM_FD_HANN_SINC) ? it.H : (it.P - 1) / 2;
         unsigned my_contrib = 0, my_taps = 0;
-        // Fixed-point accumulation (see kFix0).  d_floor bounds from below
-        // the distance of every image whose taps reach this window.
-        double d_floor, n_bound;
-        {
-            const double dx = J.src[0] - J.mic[0], dy = J.src[1] - J.mic[1],
-                         dz = J.src[2] - J.mic[2];
-            const double d_dir = sqrt(dx * dx + dy * dy + dz * dz);
-            double tau_lo, tau_hi;
-            if (KIND == ISM_FD_HANN_SINC) {
-                tau_lo = (double)(it.kb_lo + it.H) - 0.5;
-                tau_hi = (double)(it.kb_hi + it.H) + 0.5;
-            } else {
-                tau_lo = (double)(it.kb_lo + (it.P - 1) / 2);
-                tau_hi = (double)(it.kb_hi + (it.P + 1) / 2);
-            }
-            d_floor = fmax(d_dir, tau_lo / it.q) * (1.0 - 1e-6);
-            const double tb = (1.0 + 1e-5) / it.q, dmax = tau_hi / it.q + tb;
-            const double ncol = 4.0 * (2 * it.N + 1) * (double)(2 * it.N + 1);
-            n_bound = 4.0 * ncol * (sqrt(2.0 * dmax * tb + tb * tb) / (2.0 * J.dims[2]) + 1.0);
-        }
         float S = 0.f;
         auto proc = [&](float Rh, float Rl, float gxy, uint32_t code, bool valid) {
             int kb;
@@ -885,14 +953,8 @@ k_ism_sparse(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int m
         };
         float invS = 0.f;
         for (int attempt = 0;; ++attempt) {
-            // scale: a_max = 1 / (4 pi d_floor) maps to kFix0, then 2^7 less per
-            // retry; the fourth attempt takes the scale at which n_bound images
-            // at a_max cannot exceed the limit
-            double sc = kFix0 * 12.566370614359172 * d_floor;
-            if (attempt < 3) sc = ldexp(sc, -7 * attempt);
-            else sc = fmin(ldexp(sc, -21), 0.5 * (double)kFixLimit * 12.566370614359172 * d_floor / n_bound);
-            S = (float)sc;
-            invS = (float)(1.0 / sc);
+            S = s_S[attempt];
+            invS = s_invS[attempt];
             my_contrib = 0;
             my_taps = 0;
             warp_expand(T, TE, it, s_lx, s_ly, nLX, nLY,
@@ -1038,10 +1100,22 @@ int launch_sparse_t(const RirLaunch &L, cudaStream_t stream) {
     const long long items = (long long)L.n_rirs * L.wmax;
     if ((long long)grid > items) grid = (int)items;
     if (grid < 1) return ISM_OK;
+    // per-RIR tables: FP64 squares, (hi, lo, damping) and offsets
+    const size_t n_ent = (size_t)L.n_rirs * 3 * Lay.TE;
+    void *tab = nullptr;
+    if (int st = scratch_alloc(&tab, n_ent * (sizeof(double) + sizeof(float4) + sizeof(float)),
+                               stream))
+        return st;
+    double *g_sq = (double *)tab;
+    float4 *g_hlg = (float4 *)(g_sq + n_ent);
+    float *g_dl = (float *)(g_hlg + n_ent);
+    const int tgrid = (int)std::min<long long>(L.n_rirs, (long long)device_sm_count() * 8);
+    k_ism_tables<<<tgrid, 128, 0, stream>>>(L.jobs_dev, L.n_rirs, Lay.TE, g_sq, g_hlg, g_dl);
     kern<<<grid, NT, Lay.total, stream>>>(L.jobs_dev, L.n_rirs, L.wmax, L.window, L.max_order,
                                           L.max_taps, L.max_cheb, L.tabs_dev, L.h_dev,
-                                          L.stats_dev, L.counter_dev);
+                                          L.stats_dev, L.counter_dev, g_sq, g_hlg, g_dl);
     e = cudaGetLastError();
+    scratch_free(tab, stream);
     if (e != cudaSuccess) return cuda_fail(e, "launch k_ism_sparse");
     return ISM_OK;
 }
