@@ -229,6 +229,16 @@ struct Item {
     float qh, ql, dlo2, dhi2, dhe2, dhe, eps, inv2Lz;
 };
 
+// Per-RIR FP32 constants of the sparse kernel's window setup (computed once
+// in FP64, so that no window needs the FP64 pipe for them).
+struct JobConst {
+    float d_dir;   // |source - mic|: no image is closer (points inside the box)
+    float inv_q;   // c / fs, metres per sample
+    float qh, ql;  // fs / c split into two floats
+    float inv2Lz;  // 1 / (2 Lz)
+    float pad[3];
+};
+
 template <int KIND>
 __device__ __forceinline__ void item_setup(const RirJob &J, int W, int wi, Item &it) {
     it.N = J.order;
@@ -284,6 +294,46 @@ __device__ __forceinline__ void table_entry(const RirJob &J, int N, int a, int e
                       powf(b0, (float)abs(qq - p)) * powf(b1, (float)abs(qq)), 0.f);
 }
 
+// The sparse kernel's per-window constants in FP32 from the per-RIR
+// constants: the same fields as item_setup (bounds in metres carry the
+// column solve's 0.2 m margin, far above FP32 rounding).
+template <int KIND>
+__device__ __forceinline__ void item_setup_f32(const RirJob &J, const JobConst &jc, int W, int wi,
+                                               Item &it, float &tau_lo, float &tau_hi) {
+    it.N = J.order;
+    it.TEj = 2 * (2 * it.N + 1);
+    it.n_taps = J.n_taps;
+    it.H = (it.n_taps - 1) / 2;
+    it.P = it.n_taps - 1;
+    it.Lh = J.rir_len;
+    it.W = W;
+    it.w0 = wi * W;
+    it.q = J.q;
+    it.qh = jc.qh;
+    it.ql = jc.ql;
+    it.kb_lo = (long long)it.w0 - it.n_taps + 1;
+    it.kb_hi = min((long long)it.w0 + W - 1, it.Lh - 1);
+    it.kb_lo32 = (int)it.kb_lo;
+    it.kb_hi32 = (int)it.kb_hi;
+    it.Lh32 = (int)it.Lh;
+    it.wend = (int)min((long long)it.w0 + W, it.Lh);
+    if (KIND == ISM_FD_HANN_SINC) {
+        tau_lo = (float)(it.kb_lo32 + it.H) - 0.5f;
+        tau_hi = (float)(it.kb_hi32 + it.H) + 0.5f;
+    } else {
+        tau_lo = (float)(it.kb_lo32 + (it.P - 1) / 2);
+        tau_hi = (float)(it.kb_hi32 + (it.P + 1) / 2);
+    }
+    const float d_lo = fmaxf(tau_lo * jc.inv_q, 0.f);
+    const float d_hi = tau_hi * jc.inv_q;
+    it.eps = kEps + 1e-6f * d_hi;
+    it.dlo2 = d_lo * d_lo;
+    it.dhi2 = d_hi * d_hi;
+    it.dhe = d_hi + it.eps;
+    it.dhe2 = it.dhe * it.dhe;
+    it.inv2Lz = jc.inv2Lz;
+}
+
 // Per-axis tables of one job (all NT threads of the direct kernel).
 __device__ __forceinline__ void build_tables(const RirJob &J, const Tables &T, double *sq_out,
                                              int TE, const Item &it) {
@@ -305,11 +355,23 @@ __device__ __forceinline__ void build_tables(const RirJob &J, const Tables &T, d
 // entry (a, ei) at j * 3 TE + a TE + ei.
 __global__ void __launch_bounds__(128)
 k_ism_tables(const RirJob *__restrict__ jobs, int n_rirs, int TE, double *__restrict__ g_sq,
-             float4 *__restrict__ g_hlg, float *__restrict__ g_dl) {
+             float4 *__restrict__ g_hlg, float *__restrict__ g_dl, JobConst *__restrict__ g_jc) {
     for (int j = blockIdx.x; j < n_rirs; j += gridDim.x) {
         const RirJob &J = jobs[j];
         const int N = J.order, TEj = 2 * (2 * N + 1);
         const size_t base = (size_t)j * 3 * TE;
+        if (threadIdx.x == 0) {
+            const double dx = J.src[0] - J.mic[0], dy = J.src[1] - J.mic[1],
+                         dz = J.src[2] - J.mic[2];
+            JobConst c;
+            c.d_dir = (float)sqrt(dx * dx + dy * dy + dz * dz);
+            c.inv_q = (float)(1.0 / J.q);
+            c.qh = (float)J.q;
+            c.ql = (float)(J.q - (double)c.qh);
+            c.inv2Lz = (float)(0.5 / J.dims[2]);
+            c.pad[0] = c.pad[1] = c.pad[2] = 0.f;
+            g_jc[j] = c;
+        }
         for (int e = threadIdx.x; e < 3 * TEj; e += blockDim.x) {
             const int a = e / TEj, ei = e - a * TEj;
             double sq;
@@ -813,7 +875,7 @@ k_ism_sparse(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int m
              int max_taps, int max_cheb, const float *__restrict__ tabs, float *__restrict__ h,
              long long *__restrict__ stats, unsigned int *__restrict__ counter,
              const double *__restrict__ g_sq, const float4 *__restrict__ g_hlg,
-             const float *__restrict__ g_dl) {
+             const float *__restrict__ g_dl, const JobConst *__restrict__ g_jc) {
     extern __shared__ __align__(16) unsigned char smem[];
     const Layout Lay = make_layout(true, W, max_order, max_taps, max_cheb);
     const int TE = Lay.TE, CL = Lay.CL;
@@ -829,8 +891,6 @@ k_ism_sparse(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int m
     float *s_part = (float *)(smem + Lay.off_part);
     __shared__ int s_item, s_nl[2], s_ovf;
     __shared__ unsigned long long s_stat[2];
-    __shared__ Item s_it;
-    __shared__ float s_S[4], s_invS[4];
 
     const int tid = threadIdx.x;
     uint32_t *s_cq = (uint32_t *)s_c;      // the same words before conversion
@@ -861,44 +921,31 @@ k_ism_sparse(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int m
             T.sq = g_sq + base;
         }
         if (tid == 0) {
-            // per-window scalars, once (FP64 work kept off the other threads)
-            Item i0;
-            item_setup<KIND>(J, W, wi, i0);
-            s_it = i0;
-            // fixed-point scales (see kFix0): d_floor bounds from below the
-            // distance of every image whose taps reach this window
-            const double dx = J.src[0] - J.mic[0], dy = J.src[1] - J.mic[1],
-                         dz = J.src[2] - J.mic[2];
-            const double d_dir = sqrt(dx * dx + dy * dy + dz * dz);
-            double tau_lo, tau_hi;
-            if (KIND == ISM_FD_HANN_SINC) {
-                tau_lo = (double)(i0.kb_lo + i0.H) - 0.5;
-                tau_hi = (double)(i0.kb_hi + i0.H) + 0.5;
-            } else {
-                tau_lo = (double)(i0.kb_lo + (i0.P - 1) / 2);
-                tau_hi = (double)(i0.kb_hi + (i0.P + 1) / 2);
-            }
-            const double d_floor = fmax(d_dir, tau_lo / i0.q) * (1.0 - 1e-6);
-            const double tb = (1.0 + 1e-5) / i0.q, dmax = tau_hi / i0.q + tb;
-            const double ncol = 4.0 * (2 * i0.N + 1) * (double)(2 * i0.N + 1);
-            const double n_bound =
-                4.0 * ncol * (sqrt(2.0 * dmax * tb + tb * tb) / (2.0 * J.dims[2]) + 1.0);
-            // a_max = 1 / (4 pi d_floor) maps to kFix0, then 2^7 less per
-            // retry; the fourth attempt takes the scale at which n_bound
-            // images at a_max cannot exceed the limit
-            for (int at = 0; at < 4; ++at) {
-                double sc = kFix0 * 12.566370614359172 * d_floor;
-                if (at < 3) sc = ldexp(sc, -7 * at);
-                else sc = fmin(ldexp(sc, -21),
-                               0.5 * (double)kFixLimit * 12.566370614359172 * d_floor / n_bound);
-                s_S[at] = (float)sc;
-                s_invS[at] = (float)(1.0 / sc);
-            }
             s_stat[0] = s_stat[1] = 0ull;
             s_ovf = 0;
         }
         __syncthreads();
-        const Item it = s_it;
+        // per-window constants, FP32 (see item_setup_f32)
+        Item it;
+        float tau_lo, tau_hi;
+        const JobConst jc = g_jc[jr];
+        item_setup_f32<KIND>(J, jc, W, wi, it, tau_lo, tau_hi);
+        // fixed-point scales (see kFix0): d_floor bounds from below the
+        // distance of every image whose taps reach this window; one delay
+        // bucket holds at most n_bound images
+        const float d_floor = fmaxf(jc.d_dir, tau_lo * jc.inv_q) * (1.f - 1e-5f);
+        const float tb = (1.f + 1e-5f) * jc.inv_q, dmax = tau_hi * jc.inv_q + tb;
+        const float ncol = 4.f * (float)(2 * it.N + 1) * (float)(2 * it.N + 1);
+        const float n_bound = 4.f * ncol * (sqrtf(2.f * dmax * tb + tb * tb) * jc.inv2Lz + 1.f);
+        const float S0 = (float)kFix0 * 12.566370614359172f * d_floor;
+        auto scale_of = [&](int at) {
+            // a_max = 1 / (4 pi d_floor) maps to kFix0, then 2^7 less per
+            // retry; the fourth attempt takes the scale at which n_bound
+            // images at a_max cannot exceed the limit
+            if (at < 3) return ldexpf(S0, -7 * at);
+            return fminf(ldexpf(S0, -21),
+                         0.5f * (float)kFixLimit * 12.566370614359172f * d_floor / n_bound);
+        };
         const int Pc = J.n_cheb;
         const int n_taps = it.n_taps;
         build_lists(T, TE, it, s_lx, s_ly, s_nl);
@@ -953,8 +1000,8 @@ k_ism_sparse(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int m
         };
         float invS = 0.f;
         for (int attempt = 0;; ++attempt) {
-            S = s_S[attempt];
-            invS = s_invS[attempt];
+            S = scale_of(attempt);
+            invS = 1.f / S;
             my_contrib = 0;
             my_taps = 0;
             warp_expand(T, TE, it, s_lx, s_ly, nLX, nLY,
@@ -1101,19 +1148,21 @@ int launch_sparse_t(const RirLaunch &L, cudaStream_t stream) {
     if ((long long)grid > items) grid = (int)items;
     if (grid < 1) return ISM_OK;
     // per-RIR tables: FP64 squares, (hi, lo, damping) and offsets
-    const size_t n_ent = (size_t)L.n_rirs * 3 * Lay.TE;
+    const size_t n_ent = (size_t)L.n_rirs * 3 * Lay.TE;  // even: TE = 2 (2N + 1)
     void *tab = nullptr;
-    if (int st = scratch_alloc(&tab, n_ent * (sizeof(double) + sizeof(float4) + sizeof(float)),
+    if (int st = scratch_alloc(&tab, n_ent * (sizeof(double) + sizeof(float4) + sizeof(float)) +
+                                         (size_t)L.n_rirs * sizeof(JobConst),
                                stream))
         return st;
     double *g_sq = (double *)tab;
     float4 *g_hlg = (float4 *)(g_sq + n_ent);
-    float *g_dl = (float *)(g_hlg + n_ent);
+    JobConst *g_jc = (JobConst *)(g_hlg + n_ent);
+    float *g_dl = (float *)(g_jc + L.n_rirs);
     const int tgrid = (int)std::min<long long>(L.n_rirs, (long long)device_sm_count() * 8);
-    k_ism_tables<<<tgrid, 128, 0, stream>>>(L.jobs_dev, L.n_rirs, Lay.TE, g_sq, g_hlg, g_dl);
+    k_ism_tables<<<tgrid, 128, 0, stream>>>(L.jobs_dev, L.n_rirs, Lay.TE, g_sq, g_hlg, g_dl, g_jc);
     kern<<<grid, NT, Lay.total, stream>>>(L.jobs_dev, L.n_rirs, L.wmax, L.window, L.max_order,
                                           L.max_taps, L.max_cheb, L.tabs_dev, L.h_dev,
-                                          L.stats_dev, L.counter_dev, g_sq, g_hlg, g_dl);
+                                          L.stats_dev, L.counter_dev, g_sq, g_hlg, g_dl, g_jc);
     e = cudaGetLastError();
     scratch_free(tab, stream);
     if (e != cudaSuccess) return cuda_fail(e, "launch k_ism_sparse");
