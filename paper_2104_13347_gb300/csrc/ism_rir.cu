@@ -511,18 +511,21 @@ __device__ __forceinline__ void column_sweep(const Tables &T, int TE, const Item
     if (n_cand > 0) flush(n_cand);
 }
 
-// Warp-independent column sweep with lane-per-candidate expansion.  Warp w
-// takes column batches w, w + NW, ... (32 columns each, one per lane).  Each
-// lane solves its column and, if the column has candidates, its float-float
-// rho^2 = x^2 + y^2 and damping product g_xy once.  A warp-wide scan of the
-// counts numbers the batch's candidates; candidate g goes to lane g mod 32,
-// which finds its column by binary search over the inclusive counts and
-// fetches the column's data with shuffles (two packed words and three
-// floats).  Batches are always 32 candidates wide: the last < 32 candidates
-// of a column batch wait in a per-warp stash of (rho_h, rho_l, g_xy, code)
-// records for the next one.  proc(rho_h, rho_l, g_xy, code, valid) gets one
-// candidate per lane; code = iz | ix << 12 | iy << 22 (iz: absolute index of
-// the z table entry).  No block-wide barrier is involved.
+// Warp-independent column sweep with lane-per-pair expansion.  Warp w takes
+// column batches w, w + NW, ... (32 columns each, one per lane).  Each lane
+// solves its column and, if the column has candidates, its float-float
+// rho^2 = x^2 + y^2 and damping product g_xy once.  The column's candidates
+// (one or two runs of consecutive n) are cut into pairs (n, n + 1), the last
+// pair of an odd run holding one; a warp-wide scan of the pair counts
+// numbers the batch's pairs, and pair g goes to lane g mod 32, which finds
+// its column by binary search over the inclusive counts (the search also
+// yields the column's first pair index) and fetches the column's data with
+// five shuffles.  Batches are always 32 pairs wide: the last < 32 pairs of a
+// column batch wait in a per-warp stash of (rho_h, rho_l, g_xy, code)
+// records for the next one (the sign bit of g_xy >= 0 marks a full pair).
+// proc(rho_h, rho_l, g_xy, code, valid) is called twice per lane, once per
+// element of its pair; code = iz | ix << 12 | iy << 22 (iz: absolute index
+// of the z table entry).  No block-wide barrier is involved.
 template <class Proc>
 __device__ __forceinline__ void warp_expand(const Tables &T, int TE, const Item &it,
                                             const int *s_lx, const int *s_ly, int nLX, int nLY,
@@ -531,10 +534,16 @@ __device__ __forceinline__ void warp_expand(const Tables &T, int TE, const Item 
     const int n_cols = nLX * nLY * 2;  // <= 2 * 802^2
     const int N = it.N;
     int L = 0;  // warp-uniform stash count, < 32
+    auto run_pair = [&](float rh, float rl, float gg, uint32_t code, bool v0) {
+        const bool v1 = v0 && (__float_as_uint(gg) >> 31);
+        gg = fabsf(gg);
+        proc(rh, rl, gg, code, v0);
+        proc(rh, rl, gg, code + 1u, v1);
+    };
     for (int cb = warp * 32; cb < n_cols; cb += NT) {
         const Col col = column_solve(T, TE, it, s_lx, s_ly, nLY, cb + lane, n_cols);
         const int na = max(col.hi_a - col.lo_a + 1, 0), nb = max(col.hi_b - col.lo_b + 1, 0);
-        const int cnt = na + nb;
+        const int cnt = ((na + 1) >> 1) + ((nb + 1) >> 1);  // pairs
         float Rh = 0.f, Rl = 0.f, gxy = 0.f;
         if (cnt > 0) {
             const float4 X = T.hlg[col.ix], Y = T.hlg[TE + col.iy];
@@ -549,31 +558,43 @@ __device__ __forceinline__ void warp_expand(const Tables &T, int TE, const Item 
         }
         const int total = __shfl_sync(0xffffffffu, incl, 31);
         if (total == 0) continue;
-        // packed column data: (iz base, ix, iy) and (first candidate index,
-        // size of interval a, hole between the intervals); all fields fit
-        // (iz < 3 TE <= 2406, ix, iy < 1024, total <= 32 (2N+1) < 2^14,
-        // na, gap <= 2N+1 <= 401)
+        // packed column data (all fields fit: iz < 3 TE <= 2406, ix, iy <
+        // 1024, na, nb, gap <= 2N+1 <= 401)
         const int zbase = 2 * TE + col.wz * (2 * N + 1) + N + col.lo_a;
         const int gap = nb > 0 ? col.lo_b - (col.lo_a + na) : 0;
         const uint32_t k1 = cnt > 0 ? ((uint32_t)zbase | ((uint32_t)col.ix << 12) |
                                        ((uint32_t)col.iy << 22))
                                     : 0u;
-        const uint32_t k2 = (uint32_t)(incl - cnt) | ((uint32_t)na << 14) | ((uint32_t)gap << 23);
+        const uint32_t k2 = (uint32_t)gap | ((uint32_t)na << 9) | ((uint32_t)nb << 18);
+        // pair g: column, code of its first element, second element present
         auto fetch = [&](int g, float &rh, float &rl, float &gg, uint32_t &code) {
-            int c = 0;  // number of lanes whose inclusive count is <= g
+            int c = 0, ex = 0;  // c: lanes whose inclusive count is <= g; ex: their last count
 #pragma unroll
             for (int st = 16; st >= 1; st >>= 1) {
                 const int v = __shfl_sync(0xffffffffu, incl, c + st - 1);
-                if (v <= g) c += st;
+                if (v <= g) { c += st; ex = v; }
             }
             const uint32_t a1 = __shfl_sync(0xffffffffu, k1, c);
             const uint32_t a2 = __shfl_sync(0xffffffffu, k2, c);
             rh = __shfl_sync(0xffffffffu, Rh, c);
             rl = __shfl_sync(0xffffffffu, Rl, c);
-            gg = __shfl_sync(0xffffffffu, gxy, c);
-            const int r = g - (int)(a2 & 0x3fffu);
-            const int iz = (int)(a1 & 4095u) + r + (r >= (int)((a2 >> 14) & 511u) ? (int)(a2 >> 23) : 0);
-            code = (a1 & ~4095u) | (uint32_t)iz;
+            const float g0 = __shfl_sync(0xffffffffu, gxy, c);
+            const int r = g - ex;  // pair index within the column
+            const int ga = (int)(a2 >> 9) & 511, gb = (int)(a2 >> 18) & 511;
+            const int pa = (ga + 1) >> 1;
+            int off;
+            bool two;
+            if (r < pa) {
+                off = 2 * r;
+                two = off + 1 < ga;
+            } else {
+                const int rb = 2 * (r - pa);
+                off = ga + (int)(a2 & 511u) + rb;
+                two = rb + 1 < gb;
+            }
+            code = a1 + (uint32_t)off;
+            // sign bit of g_xy (>= 0): the pair's second element is present
+            gg = __uint_as_float(__float_as_uint(g0) | (two ? 0x80000000u : 0u));
         };
         int pos = 0;
         while (L + (total - pos) >= 32) {
@@ -586,7 +607,7 @@ __device__ __forceinline__ void warp_expand(const Tables &T, int TE, const Item 
             }
             pos += 32 - L;
             L = 0;
-            proc(rh, rl, gg, code, true);
+            run_pair(rh, rl, gg, code, true);
         }
         const int rem = total - pos;
         if (rem > 0) {
@@ -602,7 +623,7 @@ __device__ __forceinline__ void warp_expand(const Tables &T, int TE, const Item 
     if (L > 0) {
         const bool v = lane < L;
         const float4 sv = v ? stash[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
-        proc(sv.x, sv.y, sv.z, __float_as_uint(sv.w), v);
+        run_pair(sv.x, sv.y, sv.z, __float_as_uint(sv.w), v);
     }
     __syncwarp();
 }
