@@ -39,9 +39,13 @@ WORKLOAD = (f"{N_ROOMS} rooms U[3,10]x[3,8]x[2.5,4] m, beta U[0.5,0.95], {N_MICS
 # K1 DRAM traffic per room from the ncu capture summarised in
 # profiles/k_ism_sparse_and_k_conv_tc_1024rooms.md (None when that capture
 # predates the current kernel), and the binding resources it measured.
-K1_TRAFFIC_PER_ROOM = None
-K1_TRAFFIC_NOTE = "no capture of the current kernel yet"
-K1_BINDING = None
+K1_TRAFFIC_PER_ROOM = (8.496384e6 + 10.246656e6) / 256
+K1_TRAFFIC_NOTE = ("dram read+write of a 256-room ncu capture, scaled by rooms; h mostly "
+                   "leaves L2 after the kernel, so this understates its 268 MB write")
+K1_BINDING = {"issue_active_pct": 84.5, "smem_wavefronts_pct_of_peak": 76.0,
+              "fma_pipe_pct": 37.7, "alu_pipe_pct": 43.3, "fp64_pipe_pct": 0.03,
+              "source": "ncu --set full, 256-room case"}
+K2_TRAFFIC_PER_ROOM = (83.75424e6 + 140.089856e6) / 256
 
 
 def k2_live_chunks(n_tiles, ts, lh, kc=64, nn=256):
@@ -87,7 +91,7 @@ class Clocks:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
@@ -296,7 +300,8 @@ def run_ours(args, ws, rank):
     stats = torch.zeros(2 * n_rirs, dtype=torch.int64, device=dev)
     prep = ism.PreparedRooms(rooms)  # rooms marshalled once, outside the timed region
 
-    ism.rir_batch(rooms, h=h, stats=stats, window=args.window)
+    variant = ism.RIR_DIRECT if args.rir_variant == "direct" else ism.RIR_SPARSE
+    ism.rir_batch(rooms, h=h, stats=stats, window=args.window, variant=variant)
     torch.cuda.synchronize()
     taps = int(stats.view(-1, 2)[:, 1].sum().item())
     mic_samples = n_rooms * N_MICS * (TS + LH - 1)
@@ -307,7 +312,7 @@ def run_ours(args, ws, rank):
     def step(ev=None):
         if ev:
             ev[0].record(stream)
-        ism.rir_batch(prep, h=h, window=args.window)
+        ism.rir_batch(prep, h=h, window=args.window, variant=variant)
         if ev:
             ev[1].record(stream)
         ism.convolve_batch(jobs, h, src, y, seed=12345, precision=precision)
@@ -344,7 +349,7 @@ def run_ours(args, ws, rank):
     e_start.record(stream)
     for _ in range(e2e_steps):
         src.copy_(src_host, non_blocking=True)
-        ism.rir_batch(prep, h=h, window=args.window)
+        ism.rir_batch(prep, h=h, window=args.window, variant=variant)
         ism.convolve_batch(jobs, h, src, y, seed=12345, precision=precision)
         y_host.copy_(y, non_blocking=True)
     e_end.record(stream)
@@ -403,7 +408,7 @@ def run_ours(args, ws, rank):
         "secondary": {"mic_samples_per_s": ws * mic_samples / (ms_step * 1e-3),
                       "taps_per_step": taps, "mic_samples_per_step": mic_samples,
                       "stage_ms": {"rir": rir_med, "conv_noise": conv_med}},
-        "roofline": {"bound": "alu", "kernel": "k_ism_sparse", "achieved": k1_rate / 1e12,
+        "roofline": {"bound": "alu", "kernel": "k_ism_sparse" if args.rir_variant == "sparse" else "k_ism_taps", "achieved": k1_rate / 1e12,
                      "peak": peak_fp32 / 1e12, "unit": "TFLOP/s", "frac": k1_rate / peak_fp32,
                      "traffic": K1_TRAFFIC_PER_ROOM * n_rooms if K1_TRAFFIC_PER_ROOM else None,
                      "traffic_note": K1_TRAFFIC_NOTE,
@@ -419,6 +424,8 @@ def run_ours(args, ws, rank):
             "frac": k2_alg / (k2_ms * 1e-3) / bf16_peak,
             "executed_tflops": k2_exec / (k2_ms * 1e-3) / 1e12,
             "executed_frac": k2_exec / (k2_ms * 1e-3) / bf16_peak, "ms": k2_ms,
+            "traffic": K2_TRAFFIC_PER_ROOM * n_rooms,
+            "traffic_note": "dram read+write of a 256-room ncu capture, scaled by rooms",
             "work": "3 x 2 Ts Lh per mic (split-BF16 minimum); executed: 8 MMAs 128x256x16 "
                     "per live 64-tap chunk per tile",
             "peak_note": f"dense bf16, {pk_kind} burst (kernel timed alone)"},
@@ -440,12 +447,14 @@ def run_ours(args, ws, rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="bf16x3", choices=["f32", "bf16x3"],
                     help="convolution arithmetic (both meet 1e-5 rel-L2 on this workload)")
     ap.add_argument("--window", type=int, default=0)
+    ap.add_argument("--rir-variant", default="sparse", choices=["sparse", "direct"],
+                    help="K1 kernel: sparse Chebyshev arrays (default) or the direct per-tap one")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-rate", type=float, default=500.0,
                     help="Poisson arrival rate of the served stream (0 = skip)")
