@@ -276,6 +276,39 @@ def run_served(ism, wl, rate, seconds, precision, seed=1006):
                         "RT60 U[0.1,0.6] s (Sabine), sources 0.5-4 s, SNR U[0,30] dB"}
 
 
+def run_paper_dataset(ism, wl, n_sources, dev, stream):
+    """RIR throughput on the paper's own dataset geometry: the 7 x 10 x 3.7 m
+    classroom at RT 0.5 s, UMA-8 array, torus sources, 44.1 kHz, delay-limited
+    image sets; the benchmark spec 81-tap Hann sinc and the paper's 8-tap
+    Lagrange filter.  Projects the time of one room's 336000 RIRs."""
+    import torch
+    out = {"workload": f"{n_sources} torus sources x 7 mics, room 7x10x3.7 m, RT 0.5 s "
+                       "(Sabine), 44.1 kHz, RIR 22050, order auto"}
+    for name, kind, taps in (("hann81", 0, 81), ("lagrange8", 1, 8)):
+        rooms = wl.paper_dataset(n_sources, room=1, seed=2021, fd_kind=kind, n_taps=taps)
+        n_rirs, hl = ism.rir_batch_size(rooms)
+        h = torch.empty(hl, device=dev)
+        stats = torch.zeros(2 * n_rirs, dtype=torch.int64, device=dev)
+        ism.rir_batch(rooms, h=h, stats=stats)
+        prep = ism.PreparedRooms(rooms)
+        ism.rir_batch(prep, h=h)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        torch.cuda.synchronize()
+        e[0].record(stream)
+        for _ in range(3):
+            ism.rir_batch(prep, h=h)
+        e[1].record(stream)
+        torch.cuda.synchronize()
+        ms = e[0].elapsed_time(e[1]) / 3
+        st = stats.view(-1, 2)
+        out[name] = {"ms": ms, "rirs": n_rirs, "rirs_per_s": n_rirs / (ms * 1e-3),
+                     "taps_per_s": int(st[:, 1].sum().item()) / (ms * 1e-3),
+                     "contributing_images_per_rir": int(st[:, 0].sum().item()) / n_rirs,
+                     "s_per_336000_rirs": 336000 / (n_rirs / (ms * 1e-3))}
+        del h, stats
+    return out
+
+
 def run_ours(args, ws, rank):
     import torch
     import paper_2104_13347_gb300 as ism
@@ -435,6 +468,8 @@ def run_ours(args, ws, rank):
         "gpu_launches": args.steps * 4,  # K1 tables + K1, convolution (noise partials fused), noise
         "clocks": clk,
     }
+    if args.paper_sources > 0:
+        line["paper_dataset"] = run_paper_dataset(ism, wl, args.paper_sources, dev, stream)
     if args.serve_rate > 0:
         line["served"] = run_served(ism, wl, args.serve_rate, args.serve_seconds, precision)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -459,6 +494,8 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=500.0,
                     help="Poisson arrival rate of the served stream (0 = skip)")
     ap.add_argument("--serve-seconds", type=float, default=4.0)
+    ap.add_argument("--paper-sources", type=int, default=2048,
+                    help="sources of the paper-dataset RIR measurement (0 = skip)")
     ap.add_argument("--rooms", type=int, default=N_ROOMS,
                     help="rooms per step (smaller only for profiling captures)")
     args = ap.parse_args()

@@ -67,10 +67,18 @@ typedef enum ism_precision { ISM_F32 = 0, ISM_BF16X3 = 1 } ism_precision;
  * mics    host array of 3*n_mics doubles (x,y,z per mic), strictly inside
  *         the room and not on the source.
  * order   lattice order N >= 0: images (u,v,w,l,m,n), u,v,w in {0,1},
- *         l,m,n in [-N, N], 8 (2N+1)^3 in all.
+ *         l,m,n in [-N, N], 8 (2N+1)^3 in all.  ISM_ORDER_AUTO (any
+ *         negative value): per microphone, the smallest N whose lattice
+ *         holds every image able to put a tap into [0, rir_len) -- the
+ *         delay-limited image set of Sec. II.A (every reflection arriving
+ *         within the response).  With d = (rir_len + n_taps) c / fs,
+ *         N = max over axes a and parities p of
+ *         floor((d + |(1-2p) src_a - mic_a|) / (2 dims_a)).
  * fs, c   sampling rate (Hz) and speed of sound (m/s), both > 0.
  * n_taps  fractional-delay filter length (see ism_fd_kind).
  * rir_len RIR length Lh >= 1 in samples; taps outside [0, Lh) are dropped. */
+#define ISM_ORDER_AUTO (-1)
+
 typedef struct ism_room {
     double dims[3];
     double beta[6];

@@ -60,6 +60,8 @@ def _load():
         lib.oracle_rir.argtypes = [P, P, P, P, f64, f64, ctypes.c_int, ctypes.c_int,
                                    ctypes.c_int, i64, P, P]
         lib.oracle_rir.restype = ctypes.c_int
+        lib.oracle_auto_order.argtypes = [P, P, P, f64, f64, ctypes.c_int, i64]
+        lib.oracle_auto_order.restype = ctypes.c_int
         lib.oracle_images.argtypes = [P, P, P, P, f64, f64, ctypes.c_int, P, P, P]
         lib.oracle_images.restype = i64
         lib.oracle_rir_batch.argtypes = [i64, P, P, P, P, P, P, P, P, ctypes.c_int]
@@ -101,6 +103,13 @@ def rir(dims, beta, src, mic, fs, c, order, n_taps=81, fd_kind=FD_HANN_SINC, rir
     if return_stats:
         return h, {"images": int(st[0]), "contributing": int(st[1]), "taps": int(st[2])}
     return h
+
+
+def auto_order(dims, src, mic, fs, c, n_taps, rir_len):
+    """Order of the delay-limited image set (order < 0 in rir / rir_batch)."""
+    lib = _load()
+    return int(lib.oracle_auto_order(_p(_f64(dims)), _p(_f64(src)), _p(_f64(mic)), float(fs),
+                                     float(c), int(n_taps), int(rir_len)))
 
 
 def images(dims, beta, src, mic, fs, c, order):

@@ -142,14 +142,37 @@ void oracle_lagrange_taps(double D, int n_taps, double *out)
 /* One RIR: direct sum over every image of the (2N+1)^3 x 8 lattice.        */
 /* ------------------------------------------------------------------------ */
 
+/* Lattice order of the delay-limited image set (Sec. II.A keeps every
+ * reflection that arrives within the reverberation time, i.e. within the
+ * response): the smallest N whose cubic lattice holds every image able to
+ * put a tap into [0, Lh).  The first tap of an image with delay tau lies at
+ * or after tau - n_taps, so no image farther than
+ * d_reach = (Lh + n_taps) c / fs reaches the response; along axis a the
+ * image offset (1-2p) s + 2 q L - r is within d_reach only for
+ * |q| <= (d_reach + |(1-2p) s - r|) / (2 L). */
+int oracle_auto_order(const double *dims, const double *src, const double *mic, double fs,
+                      double c, int n_taps, int64_t rir_len)
+{
+    const double d_reach = ((double)rir_len + (double)n_taps) * c / fs;
+    int N = 0;
+    for (int a = 0; a < 3; ++a)
+        for (int p = 0; p <= 1; ++p) {
+            const double cp = (p ? -src[a] : src[a]) - mic[a];
+            const int na = (int)floor((d_reach + fabs(cp)) / (2.0 * dims[a]));
+            if (na > N) N = na;
+        }
+    return N;
+}
+
 /* stats[0] = images enumerated, stats[1] = images with at least one tap in
- * [0, Lh), stats[2] = taps that landed in [0, Lh). */
+ * [0, Lh), stats[2] = taps that landed in [0, Lh).  order < 0: the
+ * delay-limited lattice of oracle_auto_order. */
 int oracle_rir(const double *dims, const double *beta, const double *src, const double *mic,
                double fs, double c, int order, int n_taps, int fd_kind, int64_t rir_len,
                double *h, int64_t *stats)
 {
     const double q = fs / c;
-    const int N = order;
+    const int N = order < 0 ? oracle_auto_order(dims, src, mic, fs, c, n_taps, rir_len) : order;
     int64_t n_img = 0, n_contrib = 0, n_in = 0;
     for (int64_t i = 0; i < rir_len; ++i) h[i] = 0.0;
 

@@ -161,7 +161,6 @@ int validate_room(const ism_room &r, int64_t idx) {
     }
     if (!(r.fs > 0.0) || !isfinite(r.fs)) return bad("fs must be > 0");
     if (!(r.c > 0.0) || !isfinite(r.c)) return bad("c must be > 0");
-    if (r.order < 0 || r.order > 200) return bad("order must lie in [0, 200]");
     if (r.rir_len < 1 || r.rir_len > (int64_t)1 << 30) return bad("rir_len must lie in [1, 2^30]");
     if (r.fd_kind == ISM_FD_HANN_SINC) {
         if (r.n_taps < 1 || r.n_taps % 2 == 0 || r.n_taps > 255)
@@ -172,11 +171,35 @@ int validate_room(const ism_room &r, int64_t idx) {
     } else {
         return bad("unknown fd_kind");
     }
+    int order = r.order;
+    for (int m = 0; m < r.n_mics; ++m) order = std::max(order, room_order(r, m));
+    if (order > 200)
+        return bad(r.order < 0 ? "the delay-limited lattice needs an order above 200"
+                               : "order must lie in [0, 200] (or ISM_ORDER_AUTO)");
     // largest delay must stay representable in the FP32 integer part
     double reach = 0.0;
-    for (int a = 0; a < 3; ++a) reach += pow((2.0 * r.order + 1.0) * r.dims[a] * 2.0, 2.0);
+    for (int a = 0; a < 3; ++a) reach += pow((2.0 * order + 1.0) * r.dims[a] * 2.0, 2.0);
     if (sqrt(reach) * r.fs / r.c > 8.0e6) return bad("lattice delays exceed 8e6 samples");
     return ISM_OK;
+}
+
+// Lattice order of RIR (room r, mic m): the room's order, or for
+// ISM_ORDER_AUTO the smallest N whose lattice holds every image able to put
+// a tap into [0, rir_len): the first tap of an image at delay tau is at or
+// after tau - n_taps, so only images within reach = (rir_len + n_taps) c/fs
+// matter, and along axis a the offset (1-2p) s + 2 q L - r stays within
+// reach only for |q| <= (reach + |(1-2p) s - r|) / (2 L).
+int room_order(const ism_room &r, int m) {
+    if (r.order >= 0) return r.order;
+    const double reach = ((double)r.rir_len + (double)r.n_taps) * r.c / r.fs;
+    const double *mic = r.mics + 3 * m;
+    int n = 0;
+    for (int a = 0; a < 3; ++a) {
+        const double e = std::max(fabs(r.src[a] - mic[a]), fabs(-r.src[a] - mic[a]));
+        const double na = floor((reach + e) / (2.0 * r.dims[a]));
+        n = std::max(n, na > 1e6 ? 1000000 : (int)na);
+    }
+    return n;
 }
 
 // ---------------------------------------------------------------------------
@@ -322,7 +345,7 @@ int ism_rir_batch_ex(const ism_room *rooms, int64_t n_rooms, float *h_dev,
             }
             J.q = R.fs / R.c;
             for (int w = 0; w < 6; ++w) J.beta[w] = (float)R.beta[w];
-            J.order = R.order;
+            J.order = room_order(R, m);
             J.n_taps = R.n_taps;
             J.fd_kind = (int16_t)kind;
             J.rir_len = R.rir_len;
@@ -333,7 +356,7 @@ int ism_rir_batch_ex(const ism_room *rooms, int64_t n_rooms, float *h_dev,
             if (J.h_offset < 0) return fail(ISM_ERR_INVALID_ARG, "negative h offset");
             jobs[kind].push_back(J);
             room_of[kind].push_back(r);
-            max_order[kind] = std::max(max_order[kind], R.order);
+            max_order[kind] = std::max(max_order[kind], J.order);
             max_taps[kind] = std::max(max_taps[kind], R.n_taps);
             wmax[kind] = std::max(wmax[kind], J.n_windows);
         }

@@ -65,6 +65,10 @@ void scratch_free(void *p, cudaStream_t stream);
 
 int device_sm_count();
 
+// Lattice order of RIR (room r, mic m): the room's order, or the
+// delay-limited order for ISM_ORDER_AUTO (see ism.h).
+int room_order(const ism_room &r, int m);
+
 // K1: image-source taps.  jobs_dev has n_rirs jobs; every job's windows are
 // processed; wmax = max n_windows.  counter_dev: one zeroed uint32 work
 // counter.  max_order / max_taps size the shared memory and tap rows.

@@ -86,7 +86,7 @@ extern "C" int ism_rir_batch_noalloc(const ism_room *rooms, int64_t n_rooms, flo
         if (int st = validate_room(R, r)) return st;
         const int k = R.fd_kind;
         count[k] += R.n_mics;
-        max_order[k] = std::max(max_order[k], R.order);
+        for (int m = 0; m < R.n_mics; ++m) max_order[k] = std::max(max_order[k], room_order(R, m));
         max_taps[k] = std::max(max_taps[k], R.n_taps);
         wmax[k] = std::max(wmax[k], (int)((R.rir_len + W - 1) / W));
     }
@@ -128,7 +128,7 @@ extern "C" int ism_rir_batch_noalloc(const ism_room *rooms, int64_t n_rooms, flo
                 }
                 J.q = R.fs / R.c;
                 for (int w = 0; w < 6; ++w) J.beta[w] = (float)R.beta[w];
-                J.order = R.order;
+                J.order = room_order(R, m);
                 J.n_taps = R.n_taps;
                 J.fd_kind = k;
                 J.rir_len = R.rir_len;

@@ -148,3 +148,62 @@ def serve_stream(n_requests=256, rate_hz=1000.0, seed=1006, rt_lo=0.1, rt_hi=0.6
                           order=order, n_taps=n_taps, fd_kind=FD_HANN_SINC, rir_len=rir_len))
         srcs.append(rng.standard_normal(int(rng.uniform(src_lo, src_hi) * fs)).astype(np.float32))
     return t, rooms, srcs, rng.uniform(0, 30, n_requests).astype(np.float32)
+
+
+# ---------------------------------------------------------------------------
+# The paper's own dataset geometry (Sec. II.A and III.A; the recordings and
+# the trained network are not available, so only the geometry is drawn)
+# ---------------------------------------------------------------------------
+
+# Room 1: 7 x 10 x 3.7 m classroom with the array at [4, 6, 1.5]; room 2:
+# 5 x 5 x 4 m, array position not stated (taken at the horizontal centre,
+# 1.5 m high); both at RT 0.5 s.  Frames of 1024 samples last 23.2 ms, so
+# fs = 44.1 kHz.
+PAPER_ROOMS = {
+    1: (np.array([7.0, 10.0, 3.7]), np.array([4.0, 6.0, 1.5])),
+    2: (np.array([5.0, 5.0, 4.0]), np.array([2.5, 2.5, 1.5])),
+}
+PAPER_FS = 44100.0
+PAPER_RT = 0.5
+
+
+def uma8_array(center, radius=0.04):
+    """7 microphones: one at the centre and six on a horizontal circle of
+    radius 4 cm (8 cm diameter) around it."""
+    ring = circular_array(center, 6, radius)
+    return np.vstack([np.asarray(center, float)[None, :], ring])
+
+
+def torus_sources(n, center, dims, seed=1007, R=2.0, dR=0.5, dphi_deg=7.0, clearance=0.1):
+    """Source positions in the torus around the array centre: distance
+    U[R - dR, R + dR], azimuth U[0, 2 pi), elevation U[-dphi, dphi]; draws
+    closer than `clearance` to a wall are redrawn."""
+    rng = np.random.default_rng(seed)
+    c0 = np.asarray(center, float)
+    L = np.asarray(dims, float)
+    out = np.empty((n, 3))
+    k = 0
+    while k < n:
+        r = rng.uniform(R - dR, R + dR)
+        th = rng.uniform(0.0, 2.0 * np.pi)
+        ph = np.deg2rad(rng.uniform(-dphi_deg, dphi_deg))
+        p = c0 + r * np.array([np.cos(ph) * np.cos(th), np.cos(ph) * np.sin(th), np.sin(ph)])
+        if np.all(p > clearance) and np.all(p < L - clearance):
+            out[k] = p
+            k += 1
+    return out
+
+
+def paper_dataset(n_sources=1024, room=1, seed=1007, fd_kind=FD_HANN_SINC, n_taps=81, rt=None):
+    """One request per source position: the paper room `room` (1 or 2) at
+    RT 0.5 s (Sabine walls), the UMA-8 array, fs 44.1 kHz, RIR length RT fs,
+    and the delay-limited image set (order -1 = automatic).  fd_kind
+    FD_LAGRANGE with n_taps 8 is the paper's own 7th-order filter."""
+    dims, ctr = PAPER_ROOMS[room]
+    rt = PAPER_RT if rt is None else rt
+    mics = uma8_array(ctr)
+    beta = np.full(6, sabine_beta(dims, rt))
+    srcs = torus_sources(n_sources, ctr, dims, seed=seed)
+    L = int(round(rt * PAPER_FS))
+    return [dict(dims=dims, beta=beta, src=s, mics=mics, fs=PAPER_FS, c=343.0, order=-1,
+                 n_taps=n_taps, fd_kind=fd_kind, rir_len=L) for s in srcs]

@@ -65,7 +65,8 @@ BAD = {
     "unknown filter": dict(fd_kind=5),
     "fs zero": dict(fs=0.0),
     "c negative": dict(c=-343.0),
-    "order negative": dict(order=-1),
+    "auto order above 200": dict(dims=[0.5, 0.5, 0.5], src=[0.2, 0.2, 0.2],
+                                 mics=[[0.3, 0.3, 0.3]], order=-1, rir_len=100000),
     "order too high": dict(order=201),
     "empty rir": dict(rir_len=0),
     "no mics": dict(mics=np.zeros((0, 3))),

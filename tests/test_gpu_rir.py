@@ -226,3 +226,31 @@ def test_sparse_path_is_bitwise_reproducible(ism):
     h2 = ism.rir_batch(prep)
     torch.cuda.synchronize()
     assert torch.equal(h1, h2)
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_auto_order_delay_limited(ism, variant):
+    """ISM_ORDER_AUTO: per mic, the lattice that holds every image reaching
+    the response (the paper's RT-limited image set, Sec. II.A); the RIR and
+    the statistics equal the oracle's, and an explicitly larger order gives
+    the same RIR."""
+    import torch
+    dims = np.array([6.0, 4.5, 3.2])
+    rt, fs = 0.3, 16000.0
+    L = int(rt * fs)
+    room = dict(dims=dims, beta=np.full(6, wl.sabine_beta(dims, rt)), src=np.array([1.3, 3.1, 1.1]),
+                mics=wl.circular_array(np.array([4.0, 2.0, 1.4]), 3, 0.05), fs=fs, c=343.0,
+                order=-1, n_taps=81, fd_kind=0, rir_len=L)
+    stats = torch.zeros(6, dtype=torch.int64, device="cuda")
+    h = ism.rir_batch([room], stats=stats, variant=variant)
+    N = max(oracle.auto_order(dims, room["src"], m, fs, 343.0, 81, L) for m in room["mics"])
+    h_big = ism.rir_batch([dict(room, order=N + 2)], variant=variant)
+    torch.cuda.synchronize()
+    ref, ost = oracle.rir_batch([room])
+    hh = h.cpu().numpy().astype(np.float64).reshape(3, L)
+    for m in range(3):
+        assert rel_l2(hh[m], ref[0][m]) <= 1e-5
+    st = stats.view(3, 2).cpu().numpy()
+    np.testing.assert_array_equal(st[:, 0], ost[:, 1])
+    np.testing.assert_array_equal(st[:, 1], ost[:, 2])
+    assert torch.equal(h, h_big)

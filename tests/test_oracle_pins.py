@@ -348,3 +348,45 @@ def test_noise_reaches_snr():
     assert abs(sigma - math.sqrt(p_sig / 10 ** 1.25)) < 1e-15
     snr = 10 * np.log10(p_sig / np.mean(n ** 2))
     assert abs(snr - 12.5) < 0.05
+
+
+# ---------------------------------------------------------------------------
+# Delay-limited image sets (Sec. II.A: every reflection arriving within the
+# reverberation time is kept; the paper's 7 x 10 x 3.7 m room at RT 0.5 s
+# needs reflections up to about the 60th order, more than 80000 images).
+# ---------------------------------------------------------------------------
+
+def test_auto_order_covers_every_image_within_reach():
+    """No image that can put a tap into [0, Lh) lies outside the automatic
+    lattice (checked on a lattice two orders larger), and the RIR does not
+    change when the lattice grows."""
+    dims, src, mic = np.array([4.3, 3.1, 2.7]), np.array([1.1, 2.2, 0.9]), np.array([3.0, 0.7, 1.8])
+    beta = np.array([0.9, 0.7, 0.8, 0.95, 0.6, 0.85])
+    fs, c, L, taps = 16000.0, 343.0, 1500, 81
+    N = oracle.auto_order(dims, src, mic, fs, c, taps, L)
+    reach = (L + taps) * c / fs
+    big = oracle.images(dims, beta, src, mic, fs, c, N + 2)
+    far = np.abs(big["idx"][:, 3:]).max(axis=1) > N
+    assert not np.any(far & (big["d"] <= reach))
+    h_auto, st_auto = oracle.rir(dims, beta, src, mic, fs, c, -1, taps, 0, L, return_stats=True)
+    h_big, st_big = oracle.rir(dims, beta, src, mic, fs, c, N + 3, taps, 0, L, return_stats=True)
+    np.testing.assert_array_equal(h_auto, h_big)
+    assert st_auto["contributing"] == st_big["contributing"] and st_auto["taps"] == st_big["taps"]
+    assert st_auto["images"] == 8 * (2 * N + 1) ** 3
+
+
+def test_paper_room_images_within_rt():
+    """The paper's classroom (7 x 10 x 3.7 m, array at [4, 6, 1.5], RT 0.5 s,
+    44.1 kHz): more than 80000 images arrive within the RT, with reflection
+    orders up to the mid-fifties (the paper quotes 'up to the 60th order')."""
+    dims, mic, src = np.array([7.0, 10.0, 3.7]), np.array([4.0, 6.0, 1.5]), np.array([6.0, 6.5, 1.6])
+    fs, c, rt = 44100.0, 343.0, 0.5
+    N = oracle.auto_order(dims, src, mic, fs, c, 81, int(rt * fs))
+    im = oracle.images(dims, np.full(6, 0.9), src, mic, fs, c, N)
+    keep = im["d"] <= c * rt
+    u, v, w, l, m, n = (im["idx"][:, i] for i in range(6))
+    refl = np.abs(l - u) + np.abs(l) + np.abs(m - v) + np.abs(m) + np.abs(n - w) + np.abs(n)
+    assert 80000 < keep.sum() < 90000
+    assert 50 <= refl[keep].max() <= 60
+    # density check: the count matches the sphere volume over the room volume
+    assert abs(keep.sum() / (4 / 3 * np.pi * (c * rt) ** 3 / np.prod(dims)) - 1) < 0.01
