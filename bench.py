@@ -276,6 +276,36 @@ def run_served(ism, wl, rate, seconds, precision, seed=1006):
                         "RT60 U[0.1,0.6] s (Sabine), sources 0.5-4 s, SNR U[0,30] dB"}
 
 
+def run_frames(ism, n_frames, y, n_rooms, T, stream, hbm_gbs, pk_kind):
+    """Training frames (1024 samples x 8 mics) cut from the step's convolved
+    signals at random rooms and offsets, SNR 20 dB + Exp(10 dB); HBM roofline
+    on the frame's read and write."""
+    import torch
+    rng = np.random.default_rng(31)
+    rr = rng.integers(0, n_rooms, n_frames)
+    t0 = rng.integers(0, T - 1024, n_frames)
+    snr = 20.0 + rng.exponential(10.0, n_frames)
+    jobs, n_out = ism.frame_jobs(rr * N_MICS * T, [T] * n_frames, [N_MICS] * n_frames, t0, 1024,
+                                 snr_db=snr)
+    out = torch.empty(n_out, device=y.device)
+    ism.frames_batch(jobs, 1024, y, out, seed=7)
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    torch.cuda.synchronize()
+    e[0].record(stream)
+    for _ in range(3):
+        ism.frames_batch(jobs, 1024, y, out, seed=7)
+    e[1].record(stream)
+    torch.cuda.synchronize()
+    ms = e[0].elapsed_time(e[1]) / 3
+    gbs = 2.0 * n_out * 4 / (ms * 1e-3) / 1e9
+    return {"frames": n_frames, "shape": "8 mics x 1024 samples", "ms": ms,
+            "frames_per_s": n_frames / (ms * 1e-3),
+            "roofline": {"bound": "hbm", "kernel": "k_frames", "achieved": gbs, "peak": hbm_gbs,
+                         "unit": "GB/s", "frac": gbs / hbm_gbs,
+                         "work": "read + write of every frame sample (8 B)",
+                         "peak_note": f"{pk_kind} copy bandwidth"}}
+
+
 def run_paper_dataset(ism, wl, n_sources, dev, stream):
     """RIR throughput on the paper's own dataset geometry: the 7 x 10 x 3.7 m
     classroom at RT 0.5 s, UMA-8 array, torus sources, 44.1 kHz, delay-limited
@@ -468,6 +498,9 @@ def run_ours(args, ws, rank):
         "gpu_launches": args.steps * 4,  # K1 tables + K1, convolution (noise partials fused), noise
         "clocks": clk,
     }
+    if args.frames > 0:
+        line["frames"] = run_frames(ism, args.frames, y, n_rooms, TS + LH - 1, stream,
+                                    pk.get("hbm_gbs", 6800.0), pk_kind)
     if args.paper_sources > 0:
         line["paper_dataset"] = run_paper_dataset(ism, wl, args.paper_sources, dev, stream)
     if args.serve_rate > 0:
@@ -494,6 +527,8 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=500.0,
                     help="Poisson arrival rate of the served stream (0 = skip)")
     ap.add_argument("--serve-seconds", type=float, default=4.0)
+    ap.add_argument("--frames", type=int, default=65536,
+                    help="training frames of the frame measurement (0 = skip)")
     ap.add_argument("--paper-sources", type=int, default=2048,
                     help="sources of the paper-dataset RIR measurement (0 = skip)")
     ap.add_argument("--rooms", type=int, default=N_ROOMS,

@@ -222,14 +222,56 @@ int ism_convolve_batch(const ism_conv_job *jobs, int64_t n_jobs, const float *h_
                        int32_t precision, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Training frames: the network of the paper reads multichannel windows of
+ * 1024 samples (23.2 ms at 44.1 kHz) of the convolved signals, with
+ * measurement noise added at a chosen SNR as data augmentation
+ * (Sec. II.B and III.A).  (The paper draws these windows inside its
+ * training pipeline; this call is the batched GPU form of that step.)
+ * ------------------------------------------------------------------------ */
+
+/* One frame.
+ * y_offset    element offset of the room's signals in y_dev: n_mics rows of
+ *             y_len samples, mic-major, as ism_convolve_batch writes them.
+ * y_len       samples per mic of the room's signals (>= 1).
+ * t0          first sample of the frame; samples outside [0, y_len) read as
+ *             0 (t0 may be negative or run past the end).
+ * out_offset  element offset of the frame in frames_dev: n_mics rows of
+ *             frame_len samples, mic-major.
+ * noise_id    identifies the frame's noise streams (with the call's seed).
+ * n_mics      microphones (rows) of the frame, >= 1.
+ * snr_db      SNR of the added noise, relative to the frame's own mean
+ *             power over its mics and samples: sigma^2 = P / 10^(snr/10),
+ *             noise sigma z, z standard normal from SplitMix64 counters
+ *             (stream key out(seed, noise_id * 65536 + mic), uniforms from
+ *             outputs 2i and 2i + 1 at sample i of the frame, Box--Muller
+ *             cosine branch).  NaN or +inf: a clean copy. */
+typedef struct ism_frame_job {
+    int64_t y_offset;
+    int64_t y_len;
+    int64_t t0;
+    int64_t out_offset;
+    uint64_t noise_id;
+    int32_t n_mics;
+    float snr_db;
+} ism_frame_job;
+
+/* ism_frames_batch -- cut n_frames frames of frame_len samples and add their
+ * noise.  jobs: host array; y_dev, frames_dev: device floats (must not
+ * overlap).  Errors: ISM_ERR_INVALID_ARG (NULL pointers, frame_len < 1,
+ * n_mics < 1, y_len < 1, negative offsets, SNR = -inf), ISM_ERR_CUDA,
+ * ISM_ERR_OUT_OF_MEMORY (scratch). */
+int ism_frames_batch(const ism_frame_job *jobs, int64_t n_frames, int32_t frame_len,
+                     const float *y_dev, float *frames_dev, uint64_t seed, void *stream);
+
+/* ------------------------------------------------------------------------
  * Serving: continuous batching of RIR + convolution requests.
  * Requests of uneven sizes arrive at any time; a background thread admits
  * them while device memory (max_hbm_bytes) and slots allow, packs the
  * admitted ones into ragged batches, and runs them on its streams so that
  * batches overlap on the GPU.  Results stay on the device until released.
  * Each request's work items (RIR windows, convolution tiles, noise streams
- * keyed by its noise_id) are the same alone or mixed with others; the RIR
- * sums use shared-memory atomics, so results agree to FP32 rounding.
+ * keyed by its noise_id) are the same alone or mixed with others, bit for
+ * bit (the sparse RIR path sums in fixed point).
  * ------------------------------------------------------------------------ */
 typedef struct ism_server ism_server;
 

@@ -79,6 +79,8 @@ def _load():
         lib.oracle_uniforms.argtypes = [u64, u64, u64, u64, i64, P, P]
         lib.oracle_add_noise.argtypes = [P, ctypes.c_int, i64, f64, u64, u64]
         lib.oracle_add_noise.restype = f64
+        lib.oracle_frame.argtypes = [P, ctypes.c_int, i64, i64, ctypes.c_int, f64, u64, u64, P]
+        lib.oracle_frame.restype = f64
         _lib = lib
         return lib
 
@@ -252,6 +254,20 @@ def uniforms(seed, room, mic, t0, n):
     u2 = np.zeros(n, np.float64)
     _load().oracle_uniforms(seed, room, mic, t0, n, _p(u1), _p(u2))
     return u1, u2
+
+
+def frame(y, t0, frame_len, snr_db, seed, frame_id):
+    """One training frame from a room's signals y (n_mics, y_len): the slice
+    [t0, t0 + frame_len) (zero outside), plus noise at snr_db (NaN / inf =
+    clean).  Returns (frame (n_mics, frame_len) FP64, sigma)."""
+    lib = _load()
+    y = np.ascontiguousarray(np.asarray(y, np.float64))
+    if y.ndim == 1:
+        y = y[None, :]
+    out = np.zeros((y.shape[0], int(frame_len)), np.float64)
+    sig = lib.oracle_frame(_p(y), int(y.shape[0]), int(y.shape[1]), int(t0), int(frame_len),
+                           float(snr_db), int(seed), int(frame_id), _p(out))
+    return out, float(sig)
 
 
 def add_noise(y, snr_db, seed, room):

@@ -378,6 +378,32 @@ void oracle_uniforms(uint64_t seed, uint64_t room, uint64_t mic, uint64_t t0, in
     }
 }
 
+/* One training frame (Sec. II.B: the network reads multichannel windows of
+ * the convolved signals; Sec. III.A: measurement noise at a drawn SNR):
+ *   x[m][i] = y[m][t0 + i], 0 outside [0, y_len),  i < frame_len,
+ *   sigma^2 = mean of x^2 over the frame / 10^(snr/10),
+ *   out[m][i] = x[m][i] + sigma z, z = oracle_gauss(seed, id, m, i).
+ * snr_db NaN or +inf: a clean copy.  y: n_mics rows of y_len; out: n_mics
+ * rows of frame_len.  Returns sigma (0 for a clean copy). */
+double oracle_frame(const double *y, int n_mics, int64_t y_len, int64_t t0, int frame_len,
+                    double snr_db, uint64_t seed, uint64_t id, double *out)
+{
+    for (int m = 0; m < n_mics; ++m)
+        for (int i = 0; i < frame_len; ++i) {
+            int64_t t = t0 + i;
+            out[(int64_t)m * frame_len + i] = (t >= 0 && t < y_len) ? y[(int64_t)m * y_len + t] : 0.0;
+        }
+    if (isnan(snr_db) || isinf(snr_db)) return 0.0;
+    double p = 0.0;
+    for (int64_t e = 0; e < (int64_t)n_mics * frame_len; ++e) p += out[e] * out[e];
+    p /= (double)n_mics * (double)frame_len;
+    double sigma = sqrt(p / pow(10.0, snr_db / 10.0));
+    for (int m = 0; m < n_mics; ++m)
+        for (int i = 0; i < frame_len; ++i)
+            out[(int64_t)m * frame_len + i] += sigma * oracle_gauss(seed, id, (uint64_t)m, (uint64_t)i);
+    return sigma;
+}
+
 /* Adds noise in place to one room's signals y[mic][0..T) (mic-major,
  * stride T).  Returns sigma. */
 double oracle_add_noise(double *y, int n_mics, int64_t T, double snr_db, uint64_t seed,

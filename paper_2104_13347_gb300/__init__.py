@@ -3,7 +3,8 @@
 The dataset-generation hot path of arXiv 2104.13347 (Sec. II.A): shoebox
 room impulse responses from the image-source method with fractional delays,
 then batch convolution of source signals with the RIRs into microphone
-pressure, with additive noise at a chosen SNR (Sec. III.A).  The compute runs
+pressure, with additive noise at a chosen SNR (Sec. III.A), and the noisy
+multichannel training frames cut from those signals (Sec. II.B / III.A).  The compute runs
 in libism.so (hand-written CUDA for sm_103a) behind the C ABI of
 include/ism.h; this package is its Python binding.
 
@@ -11,10 +12,10 @@ include/ism.h; this package is its Python binding.
     h = ism.rir_batch(rooms)            # float32 CUDA tensor, packed RIRs
 """
 from ._lib import (BF16X3, F32, FD_HANN_SINC, FD_LAGRANGE, RIR_DIRECT, RIR_SPARSE, IsmError,  # noqa
-                   PreparedRooms, check, conv_jobs, convolve_batch, last_error, load, make_rooms,
-                   rir_batch,
+                   PreparedRooms, check, conv_jobs, convolve_batch, frame_jobs, frames_batch,
+                   last_error, load, make_rooms, rir_batch,
                    rir_batch_noalloc, rir_batch_size, rir_filter_terms, Server)
 
 __all__ = ["load", "rir_batch", "rir_batch_size", "rir_batch_noalloc", "convolve_batch",
-           "conv_jobs", "IsmError", "F32", "BF16X3", "FD_HANN_SINC", "FD_LAGRANGE", "RIR_SPARSE",
+           "conv_jobs", "frame_jobs", "frames_batch", "IsmError", "F32", "BF16X3", "FD_HANN_SINC", "FD_LAGRANGE", "RIR_SPARSE",
            "RIR_DIRECT", "last_error", "check", "make_rooms", "PreparedRooms", "rir_filter_terms", "Server"]

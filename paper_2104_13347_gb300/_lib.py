@@ -45,6 +45,11 @@ class ConvJob(ctypes.Structure):
                 ("snr_db", c_f32), ("reserved2", c_i32), ("noise_id", c_u64)]
 
 
+class FrameJob(ctypes.Structure):
+    _fields_ = [("y_offset", c_i64), ("y_len", c_i64), ("t0", c_i64), ("out_offset", c_i64),
+                ("noise_id", c_u64), ("n_mics", c_i32), ("snr_db", c_f32)]
+
+
 class ServeConfig(ctypes.Structure):
     _fields_ = [("max_hbm_bytes", c_i64), ("max_batch", c_i32), ("n_streams", c_i32),
                 ("precision", c_i32), ("max_queue", c_i32), ("seed", c_u64), ("device", c_i32),
@@ -75,6 +80,7 @@ SIGNATURES = {
     "ism_rir_batch_noalloc": (c_i32, [c_vp, c_i64, c_vp, c_vp, c_vp]),
     "ism_rir_filter_terms": (c_i32, [c_i32, c_i32, c_vp]),
     "ism_convolve_batch": (c_i32, [c_vp, c_i64, c_vp, c_vp, c_vp, c_u64, c_i32, c_vp]),
+    "ism_frames_batch": (c_i32, [c_vp, c_i64, c_i32, c_vp, c_vp, c_u64, c_vp]),
     "ism_serve_create": (c_i32, [c_vp, c_vp]),
     "ism_serve_submit": (c_i32, [c_vp, c_vp, c_vp]),
     "ism_serve_poll": (c_i32, [c_vp, c_u64, c_vp]),
@@ -251,6 +257,32 @@ def convolve_batch(jobs, h, src, y, seed=0, precision=F32, stream=None):
                                     c_vp(y.data_ptr()), c_u64(seed), int(precision),
                                     _stream_ptr(stream)))
     return y
+
+
+def frame_jobs(y_offsets, y_lens, n_mics, t0s, frame_len, snr_db=None, noise_ids=None):
+    """Builds the ism_frame_job array of a batch of frames: frame i reads the
+    room whose signals start at y_offsets[i] (n_mics[i] rows of y_lens[i]
+    samples) from sample t0s[i]; outputs are packed (frame-major, then
+    mic-major).  Returns (jobs ctypes array, packed output length)."""
+    n = len(t0s)
+    jobs = (FrameJob * n)()
+    off = 0
+    for i in range(n):
+        J = jobs[i]
+        J.y_offset, J.y_len, J.t0 = int(y_offsets[i]), int(y_lens[i]), int(t0s[i])
+        J.n_mics = int(n_mics[i])
+        J.out_offset = off
+        J.snr_db = math.nan if snr_db is None else float(snr_db[i])
+        J.noise_id = i if noise_ids is None else int(noise_ids[i])
+        off += J.n_mics * int(frame_len)
+    return jobs, off
+
+
+def frames_batch(jobs, frame_len, y, out, seed=0, stream=None):
+    """ism_frames_batch over a FrameJob array (see frame_jobs)."""
+    check(load().ism_frames_batch(jobs, len(jobs), int(frame_len), c_vp(y.data_ptr()),
+                                  c_vp(out.data_ptr()), c_u64(seed), _stream_ptr(stream)))
+    return out
 
 
 class Server:

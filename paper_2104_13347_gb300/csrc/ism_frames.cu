@@ -1,0 +1,136 @@
+// ism_frames.cu -- training frames cut from the convolved signals, with
+// measurement noise at a per-frame SNR.
+//
+// The network of arXiv 2104.13347 reads multichannel windows of 1024
+// samples (Sec. II.B: 23.2 ms at 44.1 kHz) and is trained with Gaussian
+// measurement noise added at a drawn SNR (Sec. III.A).  For frame f:
+//   x_m[i] = y_m[t0 + i] (0 outside [0, y_len)),  i < frame_len,
+//   sigma^2 = mean over m, i of x_m[i]^2 / 10^(snr/10),
+//   out_m[i] = x_m[i] + sigma z_m[i],
+// z from SplitMix64 counters (key out(seed, noise_id * 65536 + m), uniforms
+// from outputs 2i, 2i + 1, Box--Muller cosine branch), the same recipe as
+// the convolution's noise.
+//
+// One CTA per frame.  The frame's power is a float-float sum per thread and
+// an FP64 sum across threads in a fixed order, so results are bitwise
+// reproducible; the second pass re-reads the frame (L1/L2-resident) and
+// writes it.  HBM-bound: one read and one write of the frame.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "ism_internal.h"
+
+namespace ism {
+namespace {
+
+constexpr int FT = 256;  // threads per CTA
+
+struct FrameJob {
+    int64_t y_offset, y_len, t0, out_offset;
+    uint64_t noise_id;
+    int32_t n_mics;
+    float snr_db;
+};
+static_assert(sizeof(FrameJob) == 48, "FrameJob layout");
+
+__global__ void __launch_bounds__(FT)
+k_frames(const FrameJob *__restrict__ jobs, int frame_len, const float *__restrict__ y,
+         float *__restrict__ out, uint64_t seed) {
+    const FrameJob J = jobs[blockIdx.x];
+    const float *yb = y + J.y_offset;
+    float *ob = out + J.out_offset;
+    const int tid = threadIdx.x;
+    const bool noisy = !isnan(J.snr_db) && !isinf(J.snr_db);
+    float sigma = 0.f;
+    if (noisy) {
+        float ss = 0.f, se = 0.f;
+        for (int m = 0; m < J.n_mics; ++m) {
+            const float *ym = yb + (int64_t)m * J.y_len;
+            for (int i = tid; i < frame_len; i += FT) {
+                const int64_t t = J.t0 + i;
+                const float v = (t >= 0 && t < J.y_len) ? ym[t] : 0.f;
+                ff_accumulate_sq(v, ss, se);
+            }
+        }
+        __shared__ double s_red[FT / 32];
+        __shared__ float s_sigma;
+        const double r = warp_sum_f64((double)ss + (double)se);
+        if ((tid & 31) == 0) s_red[tid >> 5] = r;
+        __syncthreads();
+        if (tid == 0) {
+            double p = 0.0;
+            for (int w = 0; w < FT / 32; ++w) p += s_red[w];
+            p /= (double)J.n_mics * (double)frame_len;
+            s_sigma = (float)sqrt(p / pow(10.0, (double)J.snr_db / 10.0));
+        }
+        __syncthreads();
+        sigma = s_sigma;
+    }
+    for (int m = 0; m < J.n_mics; ++m) {
+        const float *ym = yb + (int64_t)m * J.y_len;
+        float *om = ob + (int64_t)m * frame_len;
+        const uint64_t key = noisy ? sm64_out(seed, J.noise_id * 65536ull + (uint64_t)m) : 0ull;
+        for (int i = tid; i < frame_len; i += FT) {
+            const int64_t t = J.t0 + i;
+            float v = (t >= 0 && t < J.y_len) ? ym[t] : 0.f;
+            if (noisy) {
+                const uint64_t b1 = sm64_out(key, 2 * (uint64_t)i);
+                const uint64_t b2 = sm64_out(key, 2 * (uint64_t)i + 1);
+                const float u1 = ((float)(b1 >> 40) + 0.5f) * (1.0f / 16777216.0f);
+                const float u2 = (float)(b2 >> 40) * (1.0f / 16777216.0f);
+                v += sigma * (sqrtf(-2.f * logf(u1)) * cospif(2.f * u2));
+            }
+            om[i] = v;
+        }
+    }
+}
+
+}  // namespace
+}  // namespace ism
+
+using namespace ism;
+
+extern "C" int ism_frames_batch(const ism_frame_job *jobs, int64_t n_frames, int32_t frame_len,
+                                const float *y_dev, float *frames_dev, uint64_t seed,
+                                void *stream_v) {
+    set_error("");
+    if (n_frames < 0) return fail(ISM_ERR_INVALID_ARG, "n_frames < 0");
+    if (n_frames == 0) return ISM_OK;
+    if (!jobs || !y_dev || !frames_dev) return fail(ISM_ERR_INVALID_ARG, "NULL pointer");
+    if (frame_len < 1) return fail(ISM_ERR_INVALID_ARG, "frame_len < 1");
+    if (n_frames > 0x7fffffff) return fail(ISM_ERR_INVALID_ARG, "too many frames");
+    std::vector<FrameJob> fj((size_t)n_frames);
+    for (int64_t i = 0; i < n_frames; ++i) {
+        const ism_frame_job &J = jobs[i];
+        if (J.n_mics < 1 || J.y_len < 1 || J.y_offset < 0 || J.out_offset < 0)
+            return fail(ISM_ERR_INVALID_ARG, "frame " + std::to_string(i) + ": bad sizes/offsets");
+        if (isinf(J.snr_db) && J.snr_db < 0)
+            return fail(ISM_ERR_INVALID_ARG, "frame " + std::to_string(i) + ": snr -inf");
+        FrameJob &f = fj[(size_t)i];
+        f.y_offset = J.y_offset;
+        f.y_len = J.y_len;
+        f.t0 = J.t0;
+        f.out_offset = J.out_offset;
+        f.noise_id = J.noise_id;
+        f.n_mics = J.n_mics;
+        f.snr_db = J.snr_db;
+    }
+    cudaStream_t stream = (cudaStream_t)stream_v;
+    const size_t bytes = fj.size() * sizeof(FrameJob);
+    void *scr = nullptr;
+    if (int st = scratch_alloc(&scr, bytes, stream)) return st;
+    int st = upload_async(scr, fj.data(), bytes, stream);
+    if (!st) {
+        k_frames<<<(unsigned)n_frames, FT, 0, stream>>>((const FrameJob *)scr, frame_len, y_dev,
+                                                        frames_dev, seed);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) st = cuda_fail(e, "launch k_frames");
+    }
+    scratch_free(scr, stream);
+    return st;
+}

@@ -214,3 +214,19 @@ def test_serve_wait_on_unknown_ticket(lib):
     res = lib.Result()
     assert L.ism_serve_wait(srv, 12345, 0.01, ctypes.byref(res)) == lib.ISM_ERR_UNKNOWN_TICKET
     assert L.ism_serve_destroy(srv) == lib.ISM_OK
+
+
+def test_frames_batch_argument_errors(lib):
+    L = lib.load()
+    fake = ctypes.c_void_p(0x1000)  # never dereferenced: validation comes first
+    jobs, n = lib.frame_jobs([0], [100], [2], [0], 64)
+    assert L.ism_frames_batch(jobs, 1, 64, None, fake, 0, None) == lib.ISM_ERR_INVALID_ARG
+    assert L.ism_frames_batch(jobs, 1, 0, fake, fake, 0, None) == lib.ISM_ERR_INVALID_ARG
+    assert L.ism_frames_batch(jobs, -1, 64, fake, fake, 0, None) == lib.ISM_ERR_INVALID_ARG
+    assert L.ism_frames_batch(None, 0, 64, None, None, 0, None) == lib.ISM_OK
+    for field, val in (("n_mics", 0), ("y_len", 0), ("y_offset", -1), ("out_offset", -1),
+                       ("snr_db", -math.inf)):
+        jobs, n = lib.frame_jobs([0], [100], [2], [0], 64)
+        setattr(jobs[0], field, val)
+        assert L.ism_frames_batch(jobs, 1, 64, fake, fake, 0, None) == lib.ISM_ERR_INVALID_ARG, field
+        assert lib.last_error()

@@ -390,3 +390,42 @@ def test_paper_room_images_within_rt():
     assert 50 <= refl[keep].max() <= 60
     # density check: the count matches the sphere volume over the room volume
     assert abs(keep.sum() / (4 / 3 * np.pi * (c * rt) ** 3 / np.prod(dims)) - 1) < 0.01
+
+
+# ---------------------------------------------------------------------------
+# Training frames (Sec. II.B: 1024-sample multichannel windows; Sec. III.A:
+# measurement noise at a drawn SNR)
+# ---------------------------------------------------------------------------
+
+def test_frame_is_the_slice_with_zero_padding():
+    y = np.random.default_rng(3).standard_normal((4, 300))
+    for t0 in (0, 17, -50, 280, 400, -2000):
+        f, sig = oracle.frame(y, t0, 96, math.inf, 1, 2)
+        assert sig == 0.0
+        exp = np.zeros((4, 96))
+        for i in range(96):
+            if 0 <= t0 + i < 300:
+                exp[:, i] = y[:, t0 + i]
+        np.testing.assert_array_equal(f, exp)
+    f2, _ = oracle.frame(y, 5, 96, math.nan, 1, 2)
+    np.testing.assert_array_equal(f2, y[:, 5:101])
+
+
+def test_frame_noise_snr_and_streams():
+    """The added noise is sigma times the library's Gaussian stream of the
+    frame (one stream per mic, sample index from the frame start) and
+    reaches the requested SNR against the frame's own power."""
+    rng = np.random.default_rng(4)
+    y = rng.standard_normal((7, 5000)) * np.linspace(0.2, 1.0, 5000)
+    clean, _ = oracle.frame(y, 1200, 1024, math.inf, 9, 33)
+    noisy, sig = oracle.frame(y, 1200, 1024, 13.0, 9, 33)
+    p = np.mean(clean ** 2)
+    assert abs(sig - math.sqrt(p / 10 ** 1.3)) <= 1e-15 * sig
+    z = (noisy - clean) / sig
+    for m, i in ((0, 0), (3, 511), (6, 1023)):
+        assert abs(z[m, i] - oracle.gauss(9, 33, m, i)) < 1e-9
+    # SNR of the realised noise (7168 samples: within ~0.2 dB)
+    assert abs(10 * np.log10(p / np.mean((noisy - clean) ** 2)) - 13.0) < 0.25
+    # silence stays silent whatever the SNR
+    z0, s0 = oracle.frame(np.zeros((2, 50)), 0, 32, 10.0, 1, 1)
+    assert s0 == 0.0 and not np.any(z0)
