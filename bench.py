@@ -403,11 +403,23 @@ def run_ours(args, ws, rank):
     ms_step = total_ms / args.steps
     clk = clocks.summary()
 
-    # end to end through the public API with host buffers: pinned source in,
-    # noisy microphone signals out, both copies inside the timed region
+    # end to end through the C-ABI call with HOST buffers (ism_dataset_batch):
+    # pinned sources in, noisy microphone signals out, every copy inside the
+    # timed region; the call overlaps the copies of one chunk of rooms with
+    # the kernels of another and returns when y is in host memory
     y_host = torch.empty(ylen, dtype=torch.float32).pin_memory()
+    lens = [TS] * n_rooms
+    e2e_steps = max(1, min(args.steps, 5))
+    ism.dataset_batch(prep, src_host, lens, y_host, snr_db=snr, seed=12345,
+                      noise_id_base=rank * n_rooms, precision=precision)
+    barrier(ws)
+    t_e = time.perf_counter()
+    for _ in range(e2e_steps):
+        ism.dataset_batch(prep, src_host, lens, y_host, snr_db=snr, seed=12345,
+                          noise_id_base=rank * n_rooms, precision=precision)
+    e2e_ms = max_over_ranks((time.perf_counter() - t_e) * 1e3, ws) / e2e_steps
+    # the same step with the copies and kernels in sequence on one stream
     e_start, e_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e2e_steps = max(1, min(args.steps, 3))
     torch.cuda.synchronize()
     e_start.record(stream)
     for _ in range(e2e_steps):
@@ -417,7 +429,7 @@ def run_ours(args, ws, rank):
         y_host.copy_(y, non_blocking=True)
     e_end.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = max_over_ranks(e_start.elapsed_time(e_end), ws) / e2e_steps
+    e2e_serial_ms = max_over_ranks(e_start.elapsed_time(e_end), ws) / e2e_steps
 
     pk, pk_kind = peaks()
     sm_mhz = pk.get("sm_max_mhz", 2070.0)
@@ -494,7 +506,9 @@ def run_ours(args, ws, rank):
             "peak_note": f"dense bf16, {pk_kind} burst (kernel timed alone)"},
         "e2e": {"value": ws * taps / (e2e_ms * 1e-3), "unit": "taps/s",
                 "h2d_bytes_per_step": int(src_host.numel() * 4),
-                "d2h_bytes_per_step": int(ylen * 4), "ms_per_step": e2e_ms},
+                "d2h_bytes_per_step": int(ylen * 4), "ms_per_step": e2e_ms,
+                "api": "ism_dataset_batch (host buffers, pinned; copies overlap kernels by chunk)",
+                "serial_ms_per_step": e2e_serial_ms},
         "gpu_launches": args.steps * 4,  # K1 tables + K1, convolution (noise partials fused), noise
         "clocks": clk,
     }

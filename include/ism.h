@@ -221,6 +221,36 @@ int ism_convolve_batch(const ism_conv_job *jobs, int64_t n_jobs, const float *h_
                        const float *src_dev, float *y_dev, uint64_t seed,
                        int32_t precision, void *stream);
 
+/* ism_dataset_batch -- the whole dataset step of Sec. II.A with host
+ * buffers: the RIRs of every (room, mic), the convolution of each room's
+ * source with its RIRs and the room's noise, from sources in host memory to
+ * microphone signals in host memory.  The rooms run in chunks on the
+ * library's own streams: while one chunk's kernels run, the next chunk's
+ * sources are uploaded and the previous chunk's signals downloaded (the
+ * host buffers must be page-locked for the copies to overlap; pageable
+ * memory works but serializes).  Results do not depend on the chunking.
+ * rooms, n_rooms  as ism_rir_batch (ISM_ORDER_AUTO included).
+ * src_host        room i's source: src_lens[i] floats at
+ *                 src_host + src_offsets[i] (src_offsets NULL: packed in
+ *                 room order).
+ * snr_db          host, one SNR per room (NaN: no noise), or NULL (no noise).
+ * seed            noise seed; room i's noise id is noise_id_base + i.
+ * precision       ISM_F32 or ISM_BF16X3.
+ * y_host          room i's n_mics x (src_lens[i] + rir_len - 1) floats,
+ *                 mic-major, at y_host + y_offsets[i] (NULL: packed).
+ * h_host          nullable: the RIRs too, room i's n_mics x rir_len floats
+ *                 at h_host + h_offsets[i] (NULL offsets: packed).
+ * chunk_rooms     rooms per chunk, or 0: chunks of about 256 MB of signals,
+ *                 at least four when there are four rooms.
+ * Returns when every output is in host memory.  Errors: those of
+ * ism_rir_batch and ism_convolve_batch, ISM_ERR_INVALID_ARG for NULL
+ * buffers or src_lens < 1, ISM_ERR_CUDA, ISM_ERR_OUT_OF_MEMORY. */
+int ism_dataset_batch(const ism_room *rooms, int64_t n_rooms, const float *src_host,
+                      const int64_t *src_lens, const int64_t *src_offsets,
+                      const float *snr_db, uint64_t seed, uint64_t noise_id_base,
+                      int32_t precision, float *y_host, const int64_t *y_offsets,
+                      float *h_host, const int64_t *h_offsets, int64_t chunk_rooms);
+
 /* ------------------------------------------------------------------------
  * Training frames: the network of the paper reads multichannel windows of
  * 1024 samples (23.2 ms at 44.1 kHz) of the convolved signals, with

@@ -12,10 +12,10 @@ include/ism.h; this package is its Python binding.
     h = ism.rir_batch(rooms)            # float32 CUDA tensor, packed RIRs
 """
 from ._lib import (BF16X3, F32, FD_HANN_SINC, FD_LAGRANGE, RIR_DIRECT, RIR_SPARSE, IsmError,  # noqa
-                   PreparedRooms, check, conv_jobs, convolve_batch, frame_jobs, frames_batch,
+                   PreparedRooms, check, conv_jobs, convolve_batch, dataset_batch, frame_jobs, frames_batch,
                    last_error, load, make_rooms, rir_batch,
                    rir_batch_noalloc, rir_batch_size, rir_filter_terms, Server)
 
 __all__ = ["load", "rir_batch", "rir_batch_size", "rir_batch_noalloc", "convolve_batch",
-           "conv_jobs", "frame_jobs", "frames_batch", "IsmError", "F32", "BF16X3", "FD_HANN_SINC", "FD_LAGRANGE", "RIR_SPARSE",
+           "conv_jobs", "dataset_batch", "frame_jobs", "frames_batch", "IsmError", "F32", "BF16X3", "FD_HANN_SINC", "FD_LAGRANGE", "RIR_SPARSE",
            "RIR_DIRECT", "last_error", "check", "make_rooms", "PreparedRooms", "rir_filter_terms", "Server"]

@@ -81,6 +81,8 @@ SIGNATURES = {
     "ism_rir_filter_terms": (c_i32, [c_i32, c_i32, c_vp]),
     "ism_convolve_batch": (c_i32, [c_vp, c_i64, c_vp, c_vp, c_vp, c_u64, c_i32, c_vp]),
     "ism_frames_batch": (c_i32, [c_vp, c_i64, c_i32, c_vp, c_vp, c_u64, c_vp]),
+    "ism_dataset_batch": (c_i32, [c_vp, c_i64, c_vp, c_vp, c_vp, c_vp, c_u64, c_u64, c_i32, c_vp,
+                                  c_vp, c_vp, c_vp, c_i64]),
     "ism_serve_create": (c_i32, [c_vp, c_vp]),
     "ism_serve_submit": (c_i32, [c_vp, c_vp, c_vp]),
     "ism_serve_poll": (c_i32, [c_vp, c_u64, c_vp]),
@@ -283,6 +285,39 @@ def frames_batch(jobs, frame_len, y, out, seed=0, stream=None):
     check(load().ism_frames_batch(jobs, len(jobs), int(frame_len), c_vp(y.data_ptr()),
                                   c_vp(out.data_ptr()), c_u64(seed), _stream_ptr(stream)))
     return out
+
+
+def dataset_batch(rooms, src_host, src_lens, y_host, snr_db=None, seed=0, noise_id_base=0,
+                  precision=BF16X3, h_host=None, chunk_rooms=0):
+    """ism_dataset_batch: RIRs, convolution and noise with host buffers.
+    rooms: room dicts or PreparedRooms; src_host: float32 sources packed in
+    room order (a CPU tensor, page-locked for overlapped copies, or a numpy
+    array); src_lens: samples per room; y_host (and optional h_host): CPU
+    float32 outputs, packed.  Returns y_host."""
+    import torch
+    lib = load()
+    if isinstance(rooms, PreparedRooms):
+        arr, n = rooms.arr, rooms.n
+    else:
+        arr, keep = make_rooms(rooms)
+        n = len(rooms)
+    lens = np.ascontiguousarray(np.asarray(src_lens, np.int64))
+    snr = None if snr_db is None else np.ascontiguousarray(np.asarray(snr_db, np.float32))
+
+    def ptr(x):
+        if x is None:
+            return None
+        if isinstance(x, torch.Tensor):
+            assert x.device.type == "cpu" and x.dtype == torch.float32 and x.is_contiguous()
+            return c_vp(x.data_ptr())
+        assert x.dtype == np.float32 and x.flags["C_CONTIGUOUS"]
+        return c_vp(x.ctypes.data)
+
+    check(lib.ism_dataset_batch(arr, n, ptr(src_host), c_vp(lens.ctypes.data), None,
+                                None if snr is None else c_vp(snr.ctypes.data), c_u64(seed),
+                                c_u64(noise_id_base), int(precision), ptr(y_host), None,
+                                ptr(h_host), None, int(chunk_rooms)))
+    return y_host
 
 
 class Server:

@@ -1,0 +1,214 @@
+// ism_dataset.cu -- the dataset step with host buffers (ism_dataset_batch):
+// RIRs, convolution and noise for a batch of rooms, sources read from and
+// microphone signals written to host memory, the copies of one chunk of
+// rooms overlapping the kernels of the next (arXiv 2104.13347, Sec. II.A:
+// the dataset is the batch convolution of recordings with the simulated
+// RIRs).
+//
+// Pipeline over chunks k = 0, 1, ... with two device buffer sets (k mod 2)
+// and three streams:
+//   up:   [wait compute(k-2)] sources of chunk k -> src_d[k%2]
+//   comp: [wait up(k), down(k-2)] RIRs -> h_d, convolution + noise -> y_d
+//   down: [wait comp(k)] y_d (and h_d) -> host
+// Every kernel is the batch entry points' own (ism_rir_batch_ex,
+// ism_convolve_batch); room i keeps noise id base + i, so the outputs do
+// not depend on the chunking.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "ism_internal.h"
+
+using namespace ism;
+
+namespace {
+
+struct Pipe {
+    cudaStream_t up = nullptr, comp = nullptr, down = nullptr;
+    cudaEvent_t ev_alloc = nullptr, up_done[2] = {}, comp_done[2] = {}, down_done[2] = {};
+    void *buf = nullptr;
+    ~Pipe() {
+        // every stream is synchronised before the pipe goes out of scope
+        if (buf && comp) scratch_free(buf, comp);
+        if (comp) cudaStreamSynchronize(comp);
+        for (int s = 0; s < 2; ++s) {
+            if (up_done[s]) cudaEventDestroy(up_done[s]);
+            if (comp_done[s]) cudaEventDestroy(comp_done[s]);
+            if (down_done[s]) cudaEventDestroy(down_done[s]);
+        }
+        if (ev_alloc) cudaEventDestroy(ev_alloc);
+        if (up) cudaStreamDestroy(up);
+        if (comp) cudaStreamDestroy(comp);
+        if (down) cudaStreamDestroy(down);
+    }
+};
+
+int copy_async(void *dst, const void *src, size_t bytes, cudaMemcpyKind kind, cudaStream_t s) {
+    if (!bytes) return ISM_OK;
+    cudaError_t e = cudaMemcpyAsync(dst, src, bytes, kind, s);
+    return e == cudaSuccess ? ISM_OK : cuda_fail(e, "cudaMemcpyAsync");
+}
+
+}  // namespace
+
+extern "C" int ism_dataset_batch(const ism_room *rooms, int64_t n_rooms, const float *src_host,
+                                 const int64_t *src_lens, const int64_t *src_offsets,
+                                 const float *snr_db, uint64_t seed, uint64_t noise_id_base,
+                                 int32_t precision, float *y_host, const int64_t *y_offsets,
+                                 float *h_host, const int64_t *h_offsets, int64_t chunk_rooms) {
+    set_error("");
+    if (n_rooms < 0) return fail(ISM_ERR_INVALID_ARG, "n_rooms < 0");
+    if (n_rooms == 0) return ISM_OK;
+    if (!rooms || !src_host || !src_lens || !y_host)
+        return fail(ISM_ERR_INVALID_ARG, "NULL rooms, sources, lengths or outputs");
+    if (precision != ISM_F32 && precision != ISM_BF16X3)
+        return fail(ISM_ERR_INVALID_ARG, "unknown precision");
+    if (chunk_rooms < 0) return fail(ISM_ERR_INVALID_ARG, "chunk_rooms < 0");
+    // per-room sizes and host offsets
+    std::vector<int64_t> so(n_rooms), yo(n_rooms), ho(n_rooms), ylen(n_rooms), hlen(n_rooms);
+    int64_t sp = 0, yp = 0, hp = 0, y_total = 0;
+    for (int64_t i = 0; i < n_rooms; ++i) {
+        const ism_room &R = rooms[i];
+        if (int st = validate_room(R, i)) return st;
+        if (src_lens[i] < 1) return fail(ISM_ERR_INVALID_ARG, "room " + std::to_string(i) + ": src_len < 1");
+        ylen[i] = (int64_t)R.n_mics * (src_lens[i] + R.rir_len - 1);
+        hlen[i] = (int64_t)R.n_mics * R.rir_len;
+        so[i] = src_offsets ? src_offsets[i] : sp;
+        yo[i] = y_offsets ? y_offsets[i] : yp;
+        ho[i] = h_offsets ? h_offsets[i] : hp;
+        if (so[i] < 0 || yo[i] < 0 || ho[i] < 0)
+            return fail(ISM_ERR_INVALID_ARG, "room " + std::to_string(i) + ": negative offset");
+        sp += src_lens[i];
+        yp += ylen[i];
+        hp += hlen[i];
+        y_total += ylen[i];
+    }
+    // chunks of consecutive rooms
+    int64_t per = chunk_rooms;
+    if (per == 0) {
+        const int64_t target = (256ll << 20) / 4;  // floats of signals per chunk
+        int64_t n_chunks = std::max<int64_t>((y_total + target - 1) / target, std::min<int64_t>(4, n_rooms));
+        per = (n_rooms + n_chunks - 1) / n_chunks;
+    }
+    std::vector<int64_t> cb;  // chunk boundaries
+    for (int64_t r = 0; r < n_rooms; r += per) cb.push_back(r);
+    cb.push_back(n_rooms);
+    const int n_chunks = (int)cb.size() - 1;
+    int64_t max_s = 0, max_y = 0, max_h = 0;
+    for (int c = 0; c < n_chunks; ++c) {
+        int64_t s = 0, y = 0, h = 0;
+        for (int64_t i = cb[c]; i < cb[c + 1]; ++i) { s += src_lens[i]; y += ylen[i]; h += hlen[i]; }
+        max_s = std::max(max_s, s);
+        max_y = std::max(max_y, y);
+        max_h = std::max(max_h, h);
+    }
+    auto al = [](int64_t n) { return (size_t)((n * 4 + 255) & ~(int64_t)255); };
+    const size_t set_bytes = al(max_s) + al(max_y) + al(max_h);
+
+    Pipe P;
+    cudaError_t e = cudaSuccess;
+    if ((e = cudaStreamCreateWithFlags(&P.up, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&P.comp, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&P.down, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&P.ev_alloc, cudaEventDisableTiming)) != cudaSuccess)
+        return cuda_fail(e, "dataset streams");
+    for (int s = 0; s < 2; ++s)
+        if ((e = cudaEventCreateWithFlags(&P.up_done[s], cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&P.comp_done[s], cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&P.down_done[s], cudaEventDisableTiming)) != cudaSuccess)
+            return cuda_fail(e, "dataset events");
+    if (int st = scratch_alloc(&P.buf, 2 * set_bytes, P.comp)) return st;
+    cudaEventRecord(P.ev_alloc, P.comp);
+    cudaStreamWaitEvent(P.up, P.ev_alloc, 0);
+    cudaStreamWaitEvent(P.down, P.ev_alloc, 0);
+    auto src_d = [&](int s) { return (float *)((char *)P.buf + s * set_bytes); };
+    auto y_d = [&](int s) { return (float *)((char *)P.buf + s * set_bytes + al(max_s)); };
+    auto h_d = [&](int s) { return (float *)((char *)P.buf + s * set_bytes + al(max_s) + al(max_y)); };
+
+    int st = ISM_OK;
+    std::vector<ism_conv_job> jobs;
+    for (int c = 0; c < n_chunks && !st; ++c) {
+        const int s = c & 1;
+        const int64_t r0 = cb[c], r1 = cb[c + 1];
+        // sources of the chunk, packed in src_d[s]
+        if (c >= 2) cudaStreamWaitEvent(P.up, P.comp_done[s], 0);
+        {
+            int64_t o = 0;
+            for (int64_t i = r0; i < r1 && !st; ) {
+                // one copy per run of rooms that are contiguous on the host
+                int64_t j = i + 1, n = src_lens[i];
+                while (j < r1 && so[j] == so[j - 1] + src_lens[j - 1]) n += src_lens[j++];
+                st = copy_async(src_d(s) + o, src_host + so[i], (size_t)n * 4,
+                                cudaMemcpyHostToDevice, P.up);
+                o += n;
+                i = j;
+            }
+        }
+        if (st) break;
+        cudaEventRecord(P.up_done[s], P.up);
+        // kernels of the chunk
+        cudaStreamWaitEvent(P.comp, P.up_done[s], 0);
+        if (c >= 2) cudaStreamWaitEvent(P.comp, P.down_done[s], 0);
+        st = ism_rir_batch_ex(rooms + r0, r1 - r0, h_d(s), nullptr, nullptr, P.comp);
+        if (st) break;
+        jobs.assign((size_t)(r1 - r0), ism_conv_job{});
+        {
+            int64_t hoff = 0, soff = 0, yoff = 0;
+            for (int64_t i = r0; i < r1; ++i) {
+                ism_conv_job &J = jobs[(size_t)(i - r0)];
+                J.n_mics = rooms[i].n_mics;
+                J.rir_len = rooms[i].rir_len;
+                J.src_len = src_lens[i];
+                J.h_offset = hoff;
+                J.src_offset = soff;
+                J.y_offset = yoff;
+                J.snr_db = snr_db ? snr_db[i] : NAN;
+                J.noise_id = noise_id_base + (uint64_t)i;
+                hoff += hlen[i];
+                soff += src_lens[i];
+                yoff += ylen[i];
+            }
+        }
+        st = ism_convolve_batch(jobs.data(), r1 - r0, h_d(s), src_d(s), y_d(s), seed, precision,
+                                P.comp);
+        if (st) break;
+        cudaEventRecord(P.comp_done[s], P.comp);
+        // outputs of the chunk
+        cudaStreamWaitEvent(P.down, P.comp_done[s], 0);
+        {
+            int64_t o = 0;
+            for (int64_t i = r0; i < r1 && !st; ) {
+                int64_t j = i + 1, n = ylen[i];
+                while (j < r1 && yo[j] == yo[j - 1] + ylen[j - 1]) n += ylen[j++];
+                st = copy_async(y_host + yo[i], y_d(s) + o, (size_t)n * 4, cudaMemcpyDeviceToHost,
+                                P.down);
+                o += n;
+                i = j;
+            }
+            o = 0;
+            for (int64_t i = r0; h_host && i < r1 && !st; ) {
+                int64_t j = i + 1, n = hlen[i];
+                while (j < r1 && ho[j] == ho[j - 1] + hlen[j - 1]) n += hlen[j++];
+                st = copy_async(h_host + ho[i], h_d(s) + o, (size_t)n * 4, cudaMemcpyDeviceToHost,
+                                P.down);
+                o += n;
+                i = j;
+            }
+        }
+        if (st) break;
+        cudaEventRecord(P.down_done[s], P.down);
+    }
+    // drain every stream (also after an error), then free on comp
+    const cudaError_t e1 = cudaStreamSynchronize(P.up);
+    const cudaError_t e2 = cudaStreamSynchronize(P.down);
+    const cudaError_t e3 = cudaStreamSynchronize(P.comp);
+    if (!st && e1 != cudaSuccess) st = cuda_fail(e1, "dataset upload");
+    if (!st && e2 != cudaSuccess) st = cuda_fail(e2, "dataset download");
+    if (!st && e3 != cudaSuccess) st = cuda_fail(e3, "dataset kernels");
+    return st;
+}

@@ -69,6 +69,10 @@ int device_sm_count();
 // delay-limited order for ISM_ORDER_AUTO (see ism.h).
 int room_order(const ism_room &r, int m);
 
+// Checks one room of a batch (index idx for the message); ISM_OK or the
+// error status with the last-error string set.
+int validate_room(const ism_room &r, int64_t idx);
+
 // K1: image-source taps.  jobs_dev has n_rirs jobs; every job's windows are
 // processed; wmax = max n_windows.  counter_dev: one zeroed uint32 work
 // counter.  max_order / max_taps size the shared memory and tap rows.

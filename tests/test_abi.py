@@ -230,3 +230,33 @@ def test_frames_batch_argument_errors(lib):
         setattr(jobs[0], field, val)
         assert L.ism_frames_batch(jobs, 1, 64, fake, fake, 0, None) == lib.ISM_ERR_INVALID_ARG, field
         assert lib.last_error()
+
+
+def test_dataset_batch_argument_errors(lib):
+    L = lib.load()
+    arr, keep = lib.make_rooms([good_room()])
+    src = np.zeros(100, np.float32)
+    y = np.zeros(8 * 2000, np.float32)
+    lens = np.array([100], np.int64)
+    P = lambda a: ctypes.c_void_p(a.ctypes.data)  # noqa: E731
+    ok_args = [arr, 1, P(src), P(lens), None, None, 0, 0, 1, P(y), None, None, None, 0]
+
+    def call(**kw):
+        a = list(ok_args)
+        names = ["rooms", "n", "src", "lens", "so", "snr", "seed", "base", "prec", "y", "yo", "h",
+                 "ho", "chunk"]
+        for k, v in kw.items():
+            a[names.index(k)] = v
+        return L.ism_dataset_batch(*a)
+
+    assert call(src=None) == lib.ISM_ERR_INVALID_ARG
+    assert call(y=None) == lib.ISM_ERR_INVALID_ARG
+    assert call(lens=None) == lib.ISM_ERR_INVALID_ARG
+    assert call(prec=7) == lib.ISM_ERR_INVALID_ARG
+    assert call(chunk=-1) == lib.ISM_ERR_INVALID_ARG
+    assert call(n=0) == lib.ISM_OK
+    bad = np.array([0], np.int64)
+    assert call(lens=P(bad)) == lib.ISM_ERR_INVALID_ARG
+    arr2, keep2 = lib.make_rooms([good_room(src=[9.0, 1.0, 1.0])])
+    assert call(rooms=arr2) == lib.ISM_ERR_INVALID_ARG
+    assert lib.last_error()
