@@ -213,7 +213,10 @@ typedef struct ism_conv_job {
  * jobs       host array of n_jobs jobs.
  * h_dev      device float RIRs; src_dev device float sources; y_dev device
  *            float outputs (must not overlap the inputs).
- * seed       noise seed (SplitMix64 counters, Box--Muller).
+ * seed       noise seed: stream (noise_id, mic) has key
+ *            out(seed, noise_id * 65536 + mic); samples 2k, 2k + 1 share
+ *            SplitMix64 output k of that stream (u1 from bits 63..40, u2 from
+ *            bits 39..16) and take the two Box--Muller branches.
  * precision  ISM_F32 or ISM_BF16X3.
  * Errors: ISM_ERR_INVALID_ARG (bad lengths, NULL pointers, unknown
  * precision), ISM_ERR_CUDA, ISM_ERR_OUT_OF_MEMORY (scratch). */
@@ -272,9 +275,10 @@ int ism_dataset_batch(const ism_room *rooms, int64_t n_rooms, const float *src_h
  * snr_db      SNR of the added noise, relative to the frame's own mean
  *             power over its mics and samples: sigma^2 = P / 10^(snr/10),
  *             noise sigma z, z standard normal from SplitMix64 counters
- *             (stream key out(seed, noise_id * 65536 + mic), uniforms from
- *             outputs 2i and 2i + 1 at sample i of the frame, Box--Muller
- *             cosine branch).  NaN or +inf: a clean copy. */
+ *             (stream key out(seed, noise_id * 65536 + mic); samples 2k and
+ *             2k + 1 of the frame share output k: u1 from bits 63..40,
+ *             u2 from bits 39..16, and take the two Box--Muller branches
+ *             r cos(2 pi u2), r sin(2 pi u2)).  NaN or +inf: a clean copy. */
 typedef struct ism_frame_job {
     int64_t y_offset;
     int64_t y_len;

@@ -249,10 +249,11 @@ def gauss(seed, room, mic, t) -> float:
     return float(_load().oracle_gauss(seed, room, mic, t))
 
 
-def uniforms(seed, room, mic, t0, n):
+def uniforms(seed, room, mic, k0, n):
+    """u1, u2 of sample pairs k0 .. k0+n-1 of stream (room, mic)."""
     u1 = np.zeros(n, np.float64)
     u2 = np.zeros(n, np.float64)
-    _load().oracle_uniforms(seed, room, mic, t0, n, _p(u1), _p(u2))
+    _load().oracle_uniforms(seed, room, mic, k0, n, _p(u1), _p(u2))
     return u1, u2
 
 

@@ -29,7 +29,8 @@
  *     h[k1+j] += a * prod_{i != j} (D - i) / (j - i),  j = 0..P
  *   convolution: y[t] = sum_k h[k] s[t-k],  t in [0, Ts + Lh - 1)
  *   noise: y += sigma z, sigma^2 = mean(y^2 over the room's mics and
- *     samples) / 10^(snr/10); z from SplitMix64 counters and Box--Muller.
+ *     samples) / 10^(snr/10); z from SplitMix64 counters and Box--Muller
+ *     (one counter output per pair of samples, both branches).
  *
  * Readings of what the paper leaves open (Hann window width and centring, the
  * rounding rule of the delay split, the wall-coefficient convention, the SNR
@@ -355,26 +356,30 @@ static uint64_t noise_key(uint64_t seed, uint64_t room, uint64_t mic)
     return oracle_splitmix64(seed, room * 65536ULL + mic);
 }
 
-/* Standard normal number t of stream (room, mic): two 24-bit uniforms from
- * outputs 2t and 2t+1, then Box--Muller (cosine branch). */
+/* Standard normal number t of stream (room, mic).  Samples come in pairs
+ * (2k, 2k+1) sharing output k of the stream: u1 = (bits 63..40 + 1/2) / 2^24,
+ * u2 = (bits 39..16) / 2^24, and Box--Muller gives the pair's two
+ * independent normals, r cos(2 pi u2) for the even sample and r sin(2 pi u2)
+ * for the odd one, r = sqrt(-2 ln u1). */
 double oracle_gauss(uint64_t seed, uint64_t room, uint64_t mic, uint64_t t)
 {
     uint64_t key = noise_key(seed, room, mic);
-    uint64_t b1 = oracle_splitmix64(key, 2 * t);
-    uint64_t b2 = oracle_splitmix64(key, 2 * t + 1);
-    double u1 = ((double)(b1 >> 40) + 0.5) * (1.0 / 16777216.0);
-    double u2 = (double)(b2 >> 40) * (1.0 / 16777216.0);
-    return sqrt(-2.0 * log(u1)) * cos(2.0 * ORACLE_PI * u2);
+    uint64_t b = oracle_splitmix64(key, t >> 1);
+    double u1 = ((double)(b >> 40) + 0.5) * (1.0 / 16777216.0);
+    double u2 = (double)((b >> 16) & 0xFFFFFFULL) * (1.0 / 16777216.0);
+    double r = sqrt(-2.0 * log(u1));
+    return (t & 1) ? r * sin(2.0 * ORACLE_PI * u2) : r * cos(2.0 * ORACLE_PI * u2);
 }
 
-void oracle_uniforms(uint64_t seed, uint64_t room, uint64_t mic, uint64_t t0, int64_t n,
+/* The uniforms of pairs k0 .. k0+n-1 of stream (room, mic). */
+void oracle_uniforms(uint64_t seed, uint64_t room, uint64_t mic, uint64_t k0, int64_t n,
                      double *u1, double *u2)
 {
     uint64_t key = noise_key(seed, room, mic);
     for (int64_t i = 0; i < n; ++i) {
-        uint64_t t = t0 + (uint64_t)i;
-        u1[i] = ((double)(oracle_splitmix64(key, 2 * t) >> 40) + 0.5) * (1.0 / 16777216.0);
-        u2[i] = (double)(oracle_splitmix64(key, 2 * t + 1) >> 40) * (1.0 / 16777216.0);
+        uint64_t b = oracle_splitmix64(key, k0 + (uint64_t)i);
+        u1[i] = ((double)(b >> 40) + 0.5) * (1.0 / 16777216.0);
+        u2[i] = (double)((b >> 16) & 0xFFFFFFULL) * (1.0 / 16777216.0);
     }
 }
 

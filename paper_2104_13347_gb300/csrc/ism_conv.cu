@@ -5,7 +5,8 @@
 //   y_m[t] = sum_k h_m[k] s[t - k],  t in [0, Ts + Lh - 1).
 // Noise (Sec. III.A: Gaussian noise at a drawn SNR):
 //   y_m[t] += sigma z,  sigma^2 = mean(y^2 over the room's mics and samples)
-//   / 10^(snr/10), z from SplitMix64 counters and Box--Muller.  The sums of
+//   / 10^(snr/10), z from SplitMix64 counters and Box--Muller (one counter
+//   output per pair of samples, both branches).  The sums of
 //   y^2 come from the convolution kernels' epilogues, one partial per tile
 //   (float-float per thread, FP64 across threads, fixed order).
 //
@@ -135,19 +136,22 @@ k_conv_f32(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles,
 }
 
 // Noise: sigma from the job's tile partials (fixed order), then
-// y += sigma * z with z = sqrt(-2 ln u1) cos(2 pi u2) and u1, u2 the 24-bit
-// uniforms of SplitMix64 outputs 2t, 2t+1 of the (room, mic) stream.  Block
-// x of job y covers flat indices [x NCH, (x+1) NCH) of the job's (mic, t)
-// samples; each thread walks its samples with stride 256, carrying (mic, t)
-// and the mic's stream key instead of dividing per sample.
-constexpr int NCH = 65536;  // samples per block
+// y += sigma * z.  The samples of a (room, mic) stream come in pairs
+// (2k, 2k+1) that share SplitMix64 output k: u1 = (bits 63..40 + 1/2) / 2^24,
+// u2 = (bits 39..16) / 2^24, r = sqrt(-2 ln u1), and the pair gets
+// r cos(2 pi u2) and r sin(2 pi u2) (both Box--Muller branches).  Block x of
+// job y covers pair indices [x NCH, (x+1) NCH) of the job's (mic, pair)
+// sequence; each thread walks its pairs with stride 256, carrying (mic, k)
+// and the mic's stream key.
+constexpr int NCH = 32768;  // pairs per block
 __global__ void __launch_bounds__(256)
 k_noise(const ConvJob *__restrict__ jobs, float *__restrict__ y, const double *__restrict__ part,
         uint64_t seed) {
     const ConvJob J = jobs[blockIdx.y];
     if (isnan(J.snr_db)) return;
     const int64_t ylen = J.y_len;
-    const int64_t n = (int64_t)J.n_mics * ylen;
+    const int64_t npr = (ylen + 1) >> 1;              // pairs per mic
+    const int64_t n = (int64_t)J.n_mics * npr;
     const int64_t b = (int64_t)blockIdx.x * NCH;
     if (b >= n) return;
     __shared__ float s_sigma;
@@ -155,7 +159,7 @@ k_noise(const ConvJob *__restrict__ jobs, float *__restrict__ y, const double *_
         const int np = conv_partials_per_job(J.n_mics, ylen);
         double p = 0.0;
         for (int i = 0; i < np; ++i) p += part[J.part_offset + i];
-        p /= (double)n;
+        p /= (double)J.n_mics * (double)ylen;
         s_sigma = (float)sqrt(p / pow(10.0, (double)J.snr_db / 10.0));
     }
     __syncthreads();
@@ -164,18 +168,22 @@ k_noise(const ConvJob *__restrict__ jobs, float *__restrict__ y, const double *_
     const int64_t e = min(b + NCH, n);
     int64_t i = b + threadIdx.x;
     if (i >= e) return;
-    uint64_t m = (uint64_t)(i / ylen);
-    int64_t t = i - (int64_t)m * ylen;
+    uint64_t m = (uint64_t)(i / npr);
+    int64_t k = i - (int64_t)m * npr;
     uint64_t key = sm64_out(seed, J.noise_id * 65536ull + m);
     for (; i < e; i += 256) {
-        const uint64_t b1 = sm64_out(key, 2 * (uint64_t)t), b2 = sm64_out(key, 2 * (uint64_t)t + 1);
-        const float u1 = ((float)(b1 >> 40) + 0.5f) * (1.0f / 16777216.0f);
-        const float u2 = (float)(b2 >> 40) * (1.0f / 16777216.0f);
-        const float z = sqrtf(-2.f * logf(u1)) * cospif(2.f * u2);
-        yb[i] += sigma * z;
-        t += 256;
-        if (t >= ylen) {
-            while (t >= ylen) { t -= ylen; ++m; }
+        const uint64_t bits = sm64_out(key, (uint64_t)k);
+        const float u1 = ((float)(bits >> 40) + 0.5f) * (1.0f / 16777216.0f);
+        const float u2 = (float)((bits >> 16) & 0xFFFFFFull) * (1.0f / 16777216.0f);
+        const float r = sigma * sqrtf(-2.f * logf(u1));
+        float sn, cs;
+        sincospif(2.f * u2, &sn, &cs);
+        float *ym = yb + (int64_t)m * ylen + 2 * k;
+        ym[0] += r * cs;
+        if (2 * k + 1 < ylen) ym[1] += r * sn;
+        k += 256;
+        if (k >= npr) {
+            while (k >= npr) { k -= npr; ++m; }
             key = sm64_out(seed, J.noise_id * 65536ull + m);
         }
     }
@@ -208,9 +216,9 @@ int launch_conv_f32(const ConvLaunch &L, cudaStream_t stream) {
 
 int launch_noise(const ConvLaunch &L, cudaStream_t stream) {
     if (!L.any_noise || L.n_jobs == 0) return ISM_OK;
-    int64_t max_n = 0;
+    int64_t max_n = 0;  // pairs of the largest job
     for (int j = 0; j < L.n_jobs; ++j)
-        max_n = std::max(max_n, (int64_t)L.jobs_host[j].n_mics * L.jobs_host[j].y_len);
+        max_n = std::max(max_n, (int64_t)L.jobs_host[j].n_mics * ((L.jobs_host[j].y_len + 1) / 2));
     const int64_t nb = (max_n + NCH - 1) / NCH;
     if (nb > 0x7fffffff) return fail(ISM_ERR_INVALID_ARG, "job too large for the noise grid");
     if (L.n_jobs > 65535) {

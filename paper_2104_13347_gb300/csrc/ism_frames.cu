@@ -7,9 +7,9 @@
 //   x_m[i] = y_m[t0 + i] (0 outside [0, y_len)),  i < frame_len,
 //   sigma^2 = mean over m, i of x_m[i]^2 / 10^(snr/10),
 //   out_m[i] = x_m[i] + sigma z_m[i],
-// z from SplitMix64 counters (key out(seed, noise_id * 65536 + m), uniforms
-// from outputs 2i, 2i + 1, Box--Muller cosine branch), the same recipe as
-// the convolution's noise.
+// z from SplitMix64 counters (key out(seed, noise_id * 65536 + m); samples
+// 2k, 2k+1 share output k: two 24-bit uniforms, both Box--Muller branches),
+// the same recipe as the convolution's noise.
 //
 // One CTA per frame.  The frame's power is a float-float sum per thread and
 // an FP64 sum across threads in a fixed order, so results are bitwise
@@ -75,17 +75,24 @@ k_frames(const FrameJob *__restrict__ jobs, int frame_len, const float *__restri
         const float *ym = yb + (int64_t)m * J.y_len;
         float *om = ob + (int64_t)m * frame_len;
         const uint64_t key = noisy ? sm64_out(seed, J.noise_id * 65536ull + (uint64_t)m) : 0ull;
-        for (int i = tid; i < frame_len; i += FT) {
+        // samples 2k, 2k+1 of the frame share counter output k
+        for (int k = tid; 2 * k < frame_len; k += FT) {
+            const int i = 2 * k;
             const int64_t t = J.t0 + i;
-            float v = (t >= 0 && t < J.y_len) ? ym[t] : 0.f;
+            float v0 = (t >= 0 && t < J.y_len) ? ym[t] : 0.f;
+            float v1 = (t + 1 >= 0 && t + 1 < J.y_len) ? ym[t + 1] : 0.f;
             if (noisy) {
-                const uint64_t b1 = sm64_out(key, 2 * (uint64_t)i);
-                const uint64_t b2 = sm64_out(key, 2 * (uint64_t)i + 1);
-                const float u1 = ((float)(b1 >> 40) + 0.5f) * (1.0f / 16777216.0f);
-                const float u2 = (float)(b2 >> 40) * (1.0f / 16777216.0f);
-                v += sigma * (sqrtf(-2.f * logf(u1)) * cospif(2.f * u2));
+                const uint64_t bits = sm64_out(key, (uint64_t)k);
+                const float u1 = ((float)(bits >> 40) + 0.5f) * (1.0f / 16777216.0f);
+                const float u2 = (float)((bits >> 16) & 0xFFFFFFull) * (1.0f / 16777216.0f);
+                const float r = sigma * sqrtf(-2.f * logf(u1));
+                float sn, cs;
+                sincospif(2.f * u2, &sn, &cs);
+                v0 += r * cs;
+                v1 += r * sn;
             }
-            om[i] = v;
+            om[i] = v0;
+            if (i + 1 < frame_len) om[i + 1] = v1;
         }
     }
 }

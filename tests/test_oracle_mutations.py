@@ -25,6 +25,12 @@ MUTATIONS = {
     "split_floor": ("double k = rint(im.tau);", "double k = floor(im.tau);"),
     "conv_index": ("acc += h[k] * s[t - k];\n        y[t] = acc;",
                    "acc += h[k] * s[t - k + (k > 0)];\n        y[t] = acc;"),
+    "noise_branch": ("return (t & 1) ? r * sin(2.0 * ORACLE_PI * u2) : r * cos(2.0 * ORACLE_PI * u2);",
+                     "return r * cos(2.0 * ORACLE_PI * u2);"),
+    "frame_padding": ("(t >= 0 && t < y_len) ? y[(int64_t)m * y_len + t] : 0.0;",
+                      "(t >= 0 && t <= y_len) ? y[(int64_t)m * y_len + t] : 0.0;"),
+    "auto_order": ("const double d_reach = ((double)rir_len + (double)n_taps) * c / fs;",
+                   "const double d_reach = ((double)rir_len) * c / fs / 2.0;"),
 }
 
 

@@ -324,16 +324,27 @@ def test_splitmix64_published_sequence():
 
 
 def test_noise_uniforms_and_gaussian():
+    """Uniforms of the noise streams are uniform, the even and odd samples
+    of a pair are the two Box--Muller branches of the pair's uniforms
+    (independent standard normals), and different streams are uncorrelated."""
     from scipy import stats
     u1, u2 = oracle.uniforms(1234, 7, 3, 0, 200000)
     assert u1.min() > 0 and u1.max() < 1 and u2.min() >= 0 and u2.max() < 1
     for u in (u1, u2):
         hist, _ = np.histogram(u, bins=64, range=(0, 1))
         assert stats.chisquare(hist).pvalue > 1e-4
-    z = np.sqrt(-2 * np.log(u1)) * np.cos(2 * np.pi * u2)
-    assert stats.kstest(z, "norm").pvalue > 1e-4
-    assert abs(oracle.gauss(1234, 7, 3, 11) - z[11]) < 1e-15
-    # different streams are uncorrelated
+    r = np.sqrt(-2 * np.log(u1))
+    zc, zs = r * np.cos(2 * np.pi * u2), r * np.sin(2 * np.pi * u2)
+    for z in (zc, zs):
+        assert stats.kstest(z, "norm").pvalue > 1e-4
+    assert abs(np.corrcoef(zc, zs)[0, 1]) < 0.01
+    assert abs(np.corrcoef(u1, u2)[0, 1]) < 0.01
+    for k in (0, 11, 12345):
+        assert abs(oracle.gauss(1234, 7, 3, 2 * k) - zc[k]) < 1e-15
+        assert abs(oracle.gauss(1234, 7, 3, 2 * k + 1) - zs[k]) < 1e-15
+    # the pair's uniforms are the top two 24-bit fields of one counter output
+    b = oracle.splitmix64(oracle.splitmix64(1234, 7 * 65536 + 3), 11)
+    assert u1[11] == ((b >> 40) + 0.5) / 2 ** 24 and u2[11] == ((b >> 16) & 0xFFFFFF) / 2 ** 24
     v1, _ = oracle.uniforms(1234, 7, 4, 0, 200000)
     assert abs(np.corrcoef(u1, v1)[0, 1]) < 0.01
 
