@@ -13,8 +13,9 @@
 //    lattice column (u,l,v,m,w) the admissible n are the integers with
 //    zmin <= |Delta_z(n)| <= zmax, solved in FP32 with a safety margin; each
 //    candidate is then tested exactly on its delay.
-//  * Delays: image-to-mic squared offsets per axis are tabled once per item in
-//    FP64 with the definition's rounding, d^2 and sqrt are done in
+//  * Delays: image-to-mic squared offsets per axis are tabled in FP64 with
+//    the definition's rounding (once per RIR by k_ism_tables for the sparse
+//    kernel, once per item for the direct one), d^2 and sqrt are done in
 //    float-float (FP32 pipe; GB300's FP64 rate is a small fraction of FP32),
 //    and the integer split is redone in FP64 with the definition's exact
 //    operation order whenever the float-float delay lies within 1e-6 samples
@@ -29,10 +30,13 @@
 //    below 5e-8 of the peak tap, under FP32 resolution; exact for the
 //    8-tap Lagrange filter, whose taps are degree-7 polynomials in the
 //    delay).  Each image then adds a T_p(x) to P sparse integer-delay
-//    arrays c_p[kb] (shared-memory atomics) -- the paper's representation of
-//    the integer delays as a sparse array -- and one fixed-order FIR per
+//    arrays c_p[kb] -- the paper's representation of the integer delays as a
+//    sparse array -- held in 32-bit fixed point (native u32 shared-memory
+//    atomics, order-independent sums: bitwise reproducible), and one FIR per
 //    window gives h[n] = sum_p sum_j B[p][j] c_p[n - j].  Per image: P
-//    products instead of one reciprocal and ~7 operations per tap.
+//    terms instead of one reciprocal and ~7 operations per tap.  Candidates
+//    are handed to lanes in pairs of consecutive z-images by a warp-wide
+//    expansion of the column counts.
 //  * k_ism_taps (direct): one warp per image, one lane per tap (81 taps -> 3
 //    rows of 32).  sin(pi (j-f)) = -(-1)^j sin(pi f) and the Hann term is
 //    expanded in cos/sin of pi j/(H+1) (per-lane constants) and of
