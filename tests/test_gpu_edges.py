@@ -1,0 +1,84 @@
+"""Edge cases of the RIR kernels against the FP64 oracle (Sec. II.A
+definition): the smallest lattice, RIRs of one or two samples, lengths at
+the work-item window boundary, the shortest and longest filters (the 1- and
+3-tap Hann filters need 11 Chebyshev terms, so they take the generic term
+loop; the 255-tap one needs the widest sparse arrays), the 2-tap Lagrange
+filter (linear interpolation), and mixed filters and orders in one call."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2104_13347_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+VARIANTS = [0, 1]
+
+
+def rel_l2(x, ref):
+    return float(np.linalg.norm(x - ref) / max(np.linalg.norm(ref), 1e-300))
+
+
+def run(ism, rooms, variant, tol=1e-5):
+    import torch
+    n_rirs, _ = ism.rir_batch_size(rooms)
+    stats = torch.zeros(2 * n_rirs, dtype=torch.int64, device="cuda")
+    h = ism.rir_batch(rooms, stats=stats, variant=variant)
+    torch.cuda.synchronize()
+    h = h.cpu().numpy().astype(np.float64)
+    st = stats.view(-1, 2).cpu().numpy()
+    ref, ost = oracle.rir_batch(rooms)
+    o = j = 0
+    for r, rr in zip(rooms, ref):
+        L = r["rir_len"]
+        for m in range(len(r["mics"])):
+            g = h[o:o + L]
+            if np.linalg.norm(rr[m]) == 0:
+                assert not np.any(g)
+            else:
+                assert rel_l2(g, rr[m]) <= tol, (j, rel_l2(g, rr[m]))
+            o += L
+            j += 1
+    np.testing.assert_array_equal(st[:, 0], ost[:, 1])
+    np.testing.assert_array_equal(st[:, 1], ost[:, 2])
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_order_zero_and_tiny_rirs(ism, variant):
+    rooms = []
+    for i, L in enumerate((1, 2, 3, 17)):
+        rooms += wl.room_batch(1, seed=60 + i, order=0, rir_len=L, n_mics=2)
+    # a source 0.3 m from the mic: the direct path lands in the first taps
+    rooms += [dict(dims=np.array([4.0, 3.0, 2.5]), beta=np.full(6, 0.9),
+                   src=np.array([1.0, 1.0, 1.0]), mics=np.array([[1.3, 1.0, 1.0]]), fs=16000.0,
+                   c=343.0, order=2, n_taps=81, fd_kind=0, rir_len=L) for L in (1, 5, 40)]
+    run(ism, rooms, variant)
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_lengths_at_window_boundaries(ism, variant):
+    rooms = []
+    for i, L in enumerate((1023, 1024, 1025, 2047, 2048, 2049)):
+        rooms += wl.room_batch(1, seed=70 + i, order=4, rir_len=L, n_mics=2)
+    run(ism, rooms, variant)
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_extreme_filters(ism, variant):
+    rooms = []
+    for i, (kind, nt) in enumerate(((0, 1), (0, 3), (0, 255), (1, 2), (1, 4))):
+        rooms += wl.room_batch(1, seed=80 + i, order=4, rir_len=3000, n_mics=2, n_taps=nt,
+                               fd_kind=kind)
+    run(ism, rooms, variant)
+
+
+def test_sparse_term_counts():
+    """Which filters above take the unrolled term loop: 9 terms for the
+    Hann sinc from 33 taps up (255 included), 11 for the 1- and 3-tap Hann
+    filters (their window is sharp, so the taps vary faster with the
+    fraction) and exact counts for short Lagrange filters -- so the
+    generic loop is exercised too."""
+    import paper_2104_13347_gb300 as ism
+    assert ism.rir_filter_terms(0, 81) == 9 and ism.rir_filter_terms(0, 255) == 9
+    assert ism.rir_filter_terms(0, 1) == 11 and ism.rir_filter_terms(0, 3) == 11
+    assert ism.rir_filter_terms(1, 2) == 2 and ism.rir_filter_terms(1, 8) == 8
