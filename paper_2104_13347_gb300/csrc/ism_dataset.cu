@@ -88,15 +88,28 @@ extern "C" int ism_dataset_batch(const ism_room *rooms, int64_t n_rooms, const f
         hp += hlen[i];
         y_total += ylen[i];
     }
-    // chunks of consecutive rooms
-    int64_t per = chunk_rooms;
-    if (per == 0) {
-        const int64_t target = (256ll << 20) / 4;  // floats of signals per chunk
-        int64_t n_chunks = std::max<int64_t>((y_total + target - 1) / target, std::min<int64_t>(4, n_rooms));
-        per = (n_rooms + n_chunks - 1) / n_chunks;
-    }
+    // chunks of consecutive rooms.  Automatic: K chunks (about 160 MB of
+    // signals each, at least six when there are six rooms) of decreasing
+    // size, K, K-1, ..., 1 parts of the signals, so that the upload of the
+    // first chunk and the download of the last one, which nothing overlaps,
+    // are small (a chunk's download is several times faster than its
+    // kernels, so the larger download before each smaller chunk still hides)
     std::vector<int64_t> cb;  // chunk boundaries
-    for (int64_t r = 0; r < n_rooms; r += per) cb.push_back(r);
+    if (chunk_rooms > 0) {
+        for (int64_t r = 0; r < n_rooms; r += chunk_rooms) cb.push_back(r);
+    } else {
+        const int64_t target = (160ll << 20) / 4;  // floats of signals per chunk
+        const int64_t K = std::min<int64_t>(
+            n_rooms, std::max<int64_t>((y_total + target - 1) / target, 6));
+        const double parts = 0.5 * (double)K * (double)(K + 1);
+        int64_t r = 0;
+        double acc = 0.0, goal = 0.0;
+        for (int64_t c = 0; c < K && r < n_rooms; ++c) {
+            cb.push_back(r);
+            goal += (double)(K - c) / parts * (double)y_total;
+            do { acc += (double)ylen[r]; ++r; } while (r < n_rooms && acc < goal);
+        }
+    }
     cb.push_back(n_rooms);
     const int n_chunks = (int)cb.size() - 1;
     int64_t max_s = 0, max_y = 0, max_h = 0;
