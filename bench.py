@@ -175,8 +175,8 @@ def cpu_sample(rooms, srcs, n_rir_rooms=6, n_conv_rooms=1):
     hs, st = oracle.rir_batch(rooms[:n_rir_rooms], n_threads=threads)
     t_rir = time.perf_counter() - t0
     t0 = time.perf_counter()
-    oracle.convolve_batch(hs[:n_conv_rooms], [s.astype(np.float64) for s in srcs[:n_conv_rooms]],
-                          n_threads=threads)
+    ys = oracle.convolve_batch(hs[:n_conv_rooms], [s.astype(np.float64) for s in srcs[:n_conv_rooms]],
+                               n_threads=threads)
     t_conv = (time.perf_counter() - t0) * n_rir_rooms / n_conv_rooms
     taps = int(st[:, 2].sum())
     mic_samples = n_rir_rooms * N_MICS * (TS + LH - 1)
@@ -186,7 +186,68 @@ def cpu_sample(rooms, srcs, n_rir_rooms=6, n_conv_rooms=1):
                        f"({t_rir:.1f} s) + convolutions of {n_conv_rooms} room(s) scaled to "
                        f"{n_rir_rooms} ({t_conv:.1f} s)"),
             "mic_samples_per_s": mic_samples / (t_rir + t_conv),
-            "seconds": t_rir + t_conv}
+            "seconds": t_rir + t_conv, "rirs": hs, "signals": ys}
+
+
+def parity_vs_sample(ism, cb, h, rooms, srcs, precision):
+    """rel-L2 (per room and mic) of the step's RIRs and of a noise-free
+    convolution against the oracle outputs of the CPU-baseline sample."""
+    import torch
+    def rel(a, b):
+        return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+    hh = h.view(-1, N_MICS, LH)
+    e_h = [rel(hh[i, m].cpu().numpy().astype(np.float64), cb["rirs"][i][m])
+           for i in range(len(cb["rirs"])) for m in range(N_MICS)]
+    n_c = len(cb["signals"])
+    jobs, ylen = ism.conv_jobs([N_MICS] * n_c, [LH] * n_c, [len(x) for x in srcs[:n_c]])
+    yc = torch.empty(ylen, device=h.device)
+    ism.convolve_batch(jobs, h, torch.from_numpy(np.concatenate(srcs[:n_c])).to(h.device), yc,
+                       precision=precision)
+    yv = yc.view(n_c, N_MICS, -1).cpu().numpy().astype(np.float64)
+    e_y = [rel(yv[i, m], cb["signals"][i][m]) for i in range(n_c) for m in range(N_MICS)]
+    return {"rir_rel_l2_max": max(e_h), "rir_rel_l2_median": float(np.median(e_h)),
+            "rirs_compared": len(e_h), "signal_rel_l2_max": max(e_y),
+            "signal_rel_l2_median": float(np.median(e_y)), "signals_compared": len(e_y),
+            "bar": 1e-5, "source": "the oracle outputs of the cpu_baseline sample (noise-free)"}
+
+
+def run_ragged(ism, wl, n_requests, dev, stream, n_cmp=128):
+    """The ragged batch (RT60 U[0.1, 1.0] s, fs 16/48 kHz, 4-16 mics, Sabine
+    walls, order from the length) as one launch, and its first n_cmp
+    requests both batched and one launch per room (the plain path)."""
+    import torch
+    rooms = wl.ragged_batch(n_requests, seed=1005)
+    prep = ism.PreparedRooms(rooms)
+    n_rirs, hl = ism.rir_batch_size(rooms)
+    h = torch.empty(hl, device=dev)
+    stats = torch.zeros(2 * n_rirs, dtype=torch.int64, device=dev)
+    ism.rir_batch(rooms, h=h, stats=stats)
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e[0].record(stream)
+        for _ in range(reps):
+            fn()
+        e[1].record(stream)
+        torch.cuda.synchronize()
+        return e[0].elapsed_time(e[1]) / reps
+
+    ms = timed(lambda: ism.rir_batch(prep, h=h), 2)
+    taps = int(stats.view(-1, 2)[:, 1].sum().item())
+    sub = ism.PreparedRooms(rooms[:n_cmp])
+    hs = torch.empty(sub.h_len, device=dev)
+    ms_b = timed(lambda: ism.rir_batch(sub, h=hs), 3)
+    ms_r = timed(lambda: ism.rir_batch(sub, h=hs, per_room=True), 1)
+    del h, hs
+    return {"requests": n_requests, "rirs": n_rirs, "samples": hl, "ms": ms,
+            "taps_per_s": taps / (ms * 1e-3), "rirs_per_s": n_rirs / (ms * 1e-3),
+            "workload": "RT60 U[0.1,1.0] s (Sabine walls), fs 16/48 kHz, 4-16 mics, RIR "
+                        "ceil(RT60 fs), order from the length, 81-tap Hann sinc",
+            "first_requests_batched_vs_per_room": {"requests": n_cmp, "batched_ms": ms_b,
+                                                   "per_room_ms": ms_r,
+                                                   "speedup": ms_r / ms_b}}
 
 
 def run_reference(args, ws, rank):
@@ -481,6 +542,7 @@ def run_ours(args, ws, rank):
                    "l2": f"inputs larger than L2 (h {hl * 4 / 1e6:.0f} MB, y {ylen * 4 / 1e6:.0f} MB "
                          "per step), no flush"},
         "secondary": {"mic_samples_per_s": ws * mic_samples / (ms_step * 1e-3),
+                      "mic_samples_per_s_convolution": ws * mic_samples / (conv_med * 1e-3),
                       "taps_per_step": taps, "mic_samples_per_step": mic_samples,
                       "stage_ms": {"rir": rir_med, "conv_noise": conv_med}},
         "roofline": {"bound": "alu", "kernel": "k_ism_sparse" if args.rir_variant == "sparse" else "k_ism_taps", "achieved": k1_rate / 1e12,
@@ -517,11 +579,15 @@ def run_ours(args, ws, rank):
                                     pk.get("hbm_gbs", 6800.0), pk_kind)
     if args.paper_sources > 0:
         line["paper_dataset"] = run_paper_dataset(ism, wl, args.paper_sources, dev, stream)
-    if args.serve_rate > 0:
-        line["served"] = run_served(ism, wl, args.serve_rate, args.serve_seconds, precision)
+    if args.ragged > 0:
+        line["ragged"] = run_ragged(ism, wl, args.ragged, dev, stream)
+    rates = [float(r) for r in args.serve_rates.split(",") if r] if args.serve_rate > 0 else []
+    if rates:
+        line["served"] = [run_served(ism, wl, r, args.serve_seconds, precision) for r in rates]
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cb = cpu_sample(rooms, srcs)
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        line["parity"] = parity_vs_sample(ism, cb, h, rooms, srcs, precision)
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -538,9 +604,13 @@ def main():
     ap.add_argument("--rir-variant", default="sparse", choices=["sparse", "direct"],
                     help="K1 kernel: sparse Chebyshev arrays (default) or the direct per-tap one")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--serve-rate", type=float, default=500.0,
-                    help="Poisson arrival rate of the served stream (0 = skip)")
-    ap.add_argument("--serve-seconds", type=float, default=4.0)
+    ap.add_argument("--serve-rate", type=float, default=1.0,
+                    help="0 skips the served streams (their rates: --serve-rates)")
+    ap.add_argument("--serve-seconds", type=float, default=2.0)
+    ap.add_argument("--serve-rates", default="200,1000,5000",
+                    help="Poisson rates (req/s) of the served streams, comma-separated")
+    ap.add_argument("--ragged", type=int, default=4096,
+                    help="requests of the ragged-batch measurement (0 = skip)")
     ap.add_argument("--frames", type=int, default=65536,
                     help="training frames of the frame measurement (0 = skip)")
     ap.add_argument("--paper-sources", type=int, default=2048,
