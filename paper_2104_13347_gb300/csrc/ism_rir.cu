@@ -662,6 +662,7 @@ __device__ __forceinline__ bool eval_candidate(const Tables &T, int TE, const It
 // rho^2 and the z table, window test, gain, statistics.  Returns false if
 // the image's taps miss the window.
 template <int KIND, bool STATS>
+// a is returned without the 1/(4 pi) of the spreading factor.
 __device__ __forceinline__ bool eval_expanded(const Tables &T, int TE, const Item &it, float Rh,
                                               float Rl, float gxy, uint32_t code, int &kb,
                                               float &f, float &a, unsigned &my_taps,
@@ -675,7 +676,9 @@ __device__ __forceinline__ bool eval_expanded(const Tables &T, int TE, const Ite
     split_d2<KIND>(Dh, Dl, &T.sq[ix], &T.sq[TE + iy], &T.sq[iz], it.qh, it.ql, it.q, k, f, d);
     kb = (KIND == ISM_FD_HANN_SINC) ? k - it.H : k - (it.P - 1) / 2;
     if (kb < it.kb_lo32 || kb > it.kb_hi32) return false;
-    a = (gxy * Z.z) * __frcp_rn(12.566370614359172f * d);
+    // a / (4 pi)-free form: the caller folds 1/(4 pi) into its scale;
+    // approximate reciprocal (about 1 ulp, below the FP32 accumulation)
+    a = (gxy * Z.z) * rcp_approx(d);
     if (STATS) {
         const int lo = max(kb, max(it.w0, 0));
         const int hi = min(kb + it.n_taps, it.wend);
@@ -982,7 +985,7 @@ k_ism_sparse(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int m
         const int POS0 = OFF + PADL - (int)it.kb_lo;
         const int jdelta = (KIND == ISM_FD_HANN_SINC) ? it.H : (it.P - 1) / 2;
         unsigned my_contrib = 0, my_taps = 0;
-        float S = 0.f;
+        float S = 0.f, S4 = 0.f;
         auto proc = [&](float Rh, float Rl, float gxy, uint32_t code, bool valid) {
             int kb;
             float f, a;
@@ -990,7 +993,7 @@ k_ism_sparse(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int m
                                                       my_taps, my_contrib))
                 return;
             const int pos = kb + POS0;
-            const float as = a * S;
+            const float as = a * S4;  // a S, with a = prod(beta^hits) / (4 pi d)
             const uint32_t q0 = __float2uint_rn(as);
             uint32_t *c0 = (f == 0.f) ? s_dq : s_cq;  // integer delay: exact Kronecker delta
             const uint32_t old = atomicAdd(&c0[pos], q0);
@@ -1026,6 +1029,7 @@ k_ism_sparse(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int m
         float invS = 0.f;
         for (int attempt = 0;; ++attempt) {
             S = scale_of(attempt);
+            S4 = S * 0.07957747154594767f;  // S / (4 pi)
             invS = 1.f / S;
             my_contrib = 0;
             my_taps = 0;
