@@ -180,8 +180,13 @@ def cpu_sample(rooms, srcs, n_rir_rooms=6, n_conv_rooms=1):
     t_conv = (time.perf_counter() - t0) * n_rir_rooms / n_conv_rooms
     taps = int(st[:, 2].sum())
     mic_samples = n_rir_rooms * N_MICS * (TS + LH - 1)
+    # single core: one room's RIRs and convolutions
+    t0 = time.perf_counter()
+    h1, st1 = oracle.rir_batch(rooms[:1], n_threads=1)
+    oracle.convolve_batch(h1, [srcs[0].astype(np.float64)], n_threads=1)
+    single = int(st1[:, 2].sum()) / (time.perf_counter() - t0)
     return {"value": taps / (t_rir + t_conv), "unit": "taps/s", "cores": threads,
-            "kind": "oracle",
+            "kind": "oracle", "single_core_value": single,
             "sample": (f"RIRs of {n_rir_rooms} rooms x {N_MICS} mics of the workload "
                        f"({t_rir:.1f} s) + convolutions of {n_conv_rooms} room(s) scaled to "
                        f"{n_rir_rooms} ({t_conv:.1f} s)"),
@@ -209,6 +214,26 @@ def parity_vs_sample(ism, cb, h, rooms, srcs, precision):
             "rirs_compared": len(e_h), "signal_rel_l2_max": max(e_y),
             "signal_rel_l2_median": float(np.median(e_y)), "signals_compared": len(e_y),
             "bar": 1e-5, "source": "the oracle outputs of the cpu_baseline sample (noise-free)"}
+
+
+def run_plain_path(ism, prep, h, jobs, src, y, stream, ms_step, taps):
+    """The same step on the plain GPU path: one RIR launch per room and the
+    FP32 direct convolution (same noise, same accuracy bar)."""
+    import torch
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    ism.rir_batch(prep, h=h, per_room=True)
+    ism.convolve_batch(jobs, h, src, y, seed=12345, precision=ism.F32)
+    torch.cuda.synchronize()
+    e[0].record(stream)
+    ism.rir_batch(prep, h=h, per_room=True)
+    e[1].record(stream)
+    ism.convolve_batch(jobs, h, src, y, seed=12345, precision=ism.F32)
+    e[2].record(stream)
+    torch.cuda.synchronize()
+    rir_ms, conv_ms = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
+    return {"rir_per_room_ms": rir_ms, "conv_f32_noise_ms": conv_ms, "ms_per_step": rir_ms + conv_ms,
+            "value": taps / ((rir_ms + conv_ms) * 1e-3), "unit": "taps/s",
+            "speedup_of_the_step": (rir_ms + conv_ms) / ms_step}
 
 
 def run_ragged(ism, wl, n_requests, dev, stream, n_cmp=128):
@@ -579,6 +604,8 @@ def run_ours(args, ws, rank):
                                     pk.get("hbm_gbs", 6800.0), pk_kind)
     if args.paper_sources > 0:
         line["paper_dataset"] = run_paper_dataset(ism, wl, args.paper_sources, dev, stream)
+    if args.plain_path:
+        line["plain_path"] = run_plain_path(ism, prep, h, jobs, src, y, stream, ms_step, taps)
     if args.ragged > 0:
         line["ragged"] = run_ragged(ism, wl, args.ragged, dev, stream)
     rates = [float(r) for r in args.serve_rates.split(",") if r] if args.serve_rate > 0 else []
@@ -586,7 +613,8 @@ def run_ours(args, ws, rank):
         line["served"] = [run_served(ism, wl, r, args.serve_seconds, precision) for r in rates]
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cb = cpu_sample(rooms, srcs)
-        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample",
+                                                   "single_core_value")}
         line["parity"] = parity_vs_sample(ism, cb, h, rooms, srcs, precision)
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -609,6 +637,9 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--serve-rates", default="200,1000,5000",
                     help="Poisson rates (req/s) of the served streams, comma-separated")
+    ap.add_argument("--plain-path", type=int, default=1,
+                    help="1: also time the step on the plain path (per-room RIR launches, "
+                         "FP32 convolution)")
     ap.add_argument("--ragged", type=int, default=4096,
                     help="requests of the ragged-batch measurement (0 = skip)")
     ap.add_argument("--frames", type=int, default=65536,
