@@ -216,6 +216,38 @@ def parity_vs_sample(ism, cb, h, rooms, srcs, precision):
             "bar": 1e-5, "source": "the oracle outputs of the cpu_baseline sample (noise-free)"}
 
 
+def run_single_room(ism, wl, dev, stream, reps=200):
+    """The single-room case (5 x 4 x 3 m, beta 0.8, order 10, 81 taps, RIR
+    4096 @ 16 kHz, one source and one mic): latency per call, device and
+    wall clock, for the sparse and direct paths and the allocation-free
+    entry point."""
+    import torch
+    rooms = wl.single_room(seed=1001)
+    prep = ism.PreparedRooms(rooms)
+    h = torch.empty(prep.h_len, device=dev)
+    stats = torch.zeros(2, dtype=torch.int64, device=dev)
+    ism.rir_batch(rooms, h=h, stats=stats)
+    taps = int(stats[1].item())
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    out = {"workload": "5x4x3 m, beta 0.8, order 10 (74088 images), 81 taps, RIR 4096 @ 16 kHz, "
+                       "1 source, 1 mic", "taps": taps}
+    for name, fn in (("sparse", lambda: ism.rir_batch(prep, h=h)),
+                     ("direct", lambda: ism.rir_batch(prep, h=h, variant=ism.RIR_DIRECT)),
+                     ("noalloc", lambda: ism.rir_batch_noalloc(rooms, h))):
+        for _ in range(5):
+            fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e[0].record(stream)
+        for _ in range(reps):
+            fn()
+        e[1].record(stream)
+        torch.cuda.synchronize()
+        out[name] = {"device_us": 1e3 * e[0].elapsed_time(e[1]) / reps,
+                     "wall_us": 1e6 * (time.perf_counter() - t0) / reps}
+    return out
+
+
 def run_plain_path(ism, prep, h, jobs, src, y, stream, ms_step, taps):
     """The same step on the plain GPU path: one RIR launch per room and the
     FP32 direct convolution (same noise, same accuracy bar)."""
@@ -604,6 +636,7 @@ def run_ours(args, ws, rank):
                                     pk.get("hbm_gbs", 6800.0), pk_kind)
     if args.paper_sources > 0:
         line["paper_dataset"] = run_paper_dataset(ism, wl, args.paper_sources, dev, stream)
+    line["single_room"] = run_single_room(ism, wl, dev, stream)
     if args.plain_path:
         line["plain_path"] = run_plain_path(ism, prep, h, jobs, src, y, stream, ms_step, taps)
     if args.ragged > 0:

@@ -98,8 +98,10 @@ typedef struct ism_room {
  *    fractional delay to sparse integer-delay arrays, and one FIR per output
  *    window applies the filter (P <= 16 terms; the expansion error is below
  *    5e-8 of the peak tap -- under FP32 resolution -- and zero for the 8-tap
- *    Lagrange filter).  Sums use
- *    shared-memory atomics, so repeated runs agree to FP32 rounding.
+ *    Lagrange filter).  The sparse arrays are 32-bit fixed point summed
+ *    with integer atomics, so the result does not depend on the order of
+ *    the adds: repeated runs are bitwise equal.  The fixed-point scale is
+ *    set per output window, so a different window may change the last bit.
  *  ISM_RIR_DIRECT: every tap of every image is evaluated from the filter's
  *    formula and accumulated in a fixed order (bitwise reproducible). */
 typedef enum ism_rir_variant { ISM_RIR_SPARSE = 0, ISM_RIR_DIRECT = 1 } ism_rir_variant;
@@ -107,7 +109,12 @@ typedef enum ism_rir_variant { ISM_RIR_SPARSE = 0, ISM_RIR_DIRECT = 1 } ism_rir_
 /* Options of ism_rir_batch_ex (zero-initialise for defaults). */
 typedef struct ism_rir_opts {
     int32_t window;      /* output window per work item, samples (multiple of
-                            32 in [32, 8192]); 0 = 1024 */
+                            32 in [32, 8192]); 0 = automatic: 1024, halved
+                            down to 128 while the call has fewer than four
+                            work items per SM.  The automatic window depends
+                            on the whole call, so pass a fixed window when a
+                            RIR must be bitwise equal across calls of
+                            different sizes */
     int32_t per_room;    /* 1 = one plain launch per room (the unbatched path) */
     int64_t *stats_dev;  /* optional device int64[2 * n_rirs]: per RIR, the
                             images with a tap in [0, Lh) and the taps that
@@ -166,8 +173,10 @@ int ism_rir_filter_terms(int32_t fd_kind, int32_t n_taps, int32_t *n_terms);
  * another allocator (such as a framework's caching allocator that reserved
  * the whole GPU), or they sit in a latency-bound loop where cudaMalloc's
  * implicit synchronisation and unbounded cost are not acceptable.
- * Arguments, output layout and results are those of ism_rir_batch (same
- * kernel, same 1024-sample windows); no statistics.  The call allocates
+ * Arguments and output layout are those of ism_rir_batch, and the results
+ * agree with it to FP32 rounding: it runs the direct per-tap kernel
+ * (ISM_RIR_DIRECT, which needs no per-RIR tables) on the same automatic
+ * windows; no statistics.  The call allocates
  * nothing: its scratch is one fixed 2 MiB device array inside the library,
  * which every GPU that loads the library holds until the process exits.
  * Limits and rules:
@@ -306,7 +315,8 @@ int ism_frames_batch(const ism_frame_job *jobs, int64_t n_frames, int32_t frame_
  * batches overlap on the GPU.  Results stay on the device until released.
  * Each request's work items (RIR windows, convolution tiles, noise streams
  * keyed by its noise_id) are the same alone or mixed with others, bit for
- * bit (the sparse RIR path sums in fixed point).
+ * bit (the sparse RIR path sums in fixed point, and the server always uses
+ * 1024-sample RIR windows).
  * ------------------------------------------------------------------------ */
 typedef struct ism_server ism_server;
 

@@ -183,6 +183,24 @@ int validate_room(const ism_room &r, int64_t idx) {
     return ISM_OK;
 }
 
+// Output window per work item when the caller leaves it to the library:
+// 1024 samples, halved (down to 128) while the call has fewer than four work
+// items per SM.  A single 4096-sample RIR then runs as 32 items instead of 4
+// (latency-bound calls: 55 us instead of 85 us per call on GB300), while
+// batches with enough RIRs keep the 1024 that serves them best.
+int auto_window(const ism_room *rooms, int64_t n_rooms) {
+    const int64_t target = 4 * (int64_t)device_sm_count();
+    int W = 1024;
+    while (W > 128) {
+        int64_t items = 0;
+        for (int64_t r = 0; r < n_rooms && items < target; ++r)
+            items += (int64_t)rooms[r].n_mics * ((rooms[r].rir_len + W - 1) / W);
+        if (items >= target) break;
+        W /= 2;
+    }
+    return W;
+}
+
 // Lattice order of RIR (room r, mic m): the room's order, or for
 // ISM_ORDER_AUTO the smallest N whose lattice holds every image able to put
 // a tap into [0, rir_len): the first tap of an image at delay tau is at or
@@ -320,11 +338,13 @@ int ism_rir_batch_ex(const ism_room *rooms, int64_t n_rooms, float *h_dev,
     ism_rir_opts o;
     memset(&o, 0, sizeof(o));
     if (opts) o = *opts;
-    const int W = o.window > 0 ? o.window : 1024;
-    if (W % 32 != 0 || W < 32 || W > 8192)
+    if (o.window != 0 && (o.window % 32 != 0 || o.window < 32 || o.window > 8192))
         return fail(ISM_ERR_INVALID_ARG, "window must be a multiple of 32 in [32, 8192]");
     if (o.variant != ISM_RIR_SPARSE && o.variant != ISM_RIR_DIRECT)
         return fail(ISM_ERR_INVALID_ARG, "unknown variant");
+    for (int64_t r = 0; r < n_rooms; ++r)
+        if (int st = validate_room(rooms[r], r)) return st;
+    const int W = o.window > 0 ? o.window : auto_window(rooms, n_rooms);
 
     // jobs, one per RIR; grouped by filter kind (one launch per kind)
     std::vector<RirJob> jobs[2];

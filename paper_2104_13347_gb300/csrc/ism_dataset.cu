@@ -11,8 +11,9 @@
 //   comp: [wait up(k), down(k-2)] RIRs -> h_d, convolution + noise -> y_d
 //   down: [wait comp(k)] y_d (and h_d) -> host
 // Every kernel is the batch entry points' own (ism_rir_batch_ex,
-// ism_convolve_batch); room i keeps noise id base + i, so the outputs do
-// not depend on the chunking.
+// ism_convolve_batch); the RIR window is chosen once for the whole batch
+// (ism_rir_batch's automatic rule over all rooms) and room i keeps noise id
+// base + i, so the outputs do not depend on the chunking.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -143,6 +144,12 @@ extern "C" int ism_dataset_batch(const ism_room *rooms, int64_t n_rooms, const f
     auto y_d = [&](int s) { return (float *)((char *)P.buf + s * set_bytes + al(max_s)); };
     auto h_d = [&](int s) { return (float *)((char *)P.buf + s * set_bytes + al(max_s) + al(max_y)); };
 
+    // one RIR window for every chunk: the sparse path's fixed-point scale is
+    // per window, so the window fixes the last bits of the RIRs
+    ism_rir_opts ro;
+    memset(&ro, 0, sizeof(ro));
+    ro.window = auto_window(rooms, n_rooms);
+
     int st = ISM_OK;
     std::vector<ism_conv_job> jobs;
     for (int c = 0; c < n_chunks && !st; ++c) {
@@ -167,7 +174,7 @@ extern "C" int ism_dataset_batch(const ism_room *rooms, int64_t n_rooms, const f
         // kernels of the chunk
         cudaStreamWaitEvent(P.comp, P.up_done[s], 0);
         if (c >= 2) cudaStreamWaitEvent(P.comp, P.down_done[s], 0);
-        st = ism_rir_batch_ex(rooms + r0, r1 - r0, h_d(s), nullptr, nullptr, P.comp);
+        st = ism_rir_batch_ex(rooms + r0, r1 - r0, h_d(s), nullptr, &ro, P.comp);
         if (st) break;
         jobs.assign((size_t)(r1 - r0), ism_conv_job{});
         {

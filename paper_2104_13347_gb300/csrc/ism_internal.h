@@ -73,6 +73,9 @@ int room_order(const ism_room &r, int m);
 // error status with the last-error string set.
 int validate_room(const ism_room &r, int64_t idx);
 
+// The default output window of a K1 call (see ism_api.cu).
+int auto_window(const ism_room *rooms, int64_t n_rooms);
+
 // K1: image-source taps.  jobs_dev has n_rirs jobs; every job's windows are
 // processed; wmax = max n_windows.  counter_dev: one zeroed uint32 work
 // counter.  max_order / max_taps size the shared memory and tap rows.

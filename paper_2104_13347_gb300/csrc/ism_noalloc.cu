@@ -30,10 +30,6 @@
 
 #include "ism_internal.h"
 
-namespace ism {
-int validate_room(const ism_room &r, int64_t idx);
-}
-
 using namespace ism;
 
 namespace {
@@ -77,13 +73,14 @@ extern "C" int ism_rir_batch_noalloc(const ism_room *rooms, int64_t n_rooms, flo
     if (n_rooms == 0) return ISM_OK;
     if (!rooms || !h_dev) return fail(ISM_ERR_INVALID_ARG, "NULL rooms or h_dev");
     cudaStream_t stream = (cudaStream_t)stream_v;
-    const int W = 1024;  // the same work items as ism_rir_batch's default
+    for (int64_t r = 0; r < n_rooms; ++r)
+        if (int st = validate_room(rooms[r], r)) return st;
+    const int W = auto_window(rooms, n_rooms);  // ism_rir_batch's default windows
 
     int64_t count[2] = {0, 0};
     int max_order[2] = {0, 0}, max_taps[2] = {1, 1}, wmax[2] = {0, 0};
     for (int64_t r = 0; r < n_rooms; ++r) {
         const ism_room &R = rooms[r];
-        if (int st = validate_room(R, r)) return st;
         const int k = R.fd_kind;
         count[k] += R.n_mics;
         for (int m = 0; m < R.n_mics; ++m) max_order[k] = std::max(max_order[k], room_order(R, m));
