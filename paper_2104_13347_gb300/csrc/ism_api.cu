@@ -221,6 +221,10 @@ int room_order(const ism_room &r, int m) {
 }
 
 // ---------------------------------------------------------------------------
+// Sorted column lists of one sparse launch at most this many entries (4 B
+// each): a batch whose lists would need more runs as several launches.
+constexpr long long kColBudget = 1ll << 28;
+
 // Chebyshev tables of the fractional-delay filters (FP64, cached)
 // ---------------------------------------------------------------------------
 namespace {
@@ -421,40 +425,79 @@ int ism_rir_batch_ex(const ism_room *rooms, int64_t n_rooms, float *h_dev,
         }
         if (!sparse && rir_smem_bytes(W, max_order[kind], max_taps[kind]) > 227 * 1024)
             return fail(ISM_ERR_INVALID_ARG, "window/order/taps need too much shared memory");
-        const size_t jb = jv.size() * sizeof(RirJob);
-        const size_t tb = sparse ? tabs.size() * sizeof(float) : 0;
-        void *scr = nullptr;
-        if (int st = scratch_alloc(&scr, jb + 256 + tb, stream)) return st;
-        RirJob *d_jobs = (RirJob *)scr;
-        unsigned int *d_counter = (unsigned int *)((char *)scr + jb);
-        const float *d_tabs = (const float *)((char *)scr + jb + 256);
-        long long *d_stats = (long long *)o.stats_dev;
-        int st = upload_async(d_jobs, jv.data(), jb, stream);
-        if (!st && tb) st = upload_async((void *)d_tabs, tabs.data(), tb, stream);
-        cudaError_t e = cudaSuccess;
-        auto run = [&](const RirJob *jd, int n, int wm) {
-            e = cudaMemsetAsync(d_counter, 0, sizeof(unsigned int), stream);
-            if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(counter)");
-            RirLaunch L{jd, n, wm, W, max_order[kind], max_taps[kind], kind, h_dev, d_stats,
-                        d_counter, nullptr, 0, d_tabs, max_cheb, min_cheb};
-            return sparse ? launch_rir_sparse(L, stream) : launch_rir(L, stream);
-        };
-        if (!st) {
-            if (o.per_room) {
-                // The unbatched path: one launch per room, each over that
-                // room's RIRs only.
-                size_t b = 0;
-                while (!st && b < jv.size()) {
-                    size_t e2 = b + 1;
-                    while (e2 < jv.size() && room_of[kind][e2] == room_of[kind][b]) ++e2;
-                    int wm = 0;
-                    for (size_t k = b; k < e2; ++k) wm = std::max(wm, jv[k].n_windows);
-                    st = run(d_jobs + b, (int)(e2 - b), wm);
-                    b = e2;
+        // launches: one per room on the unbatched path; otherwise the whole
+        // kind, cut where the sparse kernel's sorted column lists would pass
+        // kColBudget entries
+        std::vector<std::pair<size_t, size_t>> chunks;
+        {
+            size_t b = 0;
+            long long acc = 0;
+            for (size_t k = 0; k < jv.size(); ++k) {
+                const long long ce = sparse ? rir_col_entries(jv[k].order) : 0;
+                const bool cut = o.per_room ? room_of[kind][k] != room_of[kind][b]
+                                            : (k > b && acc + ce > kColBudget);
+                if (cut) {
+                    chunks.push_back({b, k});
+                    b = k;
+                    acc = 0;
                 }
-            } else {
-                st = run(d_jobs, (int)jv.size(), wmax[kind]);
+                acc += ce;
             }
+            chunks.push_back({b, jv.size()});
+        }
+        // per RIR: column-list and window-range offsets, relative to its launch
+        std::vector<long long> offs;
+        long long max_cols = 0, max_wins = 0;
+        if (sparse) {
+            offs.resize(2 * jv.size());
+            for (auto &c : chunks) {
+                long long co = 0, wo = 0;
+                for (size_t k = c.first; k < c.second; ++k) {
+                    offs[2 * k] = co;
+                    offs[2 * k + 1] = wo;
+                    co += rir_col_entries(jv[k].order);
+                    wo += jv[k].n_windows;
+                }
+                max_cols = std::max(max_cols, co);
+                max_wins = std::max(max_wins, wo);
+            }
+        }
+        auto al = [](size_t n) { return (n + 255) & ~(size_t)255; };
+        const size_t jb = al(jv.size() * sizeof(RirJob));
+        const size_t tb = al(sparse ? tabs.size() * sizeof(float) : 0);
+        const size_t ob = al(offs.size() * sizeof(long long));
+        const size_t cb = al((size_t)max_cols * sizeof(uint32_t));
+        const size_t wb = al((size_t)max_wins * sizeof(int2));
+        void *scr = nullptr;
+        if (int st = scratch_alloc(&scr, jb + 256 + tb + ob + cb + wb, stream)) return st;
+        char *sp = (char *)scr;
+        RirJob *d_jobs = (RirJob *)sp;
+        unsigned int *d_counter = (unsigned int *)(sp + jb);
+        const float *d_tabs = (const float *)(sp + jb + 256);
+        long long *d_offs = (long long *)(sp + jb + 256 + tb);
+        uint32_t *d_cols = (uint32_t *)(sp + jb + 256 + tb + ob);
+        int2 *d_wr = (int2 *)(sp + jb + 256 + tb + ob + cb);
+        long long *d_stats = (long long *)o.stats_dev;
+        int st = upload_async(d_jobs, jv.data(), jv.size() * sizeof(RirJob), stream);
+        if (!st && sparse) st = upload_async((void *)d_tabs, tabs.data(), tabs.size() * sizeof(float), stream);
+        if (!st && sparse) st = upload_async(d_offs, offs.data(), offs.size() * sizeof(long long), stream);
+        for (size_t ci = 0; !st && ci < chunks.size(); ++ci) {
+            const size_t b = chunks[ci].first, n = chunks[ci].second - b;
+            int wm = 0;
+            for (size_t k = b; k < b + n; ++k) wm = std::max(wm, jv[k].n_windows);
+            cudaError_t e = cudaMemsetAsync(d_counter, 0, sizeof(unsigned int), stream);
+            if (e != cudaSuccess) {
+                st = cuda_fail(e, "cudaMemsetAsync(counter)");
+                break;
+            }
+            RirLaunch L{d_jobs + b, (int)n, wm, W, max_order[kind], max_taps[kind], kind, h_dev,
+                        d_stats, d_counter, nullptr, 0, d_tabs, max_cheb, min_cheb};
+            if (sparse) {
+                L.cols_dev = d_cols;
+                L.wr_dev = d_wr;
+                L.offs_dev = d_offs + 2 * b;
+            }
+            st = sparse ? launch_rir_sparse(L, stream) : launch_rir(L, stream);
         }
         scratch_free(scr, stream);
         if (st) return st;

@@ -95,7 +95,19 @@ struct RirLaunch {
     const float *tabs_dev;  // sparse kernel: Chebyshev tables [p][n_taps]
     int max_cheb;           // sparse kernel: largest n_cheb of the jobs
     int min_cheb;           // sparse kernel: smallest n_cheb of the jobs
+    // sparse kernel scratch: per RIR j, offs_dev[2 j] is the offset of its
+    // sorted column list in cols_dev (room for TEj^2 entries, TEj = 2 (2 N_j
+    // + 1)) and offs_dev[2 j + 1] the offset of its per-window rank ranges
+    // in wr_dev (n_windows entries)
+    uint32_t *cols_dev = nullptr;
+    int2 *wr_dev = nullptr;
+    const long long *offs_dev = nullptr;
 };
+// Entries of a sparse launch's column list for a RIR of order N.
+inline long long rir_col_entries(int order) {
+    const long long te = 2 * (2 * (long long)order + 1);
+    return te * te;
+}
 // Direct per-tap kernel (bitwise reproducible).
 int launch_rir(const RirLaunch &L, cudaStream_t stream);
 size_t rir_smem_bytes(int window, int max_order, int max_taps);

@@ -34,9 +34,11 @@
 //    sparse array -- held in 32-bit fixed point (native u32 shared-memory
 //    atomics, order-independent sums: bitwise reproducible), and one FIR per
 //    window gives h[n] = sum_p sum_j B[p][j] c_p[n - j].  Per image: P
-//    terms instead of one reciprocal and ~7 operations per tap.  Candidates
-//    are handed to lanes in pairs of consecutive z-images by a warp-wide
-//    expansion of the column counts.
+//    terms instead of one reciprocal and ~7 operations per tap.  The
+//    lattice columns of each RIR are sorted once by rho^2 = x^2 + y^2
+//    (k_ism_tables); a window sweeps the contiguous range of that order
+//    that can reach it, one column per lane, each lane walking its own
+//    column's candidates (neighbouring columns have nearly equal counts).
 //  * k_ism_taps (direct): one warp per image, one lane per tap (81 taps -> 3
 //    rows of 32).  sin(pi (j-f)) = -(-1)^j sin(pi f) and the Hann term is
 //    expanded in cos/sin of pi j/(H+1) (per-lane constants) and of
@@ -104,10 +106,10 @@ struct Tables {
     float *dl;    // [3][TE] axis offset, FP32
 };
 
-// Shared-memory carve-up.  Common part: tables, axis lists, candidates.
-// Direct kernel adds one private window row per warp; sparse kernel adds
-// the P sparse arrays, the integer-delay (delta) array, the Chebyshev table
-// and the FIR partial sums.
+// Shared-memory carve-up.  Common part: the per-axis tables.  The direct
+// kernel adds the axis lists, the candidate buffer and one private window
+// row per warp; the sparse kernel the FIR partial sums (in the candidate
+// slot), the P sparse arrays and the integer-delay (delta) array.
 struct Layout {
     int TE, RL, CL;
     size_t off_sq, off_hlg, off_dl, off_lx, off_ly, off_cand, off_rows, off_c,
@@ -126,12 +128,11 @@ __host__ __device__ inline Layout make_layout(bool sparse, int window, int max_o
     L.off_sq = o;   o = align16(o + (sparse ? 0 : sizeof(double) * 3 * L.TE));
     L.off_hlg = o;  o = align16(o + sizeof(float4) * 3 * L.TE);
     L.off_dl = o;   o = align16(o + sizeof(float) * 3 * L.TE);
-    L.off_lx = o;   o = align16(o + sizeof(int) * L.TE);
-    L.off_ly = o;   o = align16(o + sizeof(int) * L.TE);
-    // sparse kernel: the per-warp candidate stashes (32 records of 16 B) and,
-    // after the sweep, the FIR partial sums (W floats) share one buffer
-    size_t cand_words = CAP;
-    if (sparse) cand_words = (size_t)(window > NW * 32 * 4 ? window : NW * 32 * 4);
+    // axis lists and the candidate buffer: direct kernel only; the sparse
+    // kernel keeps the FIR partial sums (W floats) in the candidate slot
+    L.off_lx = o;   o = align16(o + (sparse ? 0 : sizeof(int) * L.TE));
+    L.off_ly = o;   o = align16(o + (sparse ? 0 : sizeof(int) * L.TE));
+    const size_t cand_words = sparse ? (size_t)window : (size_t)CAP;
     L.off_cand = o; o = align16(o + sizeof(uint32_t) * cand_words);
     L.off_rows = L.off_c = L.off_delta = o;
     L.off_part = L.off_cand;
@@ -357,14 +358,49 @@ __device__ __forceinline__ void build_tables(const RirJob &J, const Tables &T, d
 // Per-RIR tables in global memory for the sparse kernel, computed once per
 // RIR instead of once per window (GB300's FP64 pipe is narrow): RIR j's
 // entry (a, ei) at j * 3 TE + a TE + ei.
-__global__ void __launch_bounds__(128)
-k_ism_tables(const RirJob *__restrict__ jobs, int n_rirs, int TE, double *__restrict__ g_sq,
-             float4 *__restrict__ g_hlg, float *__restrict__ g_dl, JobConst *__restrict__ g_jc) {
+//
+// The same kernel sorts the RIR's lattice columns (x entry, y entry) by
+// rho^2 = x^2 + y^2 for the sparse kernel's sweep: a counting sort into KB
+// bins of equal width over [0, R^2], R the largest distance any window of
+// the RIR reaches (columns beyond it hold no image of any window), written
+// to g_cols + offs[2 j] as ix | iy << 16.  For every window w it records in
+// g_wr[offs[2 j + 1] + w] the rank range [c_lo, c_hi) of the bins that can
+// hold a column with candidates in w: columns closer than
+// rho^2 = d_lo^2 - (Z + eps)^2 (Z: the largest |z offset| of the lattice)
+// have every image nearer than the window, columns farther than d_hi + eps
+// none that near; one bin of margin on either side.  The order inside a bin
+// is whatever the atomics give: it changes only how the sweep's lanes are
+// loaded, never which images are summed (and the sums are exact integers).
+constexpr int KB = 2048;          // rho^2 bins of the column sort
+constexpr int TNT = 128;          // threads of k_ism_tables
+constexpr int kMaxTE = 2 * (2 * 200 + 1);
+
+// rho^2 of a column and its bin, with explicit roundings: the histogram and
+// the scatter must place every column in the same bin.
+__device__ __forceinline__ float col_rho2(float x, float y) {
+    return __fmaf_rn(x, x, __fmul_rn(y, y));
+}
+__device__ __forceinline__ int rho2_bin(float r2, float sc) {
+    return (int)fminf(__fmul_rn(r2, sc), (float)(KB - 1));
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(TNT)
+k_ism_tables(const RirJob *__restrict__ jobs, int n_rirs, int TE, int W,
+             double *__restrict__ g_sq, float4 *__restrict__ g_hlg, float *__restrict__ g_dl,
+             JobConst *__restrict__ g_jc, uint32_t *__restrict__ g_cols, int2 *__restrict__ g_wr,
+             const long long *__restrict__ g_offs) {
+    __shared__ float s_x[kMaxTE], s_y[kMaxTE];
+    __shared__ unsigned s_bin[KB + 1];
+    __shared__ unsigned s_zmax;  // float bits of max |z offset| (>= 0)
+    __shared__ JobConst s_jc;
+    __shared__ unsigned s_wsum[TNT / 32];
+    const int tid = threadIdx.x;
     for (int j = blockIdx.x; j < n_rirs; j += gridDim.x) {
         const RirJob &J = jobs[j];
         const int N = J.order, TEj = 2 * (2 * N + 1);
         const size_t base = (size_t)j * 3 * TE;
-        if (threadIdx.x == 0) {
+        if (tid == 0) {
             const double dx = J.src[0] - J.mic[0], dy = J.src[1] - J.mic[1],
                          dz = J.src[2] - J.mic[2];
             JobConst c;
@@ -375,8 +411,12 @@ k_ism_tables(const RirJob *__restrict__ jobs, int n_rirs, int TE, double *__rest
             c.inv2Lz = (float)(0.5 / J.dims[2]);
             c.pad[0] = c.pad[1] = c.pad[2] = 0.f;
             g_jc[j] = c;
+            s_jc = c;
+            s_zmax = 0u;
         }
-        for (int e = threadIdx.x; e < 3 * TEj; e += blockDim.x) {
+        for (int i = tid; i <= KB; i += TNT) s_bin[i] = 0u;
+        __syncthreads();
+        for (int e = tid; e < 3 * TEj; e += TNT) {
             const int a = e / TEj, ei = e - a * TEj;
             double sq;
             float4 hlg;
@@ -385,7 +425,75 @@ k_ism_tables(const RirJob *__restrict__ jobs, int n_rirs, int TE, double *__rest
             g_sq[base + a * TE + ei] = sq;
             g_hlg[base + a * TE + ei] = hlg;
             g_dl[base + a * TE + ei] = dl;
+            if (a == 0) s_x[ei] = dl;
+            else if (a == 1) s_y[ei] = dl;
+            else atomicMax(&s_zmax, __float_as_uint(fabsf(dl)));
         }
+        __syncthreads();
+        const JobConst jc = s_jc;
+        Item it;
+        float tau_lo, tau_hi;
+        item_setup_f32<KIND>(J, jc, W, J.n_windows - 1, it, tau_lo, tau_hi);
+        const float R2 = fmaxf(it.dhe2, 1e-30f);
+        const float sc = (float)KB / R2;
+        const int n_cols = TEj * TEj;
+        // histogram of the columns within R
+        for (int c = tid; c < n_cols; c += TNT) {
+            const int ix = c / TEj, iy = c - ix * TEj;
+            const float r2 = col_rho2(s_x[ix], s_y[iy]);
+            if (r2 <= R2) atomicAdd(&s_bin[rho2_bin(r2, sc)], 1u);
+        }
+        __syncthreads();
+        // exclusive scan of the KB bins: each thread scans KB / TNT
+        // consecutive bins, the warps' totals go through shared memory
+        {
+            constexpr int PER = KB / TNT;
+            unsigned loc[PER], run = 0u;
+#pragma unroll
+            for (int k = 0; k < PER; ++k) {
+                loc[k] = run;
+                run += s_bin[tid * PER + k];
+            }
+            const int lane = tid & 31, warp = tid >> 5;
+            unsigned x = run;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            if (lane == 31) s_wsum[warp] = x;
+            __syncthreads();
+            unsigned off = x - run;
+            for (int w = 0; w < warp; ++w) off += s_wsum[w];
+#pragma unroll
+            for (int k = 0; k < PER; ++k) s_bin[tid * PER + k] = off + loc[k];
+            if (tid == TNT - 1) s_bin[KB] = off + run;
+        }
+        __syncthreads();
+        // per-window rank ranges
+        const float zr = __uint_as_float(s_zmax);
+        for (int w = tid; w < J.n_windows; w += TNT) {
+            Item iw;
+            float tl, th;
+            item_setup_f32<KIND>(J, jc, W, w, iw, tl, th);
+            const float zz = zr + iw.eps;
+            const float r2lo = fmaxf(iw.dlo2 - zz * zz, 0.f);
+            const int b_lo = max(rho2_bin(r2lo, sc) - 1, 0);
+            const int b_hi = min(rho2_bin(iw.dhe2, sc) + 1, KB - 1);
+            g_wr[g_offs[2 * j + 1] + w] = make_int2((int)s_bin[b_lo], (int)s_bin[b_hi + 1]);
+        }
+        __syncthreads();
+        // scatter (the bin starts become cursors)
+        uint32_t *out = g_cols + g_offs[2 * j];
+        for (int c = tid; c < n_cols; c += TNT) {
+            const int ix = c / TEj, iy = c - ix * TEj;
+            const float r2 = col_rho2(s_x[ix], s_y[iy]);
+            if (r2 <= R2) {
+                const unsigned pos = atomicAdd(&s_bin[rho2_bin(r2, sc)], 1u);
+                out[pos] = (uint32_t)ix | ((uint32_t)iy << 16);
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -418,31 +526,27 @@ struct Col {
     }
 };
 
-__device__ __forceinline__ Col column_solve(const Tables &T, int TE, const Item &it,
-                                            const int *s_lx, const int *s_ly, int nLY,
-                                            int c, int n_cols) {
+// sqrt(x) for x >= 0 from the approximate reciprocal square root (2 ulp);
+// the column bounds carry a margin of eps >= 0.2 m, far above its error.
+__device__ __forceinline__ float sqrt_bound(float x) {
+    return x * rsqrtf(fmaxf(x, 1e-30f));
+}
+
+// The admissible n of column (ix, iy, wz): the z runs whose image distance
+// can fall in the item's delay range [d_lo, d_hi] (widened by eps).
+__device__ __forceinline__ Col column_solve_xy(const Tables &T, int TE, const Item &it, int ix,
+                                               int iy, int wz) {
     const int N = it.N;
-    Col r{1, 0, 1, 0, 0, 0, 0};
-    if (c >= n_cols) return r;
-    r.wz = c & 1;
-    // (x, y) list positions of column pair t = c / 2 (t < 2^20): quotient
-    // by an FP32 reciprocal, corrected to the exact integer division
-    const int t = c >> 1;
-    int xi = (int)((float)t * __frcp_rn((float)nLY));
-    int yi = t - xi * nLY;
-    if (yi < 0) { --xi; yi += nLY; }
-    else if (yi >= nLY) { ++xi; yi -= nLY; }
-    r.ix = s_lx[xi];
-    r.iy = s_ly[yi];
-    const float dx = T.dl[r.ix], dy = T.dl[TE + r.iy];
+    Col r{1, 0, 1, 0, ix, iy, wz};
+    const float dx = T.dl[ix], dy = T.dl[TE + iy];
     const float rho2 = dx * dx + dy * dy;
     if (rho2 > it.dhe2) return r;
     // Delta_z(n) = cz + 2 Lz n must satisfy zmin <= |Delta_z| <= zmax:
     // the full range [-zmax, zmax] minus the open hole (-zmin, zmin).
-    const float zmax = sqrtf(fmaxf(it.dhi2 - rho2, 0.f)) + it.eps;
+    const float zmax = sqrt_bound(fmaxf(it.dhi2 - rho2, 0.f)) + it.eps;
     const float zmin2 = it.dlo2 - rho2;
-    const float zmin = zmin2 > 0.f ? sqrtf(zmin2) - it.eps : 0.f;
-    const float cz = T.dl[2 * TE + r.wz * (2 * N + 1) + N];
+    const float zmin = zmin2 > 0.f ? sqrt_bound(zmin2) - it.eps : 0.f;
+    const float cz = T.dl[2 * TE + wz * (2 * N + 1) + N];
     const float lim = (float)N + 1.f;
     const float u_lo = fminf(fmaxf((-zmax - cz) * it.inv2Lz, -lim), lim);
     const float u_hi = fminf(fmaxf((zmax - cz) * it.inv2Lz, -lim), lim);
@@ -469,6 +573,22 @@ __device__ __forceinline__ Col column_solve(const Tables &T, int TE, const Item 
     return r;
 }
 
+// Column c = ((u,l), (v,m), w) of the axis lists (direct kernel's sweep).
+// rnly: an FP32 reciprocal of nLY (any rounding: the quotient is corrected).
+__device__ __forceinline__ Col column_solve(const Tables &T, int TE, const Item &it,
+                                            const int *s_lx, const int *s_ly, int nLY,
+                                            float rnly, int c, int n_cols) {
+    if (c >= n_cols) return Col{1, 0, 1, 0, 0, 0, 0};
+    // (x, y) list positions of column pair t = c / 2 (t < 2^20): quotient
+    // by an FP32 reciprocal, corrected to the exact integer division
+    const int t = c >> 1;
+    int xi = (int)((float)t * rnly);
+    int yi = t - xi * nLY;
+    if (yi < 0) { --xi; yi += nLY; }
+    else if (yi >= nLY) { ++xi; yi -= nLY; }
+    return column_solve_xy(T, TE, it, s_lx[xi], s_ly[yi], c & 1);
+}
+
 // Writes the candidates of column col whose warp- or block-level index
 // (first index off) lies in [g_lo, g_hi), candidate index i going to
 // dst[(base + i) & mask].
@@ -491,10 +611,11 @@ __device__ __forceinline__ void column_sweep(const Tables &T, int TE, const Item
                                              int *s_scan, uint32_t *s_cand, Flush &flush) {
     const int N = it.N, tid = threadIdx.x;
     const int n_cols = nLX * nLY * 2;
+    const float rnly = __frcp_rn((float)nLY);
     int n_cand = 0;  // block-uniform
     for (int cb = 0; cb < n_cols; cb += NT) {
         const int c = cb + tid;
-        const Col col = column_solve(T, TE, it, s_lx, s_ly, nLY, c, n_cols);
+        const Col col = column_solve(T, TE, it, s_lx, s_ly, nLY, rnly, c, n_cols);
         int total;
         const int off = block_scan(col.count(), s_scan, total);
         if (total == 0) continue;
@@ -515,121 +636,54 @@ __device__ __forceinline__ void column_sweep(const Tables &T, int TE, const Item
     if (n_cand > 0) flush(n_cand);
 }
 
-// Warp-independent column sweep with lane-per-pair expansion.  Warp w takes
-// column batches w, w + NW, ... (32 columns each, one per lane).  Each lane
-// solves its column and, if the column has candidates, its float-float
-// rho^2 = x^2 + y^2 and damping product g_xy once.  The column's candidates
-// (one or two runs of consecutive n) are cut into pairs (n, n + 1), the last
-// pair of an odd run holding one; a warp-wide scan of the pair counts
-// numbers the batch's pairs, and pair g goes to lane g mod 32, which finds
-// its column by binary search over the inclusive counts (the search also
-// yields the column's first pair index) and fetches the column's data with
-// five shuffles.  Batches are always 32 pairs wide: the last < 32 pairs of a
-// column batch wait in a per-warp stash of (rho_h, rho_l, g_xy, code)
-// records for the next one (the sign bit of g_xy >= 0 marks a full pair).
-// proc(rho_h, rho_l, g_xy, code, valid) is called twice per lane, once per
-// element of its pair; code = iz | ix << 12 | iy << 22 (iz: absolute index
-// of the z table entry).  No block-wide barrier is involved.
+// Sorted column sweep of the sparse kernel.  The item's columns are the
+// ranks [c_lo, c_hi) of the RIR's column list, sorted by rho^2 = x^2 + y^2
+// (k_ism_tables), each (x, y) entry standing for two columns (z parity
+// w = 0, 1).  Warp w takes column batches w, w + NW, ... of 32 columns, one
+// per lane; each lane solves its column and walks the column's candidates
+// itself.  Neighbouring ranks have nearly the same rho and hence nearly the
+// same candidate count, so the lanes of a batch finish close together.
+// proc(rho_h, rho_l, g_xy, code) is called once per candidate; code = iz |
+// ix << 12 | iy << 22 (iz: absolute index of the z table entry).  No
+// block-wide barrier is involved.
 template <class Proc>
-__device__ __forceinline__ void warp_expand(const Tables &T, int TE, const Item &it,
-                                            const int *s_lx, const int *s_ly, int nLX, int nLY,
-                                            float4 *stash, Proc &proc) {
+__device__ __forceinline__ void sorted_sweep(const Tables &T, int TE, const Item &it,
+                                             const uint32_t *__restrict__ cols, int c_lo,
+                                             int c_hi, Proc &proc) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int n_cols = nLX * nLY * 2;  // <= 2 * 802^2
+    const int n_cols = 2 * (c_hi - c_lo);
     const int N = it.N;
-    int L = 0;  // warp-uniform stash count, < 32
-    auto run_pair = [&](float rh, float rl, float gg, uint32_t code, bool v0) {
-        const bool v1 = v0 && (__float_as_uint(gg) >> 31);
-        gg = fabsf(gg);
-        proc(rh, rl, gg, code, v0);
-        proc(rh, rl, gg, code + 1u, v1);
-    };
     for (int cb = warp * 32; cb < n_cols; cb += NT) {
-        const Col col = column_solve(T, TE, it, s_lx, s_ly, nLY, cb + lane, n_cols);
-        const int na = max(col.hi_a - col.lo_a + 1, 0), nb = max(col.hi_b - col.lo_b + 1, 0);
-        const int cnt = ((na + 1) >> 1) + ((nb + 1) >> 1);  // pairs
+        const int c = cb + lane;
+        int na = 0, nb = 0, lo_a = 0, lo_b = 0;
         float Rh = 0.f, Rl = 0.f, gxy = 0.f;
-        if (cnt > 0) {
-            const float4 X = T.hlg[col.ix], Y = T.hlg[TE + col.iy];
-            ff_add(X.x, X.y, Y.x, Y.y, Rh, Rl);
-            gxy = X.z * Y.z;
-        }
-        int incl = cnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
-        }
-        const int total = __shfl_sync(0xffffffffu, incl, 31);
-        if (total == 0) continue;
-        // packed column data (all fields fit: iz < 3 TE <= 2406, ix, iy <
-        // 1024, na, nb, gap <= 2N+1 <= 401)
-        const int zbase = 2 * TE + col.wz * (2 * N + 1) + N + col.lo_a;
-        const int gap = nb > 0 ? col.lo_b - (col.lo_a + na) : 0;
-        const uint32_t k1 = cnt > 0 ? ((uint32_t)zbase | ((uint32_t)col.ix << 12) |
-                                       ((uint32_t)col.iy << 22))
-                                    : 0u;
-        const uint32_t k2 = (uint32_t)gap | ((uint32_t)na << 9) | ((uint32_t)nb << 18);
-        // pair g: column, code of its first element, second element present
-        auto fetch = [&](int g, float &rh, float &rl, float &gg, uint32_t &code) {
-            int c = 0, ex = 0;  // c: lanes whose inclusive count is <= g; ex: their last count
-#pragma unroll
-            for (int st = 16; st >= 1; st >>= 1) {
-                const int v = __shfl_sync(0xffffffffu, incl, c + st - 1);
-                if (v <= g) { c += st; ex = v; }
+        uint32_t k1 = 0u;
+        if (c < n_cols) {
+            const uint32_t e = __ldg(cols + c_lo + (c >> 1));
+            const int ix = (int)(e & 0xffffu), iy = (int)(e >> 16);
+            // (entries are < TEj by construction; the guard keeps a bad
+            // entry from indexing past the tables)
+            const Col col = (ix < it.TEj && iy < it.TEj) ? column_solve_xy(T, TE, it, ix, iy, c & 1)
+                                                         : Col{1, 0, 1, 0, 0, 0, 0};
+            na = max(col.hi_a - col.lo_a + 1, 0);
+            nb = max(col.hi_b - col.lo_b + 1, 0);
+            lo_a = col.lo_a;
+            lo_b = col.lo_b;
+            if (na + nb > 0) {
+                const float4 X = T.hlg[ix], Y = T.hlg[TE + iy];
+                ff_add(X.x, X.y, Y.x, Y.y, Rh, Rl);
+                gxy = X.z * Y.z;
+                // iz < 3 TE <= 2406, ix, iy < 1024
+                k1 = (uint32_t)(2 * TE + col.wz * (2 * N + 1) + N) | ((uint32_t)ix << 12) |
+                     ((uint32_t)iy << 22);
             }
-            const uint32_t a1 = __shfl_sync(0xffffffffu, k1, c);
-            const uint32_t a2 = __shfl_sync(0xffffffffu, k2, c);
-            rh = __shfl_sync(0xffffffffu, Rh, c);
-            rl = __shfl_sync(0xffffffffu, Rl, c);
-            const float g0 = __shfl_sync(0xffffffffu, gxy, c);
-            const int r = g - ex;  // pair index within the column
-            const int ga = (int)(a2 >> 9) & 511, gb = (int)(a2 >> 18) & 511;
-            const int pa = (ga + 1) >> 1;
-            int off;
-            bool two;
-            if (r < pa) {
-                off = 2 * r;
-                two = off + 1 < ga;
-            } else {
-                const int rb = 2 * (r - pa);
-                off = ga + (int)(a2 & 511u) + rb;
-                two = rb + 1 < gb;
-            }
-            code = a1 + (uint32_t)off;
-            // sign bit of g_xy (>= 0): the pair's second element is present
-            gg = __uint_as_float(__float_as_uint(g0) | (two ? 0x80000000u : 0u));
-        };
-        int pos = 0;
-        while (L + (total - pos) >= 32) {
-            float rh, rl, gg;
-            uint32_t code;
-            fetch(max(pos + lane - L, 0), rh, rl, gg, code);
-            if (lane < L) {
-                const float4 sv = stash[lane];
-                rh = sv.x; rl = sv.y; gg = sv.z; code = __float_as_uint(sv.w);
-            }
-            pos += 32 - L;
-            L = 0;
-            run_pair(rh, rl, gg, code, true);
         }
-        const int rem = total - pos;
-        if (rem > 0) {
-            float rh, rl, gg;
-            uint32_t code;
-            fetch(min(pos + lane, total - 1), rh, rl, gg, code);
-            __syncwarp();
-            if (lane < rem) stash[L + lane] = make_float4(rh, rl, gg, __uint_as_float(code));
-            __syncwarp();
-            L += rem;
+        const int cnt = na + nb;
+        for (int i = 0; i < cnt; ++i) {
+            const int n = i < na ? lo_a + i : lo_b + (i - na);
+            proc(Rh, Rl, gxy, k1 + (uint32_t)n);
         }
     }
-    if (L > 0) {
-        const bool v = lane < L;
-        const float4 sv = v ? stash[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
-        run_pair(sv.x, sv.y, sv.z, __float_as_uint(sv.w), v);
-    }
-    __syncwarp();
 }
 
 // Evaluates one candidate: delay split, window test, gain, statistics.
@@ -892,6 +946,32 @@ k_ism_taps(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int max
 // length l <= sqrt(2 d t + t^2) per z-parity (t: the bucket's width in
 // metres, d: the window's largest distance).  Integer sums do not depend on
 // the order of the additions: the sparse path is bitwise reproducible.
+// Sets n4 16-byte words of shared memory to zero (all threads of the CTA).
+__device__ __forceinline__ void zero_words4(void *p, int n4) {
+    uint4 *q = reinterpret_cast<uint4 *>(p);
+    for (int i = threadIdx.x; i < n4; i += NT) q[i] = make_uint4(0u, 0u, 0u, 0u);
+}
+
+// Fixed point -> float in place over n4 16-byte words: v * inv_s, the words
+// read as int32 (SIGNED) or uint32.
+template <bool SIGNED>
+__device__ __forceinline__ void fix_to_float4(void *p, int n4, float inv_s) {
+    uint4 *q = reinterpret_cast<uint4 *>(p);
+    float4 *f = reinterpret_cast<float4 *>(p);
+    for (int i = threadIdx.x; i < n4; i += NT) {
+        const uint4 v = q[i];
+        float4 o;
+        if (SIGNED) {
+            o.x = (float)(int)v.x * inv_s; o.y = (float)(int)v.y * inv_s;
+            o.z = (float)(int)v.z * inv_s; o.w = (float)(int)v.w * inv_s;
+        } else {
+            o.x = (float)v.x * inv_s; o.y = (float)v.y * inv_s;
+            o.z = (float)v.z * inv_s; o.w = (float)v.w * inv_s;
+        }
+        f[i] = o;
+    }
+}
+
 constexpr double kFix0 = 16777216.0;           // 2^24
 constexpr uint32_t kFixLimit = 0x7e000000u;    // 2^31 - 2^25
 
@@ -903,7 +983,9 @@ k_ism_sparse(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int m
              int max_taps, int max_cheb, const float *__restrict__ tabs, float *__restrict__ h,
              long long *__restrict__ stats, unsigned int *__restrict__ counter,
              const double *__restrict__ g_sq, const float4 *__restrict__ g_hlg,
-             const float *__restrict__ g_dl, const JobConst *__restrict__ g_jc) {
+             const float *__restrict__ g_dl, const JobConst *__restrict__ g_jc,
+             const uint32_t *__restrict__ g_cols, const int2 *__restrict__ g_wr,
+             const long long *__restrict__ g_offs) {
     extern __shared__ __align__(16) unsigned char smem[];
     const Layout Lay = make_layout(true, W, max_order, max_taps, max_cheb);
     const int TE = Lay.TE, CL = Lay.CL;
@@ -911,20 +993,18 @@ k_ism_sparse(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int m
     T.sq = nullptr;  // per item: the RIR's FP64 table in global memory (exact path only)
     T.hlg = (float4 *)(smem + Lay.off_hlg);
     T.dl = (float *)(smem + Lay.off_dl);
-    int *s_lx = (int *)(smem + Lay.off_lx);
-    int *s_ly = (int *)(smem + Lay.off_ly);
-    uint32_t *s_cand = (uint32_t *)(smem + Lay.off_cand);
     float *s_c = (float *)(smem + Lay.off_c);
     float *s_delta = (float *)(smem + Lay.off_delta);
     float *s_part = (float *)(smem + Lay.off_part);
-    __shared__ int s_item, s_nl[2], s_ovf;
+    __shared__ int s_item, s_ovf;
     __shared__ unsigned long long s_stat[2];
 
     const int tid = threadIdx.x;
     uint32_t *s_cq = (uint32_t *)s_c;      // the same words before conversion
     uint32_t *s_dq = (uint32_t *)s_delta;
-    for (int i = tid; i < max_cheb * CL; i += NT) s_cq[i] = 0u;
-    for (int i = tid; i < CL; i += NT) s_dq[i] = 0u;
+    // CL is a multiple of 4 and both arrays start on 16-byte boundaries
+    zero_words4(s_cq, max_cheb * CL / 4);
+    zero_words4(s_dq, CL / 4);
     if (tid == 0) s_ovf = 0;
 
     const long long n_items = (long long)n_rirs * wmax;
@@ -976,9 +1056,9 @@ k_ism_sparse(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int m
         };
         const int Pc = J.n_cheb;
         const int n_taps = it.n_taps;
-        build_lists(T, TE, it, s_lx, s_ly, s_nl);
-        __syncthreads();
-        const int nLX = s_nl[0], nLY = s_nl[1];
+        // this window's ranks in the RIR's sorted column list
+        const int2 wr = g_wr[g_offs[2 * jr + 1] + wi];
+        const uint32_t *cols = g_cols + g_offs[2 * jr];
         // position of first-tap index kb in the sparse arrays; chosen so that
         // the FIR's 128-bit loads are aligned
         const int OFF = (4 - (n_taps - 1) % 4) % 4;
@@ -986,11 +1066,11 @@ k_ism_sparse(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int m
         const int jdelta = (KIND == ISM_FD_HANN_SINC) ? it.H : (it.P - 1) / 2;
         unsigned my_contrib = 0, my_taps = 0;
         float S = 0.f, S4 = 0.f;
-        auto proc = [&](float Rh, float Rl, float gxy, uint32_t code, bool valid) {
+        auto proc = [&](float Rh, float Rl, float gxy, uint32_t code) {
             int kb;
             float f, a;
-            if (!valid || !eval_expanded<KIND, STATS>(T, TE, it, Rh, Rl, gxy, code, kb, f, a,
-                                                      my_taps, my_contrib))
+            if (!eval_expanded<KIND, STATS>(T, TE, it, Rh, Rl, gxy, code, kb, f, a, my_taps,
+                                            my_contrib))
                 return;
             const int pos = kb + POS0;
             const float as = a * S4;  // a S, with a = prod(beta^hits) / (4 pi d)
@@ -1033,20 +1113,19 @@ k_ism_sparse(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int m
             invS = 1.f / S;
             my_contrib = 0;
             my_taps = 0;
-            warp_expand(T, TE, it, s_lx, s_ly, nLX, nLY,
-                        reinterpret_cast<float4 *>(s_cand) + (tid >> 5) * 32, proc);
+            sorted_sweep(T, TE, it, cols, wr.x, wr.y, proc);
             __syncthreads();
             const int ovf = s_ovf;
             if (!ovf || attempt >= 3) break;
             __syncthreads();
             if (tid == 0) s_ovf = 0;
-            for (int i = tid; i < Pc * CL; i += NT) s_cq[i] = 0u;
-            for (int i = tid; i < CL; i += NT) s_dq[i] = 0u;
+            zero_words4(s_cq, Pc * CL / 4);
+            zero_words4(s_dq, CL / 4);
             __syncthreads();
         }
-        // fixed point -> float, in place
-        for (int i = tid; i < Pc * CL; i += NT) s_c[i] = (float)(int)s_cq[i] * invS;
-        for (int i = tid; i < CL; i += NT) s_delta[i] = (float)s_dq[i] * invS;
+        // fixed point -> float, in place (the integer-delay sums are >= 0)
+        fix_to_float4<true>(s_c, Pc * CL / 4, invS);
+        fix_to_float4<false>(s_delta, CL / 4, invS);
         __syncthreads();
 
         // FIR: h[w0+i] = sum_p sum_j B[p][j] c_p[kb = w0+i-j] + delta.  Threads
@@ -1128,8 +1207,8 @@ k_ism_sparse(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int m
             if (n < it.Lh) hout[n] = v;
         }
         __syncthreads();
-        for (int i = tid; i < Pc * CL; i += NT) s_c[i] = 0.f;
-        for (int i = tid; i < CL; i += NT) s_delta[i] = 0.f;
+        zero_words4(s_c, Pc * CL / 4);
+        zero_words4(s_delta, CL / 4);
         flush_stats(stats, J, s_stat, my_contrib, my_taps);
         __syncthreads();
     }
@@ -1188,10 +1267,13 @@ int launch_sparse_t(const RirLaunch &L, cudaStream_t stream) {
     JobConst *g_jc = (JobConst *)(g_hlg + n_ent);
     float *g_dl = (float *)(g_jc + L.n_rirs);
     const int tgrid = (int)std::min<long long>(L.n_rirs, (long long)device_sm_count() * 8);
-    k_ism_tables<<<tgrid, 128, 0, stream>>>(L.jobs_dev, L.n_rirs, Lay.TE, g_sq, g_hlg, g_dl, g_jc);
+    k_ism_tables<KIND><<<tgrid, TNT, 0, stream>>>(L.jobs_dev, L.n_rirs, Lay.TE, L.window, g_sq,
+                                                  g_hlg, g_dl, g_jc, L.cols_dev, L.wr_dev,
+                                                  L.offs_dev);
     kern<<<grid, NT, Lay.total, stream>>>(L.jobs_dev, L.n_rirs, L.wmax, L.window, L.max_order,
                                           L.max_taps, L.max_cheb, L.tabs_dev, L.h_dev,
-                                          L.stats_dev, L.counter_dev, g_sq, g_hlg, g_dl, g_jc);
+                                          L.stats_dev, L.counter_dev, g_sq, g_hlg, g_dl, g_jc,
+                                          L.cols_dev, L.wr_dev, L.offs_dev);
     e = cudaGetLastError();
     scratch_free(tab, stream);
     if (e != cudaSuccess) return cuda_fail(e, "launch k_ism_sparse");
@@ -1228,6 +1310,9 @@ int launch_rir_sparse(const RirLaunch &L, cudaStream_t stream) {
     if (L.window % 8 != 0) return fail(ISM_ERR_INVALID_ARG, "window must be a multiple of 8");
     if (L.max_cheb < 1 || L.max_cheb > kMaxCheb)
         return fail(ISM_ERR_INVALID_ARG, "Chebyshev term count out of range");
+    if (!L.cols_dev || !L.wr_dev || !L.offs_dev)
+        return fail(ISM_ERR_INTERNAL, "sparse launch without column-list scratch");
+    if (L.max_order > 200) return fail(ISM_ERR_INVALID_ARG, "order above 200");
     const bool st = L.stats_dev != nullptr;  // statistics compiled out when not asked for
     const int pf = L.min_cheb == L.max_cheb ? L.max_cheb : 0;
     if (L.fd_kind == ISM_FD_LAGRANGE) {
