@@ -252,9 +252,10 @@ int ism_convolve_batch(const ism_conv_job *jobs, int64_t n_jobs, const float *h_
  *                 mic-major, at y_host + y_offsets[i] (NULL: packed).
  * h_host          nullable: the RIRs too, room i's n_mics x rir_len floats
  *                 at h_host + h_offsets[i] (NULL offsets: packed).
- * chunk_rooms     rooms per chunk, or 0: six or more chunks (about 160 MB of
- *                 signals each on average) of decreasing size, so that the
- *                 first upload and the last download are short.
+ * chunk_rooms     rooms per chunk, or 0: six or more chunks of about
+ *                 128 MiB of signals each, balanced by signal length.
+ *                 Consecutive chunks compute on two streams, so one chunk's
+ *                 RIR kernel overlaps the previous chunk's convolution.
  * Returns when every output is in host memory.  Errors: those of
  * ism_rir_batch and ism_convolve_batch, ISM_ERR_INVALID_ARG for NULL
  * buffers or src_lens < 1, ISM_ERR_CUDA, ISM_ERR_OUT_OF_MEMORY. */

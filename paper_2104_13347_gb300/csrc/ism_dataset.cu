@@ -6,10 +6,12 @@
 // RIRs).
 //
 // Pipeline over chunks k = 0, 1, ... with two device buffer sets (k mod 2)
-// and three streams:
-//   up:   [wait compute(k-2)] sources of chunk k -> src_d[k%2]
-//   comp: [wait up(k), down(k-2)] RIRs -> h_d, convolution + noise -> y_d
-//   down: [wait comp(k)] y_d (and h_d) -> host
+// and four streams:
+//   up:         [wait compute(k-2)] sources of chunk k -> src_d[k%2]
+//   comp[k%2]:  [wait up(k), down(k-2)] RIRs -> h_d, convolution + noise -> y_d
+//   down:       [wait comp(k)] y_d (and h_d) -> host
+// Consecutive chunks compute on different streams, so the RIR kernel of
+// chunk k+1 fills the SMs that the tail of chunk k's convolution leaves.
 // Every kernel is the batch entry points' own (ism_rir_batch_ex,
 // ism_convolve_batch); the RIR window is chosen once for the whole batch
 // (ism_rir_batch's automatic rule over all rooms) and room i keeps noise id
@@ -30,21 +32,32 @@ using namespace ism;
 namespace {
 
 struct Pipe {
-    cudaStream_t up = nullptr, comp = nullptr, down = nullptr;
-    cudaEvent_t ev_alloc = nullptr, up_done[2] = {}, comp_done[2] = {}, down_done[2] = {};
+    cudaStream_t up = nullptr, comp[2] = {}, down = nullptr;
+    cudaEvent_t ev_alloc = nullptr, ev_comp1 = nullptr, up_done[2] = {}, comp_done[2] = {},
+                down_done[2] = {};
     void *buf = nullptr;
     ~Pipe() {
-        // every stream is synchronised before the pipe goes out of scope
-        if (buf && comp) scratch_free(buf, comp);
-        if (comp) cudaStreamSynchronize(comp);
+        // every stream is synchronised before the pipe goes out of scope;
+        // the buffer is freed on comp[0] after comp[1]'s work
+        if (buf && comp[0]) {
+            if (comp[1] && ev_comp1) {
+                cudaEventRecord(ev_comp1, comp[1]);
+                cudaStreamWaitEvent(comp[0], ev_comp1, 0);
+            }
+            scratch_free(buf, comp[0]);
+        }
+        for (int s = 0; s < 2; ++s)
+            if (comp[s]) cudaStreamSynchronize(comp[s]);
         for (int s = 0; s < 2; ++s) {
             if (up_done[s]) cudaEventDestroy(up_done[s]);
             if (comp_done[s]) cudaEventDestroy(comp_done[s]);
             if (down_done[s]) cudaEventDestroy(down_done[s]);
         }
         if (ev_alloc) cudaEventDestroy(ev_alloc);
+        if (ev_comp1) cudaEventDestroy(ev_comp1);
         if (up) cudaStreamDestroy(up);
-        if (comp) cudaStreamDestroy(comp);
+        for (int s = 0; s < 2; ++s)
+            if (comp[s]) cudaStreamDestroy(comp[s]);
         if (down) cudaStreamDestroy(down);
     }
 };
@@ -89,25 +102,22 @@ extern "C" int ism_dataset_batch(const ism_room *rooms, int64_t n_rooms, const f
         hp += hlen[i];
         y_total += ylen[i];
     }
-    // chunks of consecutive rooms.  Automatic: K chunks (about 160 MB of
-    // signals each, at least six when there are six rooms) of decreasing
-    // size, K, K-1, ..., 1 parts of the signals, so that the upload of the
-    // first chunk and the download of the last one, which nothing overlaps,
-    // are small (a chunk's download is several times faster than its
-    // kernels, so the larger download before each smaller chunk still hides)
+    // chunks of consecutive rooms.  Automatic: K >= 6 chunks of about
+    // 128 MiB of signals each, balanced by signal length (ragged rooms).  With
+    // two compute streams the tails of consecutive chunks overlap; on the
+    // 1024-room step equal chunks beat chunks of decreasing size.
     std::vector<int64_t> cb;  // chunk boundaries
     if (chunk_rooms > 0) {
         for (int64_t r = 0; r < n_rooms; r += chunk_rooms) cb.push_back(r);
     } else {
-        const int64_t target = (160ll << 20) / 4;  // floats of signals per chunk
+        const int64_t target = (128ll << 20) / 4;  // floats of signals per chunk
         const int64_t K = std::min<int64_t>(
             n_rooms, std::max<int64_t>((y_total + target - 1) / target, 6));
-        const double parts = 0.5 * (double)K * (double)(K + 1);
         int64_t r = 0;
-        double acc = 0.0, goal = 0.0;
+        double acc = 0.0;
         for (int64_t c = 0; c < K && r < n_rooms; ++c) {
             cb.push_back(r);
-            goal += (double)(K - c) / parts * (double)y_total;
+            const double goal = (double)(c + 1) / (double)K * (double)y_total;
             do { acc += (double)ylen[r]; ++r; } while (r < n_rooms && acc < goal);
         }
     }
@@ -127,18 +137,21 @@ extern "C" int ism_dataset_batch(const ism_room *rooms, int64_t n_rooms, const f
     Pipe P;
     cudaError_t e = cudaSuccess;
     if ((e = cudaStreamCreateWithFlags(&P.up, cudaStreamNonBlocking)) != cudaSuccess ||
-        (e = cudaStreamCreateWithFlags(&P.comp, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&P.comp[0], cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&P.comp[1], cudaStreamNonBlocking)) != cudaSuccess ||
         (e = cudaStreamCreateWithFlags(&P.down, cudaStreamNonBlocking)) != cudaSuccess ||
-        (e = cudaEventCreateWithFlags(&P.ev_alloc, cudaEventDisableTiming)) != cudaSuccess)
+        (e = cudaEventCreateWithFlags(&P.ev_alloc, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&P.ev_comp1, cudaEventDisableTiming)) != cudaSuccess)
         return cuda_fail(e, "dataset streams");
     for (int s = 0; s < 2; ++s)
         if ((e = cudaEventCreateWithFlags(&P.up_done[s], cudaEventDisableTiming)) != cudaSuccess ||
             (e = cudaEventCreateWithFlags(&P.comp_done[s], cudaEventDisableTiming)) != cudaSuccess ||
             (e = cudaEventCreateWithFlags(&P.down_done[s], cudaEventDisableTiming)) != cudaSuccess)
             return cuda_fail(e, "dataset events");
-    if (int st = scratch_alloc(&P.buf, 2 * set_bytes, P.comp)) return st;
-    cudaEventRecord(P.ev_alloc, P.comp);
+    if (int st = scratch_alloc(&P.buf, 2 * set_bytes, P.comp[0])) return st;
+    cudaEventRecord(P.ev_alloc, P.comp[0]);
     cudaStreamWaitEvent(P.up, P.ev_alloc, 0);
+    cudaStreamWaitEvent(P.comp[1], P.ev_alloc, 0);
     cudaStreamWaitEvent(P.down, P.ev_alloc, 0);
     auto src_d = [&](int s) { return (float *)((char *)P.buf + s * set_bytes); };
     auto y_d = [&](int s) { return (float *)((char *)P.buf + s * set_bytes + al(max_s)); };
@@ -171,10 +184,11 @@ extern "C" int ism_dataset_batch(const ism_room *rooms, int64_t n_rooms, const f
         }
         if (st) break;
         cudaEventRecord(P.up_done[s], P.up);
-        // kernels of the chunk
-        cudaStreamWaitEvent(P.comp, P.up_done[s], 0);
-        if (c >= 2) cudaStreamWaitEvent(P.comp, P.down_done[s], 0);
-        st = ism_rir_batch_ex(rooms + r0, r1 - r0, h_d(s), nullptr, &ro, P.comp);
+        // kernels of the chunk, on the buffer set's own compute stream
+        cudaStream_t cs = P.comp[s];
+        cudaStreamWaitEvent(cs, P.up_done[s], 0);
+        if (c >= 2) cudaStreamWaitEvent(cs, P.down_done[s], 0);
+        st = ism_rir_batch_ex(rooms + r0, r1 - r0, h_d(s), nullptr, &ro, cs);
         if (st) break;
         jobs.assign((size_t)(r1 - r0), ism_conv_job{});
         {
@@ -195,9 +209,9 @@ extern "C" int ism_dataset_batch(const ism_room *rooms, int64_t n_rooms, const f
             }
         }
         st = ism_convolve_batch(jobs.data(), r1 - r0, h_d(s), src_d(s), y_d(s), seed, precision,
-                                P.comp);
+                                cs);
         if (st) break;
-        cudaEventRecord(P.comp_done[s], P.comp);
+        cudaEventRecord(P.comp_done[s], cs);
         // outputs of the chunk
         cudaStreamWaitEvent(P.down, P.comp_done[s], 0);
         {
@@ -223,12 +237,14 @@ extern "C" int ism_dataset_batch(const ism_room *rooms, int64_t n_rooms, const f
         if (st) break;
         cudaEventRecord(P.down_done[s], P.down);
     }
-    // drain every stream (also after an error), then free on comp
+    // drain every stream (also after an error); the pipe frees the buffer
     const cudaError_t e1 = cudaStreamSynchronize(P.up);
     const cudaError_t e2 = cudaStreamSynchronize(P.down);
-    const cudaError_t e3 = cudaStreamSynchronize(P.comp);
+    const cudaError_t e3 = cudaStreamSynchronize(P.comp[0]);
+    const cudaError_t e4 = cudaStreamSynchronize(P.comp[1]);
     if (!st && e1 != cudaSuccess) st = cuda_fail(e1, "dataset upload");
     if (!st && e2 != cudaSuccess) st = cuda_fail(e2, "dataset download");
     if (!st && e3 != cudaSuccess) st = cuda_fail(e3, "dataset kernels");
+    if (!st && e4 != cudaSuccess) st = cuda_fail(e4, "dataset kernels");
     return st;
 }
