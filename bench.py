@@ -569,6 +569,12 @@ def run_ours(args, ws, rank):
     # context: the direct per-tap formulation is bound by the reciprocal
     # (MUFU) pipe, 16 results per clock per SM, one per tap
     direct_bound = 16.0 * n_sm * sm_mhz * 1e6
+    # context: the sparse path's binding resource is the shared-memory pipe,
+    # two thirds of it the P u32 atomics per contributing image; 32 lanes at
+    # random addresses complete 9.1 atomics per clock per SM on this GPU
+    # (a loop of random-address u32 shared atomics, 3.5 wavefronts each)
+    atom_rate = P * contrib / (rir_med * 1e-3)
+    atom_peak = 9.1 * n_sm * sm_mhz * 1e6
 
     # K2 alone (no noise), timed back to back: split-BF16 needs at least the
     # three products hi.hi, hi.lo, lo.hi of 2 Ts Lh flops per mic; the kernel
@@ -613,7 +619,11 @@ def run_ours(args, ws, rank):
                                   f"{sm_mhz:.0f} MHz ({pk_kind} max clock)",
                      "binding": K1_BINDING,
                      "taps_per_s": taps / (rir_med * 1e-3),
-                     "direct_formulation_bound_taps_per_s": direct_bound},
+                     "direct_formulation_bound_taps_per_s": direct_bound,
+                     "shared_atomics": {"achieved_per_s": atom_rate, "peak_per_s": atom_peak,
+                                        "frac": atom_rate / atom_peak,
+                                        "peak_note": "random-address u32 shared atomics, "
+                                                     "9.1 per clock per SM, measured"}},
         "roofline_k2": None if k2_ms is None else {
             "bound": "tensor", "kernel": "k_conv_tc", "achieved": k2_alg / (k2_ms * 1e-3) / 1e12,
             "peak": bf16_peak / 1e12, "unit": "TFLOP/s",
