@@ -110,7 +110,7 @@ typedef enum ism_rir_variant { ISM_RIR_SPARSE = 0, ISM_RIR_DIRECT = 1 } ism_rir_
 typedef struct ism_rir_opts {
     int32_t window;      /* output window per work item, samples (multiple of
                             32 in [32, 8192]); 0 = automatic: 1024, halved
-                            down to 128 while the call has fewer than four
+                            down to 64 while the call has fewer than four
                             work items per SM.  The automatic window depends
                             on the whole call, so pass a fixed window when a
                             RIR must be bitwise equal across calls of

@@ -184,14 +184,15 @@ int validate_room(const ism_room &r, int64_t idx) {
 }
 
 // Output window per work item when the caller leaves it to the library:
-// 1024 samples, halved (down to 128) while the call has fewer than four work
-// items per SM.  A single 4096-sample RIR then runs as 32 items instead of 4
-// (latency-bound calls: 55 us instead of 85 us per call on GB300), while
-// batches with enough RIRs keep the 1024 that serves them best.
+// 1024 samples, halved (down to 64) while the call has fewer than four work
+// items per SM.  A single 4096-sample RIR then runs as 64 items instead of 4
+// (latency-bound calls: 38 us instead of 85 us per call on GB300), while
+// batches with enough RIRs keep the 1024 that serves them best.  Below 64 an
+// image's taps would straddle three windows and be summed in each.
 int auto_window(const ism_room *rooms, int64_t n_rooms) {
     const int64_t target = 4 * (int64_t)device_sm_count();
     int W = 1024;
-    while (W > 128) {
+    while (W > 64) {
         int64_t items = 0;
         for (int64_t r = 0; r < n_rooms && items < target; ++r)
             items += (int64_t)rooms[r].n_mics * ((rooms[r].rir_len + W - 1) / W);
@@ -462,33 +463,47 @@ int ism_rir_batch_ex(const ism_room *rooms, int64_t n_rooms, float *h_dev,
                 max_wins = std::max(max_wins, wo);
             }
         }
+        // one scratch block and one upload: [jobs | counter | filter tables |
+        // offsets] copied from the host, then the column lists, window
+        // ranges and per-RIR tables the kernels fill
+        size_t max_chunk = 0;
+        for (auto &c : chunks) max_chunk = std::max(max_chunk, c.second - c.first);
         auto al = [](size_t n) { return (n + 255) & ~(size_t)255; };
         const size_t jb = al(jv.size() * sizeof(RirJob));
         const size_t tb = al(sparse ? tabs.size() * sizeof(float) : 0);
         const size_t ob = al(offs.size() * sizeof(long long));
+        const size_t up_bytes = jb + 256 + tb + ob;
         const size_t cb = al((size_t)max_cols * sizeof(uint32_t));
         const size_t wb = al((size_t)max_wins * sizeof(int2));
+        const size_t gb = sparse ? al(rir_tables_bytes((long long)max_chunk, max_order[kind])) : 0;
+        std::vector<unsigned char> blob(up_bytes, 0);
+        memcpy(blob.data(), jv.data(), jv.size() * sizeof(RirJob));
+        if (sparse) {
+            memcpy(blob.data() + jb + 256, tabs.data(), tabs.size() * sizeof(float));
+            memcpy(blob.data() + jb + 256 + tb, offs.data(), offs.size() * sizeof(long long));
+        }
         void *scr = nullptr;
-        if (int st = scratch_alloc(&scr, jb + 256 + tb + ob + cb + wb, stream)) return st;
+        if (int st = scratch_alloc(&scr, up_bytes + cb + wb + gb, stream)) return st;
         char *sp = (char *)scr;
         RirJob *d_jobs = (RirJob *)sp;
         unsigned int *d_counter = (unsigned int *)(sp + jb);
         const float *d_tabs = (const float *)(sp + jb + 256);
         long long *d_offs = (long long *)(sp + jb + 256 + tb);
-        uint32_t *d_cols = (uint32_t *)(sp + jb + 256 + tb + ob);
-        int2 *d_wr = (int2 *)(sp + jb + 256 + tb + ob + cb);
+        uint32_t *d_cols = (uint32_t *)(sp + up_bytes);
+        int2 *d_wr = (int2 *)(sp + up_bytes + cb);
+        void *d_tables = sparse ? (void *)(sp + up_bytes + cb + wb) : nullptr;
         long long *d_stats = (long long *)o.stats_dev;
-        int st = upload_async(d_jobs, jv.data(), jv.size() * sizeof(RirJob), stream);
-        if (!st && sparse) st = upload_async((void *)d_tabs, tabs.data(), tabs.size() * sizeof(float), stream);
-        if (!st && sparse) st = upload_async(d_offs, offs.data(), offs.size() * sizeof(long long), stream);
+        int st = upload_async(scr, blob.data(), up_bytes, stream);  // counter uploaded as 0
         for (size_t ci = 0; !st && ci < chunks.size(); ++ci) {
             const size_t b = chunks[ci].first, n = chunks[ci].second - b;
             int wm = 0;
             for (size_t k = b; k < b + n; ++k) wm = std::max(wm, jv[k].n_windows);
-            cudaError_t e = cudaMemsetAsync(d_counter, 0, sizeof(unsigned int), stream);
-            if (e != cudaSuccess) {
-                st = cuda_fail(e, "cudaMemsetAsync(counter)");
-                break;
+            if (ci > 0) {
+                cudaError_t e = cudaMemsetAsync(d_counter, 0, sizeof(unsigned int), stream);
+                if (e != cudaSuccess) {
+                    st = cuda_fail(e, "cudaMemsetAsync(counter)");
+                    break;
+                }
             }
             RirLaunch L{d_jobs + b, (int)n, wm, W, max_order[kind], max_taps[kind], kind, h_dev,
                         d_stats, d_counter, nullptr, 0, d_tabs, max_cheb, min_cheb};
@@ -496,6 +511,7 @@ int ism_rir_batch_ex(const ism_room *rooms, int64_t n_rooms, float *h_dev,
                 L.cols_dev = d_cols;
                 L.wr_dev = d_wr;
                 L.offs_dev = d_offs + 2 * b;
+                L.tables_dev = d_tables;
             }
             st = sparse ? launch_rir_sparse(L, stream) : launch_rir(L, stream);
         }

@@ -39,6 +39,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "ism_internal.h"
@@ -473,6 +474,24 @@ k_conv_tc(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles,
     }
 }
 
+// Raises a kernel's dynamic shared memory limit to smem once per device
+// (the attribute call is not repeated for calls of the same or smaller size).
+template <class K>
+cudaError_t ensure_smem(K kern, int (&set)[64], std::mutex &mu, size_t smem) {
+    int d = 0;
+    cudaError_t e = cudaGetDevice(&d);
+    if (e != cudaSuccess) return e;
+    if (d < 0 || d >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(mu);
+    if ((size_t)set[d] >= smem) return cudaSuccess;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) set[d] = (int)smem;
+    return e;
+}
+
+std::mutex g_smem_mu;
+int g_smem_whole[64], g_smem_chunked[64];
+
 }  // namespace
 
 int launch_conv_bf16x3(const ConvLaunch &L, cudaStream_t stream) {
@@ -501,8 +520,7 @@ int launch_conv_bf16x3(const ConvLaunch &L, cudaStream_t stream) {
     cudaError_t e = cudaSuccess;
     if (!tiles[1].empty()) {
         const size_t smem = tc_layout(true, max_chunks).total;
-        e = cudaFuncSetAttribute(k_conv_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
+        e = ensure_smem(k_conv_tc<true>, g_smem_whole, g_smem_mu, smem);
         if (e == cudaSuccess)
             k_conv_tc<true><<<(unsigned)tiles[1].size(), NTHR, smem, stream>>>(
                 L.jobs_dev, (const Tile *)d_tiles, L.h_dev, L.src_dev, L.y_dev,
@@ -510,8 +528,7 @@ int launch_conv_bf16x3(const ConvLaunch &L, cudaStream_t stream) {
     }
     if (e == cudaSuccess && !tiles[0].empty()) {
         const size_t smem = tc_layout(false, 0).total;
-        e = cudaFuncSetAttribute(k_conv_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
+        e = ensure_smem(k_conv_tc<false>, g_smem_chunked, g_smem_mu, smem);
         if (e == cudaSuccess)
             k_conv_tc<false><<<(unsigned)tiles[0].size(), NTHR, smem, stream>>>(
                 L.jobs_dev, (const Tile *)d_tiles + tiles[1].size(), L.h_dev, L.src_dev, L.y_dev,

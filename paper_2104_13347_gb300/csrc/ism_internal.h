@@ -102,7 +102,13 @@ struct RirLaunch {
     uint32_t *cols_dev = nullptr;
     int2 *wr_dev = nullptr;
     const long long *offs_dev = nullptr;
+    // sparse kernel: per-RIR tables (rir_tables_bytes(n_rirs, max_order)
+    // bytes), or NULL to have the launch allocate them
+    void *tables_dev = nullptr;
 };
+// Bytes of the sparse kernel's per-RIR tables for n_rirs RIRs of order at
+// most max_order (16-byte multiple).
+size_t rir_tables_bytes(long long n_rirs, int max_order);
 // Entries of a sparse launch's column list for a RIR of order N.
 inline long long rir_col_entries(int order) {
     const long long te = 2 * (2 * (long long)order + 1);

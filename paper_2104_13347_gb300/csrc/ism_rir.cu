@@ -50,6 +50,8 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <mutex>
+#include <string>
 #include <type_traits>
 
 #include "ism_internal.h"
@@ -372,7 +374,7 @@ __device__ __forceinline__ void build_tables(const RirJob &J, const Tables &T, d
 // is whatever the atomics give: it changes only how the sweep's lanes are
 // loaded, never which images are summed (and the sums are exact integers).
 constexpr int KB = 2048;          // rho^2 bins of the column sort
-constexpr int TNT = 128;          // threads of k_ism_tables
+constexpr int TNT = 256;          // threads of k_ism_tables
 constexpr int kMaxTE = 2 * (2 * 200 + 1);
 
 // rho^2 of a column and its bin, with explicit roundings: the histogram and
@@ -1214,20 +1216,51 @@ k_ism_sparse(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int m
     }
 }
 
+// Per kernel and device: the dynamic shared memory limit set so far and the
+// occupancy measured for the last size asked, so that a call of the same
+// shape makes neither query again.
+struct KernelCache {
+    std::mutex mu;
+    int smem_set[64] = {};
+    size_t occ_smem[64] = {};
+    int occ[64] = {};
+};
+
+// Raises the kernel's dynamic shared memory limit to smem if needed and
+// returns its persistent grid (SMs x resident CTAs per SM).
+template <class K>
+int prepare_launch(K kern, KernelCache &c, size_t smem, const char *name, int *grid) {
+    int d = 0;
+    cudaError_t e = cudaGetDevice(&d);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (d < 0 || d >= 64) return fail(ISM_ERR_INTERNAL, "device ordinal out of range");
+    std::lock_guard<std::mutex> lk(c.mu);
+    if ((size_t)c.smem_set[d] < smem) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return cuda_fail(e, (std::string("cudaFuncSetAttribute(") + name + ")").c_str());
+        c.smem_set[d] = (int)smem;
+        c.occ_smem[d] = 0;
+    }
+    if (c.occ_smem[d] != smem || c.occ[d] <= 0) {
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem);
+        if (e != cudaSuccess) return cuda_fail(e, (std::string("occupancy(") + name + ")").c_str());
+        c.occ[d] = per_sm > 0 ? per_sm : 1;
+        c.occ_smem[d] = smem;
+    }
+    *grid = device_sm_count() * c.occ[d];
+    return ISM_OK;
+}
+
 template <int R, int KIND>
 int launch_direct_t(const RirLaunch &L, cudaStream_t stream) {
     const Layout Lay = make_layout(false, L.window, L.max_order, L.max_taps, 0);
     auto kern = k_ism_taps<R, KIND>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)Lay.total);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_ism_taps)");
-    int grid = L.grid;
-    if (grid <= 0) {
-        int per_sm = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, Lay.total);
-        if (e != cudaSuccess) return cuda_fail(e, "occupancy(k_ism_taps)");
-        grid = device_sm_count() * (per_sm > 0 ? per_sm : 1);
-    }
+    static KernelCache cache;
+    int grid = 0;
+    if (int st = prepare_launch(kern, cache, Lay.total, "k_ism_taps", &grid)) return st;
+    if (L.grid > 0) grid = L.grid;
+    cudaError_t e = cudaSuccess;
     const long long items = (long long)L.n_rirs * L.wmax;
     if ((long long)grid > items) grid = (int)items;
     if (grid < 1) return ISM_OK;
@@ -1242,26 +1275,21 @@ template <int KIND, bool STATS, int PFIX>
 int launch_sparse_t(const RirLaunch &L, cudaStream_t stream) {
     const Layout Lay = make_layout(true, L.window, L.max_order, L.max_taps, L.max_cheb);
     auto kern = k_ism_sparse<KIND, STATS, PFIX>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)Lay.total);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_ism_sparse)");
-    int grid = L.grid;
-    if (grid <= 0) {
-        int per_sm = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, Lay.total);
-        if (e != cudaSuccess) return cuda_fail(e, "occupancy(k_ism_sparse)");
-        grid = device_sm_count() * (per_sm > 0 ? per_sm : 1);
-    }
+    static KernelCache cache;
+    int grid = 0;
+    if (int st = prepare_launch(kern, cache, Lay.total, "k_ism_sparse", &grid)) return st;
+    if (L.grid > 0) grid = L.grid;
     const long long items = (long long)L.n_rirs * L.wmax;
     if ((long long)grid > items) grid = (int)items;
     if (grid < 1) return ISM_OK;
-    // per-RIR tables: FP64 squares, (hi, lo, damping) and offsets
+    // per-RIR tables: FP64 squares, (hi, lo, damping) and offsets, in the
+    // caller's scratch when it gave some
     const size_t n_ent = (size_t)L.n_rirs * 3 * Lay.TE;  // even: TE = 2 (2N + 1)
-    void *tab = nullptr;
-    if (int st = scratch_alloc(&tab, n_ent * (sizeof(double) + sizeof(float4) + sizeof(float)) +
-                                         (size_t)L.n_rirs * sizeof(JobConst),
-                               stream))
-        return st;
+    void *tab = L.tables_dev;
+    if (!tab) {
+        if (int st = scratch_alloc(&tab, rir_tables_bytes(L.n_rirs, L.max_order), stream))
+            return st;
+    }
     double *g_sq = (double *)tab;
     float4 *g_hlg = (float4 *)(g_sq + n_ent);
     JobConst *g_jc = (JobConst *)(g_hlg + n_ent);
@@ -1274,8 +1302,8 @@ int launch_sparse_t(const RirLaunch &L, cudaStream_t stream) {
                                           L.max_taps, L.max_cheb, L.tabs_dev, L.h_dev,
                                           L.stats_dev, L.counter_dev, g_sq, g_hlg, g_dl, g_jc,
                                           L.cols_dev, L.wr_dev, L.offs_dev);
-    e = cudaGetLastError();
-    scratch_free(tab, stream);
+    const cudaError_t e = cudaGetLastError();
+    if (!L.tables_dev) scratch_free(tab, stream);
     if (e != cudaSuccess) return cuda_fail(e, "launch k_ism_sparse");
     return ISM_OK;
 }
@@ -1288,6 +1316,12 @@ size_t rir_smem_bytes(int window, int max_order, int max_taps) {
 
 size_t rir_sparse_smem_bytes(int window, int max_order, int max_taps, int max_cheb) {
     return make_layout(true, window, max_order, max_taps, max_cheb).total;
+}
+
+size_t rir_tables_bytes(long long n_rirs, int max_order) {
+    const size_t n_ent = (size_t)n_rirs * 3 * (size_t)(2 * (2 * max_order + 1));
+    return n_ent * (sizeof(double) + sizeof(float4) + sizeof(float)) +
+           (size_t)n_rirs * sizeof(JobConst);
 }
 
 int launch_rir(const RirLaunch &L, cudaStream_t stream) {
