@@ -161,27 +161,24 @@ __device__ __forceinline__ void ff_add(float ah, float al, float bh, float bl, f
 }
 
 // Delay split of one image (Sec. II.A: the delay of every image must keep
-// its sub-sample precision) from d^2 = Dh + Dl in float-float.  Returns the
+// its sub-sample precision) from tau^2 = Th + Tl in float-float (the tables
+// hold the axis offsets in samples, q = fs / c folded in).  Returns the
 // integer part k (rint, ties to even, for Hann; floor for Lagrange) and the
-// fraction in FP32, plus d.  sqx, sqy, sqz: the FP64 squared axis offsets,
-// read only on the exact path.
+// fraction in FP32, plus tau.  sqx, sqy, sqz: the FP64 squared axis offsets
+// in metres, read only on the exact path.
 template <int KIND>
-__device__ __forceinline__ void split_d2(float Dh, float Dl, const double *sqx, const double *sqy,
-                                         const double *sqz, float qh, float ql, double q,
-                                         int &k_out, float &f_out, float &d_out) {
+__device__ __forceinline__ void split_tau2(float Th, float Tl, const double *sqx,
+                                           const double *sqy, const double *sqz, double q,
+                                           int &k_out, float &f_out, float &tau_out) {
     // sqrt: FP32 estimate plus one Newton correction in float-float.
-    const float r = rsqrtf(Dh);
-    const float s0 = __fmul_rn(Dh, r);
-    const float res = __fadd_rn(__fmaf_rn(-s0, s0, Dh), Dl);
-    float dh = s0;
-    float dl = __fmul_rn(res, __fmul_rn(0.5f, r));
-    float tt = __fadd_rn(dh, dl);
-    dl = __fsub_rn(dl, __fsub_rn(tt, dh));
-    dh = tt;
-    // tau = d * q in float-float.
-    const float th = __fmul_rn(dh, qh);
-    const float terr = __fmaf_rn(dh, qh, -th);
-    const float tl = __fadd_rn(terr, __fmaf_rn(dh, ql, __fmul_rn(dl, qh)));
+    const float r = rsqrtf(Th);
+    const float s0 = __fmul_rn(Th, r);
+    const float res = __fadd_rn(__fmaf_rn(-s0, s0, Th), Tl);
+    float th = s0;
+    float tl = __fmul_rn(res, __fmul_rn(0.5f, r));
+    const float tt = __fadd_rn(th, tl);
+    tl = __fsub_rn(tl, __fsub_rn(tt, th));
+    th = tt;
     float k, f;
     bool near;
     if (KIND == ISM_FD_HANN_SINC) {
@@ -208,22 +205,22 @@ __device__ __forceinline__ void split_d2(float Dh, float Dl, const double *sqx, 
     }
     k_out = (int)k;
     f_out = f;
-    d_out = dh;
+    tau_out = th;
 }
 
 // Delay split of image (ix, iy, iz) from the tables; also returns the wall
 // damping product g.
 template <int KIND>
 __device__ __forceinline__ void delay_split(const Tables &T, int TE, int ix, int iy, int iz,
-                                            float qh, float ql, double q, int &k_out,
-                                            float &f_out, float &d_out, float &g_out) {
+                                            double q, int &k_out, float &f_out, float &tau_out,
+                                            float &g_out) {
     const float4 X = T.hlg[ix], Y = T.hlg[TE + iy], Z = T.hlg[2 * TE + iz];
     g_out = X.z * Y.z * Z.z;
-    float s1, e1, Dh, Dl;
+    float s1, e1, Th, Tl;
     ff_add(X.x, X.y, Y.x, Y.y, s1, e1);
-    ff_add(s1, e1, Z.x, Z.y, Dh, Dl);
-    split_d2<KIND>(Dh, Dl, &T.sq[ix], &T.sq[TE + iy], &T.sq[2 * TE + iz], qh, ql, q, k_out, f_out,
-                   d_out);
+    ff_add(s1, e1, Z.x, Z.y, Th, Tl);
+    split_tau2<KIND>(Th, Tl, &T.sq[ix], &T.sq[TE + iy], &T.sq[2 * TE + iz], q, k_out, f_out,
+                     tau_out);
 }
 
 // Per-item constants (identical in every thread of the CTA).
@@ -294,10 +291,12 @@ __device__ __forceinline__ void table_entry(const RirJob &J, int N, int a, int e
     const double img = __dadd_rn(p ? -s : s, __dmul_rn((double)(2 * qq), Ld));
     const double dlt = __dsub_rn(img, r);
     sq = __dmul_rn(dlt, dlt);
-    const float sh = __double2float_rn(sq);
+    // float-float square of the offset in samples: (q dlt)^2, q = fs / c
+    const double t2 = sq * (J.q * J.q);
+    const float sh = __double2float_rn(t2);
     dl = __double2float_rn(dlt);
     const float b0 = J.beta[2 * a], b1 = J.beta[2 * a + 1];
-    hlg = make_float4(sh, __double2float_rn(sq - (double)sh),
+    hlg = make_float4(sh, __double2float_rn(t2 - (double)sh),
                       powf(b0, (float)abs(qq - p)) * powf(b1, (float)abs(qq)), 0.f);
 }
 
@@ -645,8 +644,8 @@ __device__ __forceinline__ void column_sweep(const Tables &T, int TE, const Item
 // per lane; each lane solves its column and walks the column's candidates
 // itself.  Neighbouring ranks have nearly the same rho and hence nearly the
 // same candidate count, so the lanes of a batch finish close together.
-// proc(rho_h, rho_l, g_xy, code) is called once per candidate; code = iz |
-// ix << 12 | iy << 22 (iz: absolute index of the z table entry).  No
+// proc(rho_h, rho_l, g_xy, iz, ix, iy) is called once per candidate (iz:
+// absolute index of the z table entry; ix, iy: the column's entries).  No
 // block-wide barrier is involved.
 template <class Proc>
 __device__ __forceinline__ void sorted_sweep(const Tables &T, int TE, const Item &it,
@@ -657,12 +656,12 @@ __device__ __forceinline__ void sorted_sweep(const Tables &T, int TE, const Item
     const int N = it.N;
     for (int cb = warp * 32; cb < n_cols; cb += NT) {
         const int c = cb + lane;
-        int na = 0, nb = 0, lo_a = 0, lo_b = 0;
+        int na = 0, nb = 0, lo_a = 0, lo_b = 0, ix = 0, iy = 0, iz0 = 0;
         float Rh = 0.f, Rl = 0.f, gxy = 0.f;
-        uint32_t k1 = 0u;
         if (c < n_cols) {
             const uint32_t e = __ldg(cols + c_lo + (c >> 1));
-            const int ix = (int)(e & 0xffffu), iy = (int)(e >> 16);
+            ix = (int)(e & 0xffffu);
+            iy = (int)(e >> 16);
             // (entries are < TEj by construction; the guard keeps a bad
             // entry from indexing past the tables)
             const Col col = (ix < it.TEj && iy < it.TEj) ? column_solve_xy(T, TE, it, ix, iy, c & 1)
@@ -675,15 +674,13 @@ __device__ __forceinline__ void sorted_sweep(const Tables &T, int TE, const Item
                 const float4 X = T.hlg[ix], Y = T.hlg[TE + iy];
                 ff_add(X.x, X.y, Y.x, Y.y, Rh, Rl);
                 gxy = X.z * Y.z;
-                // iz < 3 TE <= 2406, ix, iy < 1024
-                k1 = (uint32_t)(2 * TE + col.wz * (2 * N + 1) + N) | ((uint32_t)ix << 12) |
-                     ((uint32_t)iy << 22);
+                iz0 = 2 * TE + col.wz * (2 * N + 1) + N;
             }
         }
         const int cnt = na + nb;
         for (int i = 0; i < cnt; ++i) {
             const int n = i < na ? lo_a + i : lo_b + (i - na);
-            proc(Rh, Rl, gxy, k1 + (uint32_t)n);
+            proc(Rh, Rl, gxy, iz0 + n, ix, iy);
         }
     }
 }
@@ -697,11 +694,12 @@ __device__ __forceinline__ bool eval_candidate(const Tables &T, int TE, const It
                                                unsigned long long &my_contrib) {
     const int ix = cd & 1023, iy = (cd >> 10) & 1023, iz = cd >> 20;
     int k;
-    float d, g;
-    delay_split<KIND>(T, TE, ix, iy, iz, it.qh, it.ql, it.q, k, f, d, g);
+    float tau, g;
+    delay_split<KIND>(T, TE, ix, iy, iz, it.q, k, f, tau, g);
     kb = (KIND == ISM_FD_HANN_SINC) ? k - it.H : k - (it.P - 1) / 2;
     if (kb < it.kb_lo32 || kb > it.kb_hi32) return false;
-    a = g * __frcp_rn(12.566370614359172f * d);
+    // g / (4 pi d) = g q / (4 pi tau)
+    a = g * (it.qh * __frcp_rn(12.566370614359172f * tau));
     // statistics: taps in [w0, w0+W) n [0, Lh); an image counts as
     // contributing in the window of its first in-range tap.  All indices
     // here fit in 32 bits (Lh <= 2^30).
@@ -715,26 +713,25 @@ __device__ __forceinline__ bool eval_candidate(const Tables &T, int TE, const It
 }
 
 // Evaluates one column-expanded candidate: delay split from the column's
-// rho^2 and the z table, window test, gain, statistics.  Returns false if
-// the image's taps miss the window.
+// (q rho)^2 (Rh + Rl) and the z table entry iz (absolute index), window
+// test, gain, statistics.  ix, iy: the column's x and y entries (exact path
+// only).  Returns false if the image's taps miss the window.
+// a is returned as g / tau: the caller folds q / (4 pi) into its scale.
 template <int KIND, bool STATS>
-// a is returned without the 1/(4 pi) of the spreading factor.
 __device__ __forceinline__ bool eval_expanded(const Tables &T, int TE, const Item &it, float Rh,
-                                              float Rl, float gxy, uint32_t code, int &kb,
+                                              float Rl, float gxy, int iz, int ix, int iy, int &kb,
                                               float &f, float &a, unsigned &my_taps,
                                               unsigned &my_contrib) {
-    const int iz = code & 4095u, ix = (code >> 12) & 1023u, iy = code >> 22;
     const float4 Z = T.hlg[iz];
-    float Dh, Dl;
-    ff_add(Rh, Rl, Z.x, Z.y, Dh, Dl);
+    float Th, Tl;
+    ff_add(Rh, Rl, Z.x, Z.y, Th, Tl);
     int k;
-    float d;
-    split_d2<KIND>(Dh, Dl, &T.sq[ix], &T.sq[TE + iy], &T.sq[iz], it.qh, it.ql, it.q, k, f, d);
+    float tau;
+    split_tau2<KIND>(Th, Tl, &T.sq[ix], &T.sq[TE + iy], &T.sq[iz], it.q, k, f, tau);
     kb = (KIND == ISM_FD_HANN_SINC) ? k - it.H : k - (it.P - 1) / 2;
     if (kb < it.kb_lo32 || kb > it.kb_hi32) return false;
-    // a / (4 pi)-free form: the caller folds 1/(4 pi) into its scale;
     // approximate reciprocal (about 1 ulp, below the FP32 accumulation)
-    a = (gxy * Z.z) * rcp_approx(d);
+    a = (gxy * Z.z) * rcp_approx(tau);
     if (STATS) {
         const int lo = max(kb, max(it.w0, 0));
         const int hi = min(kb + it.n_taps, it.wend);
@@ -1068,14 +1065,15 @@ k_ism_sparse(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int m
         const int jdelta = (KIND == ISM_FD_HANN_SINC) ? it.H : (it.P - 1) / 2;
         unsigned my_contrib = 0, my_taps = 0;
         float S = 0.f, S4 = 0.f;
-        auto proc = [&](float Rh, float Rl, float gxy, uint32_t code) {
+        auto proc = [&](float Rh, float Rl, float gxy, int iz, int ix, int iy) {
             int kb;
             float f, a;
-            if (!eval_expanded<KIND, STATS>(T, TE, it, Rh, Rl, gxy, code, kb, f, a, my_taps,
+            if (!eval_expanded<KIND, STATS>(T, TE, it, Rh, Rl, gxy, iz, ix, iy, kb, f, a, my_taps,
                                             my_contrib))
                 return;
             const int pos = kb + POS0;
             const float as = a * S4;  // a S, with a = prod(beta^hits) / (4 pi d)
+                                      // (a = g / tau here, S4 = S q / (4 pi))
             const uint32_t q0 = __float2uint_rn(as);
             uint32_t *c0 = (f == 0.f) ? s_dq : s_cq;  // integer delay: exact Kronecker delta
             const uint32_t old = atomicAdd(&c0[pos], q0);
@@ -1111,7 +1109,7 @@ k_ism_sparse(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int m
         float invS = 0.f;
         for (int attempt = 0;; ++attempt) {
             S = scale_of(attempt);
-            S4 = S * 0.07957747154594767f;  // S / (4 pi)
+            S4 = S * (0.07957747154594767f * it.qh);  // S q / (4 pi): a = g / tau
             invS = 1.f / S;
             my_contrib = 0;
             my_taps = 0;
