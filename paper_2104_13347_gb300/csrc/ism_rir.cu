@@ -179,19 +179,18 @@ __device__ __forceinline__ void split_tau2(float Th, float Tl, const double *sqx
     const float tt = __fadd_rn(th, tl);
     tl = __fsub_rn(tl, __fsub_rn(tt, th));
     th = tt;
+    // The low part can carry f just past the rounding boundary (|tl| is at
+    // most half an ulp of th); every such f lies within 1e-6 of it and takes
+    // the exact path below, so no correction is made here.
     float k, f;
     bool near;
     if (KIND == ISM_FD_HANN_SINC) {
         k = rintf(th);
         f = __fadd_rn(__fsub_rn(th, k), tl);
-        if (f > 0.5f) { k += 1.f; f -= 1.f; }
-        else if (f < -0.5f) { k -= 1.f; f += 1.f; }
         near = fabsf(f) > 0.5f - 1e-6f || fabsf(f) < 1e-6f;  // ties and integers
     } else {
         k = floorf(th);
         f = __fadd_rn(__fsub_rn(th, k), tl);
-        if (f >= 1.f) { k += 1.f; f -= 1.f; }
-        else if (f < 0.f) { k -= 1.f; f += 1.f; }
         near = f < 1e-6f || f > 1.f - 1e-6f;
     }
     if (near) {
@@ -656,7 +655,7 @@ __device__ __forceinline__ void sorted_sweep(const Tables &T, int TE, const Item
     const int N = it.N;
     for (int cb = warp * 32; cb < n_cols; cb += NT) {
         const int c = cb + lane;
-        int na = 0, nb = 0, lo_a = 0, lo_b = 0, ix = 0, iy = 0, iz0 = 0;
+        int na = 0, nb = 0, iz_a = 0, iz_b = 0, ix = 0, iy = 0;
         float Rh = 0.f, Rl = 0.f, gxy = 0.f;
         if (c < n_cols) {
             const uint32_t e = __ldg(cols + c_lo + (c >> 1));
@@ -668,20 +667,18 @@ __device__ __forceinline__ void sorted_sweep(const Tables &T, int TE, const Item
                                                          : Col{1, 0, 1, 0, 0, 0, 0};
             na = max(col.hi_a - col.lo_a + 1, 0);
             nb = max(col.hi_b - col.lo_b + 1, 0);
-            lo_a = col.lo_a;
-            lo_b = col.lo_b;
             if (na + nb > 0) {
                 const float4 X = T.hlg[ix], Y = T.hlg[TE + iy];
                 ff_add(X.x, X.y, Y.x, Y.y, Rh, Rl);
                 gxy = X.z * Y.z;
-                iz0 = 2 * TE + col.wz * (2 * N + 1) + N;
+                // candidate i is z entry iz_a + i (i < na) or iz_b + i
+                const int iz0 = 2 * TE + col.wz * (2 * N + 1) + N;
+                iz_a = iz0 + col.lo_a;
+                iz_b = iz0 + col.lo_b - na;
             }
         }
         const int cnt = na + nb;
-        for (int i = 0; i < cnt; ++i) {
-            const int n = i < na ? lo_a + i : lo_b + (i - na);
-            proc(Rh, Rl, gxy, iz0 + n, ix, iy);
-        }
+        for (int i = 0; i < cnt; ++i) proc(Rh, Rl, gxy, (i < na ? iz_a : iz_b) + i, ix, iy);
     }
 }
 
@@ -729,7 +726,8 @@ __device__ __forceinline__ bool eval_expanded(const Tables &T, int TE, const Ite
     float tau;
     split_tau2<KIND>(Th, Tl, &T.sq[ix], &T.sq[TE + iy], &T.sq[iz], it.q, k, f, tau);
     kb = (KIND == ISM_FD_HANN_SINC) ? k - it.H : k - (it.P - 1) / 2;
-    if (kb < it.kb_lo32 || kb > it.kb_hi32) return false;
+    // kb in [kb_lo, kb_hi], one unsigned comparison
+    if ((unsigned)(kb - it.kb_lo32) > (unsigned)(it.kb_hi32 - it.kb_lo32)) return false;
     // approximate reciprocal (about 1 ulp, below the FP32 accumulation)
     a = (gxy * Z.z) * rcp_approx(tau);
     if (STATS) {
