@@ -171,20 +171,41 @@ k_noise(const ConvJob *__restrict__ jobs, float *__restrict__ y, const double *_
     uint64_t m = (uint64_t)(i / npr);
     int64_t k = i - (int64_t)m * npr;
     uint64_t key = sm64_out(seed, J.noise_id * 65536ull + m);
-    for (; i < e; i += 256) {
-        const uint64_t bits = sm64_out(key, (uint64_t)k);
-        const float u1 = ((float)(bits >> 40) + 0.5f) * (1.0f / 16777216.0f);
-        const float u2 = (float)((bits >> 16) & 0xFFFFFFull) * (1.0f / 16777216.0f);
-        const float r = sigma * sqrtf(-2.f * logf(u1));
-        float sn, cs;
-        sincospif(2.f * u2, &sn, &cs);
-        float *ym = yb + (int64_t)m * ylen + 2 * k;
-        ym[0] += r * cs;
-        if (2 * k + 1 < ylen) ym[1] += r * sn;
-        k += 256;
-        if (k >= npr) {
-            while (k >= npr) { k -= npr; ++m; }
-            key = sm64_out(seed, J.noise_id * 65536ull + m);
+    // U pairs per round: their loads are all issued before any is used, so
+    // each thread keeps U read-modify-writes in flight
+    constexpr int U = 4;
+    while (i < e) {
+        float *ptr[U];
+        float v0[U], v1[U];
+        uint64_t kk[U], keys[U];
+        bool ok[U], ok1[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            ok[u] = i < e;
+            ok1[u] = ok[u] && 2 * k + 1 < ylen;
+            kk[u] = (uint64_t)k;
+            keys[u] = key;
+            ptr[u] = yb + (int64_t)m * ylen + 2 * k;
+            v0[u] = ok[u] ? ptr[u][0] : 0.f;
+            v1[u] = ok1[u] ? ptr[u][1] : 0.f;
+            i += 256;
+            k += 256;
+            if (k >= npr) {
+                while (k >= npr) { k -= npr; ++m; }
+                key = sm64_out(seed, J.noise_id * 65536ull + m);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (!ok[u]) continue;
+            const uint64_t bits = sm64_out(keys[u], kk[u]);
+            const float u1 = ((float)(bits >> 40) + 0.5f) * (1.0f / 16777216.0f);
+            const float u2 = (float)((bits >> 16) & 0xFFFFFFull) * (1.0f / 16777216.0f);
+            const float r = sigma * sqrtf(-2.f * logf(u1));
+            float sn, cs;
+            sincospif(2.f * u2, &sn, &cs);
+            ptr[u][0] = v0[u] + r * cs;
+            if (ok1[u]) ptr[u][1] = v1[u] + r * sn;
         }
     }
 }
