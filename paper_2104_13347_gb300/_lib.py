@@ -320,6 +320,16 @@ def dataset_batch(rooms, src_host, src_lens, y_host, snr_db=None, seed=0, noise_
     return y_host
 
 
+class PreparedRequest:
+    """A marshalled serving request (see Server.request)."""
+
+    __slots__ = ("rq", "keep")
+
+    def __init__(self, rq, keep):
+        self.rq = rq
+        self.keep = keep
+
+
 class Server:
     """ism_serve_*: continuous-batching server (argument marshalling only)."""
 
@@ -334,9 +344,11 @@ class Server:
         self._h = c_vp()
         check(self._lib.ism_serve_create(ctypes.byref(cfg), ctypes.byref(self._h)))
 
-    def submit(self, room, src, snr_db=math.nan, noise_id=0):
-        """Submits one room dict and its float32 source; returns the ticket
-        (raises IsmError with status ISM_ERR_BUSY when not admitted)."""
+    @staticmethod
+    def request(room, src, snr_db=math.nan, noise_id=0):
+        """Marshals one room dict and its float32 source into a request that
+        submit() takes as is (argument marshalling only; the server copies
+        the source when the request is submitted)."""
         arr, keep = make_rooms([room])
         src = np.ascontiguousarray(src, np.float32)
         rq = Request()
@@ -345,8 +357,16 @@ class Server:
         rq.src_len = len(src)
         rq.snr_db = float(snr_db)
         rq.noise_id = int(noise_id)
+        return PreparedRequest(rq, (arr, keep, src))
+
+    def submit(self, room, src=None, snr_db=math.nan, noise_id=0):
+        """Submits one room dict and its float32 source, or a request made by
+        request(); returns the ticket (raises IsmError with status
+        ISM_ERR_BUSY when not admitted)."""
+        if not isinstance(room, PreparedRequest):
+            room = self.request(room, src, snr_db, noise_id)
         t = c_u64()
-        check(self._lib.ism_serve_submit(self._h, ctypes.byref(rq), ctypes.byref(t)))
+        check(self._lib.ism_serve_submit(self._h, ctypes.byref(room.rq), ctypes.byref(t)))
         return t.value
 
     def poll(self, ticket):

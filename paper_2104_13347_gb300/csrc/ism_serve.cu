@@ -26,6 +26,7 @@
 #include <chrono>
 #include <condition_variable>
 #include <deque>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <string>
@@ -47,13 +48,77 @@ using Clock = std::chrono::steady_clock;
 
 enum State { QUEUED, RUNNING, DONE, FAILED };
 
+// Page-locked host blocks by power-of-two size class, kept for reuse:
+// cudaHostAlloc and cudaFreeHost are slow and cudaFreeHost can wait for the
+// device, so a request's source copy and a batch's statistics readback take
+// a cached block.  At most kMaxCached bytes stay cached; blocks beyond that
+// are freed.  A block that cudaHostAlloc could not provide comes from malloc
+// (pageable: its copies do not overlap) and is freed on return.
+class PinnedPool {
+  public:
+    static constexpr size_t kMaxCached = size_t(1) << 30;
+    struct Block {
+        void *ptr = nullptr;
+        size_t cls = 0;      // size class, bytes
+        bool pinned = false;
+    };
+    Block get(size_t bytes) {
+        size_t cls = 4096;
+        while (cls < bytes) cls <<= 1;
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            auto &v = free_[cls];
+            if (!v.empty()) {
+                Block b{v.back(), cls, true};
+                v.pop_back();
+                cached_ -= cls;
+                return b;
+            }
+        }
+        Block b{nullptr, cls, true};
+        if (cudaHostAlloc(&b.ptr, cls, 0) != cudaSuccess) {
+            cudaGetLastError();
+            b.ptr = malloc(cls);
+            b.pinned = false;
+        }
+        return b;
+    }
+    void put(const Block &b) {
+        if (!b.ptr) return;
+        if (!b.pinned) {
+            free(b.ptr);
+            return;
+        }
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            if (cached_ + b.cls <= kMaxCached) {
+                free_[b.cls].push_back(b.ptr);
+                cached_ += b.cls;
+                return;
+            }
+        }
+        if (cudaFreeHost(b.ptr) != cudaSuccess) cudaGetLastError();
+    }
+    ~PinnedPool() {
+        for (auto &kv : free_)
+            for (void *p : kv.second)
+                if (cudaFreeHost(p) != cudaSuccess) cudaGetLastError();
+    }
+
+  private:
+    std::mutex mu_;
+    std::map<size_t, std::vector<void *>> free_;
+    size_t cached_ = 0;
+};
+
 struct Batch;
 
 struct Req {
     uint64_t ticket;
     ism_room room;
     std::vector<double> mics;
-    float *src_pinned = nullptr;
+    float *src_pinned = nullptr;  // the source copy (src_block.ptr)
+    PinnedPool::Block src_block;
     int64_t src_len = 0;
     float snr_db = NAN;
     uint64_t noise_id = 0;
@@ -73,7 +138,8 @@ struct Batch {
     char *block = nullptr;
     int64_t bytes = 0;
     cudaEvent_t done = nullptr;
-    long long *stats_host = nullptr;
+    long long *stats_host = nullptr;  // stats_block.ptr
+    PinnedPool::Block stats_block;
     int64_t n_rirs = 0;
     int64_t mic_samples = 0;
     std::vector<std::shared_ptr<Req>> reqs;
@@ -103,6 +169,8 @@ struct ism_server {
     std::thread th;
 
     int64_t bytes_in_use = 0;
+    PinnedPool pool;                     // sources and statistics readbacks
+    std::vector<cudaEvent_t> free_events;  // completion events for reuse (mu)
 
     void loop();
     bool setup_device();
@@ -192,8 +260,24 @@ void ism_server::launch(std::vector<std::shared_ptr<Req>> &take) {
     }
     bp->block = (char *)blk;
     float *base = (float *)blk;
-    if (status == ISM_OK) cerr(cudaHostAlloc(&bp->stats_host, 16 * n_rirs + 16, 0), "cudaHostAlloc");
-    if (status == ISM_OK) cerr(cudaEventCreateWithFlags(&bp->done, cudaEventDisableTiming), "event");
+    if (status == ISM_OK) {
+        bp->stats_block = pool.get(16 * n_rirs + 16);
+        bp->stats_host = (long long *)bp->stats_block.ptr;
+        if (!bp->stats_host) {
+            status = ISM_ERR_OUT_OF_MEMORY;
+            err = "statistics readback buffer";
+        }
+    }
+    if (status == ISM_OK) {
+        {
+            std::lock_guard<std::mutex> lk2(mu);
+            if (!free_events.empty()) {
+                bp->done = free_events.back();
+                free_events.pop_back();
+            }
+        }
+        if (!bp->done) cerr(cudaEventCreateWithFlags(&bp->done, cudaEventDisableTiming), "event");
+    }
     if (status == ISM_OK) {
         for (auto &r : take)
             cerr(cudaMemcpyAsync(base + r->src_off, r->src_pinned, 4 * r->src_len,
@@ -295,8 +379,8 @@ void ism_server::free_released() {
         Batch *b = batches[i].get();
         if (b->complete && b->refs == 0) {
             if (b->block) scratch_free(b->block, streams[b->slot]);
-            if (b->stats_host) cudaFreeHost(b->stats_host);
-            if (b->done) cudaEventDestroy(b->done);
+            pool.put(b->stats_block);
+            if (b->done) free_events.push_back(b->done);
             bytes_in_use -= b->bytes;
             st.bytes_in_use = bytes_in_use;
             batches.erase(batches.begin() + i);
@@ -407,12 +491,10 @@ int ism_serve_submit(ism_server *s, const ism_request *rq, uint64_t *ticket) {
         }
         if (s->stop) return fail(ISM_ERR_BUSY, "server is stopping");
     }
-    // pinned copy of the source (host memory only; no device needed)
-    if (cudaHostAlloc(&r->src_pinned, 4 * rq->src_len, 0) != cudaSuccess) {
-        cudaGetLastError();
-        r->src_pinned = (float *)malloc(4 * rq->src_len);
-        if (!r->src_pinned) return fail(ISM_ERR_OUT_OF_MEMORY, "host source copy");
-    }
+    // page-locked copy of the source (host memory only; no device needed)
+    r->src_block = s->pool.get((size_t)4 * rq->src_len);
+    r->src_pinned = (float *)r->src_block.ptr;
+    if (!r->src_pinned) return fail(ISM_ERR_OUT_OF_MEMORY, "host source copy");
     memcpy(r->src_pinned, rq->src_host, 4 * rq->src_len);
     {
         std::lock_guard<std::mutex> lk(s->mu);
@@ -509,13 +591,9 @@ int ism_serve_release(ism_server *s, uint64_t ticket) {
         if (r->batch) r->batch->refs--;
     }
     s->cv_work.notify_one();
-    if (r->src_pinned) {
-        if (cudaFreeHost(r->src_pinned) != cudaSuccess) {
-            cudaGetLastError();
-            free(r->src_pinned);
-        }
-        r->src_pinned = nullptr;
-    }
+    s->pool.put(r->src_block);
+    r->src_block = PinnedPool::Block{};
+    r->src_pinned = nullptr;
     return ISM_OK;
 }
 
@@ -543,19 +621,16 @@ int ism_serve_destroy(ism_server *s) {
     s->th.join();
     for (auto &b : s->batches) {
         if (b->block) scratch_free(b->block, s->streams[b->slot]);
-        if (b->stats_host) cudaFreeHost(b->stats_host);
+        s->pool.put(b->stats_block);
         if (b->done) cudaEventDestroy(b->done);
     }
     for (auto st : s->streams) {
         cudaStreamSynchronize(st);
         cudaStreamDestroy(st);
     }
-    for (auto &kv : s->reqs)
-        if (kv.second->src_pinned && cudaFreeHost(kv.second->src_pinned) != cudaSuccess) {
-            cudaGetLastError();
-            free(kv.second->src_pinned);
-        }
-    delete s;
+    for (cudaEvent_t e : s->free_events) cudaEventDestroy(e);
+    for (auto &kv : s->reqs) s->pool.put(kv.second->src_block);
+    delete s;  // frees the cached page-locked blocks
     return ISM_OK;
 }
 
