@@ -230,6 +230,7 @@ def run_single_room(ism, wl, dev, stream, reps=200):
     stats = torch.zeros(2, dtype=torch.int64, device=dev)
     ism.rir_batch(rooms, h=h, stats=stats)
     taps = int(stats[1].item())
+    contrib = int(stats[0].item())
     e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     out = {"workload": "5x4x3 m, beta 0.8, order 10 (74088 images), 81 taps, RIR 4096 @ 16 kHz, "
                        "1 source, 1 mic", "taps": taps}
@@ -247,6 +248,14 @@ def run_single_room(ism, wl, dev, stream, reps=200):
         torch.cuda.synchronize()
         out[name] = {"device_us": 1e3 * e[0].elapsed_time(e[1]) / reps,
                      "wall_us": 1e6 * (time.perf_counter() - t0) / reps}
+    # FP32-pipe fraction of the sparse call, on the same algorithmic count as
+    # the batch roofline (FIR per output, delay split and terms per image)
+    P = ism.rir_filter_terms(0, 81)
+    flops = 2.0 * P * 81 * prep.h_len + (40.0 + 2 * P - 1) * contrib
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = 2.0 * 128 * n_sm * peaks()[0].get("sm_max_mhz", 2070.0) * 1e6
+    out["sparse"]["fp32_pipe_frac"] = flops / (out["sparse"]["device_us"] * 1e-6) / peak
+    out["contributing_images"] = contrib
     return out
 
 
@@ -395,6 +404,7 @@ def run_served(ism, wl, rate, seconds, precision, seed=1006):
             "p99_ms": float(np.percentile(lat_ms, 99)), "completed_req_s": n / wall,
             "taps_per_s": st["taps"] / wall, "mic_samples_per_s": st["mic_samples"] / wall,
             "batches": st["batches"], "busy_retries": rejected[0],
+            "hbm_peak_bytes": st.get("bytes_peak"), "hbm_limit_bytes": 32 << 30,
             "workload": "Poisson arrivals; rooms U[3,20]^3 m, 4-32 mics, fs 16/48 kHz, "
                         "RT60 U[0.1,0.6] s (Sabine), sources 0.5-4 s, SNR U[0,30] dB"}
 
