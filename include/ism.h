@@ -361,12 +361,18 @@ typedef struct ism_serve_stats {
     int64_t mic_samples;     /* convolution outputs written */
 } ism_serve_stats;
 
-/* Creates a server on config->device.  Errors: INVALID_ARG, CUDA. */
+/* Creates a server on config->device.  Besides at most max_hbm_bytes of
+ * device memory, the server keeps page-locked host blocks (request source
+ * copies, statistics readbacks) in a cache for reuse, at most 1 GiB of
+ * them, returned at ism_serve_destroy.  Errors: INVALID_ARG, CUDA. */
 int ism_serve_create(const ism_serve_config *config, ism_server **out);
 
-/* Validates and enqueues a request; returns its ticket.  ISM_ERR_BUSY if
- * the queue is full or the request alone needs more than max_hbm_bytes;
- * ISM_ERR_INVALID_ARG for an invalid room or source. */
+/* Validates and enqueues a request; returns its ticket.  The source is
+ * copied into a page-locked host block before the call returns, so the
+ * caller's buffer may be reused at once.  ISM_ERR_BUSY if the queue is full
+ * or the request alone needs more than max_hbm_bytes; ISM_ERR_INVALID_ARG
+ * for an invalid room or source; ISM_ERR_OUT_OF_MEMORY if no host block
+ * can be had. */
 int ism_serve_submit(ism_server *server, const ism_request *request, uint64_t *ticket);
 
 /* ISM_OK and the result if ready, ISM_PENDING if not yet,
