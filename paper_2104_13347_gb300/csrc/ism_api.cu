@@ -421,10 +421,10 @@ int ism_rir_batch_ex(const ism_room *rooms, int64_t n_rooms, float *h_dev,
                 min_cheb = std::min(min_cheb, ct.n_cheb);
             }
             if (sparse && rir_sparse_smem_bytes(W, max_order[kind], max_taps[kind], max_cheb) >
-                              227 * 1024)
+                              kMaxDynSmem)
                 sparse = false;
         }
-        if (!sparse && rir_smem_bytes(W, max_order[kind], max_taps[kind]) > 227 * 1024)
+        if (!sparse && rir_smem_bytes(W, max_order[kind], max_taps[kind]) > kMaxDynSmem)
             return fail(ISM_ERR_INVALID_ARG, "window/order/taps need too much shared memory");
         // launches: one per room on the unbatched path; otherwise the whole
         // kind, cut where the sparse kernel's sorted column lists would pass

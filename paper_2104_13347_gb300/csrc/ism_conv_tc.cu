@@ -5,35 +5,36 @@
 // convolution of the RIRs with source signals), for every mic m of a room:
 //   y_m[t] = sum_k h_m[k] s[t - k],  t in [0, Ts + Lh - 1).
 //
-// Block-Toeplitz GEMM.  A tile of 2048 outputs t = T0 + 8n + p (n < 256
-// columns, p < 8 phases) of 8 mics is one GEMM D (128 x 256) = A (128 x K) B
-// (K x 256) over the RIR taps:
-//   B[k][n] = s[c + k + 8n],  c = T0 - Lh + 1      (source, forward)
-//   A[(q,m,p)][k] = part_q(h_m[Lh - 1 + p - k])    (RIR, reversed, phase p)
-// so that D[(q,m,p)][n] = sum_k A B accumulates, over q in {hi, lo},
-// y_m[T0 + 8n + p] (each row's j = Lh-1+p-k runs over the whole RIR).
-// B is a Toeplitz matrix whose rows shift by 8 elements = 16 bytes, so it is
-// read straight from a linear copy of the source in shared memory through a
-// no-swizzle K-major descriptor with leading-dimension offset 16 B and
-// stride offset 128 B (core matrices overlap); A is materialised per chunk
-// of 64 taps (8 phases x 8 mics x hi/lo = 128 rows, 16 KB).  Per chunk the
-// MMA issuer runs 4 K-steps x {B_hi, B_lo} = 8 MMAs of 128 x 256 x 16 into
-// one TMEM accumulator, so the result holds all four products hi/lo x hi/lo.
-// Chunks whose source window is all zero padding are skipped.
+// Two kernels share the block-Toeplitz formulation: outputs of a tile are
+// split into phases so that the source operand B is a Toeplitz matrix whose
+// rows shift by 8 elements = 16 bytes, read straight from a linear copy of
+// the source in shared memory through a no-swizzle K-major descriptor with
+// leading-dimension offset 16 B and stride offset 128 B (core matrices
+// overlap), and the RIR operand A is materialised per chunk of taps.
 //
-// The tile's whole source window is converted to bf16 hi/lo once at the
-// start when it fits in shared memory (RIRs up to ~9k samples); longer RIRs
-// convert each chunk's 2112-sample window into its pipeline stage instead.
-// The raw RIR values of each chunk are staged with cp.async (double
-// buffered, zero-filled outside the RIR) and each producer thread builds one
-// 16-byte row (one row group, one phase) per k-group, so a warp's 128-bit
-// stores cover 512 contiguous bytes.
+// k_conv_tcp (RIRs up to 10609 samples, the dataset's case): a persistent
+// kernel, one CTA per SM.  A tile is 8 mics x 4096 outputs, 16 phases; the
+// taps are split by parity so that both parity windows of the source are
+// again 16-byte-shifted Toeplitz matrices.  Its 128 GEMM rows are (mic,
+// phase) of one part, and the MMAs hi.hi, lo.hi and hi.lo accumulate into
+// one FP32 accumulator: the split-BF16 product without its lo.lo term
+// (2^-32 relative).  Two 256-column TMEM accumulators and two source-window
+// buffers let one tile's epilogue and the next tile's window conversion run
+// under the current tile's MMAs.
 //
-// Warp roles (160 threads): warps 0-3 produce the pipeline stages and run
-// the epilogue; warp 4 allocates TMEM and one of its lanes issues the MMAs.  Stages hand over through mbarriers
-// (full: 128 producer arrivals; empty: tcgen05.commit).  Every wait is
-// bounded: on timeout the kernel records an error, stops issuing, waits
-// (bounded) for its own MMAs, frees TMEM and returns.
+// k_conv_tc (longer RIRs): one CTA per tile of 8 mics x 2048 outputs, 8
+// phases; A holds (hi / lo, mic, phase) rows, so the MMAs with B_hi and
+// B_lo give all four products, and each chunk converts its own 2112-sample
+// source window into its pipeline stage.
+//
+// In both, the raw RIR values of each chunk are staged with cp.async
+// (zero-filled outside the RIR), converted once per value into bf16 hi / lo
+// pairs, and each producer thread builds 16-byte rows of A with byte
+// permutes.  Chunks whose source window is all zero padding are skipped.
+// Stages hand over through mbarriers (full: producer arrivals; empty:
+// tcgen05.commit).  Every wait is bounded: on timeout the kernel records an
+// error, stops issuing, waits (bounded) for its own MMAs, frees TMEM and
+// returns.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -153,39 +154,23 @@ __device__ __forceinline__ void producers_sync() {
     asm volatile("bar.sync 1, 128;" ::: "memory");
 }
 
-// Shared-memory layout.  whole_b: NS A stages (16 KB each), RIR staging
-// (two raw chunks), the converted RIR (one chunk of bf16 hi / lo: the
-// barrier that opens each chunk orders every read of it before the next
-// conversion), then the tile's source window (bf16 hi, bf16 lo; bl elements
-// each).  Otherwise NS stages of (A, window hi, window lo), then the RIR
-// staging and conversion.
+// Shared-memory layout: NS stages of (A, window hi, window lo), then the
+// RIR staging (two raw chunks) and the converted RIR (one chunk of bf16 hi /
+// lo: the barrier that opens each chunk orders every read of it before the
+// next conversion).
 struct TcLayout {
-    size_t a_stride, stg, cv, bhi, blo, total;
-    int bl;
+    size_t a_stride, stg, cv, total;
 };
 
-__host__ __device__ inline TcLayout tc_layout(bool whole_b, int n_chunks) {
+__host__ __device__ inline TcLayout tc_layout() {
     TcLayout L;
-    if (whole_b) {
-        L.bl = (n_chunks * KC + 8 * (NN - 1) + 8 + 7) & ~7;
-        L.a_stride = A_BYTES;
-        L.stg = (size_t)NS * A_BYTES;
-        L.cv = L.stg + STG_FLOATS * 2 * 4;
-        L.bhi = L.cv + CV_BYTES;
-        L.blo = L.bhi + (size_t)L.bl * 2;
-        L.total = L.blo + (size_t)L.bl * 2;
-    } else {
-        L.bl = BW;
-        L.a_stride = STAGE;
-        L.stg = (size_t)NS * STAGE;
-        L.cv = L.stg + STG_FLOATS * 2 * 4;
-        L.bhi = L.blo = 0;  // per stage, after A
-        L.total = L.cv + CV_BYTES;
-    }
+    L.a_stride = STAGE;
+    L.stg = (size_t)NS * STAGE;
+    L.cv = L.stg + STG_FLOATS * 2 * 4;
+    L.total = L.cv + CV_BYTES;
     return L;
 }
 
-template <bool WHOLE_B>
 __global__ void __launch_bounds__(NTHR, 1)
 k_conv_tc(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles,
           const float *__restrict__ h, const float *__restrict__ src, float *__restrict__ y,
@@ -205,7 +190,7 @@ k_conv_tc(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles,
     const float *sb = src + J.src_offset;
     const int64_t c0 = T0 - Lh + 1;                    // source index of B[0][0] at k = 0
     const int n_chunks = (int)((Lh + 7 + KC - 1) / KC);
-    const TcLayout Lay = tc_layout(WHOLE_B, n_chunks);
+    const TcLayout Lay = tc_layout();
     // live chunks (source window not all zero padding) form one range
     int64_t lo_c = -c0 - (KC - 1 + 8 * (NN - 1));
     lo_c = lo_c <= 0 ? 0 : (lo_c + KC - 1) / KC;
@@ -224,20 +209,6 @@ k_conv_tc(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles,
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_done)), "r"(1));
         asm volatile("fence.mbarrier_init.release.cluster;");
         s_abort = 0;
-    }
-    if (WHOLE_B && n_live > 0) {
-        // the tile's source window s[c0 + e], e in [0, bl), as bf16 hi / lo
-        uint32_t *bh = reinterpret_cast<uint32_t *>(smem + Lay.bhi);
-        uint32_t *bl = reinterpret_cast<uint32_t *>(smem + Lay.blo);
-        for (int e2 = tid; e2 < Lay.bl / 2; e2 += NTHR) {
-            const int64_t i0 = c0 + 2 * e2;
-            const float x0 = (i0 >= 0 && i0 < Ts) ? __ldg(sb + i0) : 0.f;
-            const float x1 = (i0 + 1 >= 0 && i0 + 1 < Ts) ? __ldg(sb + i0 + 1) : 0.f;
-            const float h0 = bf16_round(x0), h1 = bf16_round(x1);
-            bh[e2] = pack_bf16(h0, h1);
-            bl[e2] = pack_bf16(x0 - h0, x1 - h1);
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     if (warp == 4) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -320,7 +291,7 @@ k_conv_tc(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles,
                     *reinterpret_cast<uint4 *>(st + kg * 2048 + g * 128 + p * 16) = row;
                 }
             }
-            if (!WHOLE_B) {
+            {
                 // the chunk's source window, s[c0 + 64 ch + e], split hi / lo
                 unsigned char *st = smem + (size_t)s * Lay.a_stride;
                 uint32_t *bh = reinterpret_cast<uint32_t *>(st + A_BYTES);
@@ -345,21 +316,14 @@ k_conv_tc(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles,
         // ------------------------------------------------------------------
         uint32_t acc = 0;
         for (int i = 0; i < n_live; ++i) {
-            const int ch = ch_lo + i, s = i % NS, u = i / NS;
+            const int s = i % NS, u = i / NS;
             if (!mbar_wait(smem_u32(&bar_full[s]), u & 1)) {
                 s_abort = 1;
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;");
             const uint32_t a0 = smem_u32(smem + (size_t)s * Lay.a_stride);
-            uint32_t bh0, bl0;
-            if (WHOLE_B) {
-                bh0 = smem_u32(smem + Lay.bhi) + 2u * (uint32_t)(ch * KC);
-                bl0 = smem_u32(smem + Lay.blo) + 2u * (uint32_t)(ch * KC);
-            } else {
-                bh0 = a0 + A_BYTES;
-                bl0 = bh0 + BW * 2;
-            }
+            const uint32_t bh0 = a0 + A_BYTES, bl0 = bh0 + BW * 2;
 #pragma unroll
             for (int kk = 0; kk < KC / 16; ++kk) {
                 const uint64_t ad = make_desc(a0 + kk * 2 * 2048, 2048, 128);
@@ -474,6 +438,522 @@ k_conv_tc(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles,
     }
 }
 
+// ===========================================================================
+// k_conv_tcp: persistent convolution with three products and no lo rows,
+// for RIRs whose two tile windows fit (rir_len up to 10609 samples)
+// ===========================================================================
+// A tile is 8 mics x 4096 outputs t = T0 + 16 n + p (n < 256, p < 16).
+// With k = 2 kappa + b split by parity b, B_b[kappa][n] = s[c0 + b + 2 kappa
+// + 16 n] is the Toeplitz matrix of the source's parity-b samples, whose
+// rows again shift by 8 elements (16 bytes), and A_b[(m, p)][kappa] =
+// h_m[Lh - 1 + p - b - 2 kappa].  GEMM row R = 16 m + 8 (p % 2) + p / 2 holds
+// (mic m, phase p): the eight lanes of a producer's 128-bit store phase then
+// fill one 128-byte row group without bank conflicts.  Per parity the MMAs
+// hi.hi, lo.hi and hi.lo accumulate into one 128 x 256 FP32 accumulator, so
+// no hi / lo rows are merged in the epilogue.
+//
+// One CTA per SM walks its tiles (blockIdx.x, + gridDim.x, ...).  Warps 0-7
+// build the operands of 64-tap chunks into three stages (warps 0-3 the hi
+// parts, 4-7 the lo parts) and, a slice per chunk, convert the next tile's
+// source window into the other of two window buffers (the slice's source
+// values are loaded one chunk before they are stored); warp 8 allocates 512
+// TMEM columns (two accumulators) and one lane issues the MMAs; warps 9-12
+// drain one accumulator (write y, sum y^2) while the next tile's MMAs fill
+// the other.  Barriers: full / empty per stage; win[b] (the window buffer's
+// tile has had its last MMA); accf[b] (a tile's MMAs are done); acce[b] (its
+// accumulator is drained).  Every wait is bounded.
+constexpr int P_PH = 16;                 // output phases per row set
+constexpr int P_TT = P_PH * NN;          // outputs per tile (4096)
+static_assert(P_TT == 2 * kConvTT, "a tile covers two noise-partial slots");
+constexpr int P_KC = 64;                 // k values per chunk: 32 per parity
+constexpr int P_NS = 3;                  // operand stages
+constexpr int P_AMAT = 128 * 32 * 2;     // one operand: 128 rows x 32 kappa, bf16 (8 KB)
+constexpr int P_ABYTES = 4 * P_AMAT;     // (parity, hi / lo) operands of one chunk
+constexpr int P_STG = 8 * 80;            // raw RIR per chunk: 8 mics x 80 values
+constexpr int P_PB = 4;                  // raw RIR staging buffers (ring)
+constexpr int P_PD = 3;                  // chunks staged ahead
+constexpr int P_CVW = 2 * 8 * 40;        // the chunk as bf16 pairs: [hi/lo][mic][40 words]
+constexpr int P_NPROD = 256;             // producer threads (warps 0-7)
+constexpr int P_NT = 416;                // 13 warps: producers, MMA (warp 8), epilogue (9-12)
+
+// OR of pred over the P_NPROD producer threads (named barrier 1); also a barrier.
+__device__ __forceinline__ bool p_producers_any(bool pred) {
+    uint32_t r;
+    asm volatile(
+        "{\n.reg .pred p, q;\nsetp.ne.u32 p, %1, 0;\nbar.red.or.pred q, 1, 256, p;\n"
+        "selp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(r)
+        : "r"((uint32_t)pred)
+        : "memory");
+    return r != 0;
+}
+
+struct PLayout {
+    size_t stg, cv, win, win_bytes, total;
+    int bl;
+};
+
+// Layout for RIRs of at most max_lh samples: stages, raw staging (P_PB
+// chunks), two converted chunks, two tile windows of four [parity][hi / lo]
+// arrays of bl elements.
+__host__ __device__ inline PLayout p_layout(int64_t max_lh) {
+    PLayout L;
+    const int n_ch = (int)((max_lh + 15 + P_KC - 1) / P_KC);
+    L.bl = (n_ch * 32 + 8 * (NN - 1) + 8 + 7) & ~7;
+    L.stg = (size_t)P_NS * P_ABYTES;
+    L.cv = L.stg + (size_t)P_STG * P_PB * 4;
+    L.win = L.cv + (size_t)2 * P_CVW * 4;
+    L.win_bytes = (size_t)4 * L.bl * 2;
+    L.total = L.win + 2 * L.win_bytes;
+    return L;
+}
+
+// Source samples s[i0 .. i0 + 3], zero outside [0, Ts).
+__device__ __forceinline__ void load_source4(float (&x)[4], const float *sb, int64_t i0,
+                                             int64_t Ts) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int64_t idx = i0 + k;
+        x[k] = (idx >= 0 && idx < Ts) ? __ldg(sb + idx) : 0.f;
+    }
+}
+
+// Four source samples x = s[i0 .. i0 + 3] as the words of the two parity
+// windows at one word position: w[(2 b + q) * stride] = (part_q(x[b]),
+// part_q(x[b + 2])).
+__device__ __forceinline__ void store_split4(uint32_t *w, int stride, const float (&x)[4]) {
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+        const float h0 = bf16_round(x[b]), h1 = bf16_round(x[b + 2]);
+        w[(2 * b) * stride] = pack_bf16(h0, h1);
+        w[(2 * b + 1) * stride] = pack_bf16(x[b] - h0, x[b + 2] - h1);
+    }
+}
+
+__device__ __forceinline__ void store_decimated(uint32_t *w, int stride, const float *sb,
+                                                int64_t i0, int64_t Ts) {
+    float x[4];
+    load_source4(x, sb, i0, Ts);
+    store_split4(w, stride, x);
+}
+
+// Per-tile constants shared by the three roles.
+struct PTile {
+    Tile tl;
+    int64_t Lh, Ts, T0, c0;
+    int ch_lo, n_live, nm;
+};
+
+__device__ __forceinline__ PTile p_tile(const ConvJob *jobs, const Tile *tiles, int idx) {
+    PTile t;
+    t.tl = tiles[idx];
+    const ConvJob &J = jobs[t.tl.job];
+    t.Lh = J.rir_len;
+    t.Ts = J.src_len;
+    t.T0 = t.tl.t0;
+    t.c0 = t.T0 - t.Lh + 1;
+    t.nm = min(MG, J.n_mics - t.tl.mic0);
+    const int n_chunks = (int)((t.Lh + 15 + P_KC - 1) / P_KC);
+    // chunk ch reads s[c0 + 64 ch .. c0 + 64 ch + 63 + 16 (NN - 1)]
+    int64_t lo_c = -t.c0 - (P_KC - 1 + P_PH * (NN - 1));
+    lo_c = lo_c <= 0 ? 0 : (lo_c + P_KC - 1) / P_KC;
+    int64_t hi_c = t.Ts - 1 - t.c0;
+    hi_c = hi_c < 0 ? -1 : hi_c / P_KC;
+    t.ch_lo = (int)lo_c;
+    const int ch_hi = (int)min(hi_c, (int64_t)n_chunks - 1);
+    t.n_live = ch_hi >= t.ch_lo ? ch_hi - t.ch_lo + 1 : 0;
+    return t;
+}
+
+// Operand rows of thread (m, p) for one chunk, p of parity PAR.  Element kl
+// (kappa = 32 ch + kl) of operand (b, q) is part_q(stg[m][e_b - 2 kl]), e_b =
+// 63 + p - b; word w of k-group kg takes kl = 8 kg + 2w, 8 kg + 2w + 1, the
+// same half (high if e_b is odd) of cv words I_b - kl and I_b - kl - 1, I_b =
+// e_b >> 1.  For even p, I_0 = I_1; for odd p, I_0 = I_1 + 1.
+template <int PAR>
+__device__ __forceinline__ void p_rows(const uint32_t *cvb, unsigned char *st, int m, int p,
+                                       int q, uint32_t rowoff) {
+    const int I1 = (62 + p) >> 1;  // I_1 (odd p: (61 + p) / 2 = (62 + p) >> 1 too)
+    {
+        const uint32_t *cv = cvb + q * (P_CVW / 2) + m * 40 + (I1 - 31);
+        uint32_t W[33];
+#pragma unroll
+        for (int k = 0; k < 33; ++k) W[k] = (PAR == 1 || k < 32) ? cv[k] : 0u;
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            // window offset of operand b in W, and its half
+            const int off = (PAR == 1 && b == 0) ? 1 : 0;
+            const uint32_t sel = ((PAR == 0) == (b == 0)) ? 0x7632u : 0x5410u;
+#pragma unroll
+            for (int kg = 0; kg < 4; ++kg) {
+                uint4 row;
+                row.x = __byte_perm(W[off + 31 - 8 * kg], W[off + 30 - 8 * kg], sel);
+                row.y = __byte_perm(W[off + 29 - 8 * kg], W[off + 28 - 8 * kg], sel);
+                row.z = __byte_perm(W[off + 27 - 8 * kg], W[off + 26 - 8 * kg], sel);
+                row.w = __byte_perm(W[off + 25 - 8 * kg], W[off + 24 - 8 * kg], sel);
+                *reinterpret_cast<uint4 *>(st + (2 * b + q) * P_AMAT + kg * 2048 + rowoff) = row;
+            }
+        }
+    }
+}
+
+// D (TMEM) (+)= A B, instruction descriptor idesc (kIdesc with its N field
+// replaced for narrower MMAs).
+__device__ __forceinline__ void mma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t acc,
+                                        uint32_t idesc) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar));
+}
+
+__global__ void __launch_bounds__(P_NT, 1)
+k_conv_tcp(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles, int n_tiles,
+           int max_lh, const float *__restrict__ h, const float *__restrict__ src,
+           float *__restrict__ y, double *__restrict__ part) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar_full[P_NS], bar_empty[P_NS], bar_win[2], bar_accf[2],
+        bar_acce[2], bar_done;
+    __shared__ double s_red[2][4];
+    __shared__ uint32_t s_tmem;
+    __shared__ volatile int s_abort;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const PLayout Lay = p_layout(max_lh);
+    const int bl = Lay.bl;
+    const int n_my = (int)blockIdx.x < n_tiles ? (n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1
+                                               : 0;
+
+    if (tid == 0) {
+        for (int s = 0; s < P_NS; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_full[s])),
+                         "r"(P_NPROD));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_empty[s])),
+                         "r"(1));
+        }
+        for (int b = 0; b < 2; ++b) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_win[b])),
+                         "r"(1));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_accf[b])),
+                         "r"(1));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_acce[b])),
+                         "r"(128));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_done)), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+        s_abort = 0;
+    }
+    if (warp == 8) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&s_tmem)),
+                     "r"(512));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = s_tmem;
+
+    if (warp < 8) {
+        // ------------------------------------------------------------------
+        // producers: warps 0-3 build the hi operands, warps 4-7 the lo ones;
+        // in each group warps 0, 1 take the even phases, warps 2, 3 the odd
+        // ------------------------------------------------------------------
+        const int q = warp >> 2;
+        const int par = (warp >> 1) & 1;
+        const int i64 = (warp & 1) * 32 + lane;
+        // operand row R = 16 m + 8 par + j holds phase p = 2 j + par of mic m
+        // (the eight lanes of a store phase then fill one 128-byte row group)
+        const int m = i64 >> 3, p = 2 * (i64 & 7) + par;
+        const int R = 16 * m + 8 * par + (i64 & 7);
+        const uint32_t rowoff = (uint32_t)((R >> 3) * 128 + (R & 7) * 16);
+        float *stg = reinterpret_cast<float *>(smem + Lay.stg);
+        const uint32_t stg_u32 = smem_u32(stg);
+        uint32_t *cvb0 = reinterpret_cast<uint32_t *>(smem + Lay.cv);
+        // this thread's raw staging pairs w = tid + P_NPROD r (elements 2 w,
+        // 2 w + 1: mic st_mm, offsets st_ee, st_ee + 1).  A thread converts
+        // exactly the pairs it staged, so its own cp.async wait covers them.
+        constexpr int SR = (P_STG / 2 + P_NPROD - 1) / P_NPROD;
+        int st_mm[SR], st_ee[SR];
+#pragma unroll
+        for (int r = 0; r < SR; ++r) {
+            const int w = tid + P_NPROD * r;
+            st_mm[r] = w / 40;
+            st_ee[r] = 2 * w - 80 * st_mm[r];
+        }
+        int gi = 0;  // chunks produced by this CTA so far
+        // window of tile lt into buffer lt & 1, words [w_lo, w_hi) of each array
+        auto convert_window = [&](const PTile &T, int lt, int w_lo, int w_hi) {
+            const ConvJob &J = jobs[T.tl.job];
+            const float *sb = src + J.src_offset;
+            uint32_t *w = reinterpret_cast<uint32_t *>(smem + Lay.win + (lt & 1) * Lay.win_bytes);
+            for (int e2 = w_lo + tid; e2 < w_hi; e2 += P_NPROD)
+                store_decimated(w + e2, bl / 2, sb, T.c0 + 4 * (int64_t)e2, T.Ts);
+        };
+        // the window buffer of tile lt is free once tile lt - 2's MMAs are done
+        auto wait_window = [&](int lt) {
+            if (lt >= 2 && !mbar_wait(smem_u32(&bar_win[lt & 1]), ((lt >> 1) - 1) & 1)) s_abort = 1;
+        };
+        if (n_my > 0) {
+            const PTile T = p_tile(jobs, tiles, (int)blockIdx.x);
+            if (T.n_live > 0) convert_window(T, 0, 0, bl / 2);
+        }
+        for (int lt = 0; lt < n_my; ++lt) {
+            const PTile T = p_tile(jobs, tiles, (int)blockIdx.x + lt * (int)gridDim.x);
+            const ConvJob &J = jobs[T.tl.job];
+            const float *hb = h + J.h_offset + (int64_t)T.tl.mic0 * T.Lh;
+            // the next tile's window is converted a slice per chunk of this one
+            const bool has_next = lt + 1 < n_my;
+            PTile Tn = T;
+            if (has_next) Tn = p_tile(jobs, tiles, (int)blockIdx.x + (lt + 1) * (int)gridDim.x);
+            const int next_words = (has_next && Tn.n_live > 0) ? bl / 2 : 0;
+            int next_pos = 0;
+            bool next_waited = false;
+            // source samples of this thread's word (next_pos + tid) of the next
+            // slice, loaded one chunk before they are stored
+            const float *sbn = src + jobs[Tn.tl.job].src_offset;
+            uint32_t *wn = reinterpret_cast<uint32_t *>(smem + Lay.win + ((lt + 1) & 1) * Lay.win_bytes);
+            float px[4];
+            if (tid < next_words) load_source4(px, sbn, Tn.c0 + 4 * (int64_t)tid, Tn.Ts);
+            if (p_producers_any(s_abort)) break;
+            auto stage_rir = [&](int ch, int buf) {
+                // stg[buf][mm][e] = h_mm[Lh - 64 - 64 ch + e], e in [0, 80)
+                const int64_t start = T.Lh - 64 - (int64_t)ch * P_KC;
+#pragma unroll
+                for (int r = 0; r < SR; ++r) {
+                    const int w = tid + P_NPROD * r;
+                    if (w < P_STG / 2) {
+                        const float *row = hb + (int64_t)st_mm[r] * T.Lh;
+#pragma unroll
+                        for (int c = 0; c < 2; ++c) {
+                            const int64_t idx = start + st_ee[r] + c;
+                            const bool ok = st_mm[r] < T.nm && idx >= 0 && idx < T.Lh;
+                            cp_async4(stg_u32 + 4u * (uint32_t)(buf * P_STG + 2 * w + c),
+                                      ok ? row + idx : hb, ok);
+                        }
+                    }
+                }
+                asm volatile("cp.async.commit_group;" ::: "memory");
+            };
+            // one cp.async group per chunk, P_PD chunks ahead (empty groups
+            // keep the count when the tile has fewer)
+            for (int k = 0; k < P_PD; ++k) {
+                if (k < T.n_live) stage_rir(T.ch_lo + k, k);
+                else asm volatile("cp.async.commit_group;" ::: "memory");
+            }
+            bool aborted = false;
+            for (int i = 0; i < T.n_live; ++i, ++gi) {
+                const int ch = T.ch_lo + i, s = gi % P_NS, u = gi / P_NS, buf = i % P_PB;
+                asm volatile("cp.async.wait_group %0;" ::"n"(P_PD - 1) : "memory");
+                const bool ok = (u == 0) || mbar_wait(smem_u32(&bar_empty[s]), (u - 1) & 1);
+                // the chunk as bf16 pairs (the pairs this thread staged), into
+                // the converted buffer that chunk gi - 2 read (every producer
+                // passed chunk gi - 1's barrier after its reads)
+                uint32_t *cvb = cvb0 + (gi & 1) * P_CVW;
+                {
+                    const float2 *sv2 = reinterpret_cast<const float2 *>(stg + buf * P_STG);
+                    for (int w = tid; w < P_STG / 2; w += P_NPROD) {
+                        const float2 x = sv2[w];
+                        const float h0 = bf16_round(x.x), h1 = bf16_round(x.y);
+                        cvb[w] = pack_bf16(h0, h1);
+                        cvb[P_STG / 2 + w] = pack_bf16(x.x - h0, x.y - h1);
+                    }
+                }
+                // one barrier: conversions visible, stg[buf] free again, and a
+                // uniform abort decision before the stage is written
+                if (p_producers_any(!ok || s_abort)) {
+                    s_abort = 1;
+                    aborted = true;
+                    break;
+                }
+                // buffer (i + P_PD) % P_PB was last read by chunk i - 1's conversion
+                if (i + P_PD < T.n_live) stage_rir(ch + P_PD, (i + P_PD) % P_PB);
+                else asm volatile("cp.async.commit_group;" ::: "memory");
+                unsigned char *st = smem + (size_t)s * P_ABYTES;
+                if (par) p_rows<1>(cvb, st, m, p, q, rowoff);
+                else p_rows<0>(cvb, st, m, p, q, rowoff);
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_arrive(smem_u32(&bar_full[s]));
+                // a slice of the next tile's window, after the chunk is released
+                // (the next chunk's fence orders these writes)
+                if (next_pos < next_words && i >= P_NS) {
+                    if (!next_waited) {
+                        wait_window(lt + 1);
+                        next_waited = true;
+                    }
+                    const int e2 = next_pos + tid;
+                    if (e2 < next_words) store_split4(wn + e2, bl / 2, px);
+                    next_pos += P_NPROD;
+                    if (e2 + P_NPROD < next_words)
+                        load_source4(px, sbn, Tn.c0 + 4 * (int64_t)(e2 + P_NPROD), Tn.Ts);
+                }
+            }
+            asm volatile("cp.async.wait_all;" ::: "memory");
+            if (aborted) break;
+            if (next_pos < next_words) {
+                if (!next_waited) wait_window(lt + 1);
+                const int e2 = next_pos + tid;
+                if (e2 < next_words) store_split4(wn + e2, bl / 2, px);
+                convert_window(Tn, lt + 1, next_pos + P_NPROD, next_words);
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        }
+    } else if (warp == 8) {
+        // ------------------------------------------------------------------
+        // MMA issuer (one lane)
+        // ------------------------------------------------------------------
+        if (lane == 0) {
+            int gi = 0;
+            for (int lt = 0; lt < n_my && !s_abort; ++lt) {
+                const PTile T = p_tile(jobs, tiles, (int)blockIdx.x + lt * (int)gridDim.x);
+                const int ab = lt & 1, wb = lt & 1;
+                if (lt >= 2 && !mbar_wait(smem_u32(&bar_acce[ab]), ((lt >> 1) - 1) & 1)) {
+                    s_abort = 1;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const uint32_t d = tmem + (uint32_t)(ab * 256);
+                const uint32_t w0 = smem_u32(smem + Lay.win + wb * Lay.win_bytes);
+                const uint32_t wstr = (uint32_t)bl * 2u;
+                uint32_t acc = 0;
+                bool aborted = false;
+                for (int i = 0; i < T.n_live; ++i, ++gi) {
+                    const int ch = T.ch_lo + i, s = gi % P_NS, u = gi / P_NS;
+                    if (!mbar_wait(smem_u32(&bar_full[s]), u & 1)) {
+                        s_abort = 1;
+                        aborted = true;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;");
+                    const uint32_t a0 = smem_u32(smem + (size_t)s * P_ABYTES);
+                    // live columns: column n of chunk ch reads source samples
+                    // base + 16 n + [0, 64); the others only multiply zero
+                    // padding and are left out (the first chunk takes all 256
+                    // columns, which initialises the accumulator).  Rounded
+                    // to 32 columns, the TMEM allocation granularity.
+                    int n0 = 0, nw = NN;
+                    if (i > 0) {
+                        const int64_t base = T.c0 + (int64_t)P_KC * ch;
+                        const int64_t lo = -((63 + base) >> 4);           // ceil((-63 - base) / 16)
+                        const int64_t hi = (T.Ts - 1 - base) >> 4;        // floor
+                        const int nl = lo > 0 ? (int)lo : 0, nh = hi < NN - 1 ? (int)hi : NN - 1;
+                        if (nl <= nh) {
+                            n0 = nl & ~31;
+                            nw = ((nh | 31) + 1) - n0;
+                        }
+                    }
+                    const uint32_t idesc = (kIdesc & ~(0x3Fu << 17)) | ((uint32_t)(nw >> 3) << 17);
+                    const uint32_t dn = d + (uint32_t)n0;
+#pragma unroll
+                    for (int kk = 0; kk < 2; ++kk) {
+#pragma unroll
+                        for (int b = 0; b < 2; ++b) {
+                            const uint64_t ahi = make_desc(a0 + (2 * b) * P_AMAT + kk * 4096, 2048, 128);
+                            const uint64_t alo =
+                                make_desc(a0 + (2 * b + 1) * P_AMAT + kk * 4096, 2048, 128);
+                            const uint32_t bb = w0 + 64u * (uint32_t)ch + 32u * (uint32_t)kk +
+                                                16u * (uint32_t)n0;
+                            const uint64_t bhi = make_desc(bb + (2 * b) * wstr, 16, 128);
+                            const uint64_t blo = make_desc(bb + (2 * b + 1) * wstr, 16, 128);
+                            mma_f16(dn, ahi, bhi, acc, idesc);
+                            acc = 1;
+                            mma_f16(dn, alo, bhi, 1, idesc);
+                            mma_f16(dn, ahi, blo, 1, idesc);
+                        }
+                    }
+                    mma_commit(smem_u32(&bar_empty[s]));
+                }
+                mma_commit(smem_u32(&bar_accf[ab]));  // the tile's MMAs done
+                mma_commit(smem_u32(&bar_win[wb]));   // its window buffer free
+                if (aborted) break;
+            }
+            mma_commit(smem_u32(&bar_done));
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------------------------------------------
+        // epilogue (warps 9-12): TMEM lane quadrant warp % 4 = rows 32 qd ..
+        // 32 qd + 31 = (m = R / 16, p = 2 (R % 8) + (R / 8) % 2); column n is
+        // output T0 + 16 n + p
+        // ------------------------------------------------------------------
+        const int qd = warp & 3;
+        const int R = 32 * qd + lane, m = R >> 4, p = 2 * (R & 7) + ((R >> 3) & 1);
+        const int et = tid - 288;  // 0..127
+        for (int lt = 0; lt < n_my; ++lt) {
+            const PTile T = p_tile(jobs, tiles, (int)blockIdx.x + lt * (int)gridDim.x);
+            const ConvJob &J = jobs[T.tl.job];
+            const int ab = lt & 1;
+            // after an abort the remaining tiles are written as zeros at once
+            bool ok = !s_abort && mbar_wait(smem_u32(&bar_accf[ab]), (lt >> 1) & 1);
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            ok = ok && !s_abort && T.n_live > 0;
+            const int64_t ylen = J.y_len;
+            float *ym = y + J.y_offset + (int64_t)(T.tl.mic0 + m) * ylen;
+            float ss = 0.f, se = 0.f;
+            for (int cb = 0; cb < NN; cb += 32) {
+                uint32_t r[32];
+                if (ok) {
+                    const uint32_t addr =
+                        tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(ab * 256 + cb);
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,"
+                        "%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,"
+                        "%29,%30,%31}, [%32];"
+                        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                          "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]),
+                          "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+                          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+                          "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+                          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+                          "=r"(r[31])
+                        : "r"(addr));
+                    asm volatile("tcgen05.wait::ld.sync.aligned;");
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) r[j] = 0u;
+                }
+                if (m < T.nm) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int64_t t = T.T0 + P_PH * (cb + j) + p;
+                        const float v = __uint_as_float(r[j]);
+                        if (t < ylen) {
+                            ym[t] = v;
+                            ff_accumulate_sq(v, ss, se);
+                        }
+                    }
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            mbar_arrive(smem_u32(&bar_acce[ab]));  // the accumulator may be refilled
+            const double rs = warp_sum_f64((double)ss + (double)se);
+            if (lane == 0) s_red[ab][qd] = rs;
+            asm volatile("bar.sync 2, 128;" ::: "memory");
+            if (et == 0 && part) {
+                // the tile spans two slots of the noise-partial grid: its sum
+                // in the first, zero in the second
+                part[J.part_offset + conv_partial_slot(T.tl.mic0, T.T0, ylen)] =
+                    (s_red[ab][0] + s_red[ab][1]) + (s_red[ab][2] + s_red[ab][3]);
+                if (T.T0 + kConvTT < ylen)
+                    part[J.part_offset + conv_partial_slot(T.tl.mic0, T.T0 + kConvTT, ylen)] = 0.0;
+            }
+        }
+    }
+    __syncthreads();
+    if (warp == 8) {
+        // every issued MMA has completed before the columns are freed
+        mbar_wait(smem_u32(&bar_done), 0);
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        __syncwarp();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+    }
+}
+
 // Raises a kernel's dynamic shared memory limit to smem once per device
 // (the attribute call is not repeated for calls of the same or smaller size).
 template <class K>
@@ -490,48 +970,54 @@ cudaError_t ensure_smem(K kern, int (&set)[64], std::mutex &mu, size_t smem) {
 }
 
 std::mutex g_smem_mu;
-int g_smem_whole[64], g_smem_chunked[64];
+int g_smem_chunked[64], g_smem_persistent[64];
 
 }  // namespace
 
 int launch_conv_bf16x3(const ConvLaunch &L, cudaStream_t stream) {
-    // one launch per layout: tiles whose whole source window fits in shared
-    // memory, and the rest (long RIRs) with per-chunk windows
-    std::vector<Tile> tiles[2];
-    int max_chunks = 0;
+    // one launch per kernel: the persistent three-product kernel for every
+    // RIR whose two tile windows fit beside its stages, the per-chunk window
+    // kernel for longer RIRs
+    std::vector<Tile> tiles, ptiles;
+    int64_t p_max_lh = 0;
     for (int j = 0; j < L.n_jobs; ++j) {
         const ConvJob &J = L.jobs_host[j];
-        const int n_chunks = (int)((J.rir_len + 7 + KC - 1) / KC);
-        const bool whole = tc_layout(true, n_chunks).total <= 227 * 1024;
-        if (whole) max_chunks = std::max(max_chunks, n_chunks);
+        if (p_layout(J.rir_len).total <= kMaxDynSmem) {
+            p_max_lh = std::max(p_max_lh, J.rir_len);
+            for (int m0 = 0; m0 < J.n_mics; m0 += MG)
+                for (int64_t t0 = 0; t0 < J.y_len; t0 += P_TT) ptiles.push_back(Tile{j, m0, t0});
+            continue;
+        }
         for (int m0 = 0; m0 < J.n_mics; m0 += MG)
-            for (int64_t t0 = 0; t0 < J.y_len; t0 += TT) tiles[whole].push_back(Tile{j, m0, t0});
+            for (int64_t t0 = 0; t0 < J.y_len; t0 += TT) tiles.push_back(Tile{j, m0, t0});
     }
-    const size_t n_tiles = tiles[0].size() + tiles[1].size();
+    const size_t n_tiles = tiles.size() + ptiles.size();
     if (n_tiles == 0) return ISM_OK;
     if (n_tiles > 0x7fffffffULL) return fail(ISM_ERR_INVALID_ARG, "too many tiles");
     void *d_tiles = nullptr;
     int st = scratch_alloc(&d_tiles, n_tiles * sizeof(Tile), stream);
     if (st) return st;
-    std::vector<Tile> all(tiles[1]);
-    all.insert(all.end(), tiles[0].begin(), tiles[0].end());
+    std::vector<Tile> all(tiles);
+    all.insert(all.end(), ptiles.begin(), ptiles.end());
     st = upload_async(d_tiles, all.data(), n_tiles * sizeof(Tile), stream);
     if (st) { scratch_free(d_tiles, stream); return st; }
     cudaError_t e = cudaSuccess;
-    if (!tiles[1].empty()) {
-        const size_t smem = tc_layout(true, max_chunks).total;
-        e = ensure_smem(k_conv_tc<true>, g_smem_whole, g_smem_mu, smem);
+    if (!ptiles.empty()) {
+        const size_t smem = p_layout(p_max_lh).total;
+        e = ensure_smem(k_conv_tcp, g_smem_persistent, g_smem_mu, smem);
+        const int grid = (int)std::min<size_t>(ptiles.size(), (size_t)device_sm_count());
         if (e == cudaSuccess)
-            k_conv_tc<true><<<(unsigned)tiles[1].size(), NTHR, smem, stream>>>(
-                L.jobs_dev, (const Tile *)d_tiles, L.h_dev, L.src_dev, L.y_dev,
+            k_conv_tcp<<<grid, P_NT, smem, stream>>>(
+                L.jobs_dev, (const Tile *)d_tiles + tiles.size(),
+                (int)ptiles.size(), (int)p_max_lh, L.h_dev, L.src_dev, L.y_dev,
                 L.noise_partials_dev);
     }
-    if (e == cudaSuccess && !tiles[0].empty()) {
-        const size_t smem = tc_layout(false, 0).total;
-        e = ensure_smem(k_conv_tc<false>, g_smem_chunked, g_smem_mu, smem);
+    if (e == cudaSuccess && !tiles.empty()) {
+        const size_t smem = tc_layout().total;
+        e = ensure_smem(k_conv_tc, g_smem_chunked, g_smem_mu, smem);
         if (e == cudaSuccess)
-            k_conv_tc<false><<<(unsigned)tiles[0].size(), NTHR, smem, stream>>>(
-                L.jobs_dev, (const Tile *)d_tiles + tiles[1].size(), L.h_dev, L.src_dev, L.y_dev,
+            k_conv_tc<<<(unsigned)tiles.size(), NTHR, smem, stream>>>(
+                L.jobs_dev, (const Tile *)d_tiles, L.h_dev, L.src_dev, L.y_dev,
                 L.noise_partials_dev);
     }
     if (e == cudaSuccess) e = cudaGetLastError();

@@ -65,6 +65,12 @@ void scratch_free(void *p, cudaStream_t stream);
 
 int device_sm_count();
 
+// Largest dynamic shared memory a launch of this library asks for: the 227 KB
+// a block may opt into, less 1 KB for the kernels' static shared memory (the
+// convolution kernels declare 1 KB, their dynamic array's 1024-byte
+// alignment; the image-source kernels less than 100 bytes).
+constexpr size_t kMaxDynSmem = 227 * 1024 - 1024;
+
 // Lattice order of RIR (room r, mic m): the room's order, or the
 // delay-limited order for ISM_ORDER_AUTO (see ism.h).
 int room_order(const ism_room &r, int m);

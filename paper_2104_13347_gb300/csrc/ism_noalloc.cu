@@ -93,7 +93,7 @@ extern "C" int ism_rir_batch_noalloc(const ism_room *rooms, int64_t n_rooms, flo
                         " RIRs exceed its fixed scratch of " +
                         std::to_string(ISM_NOALLOC_MAX_RIRS) + " RIRs per call");
     for (int k = 0; k < 2; ++k)
-        if (count[k] && rir_smem_bytes(W, max_order[k], max_taps[k]) > 227 * 1024)
+        if (count[k] && rir_smem_bytes(W, max_order[k], max_taps[k]) > kMaxDynSmem)
             return fail(ISM_ERR_INVALID_ARG, "window/order/taps need too much shared memory");
 
     unsigned char *base = nullptr;

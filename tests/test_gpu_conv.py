@@ -94,6 +94,29 @@ def test_conv_long_rir_and_many_mics(ism):
             assert rel_l2(y[m], ref[m]) <= TOL[precision]
 
 
+def test_conv_kernel_boundary(ism):
+    """RIRs of 10609 samples (the longest the persistent three-product kernel
+    takes: its stages, two tile windows and 1 KB of static shared memory fill
+    exactly the 227 KB a block may use) and 10610 (the per-chunk kernel) in
+    one batch, both precisions; each room's result is the same, bit for bit,
+    when it is convolved alone."""
+    rng = np.random.default_rng(21)
+    lens, mics, srcl = (10609, 10610, 37), (3, 2, 9), (3000, 5000, 4100)
+    hs = [(rng.standard_normal((M, L)) * np.exp(-np.arange(L) / 2500)).astype(np.float32)
+          for M, L in zip(mics, lens)]
+    ss = [rng.standard_normal(T).astype(np.float32) for T in srcl]
+    ref = oracle.convolve_batch([h.astype(np.float64) for h in hs],
+                                [s.astype(np.float64) for s in ss])
+    for precision in (0, 1):
+        got = run_conv(ism, hs, ss, precision)
+        for i, (g, r) in enumerate(zip(got, ref)):
+            assert g.shape == r.shape
+            for m in range(g.shape[0]):
+                assert rel_l2(g[m], r[m]) <= TOL[precision], (precision, i, m)
+            (alone,) = run_conv(ism, [hs[i]], [ss[i]], precision)
+            np.testing.assert_array_equal(alone, g)
+
+
 def test_conv_delta_rir_exact(ism):
     rng = np.random.default_rng(8)
     s = rng.standard_normal(3000).astype(np.float32)
