@@ -17,10 +17,13 @@
 // taps are split by parity so that both parity windows of the source are
 // again 16-byte-shifted Toeplitz matrices.  Its 128 GEMM rows are (mic,
 // phase) of one part, and the MMAs hi.hi, lo.hi and hi.lo accumulate into
-// one FP32 accumulator: the split-BF16 product without its lo.lo term
-// (2^-32 relative).  Two 256-column TMEM accumulators and two source-window
-// buffers let one tile's epilogue and the next tile's window conversion run
-// under the current tile's MMAs.
+// one FP32 accumulator: the split-BF16 product without its lo.lo term (each
+// lo part is within 2^-8 of its value, so lo.lo is within 2^-16 of the
+// product: the order of the split's own representation error, and adding it
+// back does not lower the largest rel-L2 error over the dataset's RIRs).
+// Two 256-column TMEM accumulators and two source-window buffers let one
+// tile's epilogue and the next tile's window conversion run under the
+// current tile's MMAs.
 //
 // k_conv_tc (longer RIRs): one CTA per tile of 8 mics x 2048 outputs, 8
 // phases; A holds (hi / lo, mic, phase) rows, so the MMAs with B_hi and
@@ -131,6 +134,12 @@ __device__ __forceinline__ float bf16_round(float x) {
 constexpr int STG_FLOATS = 8 * 72;     // raw RIR staging per chunk: 8 mics x 72 values
 constexpr int CV_WORDS = 2 * 8 * 36;   // one chunk's RIR as bf16 pairs: [hi/lo][mic][36 words]
 constexpr int CV_BYTES = CV_WORDS * 4;
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const float *src, bool ok) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src),
+                 "r"(ok ? 16 : 0)
+                 : "memory");
+}
 
 __device__ __forceinline__ void cp_async4(uint32_t dst, const float *src, bool ok) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src),
@@ -615,7 +624,7 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
 __global__ void __launch_bounds__(P_NT, 1)
 k_conv_tcp(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles, int n_tiles,
            int max_lh, const float *__restrict__ h, const float *__restrict__ src,
-           float *__restrict__ y, double *__restrict__ part) {
+           float *__restrict__ y, double *__restrict__ part, int h_aligned16) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) uint64_t bar_full[P_NS], bar_empty[P_NS], bar_win[2], bar_accf[2],
         bar_acce[2], bar_done;
@@ -676,8 +685,11 @@ k_conv_tcp(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles, int
         const uint32_t stg_u32 = smem_u32(stg);
         uint32_t *cvb0 = reinterpret_cast<uint32_t *>(smem + Lay.cv);
         // this thread's raw staging pairs w = tid + P_NPROD r (elements 2 w,
-        // 2 w + 1: mic st_mm, offsets st_ee, st_ee + 1).  A thread converts
-        // exactly the pairs it staged, so its own cp.async wait covers them.
+        // 2 w + 1: mic st_mm, offsets st_ee, st_ee + 1), or, for RIRs whose
+        // rows start on 16-byte boundaries, its quad tid < P_STG / 4 (elements
+        // 4 tid .. 4 tid + 3: mic qd_mm, offset qd_ee) in one 16-byte copy.  A
+        // thread converts exactly the values it staged, so its own cp.async
+        // wait covers them.
         constexpr int SR = (P_STG / 2 + P_NPROD - 1) / P_NPROD;
         int st_mm[SR], st_ee[SR];
 #pragma unroll
@@ -686,6 +698,8 @@ k_conv_tcp(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles, int
             st_mm[r] = w / 40;
             st_ee[r] = 2 * w - 80 * st_mm[r];
         }
+        static_assert(P_STG / 4 <= P_NPROD, "one quad per thread");
+        const int qd_mm = tid / 20, qd_ee = 4 * tid - 80 * qd_mm;
         int gi = 0;  // chunks produced by this CTA so far
         // window of tile lt into buffer lt & 1, words [w_lo, w_hi) of each array
         auto convert_window = [&](const PTile &T, int lt, int w_lo, int w_hi) {
@@ -707,6 +721,8 @@ k_conv_tcp(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles, int
             const PTile T = p_tile(jobs, tiles, (int)blockIdx.x + lt * (int)gridDim.x);
             const ConvJob &J = jobs[T.tl.job];
             const float *hb = h + J.h_offset + (int64_t)T.tl.mic0 * T.Lh;
+            // every row start and chunk offset a multiple of 4 elements
+            const bool quad = h_aligned16 && (T.Lh & 3) == 0 && (J.h_offset & 3) == 0;
             // the next tile's window is converted a slice per chunk of this one
             const bool has_next = lt + 1 < n_my;
             PTile Tn = T;
@@ -724,6 +740,17 @@ k_conv_tcp(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles, int
             auto stage_rir = [&](int ch, int buf) {
                 // stg[buf][mm][e] = h_mm[Lh - 64 - 64 ch + e], e in [0, 80)
                 const int64_t start = T.Lh - 64 - (int64_t)ch * P_KC;
+                if (quad) {
+                    if (tid < P_STG / 4) {
+                        // idx and Lh multiples of 4: the quad is all in or all out
+                        const int64_t idx = start + qd_ee;
+                        const bool ok = qd_mm < T.nm && idx >= 0 && idx < T.Lh;
+                        cp_async16(stg_u32 + 16u * (uint32_t)(buf * (P_STG / 4) + tid),
+                                   ok ? hb + (int64_t)qd_mm * T.Lh + idx : hb, ok);
+                    }
+                    asm volatile("cp.async.commit_group;" ::: "memory");
+                    return;
+                }
 #pragma unroll
                 for (int r = 0; r < SR; ++r) {
                     const int w = tid + P_NPROD * r;
@@ -755,7 +782,17 @@ k_conv_tcp(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles, int
                 // the converted buffer that chunk gi - 2 read (every producer
                 // passed chunk gi - 1's barrier after its reads)
                 uint32_t *cvb = cvb0 + (gi & 1) * P_CVW;
-                {
+                if (quad) {
+                    if (tid < P_STG / 4) {
+                        const float4 x = reinterpret_cast<const float4 *>(stg + buf * P_STG)[tid];
+                        const float h0 = bf16_round(x.x), h1 = bf16_round(x.y);
+                        const float h2 = bf16_round(x.z), h3 = bf16_round(x.w);
+                        reinterpret_cast<uint2 *>(cvb)[tid] =
+                            make_uint2(pack_bf16(h0, h1), pack_bf16(h2, h3));
+                        reinterpret_cast<uint2 *>(cvb + P_STG / 2)[tid] = make_uint2(
+                            pack_bf16(x.x - h0, x.y - h1), pack_bf16(x.z - h2, x.w - h3));
+                    }
+                } else {
                     const float2 *sv2 = reinterpret_cast<const float2 *>(stg + buf * P_STG);
                     for (int w = tid; w < P_STG / 2; w += P_NPROD) {
                         const float2 x = sv2[w];
@@ -1010,7 +1047,7 @@ int launch_conv_bf16x3(const ConvLaunch &L, cudaStream_t stream) {
             k_conv_tcp<<<grid, P_NT, smem, stream>>>(
                 L.jobs_dev, (const Tile *)d_tiles + tiles.size(),
                 (int)ptiles.size(), (int)p_max_lh, L.h_dev, L.src_dev, L.y_dev,
-                L.noise_partials_dev);
+                L.noise_partials_dev, (int)(((uintptr_t)L.h_dev & 15) == 0));
     }
     if (e == cudaSuccess && !tiles.empty()) {
         const size_t smem = tc_layout().total;
