@@ -37,7 +37,7 @@ WORKLOAD = (f"{N_ROOMS} rooms U[3,10]x[3,8]x[2.5,4] m, beta U[0.5,0.95], {N_MICS
 
 
 # K1 DRAM traffic per room from the ncu capture summarised in
-# profiles/k_ism_sparse_and_k_conv_tc_1024rooms.md (None when that capture
+# profiles/k_ism_sparse_and_k_conv_tcp_1024rooms.md (None when that capture
 # predates the current kernel), and the binding resources it measured.
 K1_TRAFFIC_PER_ROOM = (33.762048e6 + 16.236544e6) / 256
 K1_TRAFFIC_NOTE = ("dram read+write of a 256-room ncu capture, scaled by rooms; reads are "
@@ -47,7 +47,7 @@ K1_BINDING = {"issue_active_pct": 78.8, "smem_wavefronts_pct_of_peak": 85.4,
               "fma_pipe_pct": 39.6, "alu_pipe_pct": 29.9, "xu_pipe_pct": 22.9,
               "fp64_pipe_pct": 2.7, "shared_atomic_wavefronts_per_instruction": 3.63,
               "source": "ncu --set full, 256-room case"}
-K2_TRAFFIC_PER_ROOM = (83.75424e6 + 140.089856e6) / 256
+K2_TRAFFIC_PER_ROOM = (83.592192e6 + 138.994176e6) / 256
 
 
 def k2_live_chunks(ts, lh, kc=64, nn=256, phases=16):

@@ -1011,6 +1011,11 @@ int g_smem_chunked[64], g_smem_persistent[64];
 
 }  // namespace
 
+int64_t conv_bf16x3_persistent_tiles(int n_mics, int64_t rir_len, int64_t y_len) {
+    if (p_layout(rir_len).total > kMaxDynSmem) return -1;
+    return (int64_t)((n_mics + MG - 1) / MG) * ((y_len + P_TT - 1) / P_TT);
+}
+
 int launch_conv_bf16x3(const ConvLaunch &L, cudaStream_t stream) {
     // one launch per kernel: the persistent three-product kernel for every
     // RIR whose two tile windows fit beside its stages, the per-chunk window

@@ -105,14 +105,46 @@ extern "C" int ism_dataset_batch(const ism_room *rooms, int64_t n_rooms, const f
     // chunks of consecutive rooms.  Automatic: K >= 6 chunks of about
     // 128 MiB of signals each, balanced by signal length (ragged rooms).  With
     // two compute streams the tails of consecutive chunks overlap; on the
-    // 1024-room step equal chunks beat chunks of decreasing size.
+    // 1024-room step equal chunks beat chunks of decreasing size.  When every
+    // room goes to the persistent tensor-core convolution (one CTA per SM
+    // walking the chunk's tiles), chunks are instead cut at a whole number of
+    // rounds of tiles over the SMs -- as many rounds as still give K chunks --
+    // so that no chunk ends with a partly filled round (1024 8-mic rooms with
+    // 1 s sources and 8192-sample RIRs: chunks of 152 rooms, six rounds each,
+    // 2 % faster end to end than six equal chunks).
     std::vector<int64_t> cb;  // chunk boundaries
-    if (chunk_rooms > 0) {
+    const int64_t target = (128ll << 20) / 4;  // floats of signals per chunk
+    const int64_t K = std::min<int64_t>(n_rooms,
+                                        std::max<int64_t>((y_total + target - 1) / target, 6));
+    std::vector<int64_t> tiles;
+    if (chunk_rooms == 0 && precision == ISM_BF16X3) {
+        tiles.resize(n_rooms);
+        int64_t total = 0;
+        for (int64_t i = 0; i < n_rooms && !tiles.empty(); ++i) {
+            const ism_room &R = rooms[i];
+            tiles[i] = conv_bf16x3_persistent_tiles(R.n_mics, R.rir_len, src_lens[i] + R.rir_len - 1);
+            if (tiles[i] < 0) tiles.clear();
+            else total += tiles[i];
+        }
+        const int64_t sms = device_sm_count();
+        const int64_t rounds = total / (K * sms);
+        if (!tiles.empty() && rounds >= 1) {
+            const int64_t cap = rounds * sms;
+            int64_t acc = 0;
+            for (int64_t r = 0; r < n_rooms; ++r) {
+                if (r == 0 || acc + tiles[r] > cap) {
+                    cb.push_back(r);
+                    acc = 0;
+                }
+                acc += tiles[r];
+            }
+        }
+    }
+    if (!cb.empty()) {
+        // cut by tile rounds above
+    } else if (chunk_rooms > 0) {
         for (int64_t r = 0; r < n_rooms; r += chunk_rooms) cb.push_back(r);
     } else {
-        const int64_t target = (128ll << 20) / 4;  // floats of signals per chunk
-        const int64_t K = std::min<int64_t>(
-            n_rooms, std::max<int64_t>((y_total + target - 1) / target, 6));
         int64_t r = 0;
         double acc = 0.0;
         for (int64_t c = 0; c < K && r < n_rooms; ++c) {

@@ -165,6 +165,10 @@ __host__ __device__ inline int conv_partial_slot(int mic0, int64_t t0, int64_t y
 }
 int launch_conv_f32(const ConvLaunch &L, cudaStream_t stream);
 int launch_conv_bf16x3(const ConvLaunch &L, cudaStream_t stream);
+// Tiles the persistent split-BF16 kernel makes of a room (n_mics mics,
+// RIRs of rir_len samples, signals of y_len = src_len + rir_len - 1), or -1
+// when its RIRs are too long for that kernel.
+int64_t conv_bf16x3_persistent_tiles(int n_mics, int64_t rir_len, int64_t y_len);
 int launch_noise(const ConvLaunch &L, cudaStream_t stream);
 
 #ifdef __CUDACC__

@@ -39,3 +39,25 @@ def test_dataset_batch_matches_device_path(ism, precision):
     ism.dataset_batch(rooms, src_cat, lens, y_np, snr_db=snr, seed=8, noise_id_base=500,
                       precision=precision)
     np.testing.assert_array_equal(y_np, y_ref.numpy())
+
+
+def test_dataset_batch_tile_round_chunks(ism):
+    """Enough 8-mic rooms (160 rooms, 1 s sources, 8192-sample RIRs: 960
+    convolution tiles) for the automatic split to cut chunks at whole rounds
+    of tiles over the SMs: the outputs equal one chunk's bit for bit."""
+    import torch
+    n = 160
+    rooms = wl.room_batch(n, seed=407)
+    srcs = wl.sources(rooms, 1.0, seed=408)
+    snr = wl.snrs(n, seed=409)
+    lens = [len(s) for s in srcs]
+    src_pin = torch.from_numpy(np.concatenate(srcs)).pin_memory()
+    ylen = sum(8 * (t + r["rir_len"] - 1) for t, r in zip(lens, rooms))
+    outs = []
+    for chunk in (0, n):
+        y_host = torch.full((ylen,), float("nan")).pin_memory()
+        ism.dataset_batch(rooms, src_pin, lens, y_host, snr_db=snr, seed=9, noise_id_base=7,
+                          precision=1, chunk_rooms=chunk)
+        outs.append(y_host)
+    assert not torch.isnan(outs[0]).any()
+    assert torch.equal(outs[0], outs[1])
