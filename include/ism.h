@@ -57,7 +57,8 @@ typedef enum ism_fd_kind { ISM_FD_HANN_SINC = 0, ISM_FD_LAGRANGE = 1 } ism_fd_ki
  *  ISM_BF16X3: tensor-core convolution with each operand split into
  *    bf16 hi + lo parts, the cross products accumulated in FP32: hi.hi,
  *    hi.lo and lo.hi in a persistent kernel (one CTA per SM) for RIRs of at
- *    most 10609 samples; all four in a per-tile kernel for longer RIRs.
+ *    most 10609 samples; all four in a per-tile kernel for longer RIRs and
+ *    for the server's requests (small batches).
  *    Rel-L2 error against FP64 below 1e-5 per (room, mic) on the dataset's
  *    rooms (the bf16 hi + lo split itself keeps about 16 bits of each
  *    operand). */
@@ -327,7 +328,10 @@ int ism_frames_batch(const ism_frame_job *jobs, int64_t n_frames, int32_t frame_
  * Each request's work items (RIR windows, convolution tiles, noise streams
  * keyed by its noise_id) are the same alone or mixed with others, bit for
  * bit (the sparse RIR path sums in fixed point, and the server always uses
- * 1024-sample RIR windows).
+ * 1024-sample RIR windows).  With ISM_BF16X3 the server convolves with the
+ * per-tile tensor-core kernel (see ism_precision), whatever the mix, so its
+ * signals match ism_convolve_batch's to within the split-BF16 error, not
+ * bit for bit.
  * ------------------------------------------------------------------------ */
 typedef struct ism_server ism_server;
 

@@ -25,10 +25,12 @@
 // tile's epilogue and the next tile's window conversion run under the
 // current tile's MMAs.
 //
-// k_conv_tc (longer RIRs): one CTA per tile of 8 mics x 2048 outputs, 8
-// phases; A holds (hi / lo, mic, phase) rows, so the MMAs with B_hi and
-// B_lo give all four products, and each chunk converts its own 2112-sample
-// source window into its pipeline stage.
+// k_conv_tc (longer RIRs, and every RIR of the server's small batches): one
+// CTA per tile of 8 mics x 2048 outputs, 8 phases, two CTAs per SM; A holds
+// (hi / lo, mic, phase) rows, so the MMAs with B_hi and B_lo give all four
+// products.  The tile's whole source window is converted once when it fits
+// in shared memory (RIRs up to ~9k samples); beyond that each chunk converts
+// its own 2112-sample source window into its pipeline stage.
 //
 // In both, the raw RIR values of each chunk are staged with cp.async
 // (zero-filled outside the RIR), converted once per value into bf16 hi / lo
@@ -163,23 +165,39 @@ __device__ __forceinline__ void producers_sync() {
     asm volatile("bar.sync 1, 128;" ::: "memory");
 }
 
-// Shared-memory layout: NS stages of (A, window hi, window lo), then the
-// RIR staging (two raw chunks) and the converted RIR (one chunk of bf16 hi /
-// lo: the barrier that opens each chunk orders every read of it before the
-// next conversion).
+// Shared-memory layout.  whole_b: NS A stages (16 KB each), RIR staging
+// (two raw chunks), the converted RIR (one chunk of bf16 hi / lo: the
+// barrier that opens each chunk orders every read of it before the next
+// conversion), then the tile's source window (bf16 hi, bf16 lo; bl elements
+// each).  Otherwise NS stages of (A, window hi, window lo), then the RIR
+// staging and conversion.
 struct TcLayout {
-    size_t a_stride, stg, cv, total;
+    size_t a_stride, stg, cv, bhi, blo, total;
+    int bl;
 };
 
-__host__ __device__ inline TcLayout tc_layout() {
+__host__ __device__ inline TcLayout tc_layout(bool whole_b, int n_chunks) {
     TcLayout L;
-    L.a_stride = STAGE;
-    L.stg = (size_t)NS * STAGE;
-    L.cv = L.stg + STG_FLOATS * 2 * 4;
-    L.total = L.cv + CV_BYTES;
+    if (whole_b) {
+        L.bl = (n_chunks * KC + 8 * (NN - 1) + 8 + 7) & ~7;
+        L.a_stride = A_BYTES;
+        L.stg = (size_t)NS * A_BYTES;
+        L.cv = L.stg + STG_FLOATS * 2 * 4;
+        L.bhi = L.cv + CV_BYTES;
+        L.blo = L.bhi + (size_t)L.bl * 2;
+        L.total = L.blo + (size_t)L.bl * 2;
+    } else {
+        L.bl = BW;
+        L.a_stride = STAGE;
+        L.stg = (size_t)NS * STAGE;
+        L.cv = L.stg + STG_FLOATS * 2 * 4;
+        L.bhi = L.blo = 0;  // per stage, after A
+        L.total = L.cv + CV_BYTES;
+    }
     return L;
 }
 
+template <bool WHOLE_B>
 __global__ void __launch_bounds__(NTHR, 1)
 k_conv_tc(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles,
           const float *__restrict__ h, const float *__restrict__ src, float *__restrict__ y,
@@ -199,7 +217,7 @@ k_conv_tc(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles,
     const float *sb = src + J.src_offset;
     const int64_t c0 = T0 - Lh + 1;                    // source index of B[0][0] at k = 0
     const int n_chunks = (int)((Lh + 7 + KC - 1) / KC);
-    const TcLayout Lay = tc_layout();
+    const TcLayout Lay = tc_layout(WHOLE_B, n_chunks);
     // live chunks (source window not all zero padding) form one range
     int64_t lo_c = -c0 - (KC - 1 + 8 * (NN - 1));
     lo_c = lo_c <= 0 ? 0 : (lo_c + KC - 1) / KC;
@@ -218,6 +236,20 @@ k_conv_tc(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles,
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_done)), "r"(1));
         asm volatile("fence.mbarrier_init.release.cluster;");
         s_abort = 0;
+    }
+    if (WHOLE_B && n_live > 0) {
+        // the tile's source window s[c0 + e], e in [0, bl), as bf16 hi / lo
+        uint32_t *bh = reinterpret_cast<uint32_t *>(smem + Lay.bhi);
+        uint32_t *bl = reinterpret_cast<uint32_t *>(smem + Lay.blo);
+        for (int e2 = tid; e2 < Lay.bl / 2; e2 += NTHR) {
+            const int64_t i0 = c0 + 2 * e2;
+            const float x0 = (i0 >= 0 && i0 < Ts) ? __ldg(sb + i0) : 0.f;
+            const float x1 = (i0 + 1 >= 0 && i0 + 1 < Ts) ? __ldg(sb + i0 + 1) : 0.f;
+            const float h0 = bf16_round(x0), h1 = bf16_round(x1);
+            bh[e2] = pack_bf16(h0, h1);
+            bl[e2] = pack_bf16(x0 - h0, x1 - h1);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     if (warp == 4) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -300,7 +332,7 @@ k_conv_tc(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles,
                     *reinterpret_cast<uint4 *>(st + kg * 2048 + g * 128 + p * 16) = row;
                 }
             }
-            {
+            if (!WHOLE_B) {
                 // the chunk's source window, s[c0 + 64 ch + e], split hi / lo
                 unsigned char *st = smem + (size_t)s * Lay.a_stride;
                 uint32_t *bh = reinterpret_cast<uint32_t *>(st + A_BYTES);
@@ -325,14 +357,21 @@ k_conv_tc(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles,
         // ------------------------------------------------------------------
         uint32_t acc = 0;
         for (int i = 0; i < n_live; ++i) {
-            const int s = i % NS, u = i / NS;
+            const int ch = ch_lo + i, s = i % NS, u = i / NS;
             if (!mbar_wait(smem_u32(&bar_full[s]), u & 1)) {
                 s_abort = 1;
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;");
             const uint32_t a0 = smem_u32(smem + (size_t)s * Lay.a_stride);
-            const uint32_t bh0 = a0 + A_BYTES, bl0 = bh0 + BW * 2;
+            uint32_t bh0, bl0;
+            if (WHOLE_B) {
+                bh0 = smem_u32(smem + Lay.bhi) + 2u * (uint32_t)(ch * KC);
+                bl0 = smem_u32(smem + Lay.blo) + 2u * (uint32_t)(ch * KC);
+            } else {
+                bh0 = a0 + A_BYTES;
+                bl0 = bh0 + BW * 2;
+            }
 #pragma unroll
             for (int kk = 0; kk < KC / 16; ++kk) {
                 const uint64_t ad = make_desc(a0 + kk * 2 * 2048, 2048, 128);
@@ -1007,7 +1046,7 @@ cudaError_t ensure_smem(K kern, int (&set)[64], std::mutex &mu, size_t smem) {
 }
 
 std::mutex g_smem_mu;
-int g_smem_chunked[64], g_smem_persistent[64];
+int g_smem_whole[64], g_smem_chunked[64], g_smem_persistent[64];
 
 }  // namespace
 
@@ -1018,28 +1057,39 @@ int64_t conv_bf16x3_persistent_tiles(int n_mics, int64_t rir_len, int64_t y_len)
 
 int launch_conv_bf16x3(const ConvLaunch &L, cudaStream_t stream) {
     // one launch per kernel: the persistent three-product kernel for every
-    // RIR whose two tile windows fit beside its stages, the per-chunk window
-    // kernel for longer RIRs
-    std::vector<Tile> tiles, ptiles;
+    // RIR whose two tile windows fit beside its stages; the per-tile kernel
+    // for longer RIRs, with the tile's whole source window converted once
+    // where it fits and per chunk beyond.  L.per_tile (the server's small
+    // latency-bound batches) takes the per-tile kernel for every RIR: its
+    // 2048-output tiles give twice the CTAs, two per SM, so a batch below
+    // one round of the persistent kernel's tiles finishes sooner.  The choice
+    // depends on the call's kind and the RIR length only, never on the rest
+    // of the batch, so a job's result is the same in any batch of its kind.
+    std::vector<Tile> tiles[2], ptiles;
+    int max_chunks = 0;
     int64_t p_max_lh = 0;
     for (int j = 0; j < L.n_jobs; ++j) {
         const ConvJob &J = L.jobs_host[j];
-        if (p_layout(J.rir_len).total <= kMaxDynSmem) {
+        if (!L.per_tile && p_layout(J.rir_len).total <= kMaxDynSmem) {
             p_max_lh = std::max(p_max_lh, J.rir_len);
             for (int m0 = 0; m0 < J.n_mics; m0 += MG)
                 for (int64_t t0 = 0; t0 < J.y_len; t0 += P_TT) ptiles.push_back(Tile{j, m0, t0});
             continue;
         }
+        const int n_chunks = (int)((J.rir_len + 7 + KC - 1) / KC);
+        const bool whole = tc_layout(true, n_chunks).total <= kMaxDynSmem;
+        if (whole) max_chunks = std::max(max_chunks, n_chunks);
         for (int m0 = 0; m0 < J.n_mics; m0 += MG)
-            for (int64_t t0 = 0; t0 < J.y_len; t0 += TT) tiles.push_back(Tile{j, m0, t0});
+            for (int64_t t0 = 0; t0 < J.y_len; t0 += TT) tiles[whole].push_back(Tile{j, m0, t0});
     }
-    const size_t n_tiles = tiles.size() + ptiles.size();
+    const size_t n_tiles = tiles[0].size() + tiles[1].size() + ptiles.size();
     if (n_tiles == 0) return ISM_OK;
     if (n_tiles > 0x7fffffffULL) return fail(ISM_ERR_INVALID_ARG, "too many tiles");
     void *d_tiles = nullptr;
     int st = scratch_alloc(&d_tiles, n_tiles * sizeof(Tile), stream);
     if (st) return st;
-    std::vector<Tile> all(tiles);
+    std::vector<Tile> all(tiles[1]);
+    all.insert(all.end(), tiles[0].begin(), tiles[0].end());
     all.insert(all.end(), ptiles.begin(), ptiles.end());
     st = upload_async(d_tiles, all.data(), n_tiles * sizeof(Tile), stream);
     if (st) { scratch_free(d_tiles, stream); return st; }
@@ -1050,16 +1100,24 @@ int launch_conv_bf16x3(const ConvLaunch &L, cudaStream_t stream) {
         const int grid = (int)std::min<size_t>(ptiles.size(), (size_t)device_sm_count());
         if (e == cudaSuccess)
             k_conv_tcp<<<grid, P_NT, smem, stream>>>(
-                L.jobs_dev, (const Tile *)d_tiles + tiles.size(),
+                L.jobs_dev, (const Tile *)d_tiles + tiles[1].size() + tiles[0].size(),
                 (int)ptiles.size(), (int)p_max_lh, L.h_dev, L.src_dev, L.y_dev,
                 L.noise_partials_dev, (int)(((uintptr_t)L.h_dev & 15) == 0));
     }
-    if (e == cudaSuccess && !tiles.empty()) {
-        const size_t smem = tc_layout().total;
-        e = ensure_smem(k_conv_tc, g_smem_chunked, g_smem_mu, smem);
+    if (e == cudaSuccess && !tiles[1].empty()) {
+        const size_t smem = tc_layout(true, max_chunks).total;
+        e = ensure_smem(k_conv_tc<true>, g_smem_whole, g_smem_mu, smem);
         if (e == cudaSuccess)
-            k_conv_tc<<<(unsigned)tiles.size(), NTHR, smem, stream>>>(
+            k_conv_tc<true><<<(unsigned)tiles[1].size(), NTHR, smem, stream>>>(
                 L.jobs_dev, (const Tile *)d_tiles, L.h_dev, L.src_dev, L.y_dev,
+                L.noise_partials_dev);
+    }
+    if (e == cudaSuccess && !tiles[0].empty()) {
+        const size_t smem = tc_layout(false, 0).total;
+        e = ensure_smem(k_conv_tc<false>, g_smem_chunked, g_smem_mu, smem);
+        if (e == cudaSuccess)
+            k_conv_tc<false><<<(unsigned)tiles[0].size(), NTHR, smem, stream>>>(
+                L.jobs_dev, (const Tile *)d_tiles + tiles[1].size(), L.h_dev, L.src_dev, L.y_dev,
                 L.noise_partials_dev);
     }
     if (e == cudaSuccess) e = cudaGetLastError();

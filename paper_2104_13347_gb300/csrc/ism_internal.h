@@ -153,6 +153,9 @@ struct ConvLaunch {
     // in slot part_offset(j) + g * ceil(y_len / kConvTT) + b, written by the
     // convolution kernels when non-null (noise requested)
     double *noise_partials_dev;
+    // split-BF16 only: per-tile kernels for every RIR (small latency-bound
+    // batches) instead of the persistent kernel
+    int per_tile;
 };
 // Tile shape shared by both convolution kernels (and the noise partials).
 constexpr int kConvMG = 8;     // mics per tile
@@ -163,6 +166,11 @@ __host__ __device__ inline int conv_partials_per_job(int n_mics, int64_t y_len) 
 __host__ __device__ inline int conv_partial_slot(int mic0, int64_t t0, int64_t y_len) {
     return (int)(mic0 / kConvMG * ((y_len + kConvTT - 1) / kConvTT) + t0 / kConvTT);
 }
+// ism_convolve_batch with the kernel choice of ConvLaunch::per_tile (the
+// server passes true).
+int convolve_batch(const ism_conv_job *jobs, int64_t n_jobs, const float *h_dev,
+                   const float *src_dev, float *y_dev, uint64_t seed, int32_t precision,
+                   void *stream, bool per_tile);
 int launch_conv_f32(const ConvLaunch &L, cudaStream_t stream);
 int launch_conv_bf16x3(const ConvLaunch &L, cudaStream_t stream);
 // Tiles the persistent split-BF16 kernel makes of a room (n_mics mics,

@@ -311,8 +311,8 @@ void ism_server::launch(std::vector<std::shared_ptr<Req>> &take) {
         o.stats_dev = (int64_t *)(base + stats_off);
         int rc = ism_rir_batch_ex(rooms.data(), (int64_t)rooms.size(), base, hoffs.data(), &o, s);
         if (rc == ISM_OK)
-            rc = ism_convolve_batch(jobs.data(), (int64_t)jobs.size(), base, base, base, cfg.seed,
-                                    cfg.precision, s);
+            rc = convolve_batch(jobs.data(), (int64_t)jobs.size(), base, base, base, cfg.seed,
+                                cfg.precision, s, true);
         if (rc != ISM_OK) {
             status = rc;
             err = ism_last_error_string();
