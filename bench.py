@@ -169,10 +169,11 @@ def rank_seed(rank):
     return 1002 + 7919 * rank
 
 
-def cpu_sample(rooms, srcs, n_rir_rooms=6, n_conv_rooms=1):
+def cpu_sample(rooms, srcs, n_rir_rooms=6, n_conv_rooms=1, single_core=True):
     """Times the oracle (as it stands) on a bounded sample of the workload:
     the RIRs of n_rir_rooms rooms and the convolutions of n_conv_rooms rooms.
-    Returns step-equivalent taps/s for the sampled rooms."""
+    Returns step-equivalent taps/s for the sampled rooms (and, with
+    single_core, the same for one room on one core, timed separately)."""
     import oracle
     threads = oracle.max_threads()
     t0 = time.perf_counter()
@@ -184,11 +185,12 @@ def cpu_sample(rooms, srcs, n_rir_rooms=6, n_conv_rooms=1):
     t_conv = (time.perf_counter() - t0) * n_rir_rooms / n_conv_rooms
     taps = int(st[:, 2].sum())
     mic_samples = n_rir_rooms * N_MICS * (TS + LH - 1)
-    # single core: one room's RIRs and convolutions
-    t0 = time.perf_counter()
-    h1, st1 = oracle.rir_batch(rooms[:1], n_threads=1)
-    oracle.convolve_batch(h1, [srcs[0].astype(np.float64)], n_threads=1)
-    single = int(st1[:, 2].sum()) / (time.perf_counter() - t0)
+    single = None
+    if single_core:  # one room's RIRs and convolutions on one core
+        t0 = time.perf_counter()
+        h1, st1 = oracle.rir_batch(rooms[:1], n_threads=1)
+        oracle.convolve_batch(h1, [srcs[0].astype(np.float64)], n_threads=1)
+        single = int(st1[:, 2].sum()) / (time.perf_counter() - t0)
     return {"value": taps / (t_rir + t_conv), "unit": "taps/s", "cores": threads,
             "kind": "oracle", "single_core_value": single,
             "sample": (f"RIRs of {n_rir_rooms} rooms x {N_MICS} mics of the workload "
@@ -329,7 +331,7 @@ def run_reference(args, ws, rank):
     times, last = [], None
     for i in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        last = cpu_sample(rooms, srcs, n_rir_rooms=1, n_conv_rooms=1)
+        last = cpu_sample(rooms, srcs, n_rir_rooms=1, n_conv_rooms=1, single_core=False)
         if i >= args.warmup:
             times.append(time.perf_counter() - t0)
     line = {"metric": METRIC, "value": last["value"], "unit": "taps/s", "n_gpus": args.gpus,

@@ -257,8 +257,10 @@ int oracle_rir_batch(int64_t n_rirs, const int32_t *room_of, const double *room_
                      double *h, const int64_t *h_off, int64_t *stats, int n_threads)
 {
 #ifdef _OPENMP
-    if (n_threads > 0) omp_set_num_threads(n_threads);
-#pragma omp parallel for schedule(dynamic, 1)
+    /* a num_threads clause, not omp_set_num_threads: a one-thread call must
+     * not lower the thread count of later calls in the process */
+    const int nt = n_threads > 0 ? n_threads : omp_get_max_threads();
+#pragma omp parallel for num_threads(nt) schedule(dynamic, 1)
 #endif
     for (int64_t j = 0; j < n_rirs; ++j) {
         int r = room_of[j];
@@ -320,8 +322,8 @@ void oracle_convolve_batch(int64_t n_conv, const int32_t *room_of, const double 
                            const int64_t *y_off, int n_threads)
 {
 #ifdef _OPENMP
-    if (n_threads > 0) omp_set_num_threads(n_threads);
-#pragma omp parallel for schedule(dynamic, 1)
+    const int nt = n_threads > 0 ? n_threads : omp_get_max_threads();
+#pragma omp parallel for num_threads(nt) schedule(dynamic, 1)
 #endif
     for (int64_t j = 0; j < n_conv; ++j) {
         int r = room_of[j];
