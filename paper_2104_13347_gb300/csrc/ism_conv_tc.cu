@@ -26,11 +26,12 @@
 // current tile's MMAs.
 //
 // k_conv_tc (longer RIRs, and every RIR of the server's small batches): one
-// CTA per tile of 8 mics x 2048 outputs, 8 phases, two CTAs per SM; A holds
-// (hi / lo, mic, phase) rows, so the MMAs with B_hi and B_lo give all four
-// products.  The tile's whole source window is converted once when it fits
-// in shared memory (RIRs up to ~9k samples); beyond that each chunk converts
-// its own 2112-sample source window into its pipeline stage.
+// CTA per tile of 8 mics x 2048 outputs, 8 phases; A holds (hi / lo, mic,
+// phase) rows, so the MMAs with B_hi and B_lo give all four products.  The
+// tile's whole source window is converted once when it fits in shared
+// memory (RIRs up to 37689 samples; two CTAs per SM up to ~8.7k); beyond
+// that each chunk converts its own 2112-sample source window into its
+// pipeline stage.
 //
 // In both, the raw RIR values of each chunk are staged with cp.async
 // (zero-filled outside the RIR), converted once per value into bf16 hi / lo

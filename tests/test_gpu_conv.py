@@ -97,7 +97,7 @@ def test_conv_long_rir_and_many_mics(ism):
 def test_conv_kernel_boundary(ism):
     """RIRs of 10609 samples (the longest the persistent three-product kernel
     takes: its stages, two tile windows and 1 KB of static shared memory fill
-    exactly the 227 KB a block may use) and 10610 (the per-chunk kernel) in
+    exactly the 227 KB a block may use) and 10610 (the per-tile kernel) in
     one batch, both precisions; each room's result is the same, bit for bit,
     when it is convolved alone."""
     rng = np.random.default_rng(21)
