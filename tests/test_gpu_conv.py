@@ -117,6 +117,40 @@ def test_conv_kernel_boundary(ism):
             np.testing.assert_array_equal(alone, g)
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_conv_degenerate_sizes(ism, precision):
+    """1-sample RIRs and sources, one mic and nine mics (a partial 8-mic
+    group), in one batch: each (room, mic) within the bar of the oracle."""
+    rng = np.random.default_rng(31)
+    shapes = [(1, 1, 1), (1, 1, 5000), (2, 3000, 1), (9, 1, 2), (9, 700, 3), (1, 4097, 4095)]
+    hs = [(rng.standard_normal((M, L)) + 0.5).astype(np.float32) for M, L, _ in shapes]
+    ss = [(rng.standard_normal(T) + 0.25).astype(np.float32) for _, _, T in shapes]
+    got = run_conv(ism, hs, ss, precision)
+    ref = oracle.convolve_batch([h.astype(np.float64) for h in hs],
+                                [s.astype(np.float64) for s in ss])
+    for i, (g, r) in enumerate(zip(got, ref)):
+        assert g.shape == r.shape, i
+        for m in range(g.shape[0]):
+            assert rel_l2(g[m], r[m]) <= TOL[precision], (i, m)
+
+
+def test_conv_all_three_tensor_core_paths_in_one_call(ism):
+    """RIRs of 2000 (persistent three-product kernel), 20000 (per-tile
+    kernel, whole source window) and 40000 samples (per-tile kernel,
+    per-chunk windows) in one split-BF16 call, against the oracle."""
+    rng = np.random.default_rng(32)
+    lens, mics, srcl = (2000, 20000, 40000), (3, 2, 2), (6000, 3000, 2500)
+    hs = [(rng.standard_normal((M, L)) * np.exp(-np.arange(L) / 4000)).astype(np.float32)
+          for M, L in zip(mics, lens)]
+    ss = [rng.standard_normal(T).astype(np.float32) for T in srcl]
+    got = run_conv(ism, hs, ss, 1)
+    ref = oracle.convolve_batch([h.astype(np.float64) for h in hs],
+                                [s.astype(np.float64) for s in ss])
+    for i, (g, r) in enumerate(zip(got, ref)):
+        for m in range(g.shape[0]):
+            assert rel_l2(g[m], r[m]) <= TOL[1], (i, m)
+
+
 def test_conv_delta_rir_exact(ism):
     rng = np.random.default_rng(8)
     s = rng.standard_normal(3000).astype(np.float32)
