@@ -10,9 +10,10 @@
 // rows shift by 8 elements = 16 bytes, read straight from a linear copy of
 // the source in shared memory through a no-swizzle K-major descriptor with
 // leading-dimension offset 16 B and stride offset 128 B (core matrices
-// overlap), and the RIR operand A is materialised per chunk of taps.
+// overlap), and the RIR operand A is materialised per chunk of taps (in
+// TMEM for k_conv_tcp, in shared memory for k_conv_tc).
 //
-// k_conv_tcp (RIRs up to 10609 samples, the dataset's case): a persistent
+// k_conv_tcp (RIRs up to 22897 samples, the dataset's case): a persistent
 // kernel, one CTA per SM.  A tile is 8 mics x 4096 outputs, 16 phases; the
 // taps are split by parity so that both parity windows of the source are
 // again 16-byte-shifted Toeplitz matrices.  Its 128 GEMM rows are (mic,
@@ -21,9 +22,10 @@
 // lo part is within 2^-8 of its value, so lo.lo is within 2^-16 of the
 // product: the order of the split's own representation error, and adding it
 // back does not lower the largest rel-L2 error over the dataset's RIRs).
-// Two 256-column TMEM accumulators and two source-window buffers let one
-// tile's epilogue and the next tile's window conversion run under the
-// current tile's MMAs.
+// The A operands go straight from the producers' registers into TMEM
+// (tcgen05.st), so shared memory carries only the source windows the MMAs
+// read as B; two source-window buffers let the next tile's window
+// conversion run under the current tile's MMAs.
 //
 // k_conv_tc (longer RIRs, and every RIR of the server's small batches): one
 // CTA per tile of 8 mics x 2048 outputs, 8 phases; A holds (hi / lo, mic,
@@ -488,36 +490,37 @@ k_conv_tc(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles,
 }
 
 // ===========================================================================
-// k_conv_tcp: persistent convolution with three products and no lo rows,
-// for RIRs whose two tile windows fit (rir_len up to 10609 samples)
+// k_conv_tcp: persistent convolution with three products, A in TMEM, for
+// RIRs whose two tile windows fit (rir_len up to 22897 samples)
 // ===========================================================================
 // A tile is 8 mics x 4096 outputs t = T0 + 16 n + p (n < 256, p < 16).
 // With k = 2 kappa + b split by parity b, B_b[kappa][n] = s[c0 + b + 2 kappa
 // + 16 n] is the Toeplitz matrix of the source's parity-b samples, whose
 // rows again shift by 8 elements (16 bytes), and A_b[(m, p)][kappa] =
-// h_m[Lh - 1 + p - b - 2 kappa].  GEMM row R = 16 m + 8 (p % 2) + p / 2 holds
-// (mic m, phase p): the eight lanes of a producer's 128-bit store phase then
-// fill one 128-byte row group without bank conflicts.  Per parity the MMAs
-// hi.hi, lo.hi and hi.lo accumulate into one 128 x 256 FP32 accumulator, so
-// no hi / lo rows are merged in the epilogue.
+// h_m[Lh - 1 + p - b - 2 kappa].  GEMM row (TMEM lane) R = 64 (p % 2) +
+// 8 m + p / 2 holds (mic m, phase p), so that each producer warp writes the
+// 32 lanes of its own TMEM lane quadrant.  Per parity the MMAs hi.hi, lo.hi
+// and hi.lo (A from TMEM, B from shared memory) accumulate into one
+// 128 x 256 FP32 accumulator, so no hi / lo rows are merged in the epilogue.
 //
 // One CTA per SM walks its tiles (blockIdx.x, + gridDim.x, ...).  Warps 0-7
-// build the operands of 64-tap chunks into three stages (warps 0-3 the hi
-// parts, 4-7 the lo parts) and, a slice per chunk, convert the next tile's
-// source window into the other of two window buffers (the slice's source
-// values are loaded one chunk before they are stored); warp 8 allocates 512
-// TMEM columns (two accumulators) and one lane issues the MMAs; warps 9-12
-// drain one accumulator (write y, sum y^2) while the next tile's MMAs fill
-// the other.  Barriers: full / empty per stage; win[b] (the window buffer's
-// tile has had its last MMA); accf[b] (a tile's MMAs are done); acce[b] (its
-// accumulator is drained).  Every wait is bounded.
+// build the A operands of 64-tap chunks into three TMEM stages of 64
+// columns (warps 0-3 the hi parts, 4-7 the lo parts) and, a slice per chunk,
+// convert the next tile's source window into the other of two window
+// buffers (the slice's source values are loaded one chunk before they are
+// stored); warp 8 allocates 512 TMEM columns (the accumulator in 0-255, the
+// stages from 256) and one lane issues the MMAs; warps 9-12 drain the
+// accumulator (write y, sum y^2), which the next tile's first MMA waits for.
+// Barriers: full / empty per stage; win[b] (the window buffer's tile has had
+// its last MMA); accf (a tile's MMAs are done); acce (the accumulator is
+// drained).  Every wait is bounded.
 constexpr int P_PH = 16;                 // output phases per row set
 constexpr int P_TT = P_PH * NN;          // outputs per tile (4096)
 static_assert(P_TT == 2 * kConvTT, "a tile covers two noise-partial slots");
 constexpr int P_KC = 64;                 // k values per chunk: 32 per parity
-constexpr int P_NS = 3;                  // operand stages
-constexpr int P_AMAT = 128 * 32 * 2;     // one operand: 128 rows x 32 kappa, bf16 (8 KB)
-constexpr int P_ABYTES = 4 * P_AMAT;     // (parity, hi / lo) operands of one chunk
+constexpr int P_NS = 3;                  // operand stages (in TMEM)
+constexpr int P_ACOL = 256;              // TMEM column of stage 0 (after the accumulator)
+constexpr int P_SCOL = 64;               // TMEM columns per stage: [parity][hi / lo][32 kappa / 2]
 constexpr int P_STG = 8 * 80;            // raw RIR per chunk: 8 mics x 80 values
 constexpr int P_PB = 4;                  // raw RIR staging buffers (ring)
 constexpr int P_PD = 3;                  // chunks staged ahead
@@ -542,14 +545,14 @@ struct PLayout {
     int bl;
 };
 
-// Layout for RIRs of at most max_lh samples: stages, raw staging (P_PB
+// Shared-memory layout for RIRs of at most max_lh samples: raw staging (P_PB
 // chunks), two converted chunks, two tile windows of four [parity][hi / lo]
-// arrays of bl elements.
+// arrays of bl elements (the A operands live in TMEM).
 __host__ __device__ inline PLayout p_layout(int64_t max_lh) {
     PLayout L;
     const int n_ch = (int)((max_lh + 15 + P_KC - 1) / P_KC);
     L.bl = (n_ch * 32 + 8 * (NN - 1) + 8 + 7) & ~7;
-    L.stg = (size_t)P_NS * P_ABYTES;
+    L.stg = 0;
     L.cv = L.stg + (size_t)P_STG * P_PB * 4;
     L.win = L.cv + (size_t)2 * P_CVW * 4;
     L.win_bytes = (size_t)4 * L.bl * 2;
@@ -614,46 +617,51 @@ __device__ __forceinline__ PTile p_tile(const ConvJob *jobs, const Tile *tiles, 
     return t;
 }
 
-// Operand rows of thread (m, p) for one chunk, p of parity PAR.  Element kl
-// (kappa = 32 ch + kl) of operand (b, q) is part_q(stg[m][e_b - 2 kl]), e_b =
-// 63 + p - b; word w of k-group kg takes kl = 8 kg + 2w, 8 kg + 2w + 1, the
-// same half (high if e_b is odd) of cv words I_b - kl and I_b - kl - 1, I_b =
-// e_b >> 1.  For even p, I_0 = I_1; for odd p, I_0 = I_1 + 1.
+// Operand rows of thread (m, p) for one chunk, p of parity PAR, written
+// into the thread's TMEM lane.  Element kl (kappa = 32 ch + kl) of operand
+// (b, q) is part_q(stg[m][e_b - 2 kl]), e_b = 63 + p - b; word w of k-group
+// kg takes kl = 8 kg + 2w, 8 kg + 2w + 1, the same half (high if e_b is odd)
+// of cv words I_b - kl and I_b - kl - 1, I_b = e_b >> 1.  For even p, I_0 =
+// I_1; for odd p, I_0 = I_1 + 1.  Operand (b, q) takes the 16 columns
+// taddr + (2 b + q) 16 + [0, 16): column c holds kl = 2c (low half) and
+// 2c + 1, the packing of a K-major A operand in TMEM.
 template <int PAR>
-__device__ __forceinline__ void p_rows(const uint32_t *cvb, unsigned char *st, int m, int p,
-                                       int q, uint32_t rowoff) {
+__device__ __forceinline__ void p_rows(const uint32_t *cvb, uint32_t taddr, int m, int p, int q) {
     const int I1 = (62 + p) >> 1;  // I_1 (odd p: (61 + p) / 2 = (62 + p) >> 1 too)
-    {
-        const uint32_t *cv = cvb + q * (P_CVW / 2) + m * 40 + (I1 - 31);
-        uint32_t W[33];
+    const uint32_t *cv = cvb + q * (P_CVW / 2) + m * 40 + (I1 - 31);
+    uint32_t W[33];
 #pragma unroll
-        for (int k = 0; k < 33; ++k) W[k] = (PAR == 1 || k < 32) ? cv[k] : 0u;
+    for (int k = 0; k < 33; ++k) W[k] = (PAR == 1 || k < 32) ? cv[k] : 0u;
 #pragma unroll
-        for (int b = 0; b < 2; ++b) {
-            // window offset of operand b in W, and its half
-            const int off = (PAR == 1 && b == 0) ? 1 : 0;
-            const uint32_t sel = ((PAR == 0) == (b == 0)) ? 0x7632u : 0x5410u;
+    for (int b = 0; b < 2; ++b) {
+        // window offset of operand b in W, and its half
+        const int off = (PAR == 1 && b == 0) ? 1 : 0;
+        const uint32_t sel = ((PAR == 0) == (b == 0)) ? 0x7632u : 0x5410u;
+        uint32_t v[16];
 #pragma unroll
-            for (int kg = 0; kg < 4; ++kg) {
-                uint4 row;
-                row.x = __byte_perm(W[off + 31 - 8 * kg], W[off + 30 - 8 * kg], sel);
-                row.y = __byte_perm(W[off + 29 - 8 * kg], W[off + 28 - 8 * kg], sel);
-                row.z = __byte_perm(W[off + 27 - 8 * kg], W[off + 26 - 8 * kg], sel);
-                row.w = __byte_perm(W[off + 25 - 8 * kg], W[off + 24 - 8 * kg], sel);
-                *reinterpret_cast<uint4 *>(st + (2 * b + q) * P_AMAT + kg * 2048 + rowoff) = row;
-            }
-        }
+        for (int kg = 0; kg < 4; ++kg)
+#pragma unroll
+            for (int w = 0; w < 4; ++w)
+                v[4 * kg + w] = __byte_perm(W[off + 31 - 8 * kg - 2 * w],
+                                            W[off + 30 - 8 * kg - 2 * w], sel);
+        asm volatile(
+            "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,"
+            "%12,%13,%14,%15,%16};" ::"r"(taddr + (uint32_t)((2 * b + q) * 16)),
+            "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]),
+            "r"(v[7]), "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]),
+            "r"(v[14]), "r"(v[15])
+            : "memory");
     }
 }
 
-// D (TMEM) (+)= A B, instruction descriptor idesc (kIdesc with its N field
-// replaced for narrower MMAs).
-__device__ __forceinline__ void mma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t acc,
-                                        uint32_t idesc) {
+// D (TMEM) (+)= A (TMEM, K-major bf16 pairs) B (shared-memory descriptor), instruction
+// descriptor idesc (kIdesc with its N field replaced for narrower MMAs).
+__device__ __forceinline__ void mma_f16_ts(uint32_t d, uint32_t a_tmem, uint64_t b, uint32_t acc,
+                                           uint32_t idesc) {
     asm volatile(
         "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
+        "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc));
 }
 
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
@@ -716,11 +724,10 @@ k_conv_tcp(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles, int
         const int q = warp >> 2;
         const int par = (warp >> 1) & 1;
         const int i64 = (warp & 1) * 32 + lane;
-        // operand row R = 16 m + 8 par + j holds phase p = 2 j + par of mic m
-        // (the eight lanes of a store phase then fill one 128-byte row group)
+        // operand row R = 64 par + 8 m + j (the warp's TMEM lane quadrant,
+        // warp % 4, times 32, plus its lane) holds phase p = 2 j + par of mic m
         const int m = i64 >> 3, p = 2 * (i64 & 7) + par;
-        const int R = 16 * m + 8 * par + (i64 & 7);
-        const uint32_t rowoff = (uint32_t)((R >> 3) * 128 + (R & 7) * 16);
+        const uint32_t tlane = (uint32_t)(32 * (warp & 3)) << 16;
         float *stg = reinterpret_cast<float *>(smem + Lay.stg);
         const uint32_t stg_u32 = smem_u32(stg);
         uint32_t *cvb0 = reinterpret_cast<uint32_t *>(smem + Lay.cv);
@@ -851,9 +858,14 @@ k_conv_tcp(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles, int
                 // buffer (i + P_PD) % P_PB was last read by chunk i - 1's conversion
                 if (i + P_PD < T.n_live) stage_rir(ch + P_PD, (i + P_PD) % P_PB);
                 else asm volatile("cp.async.commit_group;" ::: "memory");
-                unsigned char *st = smem + (size_t)s * P_ABYTES;
-                if (par) p_rows<1>(cvb, st, m, p, q, rowoff);
-                else p_rows<0>(cvb, st, m, p, q, rowoff);
+                // stage s's TMEM columns are free (its MMAs completed)
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t ta = tmem + tlane + (uint32_t)(P_ACOL + s * P_SCOL);
+                if (par) p_rows<1>(cvb, ta, m, p, q);
+                else p_rows<0>(cvb, ta, m, p, q);
+                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                // (orders this thread's earlier window-slice stores for the MMAs)
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 mbar_arrive(smem_u32(&bar_full[s]));
                 // a slice of the next tile's window, after the chunk is released
@@ -888,13 +900,14 @@ k_conv_tcp(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles, int
             int gi = 0;
             for (int lt = 0; lt < n_my && !s_abort; ++lt) {
                 const PTile T = p_tile(jobs, tiles, (int)blockIdx.x + lt * (int)gridDim.x);
-                const int ab = lt & 1, wb = lt & 1;
-                if (lt >= 2 && !mbar_wait(smem_u32(&bar_acce[ab]), ((lt >> 1) - 1) & 1)) {
+                const int wb = lt & 1;
+                // one accumulator: the previous tile's epilogue has drained it
+                if (lt >= 1 && !mbar_wait(smem_u32(&bar_acce[0]), (lt - 1) & 1)) {
                     s_abort = 1;
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;");
-                const uint32_t d = tmem + (uint32_t)(ab * 256);
+                const uint32_t d = tmem;
                 const uint32_t w0 = smem_u32(smem + Lay.win + wb * Lay.win_bytes);
                 const uint32_t wstr = (uint32_t)bl * 2u;
                 uint32_t acc = 0;
@@ -907,7 +920,7 @@ k_conv_tcp(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles, int
                         break;
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;");
-                    const uint32_t a0 = smem_u32(smem + (size_t)s * P_ABYTES);
+                    const uint32_t a0 = tmem + (uint32_t)(P_ACOL + s * P_SCOL);
                     // live columns: column n of chunk ch reads source samples
                     // base + 16 n + [0, 64); the others only multiply zero
                     // padding and are left out (the first chunk takes all 256
@@ -930,22 +943,22 @@ k_conv_tcp(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles, int
                     for (int kk = 0; kk < 2; ++kk) {
 #pragma unroll
                         for (int b = 0; b < 2; ++b) {
-                            const uint64_t ahi = make_desc(a0 + (2 * b) * P_AMAT + kk * 4096, 2048, 128);
-                            const uint64_t alo =
-                                make_desc(a0 + (2 * b + 1) * P_AMAT + kk * 4096, 2048, 128);
+                            // A (hi, lo) of parity b, k-slice kk: 8 TMEM columns each
+                            const uint32_t ahi = a0 + (uint32_t)((2 * b) * 16 + 8 * kk);
+                            const uint32_t alo = ahi + 16u;
                             const uint32_t bb = w0 + 64u * (uint32_t)ch + 32u * (uint32_t)kk +
                                                 16u * (uint32_t)n0;
                             const uint64_t bhi = make_desc(bb + (2 * b) * wstr, 16, 128);
                             const uint64_t blo = make_desc(bb + (2 * b + 1) * wstr, 16, 128);
-                            mma_f16(dn, ahi, bhi, acc, idesc);
+                            mma_f16_ts(dn, ahi, bhi, acc, idesc);
                             acc = 1;
-                            mma_f16(dn, alo, bhi, 1, idesc);
-                            mma_f16(dn, ahi, blo, 1, idesc);
+                            mma_f16_ts(dn, alo, bhi, 1, idesc);
+                            mma_f16_ts(dn, ahi, blo, 1, idesc);
                         }
                     }
                     mma_commit(smem_u32(&bar_empty[s]));
                 }
-                mma_commit(smem_u32(&bar_accf[ab]));  // the tile's MMAs done
+                mma_commit(smem_u32(&bar_accf[0]));  // the tile's MMAs done
                 mma_commit(smem_u32(&bar_win[wb]));   // its window buffer free
                 if (aborted) break;
             }
@@ -955,18 +968,18 @@ k_conv_tcp(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles, int
     } else {
         // ------------------------------------------------------------------
         // epilogue (warps 9-12): TMEM lane quadrant warp % 4 = rows 32 qd ..
-        // 32 qd + 31 = (m = R / 16, p = 2 (R % 8) + (R / 8) % 2); column n is
-        // output T0 + 16 n + p
+        // 32 qd + 31 = (par = R / 64, m = (R / 8) % 8, p = 2 (R % 8) + par);
+        // column n is output T0 + 16 n + p
         // ------------------------------------------------------------------
         const int qd = warp & 3;
-        const int R = 32 * qd + lane, m = R >> 4, p = 2 * (R & 7) + ((R >> 3) & 1);
+        const int R = 32 * qd + lane, m = (R >> 3) & 7, p = 2 * (R & 7) + (R >> 6);
         const int et = tid - 288;  // 0..127
         for (int lt = 0; lt < n_my; ++lt) {
             const PTile T = p_tile(jobs, tiles, (int)blockIdx.x + lt * (int)gridDim.x);
             const ConvJob &J = jobs[T.tl.job];
-            const int ab = lt & 1;
+            const int ab = lt & 1;  // s_red buffer
             // after an abort the remaining tiles are written as zeros at once
-            bool ok = !s_abort && mbar_wait(smem_u32(&bar_accf[ab]), (lt >> 1) & 1);
+            bool ok = !s_abort && mbar_wait(smem_u32(&bar_accf[0]), lt & 1);
             asm volatile("tcgen05.fence::after_thread_sync;");
             ok = ok && !s_abort && T.n_live > 0;
             const int64_t ylen = J.y_len;
@@ -976,7 +989,7 @@ k_conv_tcp(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles, int
                 uint32_t r[32];
                 if (ok) {
                     const uint32_t addr =
-                        tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(ab * 256 + cb);
+                        tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)cb;
                     asm volatile(
                         "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,"
                         "%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,"
@@ -1007,7 +1020,7 @@ k_conv_tcp(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles, int
                 }
             }
             asm volatile("tcgen05.fence::before_thread_sync;");
-            mbar_arrive(smem_u32(&bar_acce[ab]));  // the accumulator may be refilled
+            mbar_arrive(smem_u32(&bar_acce[0]));  // the accumulator may be refilled
             const double rs = warp_sum_f64((double)ss + (double)se);
             if (lane == 0) s_red[ab][qd] = rs;
             asm volatile("bar.sync 2, 128;" ::: "memory");

@@ -95,13 +95,13 @@ def test_conv_long_rir_and_many_mics(ism):
 
 
 def test_conv_kernel_boundary(ism):
-    """RIRs of 10609 samples (the longest the persistent three-product kernel
-    takes: its stages, two tile windows and 1 KB of static shared memory fill
-    exactly the 227 KB a block may use) and 10610 (the per-tile kernel) in
-    one batch, both precisions; each room's result is the same, bit for bit,
-    when it is convolved alone."""
+    """RIRs of 22897 samples (the longest the persistent three-product kernel
+    takes: its RIR staging, two tile windows and 1 KB of static shared memory
+    fill exactly the 227 KB a block may use) and 22898 (the per-tile kernel)
+    in one batch, both precisions; each room's result is the same, bit for
+    bit, when it is convolved alone."""
     rng = np.random.default_rng(21)
-    lens, mics, srcl = (10609, 10610, 37), (3, 2, 9), (3000, 5000, 4100)
+    lens, mics, srcl = (22897, 22898, 37), (3, 2, 9), (3000, 5000, 4100)
     hs = [(rng.standard_normal((M, L)) * np.exp(-np.arange(L) / 2500)).astype(np.float32)
           for M, L in zip(mics, lens)]
     ss = [rng.standard_normal(T).astype(np.float32) for T in srcl]
@@ -135,11 +135,11 @@ def test_conv_degenerate_sizes(ism, precision):
 
 
 def test_conv_all_three_tensor_core_paths_in_one_call(ism):
-    """RIRs of 2000 (persistent three-product kernel), 20000 (per-tile
+    """RIRs of 2000 (persistent three-product kernel), 30000 (per-tile
     kernel, whole source window) and 40000 samples (per-tile kernel,
     per-chunk windows) in one split-BF16 call, against the oracle."""
     rng = np.random.default_rng(32)
-    lens, mics, srcl = (2000, 20000, 40000), (3, 2, 2), (6000, 3000, 2500)
+    lens, mics, srcl = (2000, 30000, 40000), (3, 2, 2), (6000, 3000, 2500)
     hs = [(rng.standard_normal((M, L)) * np.exp(-np.arange(L) / 4000)).astype(np.float32)
           for M, L in zip(mics, lens)]
     ss = [rng.standard_normal(T).astype(np.float32) for T in srcl]
