@@ -47,16 +47,18 @@ K1_BINDING = {"issue_active_pct": 78.8, "smem_wavefronts_pct_of_peak": 85.4,
               "fma_pipe_pct": 39.6, "alu_pipe_pct": 29.9, "xu_pipe_pct": 22.9,
               "fp64_pipe_pct": 2.7, "shared_atomic_wavefronts_per_instruction": 3.63,
               "source": "ncu --set full, 256-room case"}
-K2_TRAFFIC_PER_ROOM = (83.592192e6 + 138.994176e6) / 256
+K2_TRAFFIC_PER_ROOM = (83.967744e6 + 139.09248e6) / 256
 
 
 def k2_live_chunks(ts, lh, kc=64, nn=256, phases=16):
-    """Live 64-tap chunks summed over the time tiles (phases x nn outputs) of
-    one mic group: the persistent tensor-core kernel skips chunks whose
-    source window is all padding."""
+    """Full-width chunk equivalents the persistent tensor-core kernel executes
+    for one mic group: its live 64-tap chunks over the time tiles (phases x nn
+    outputs), each weighted by the columns its MMAs cover (where the source's
+    edge cuts a chunk, only the live columns, in steps of 32; the first chunk
+    of a tile at full width)."""
     n_chunks = (lh + phases - 1 + kc - 1) // kc
     n_tiles = -(-(ts + lh - 1) // (phases * nn))
-    tot = 0
+    tot = 0.0
     for t in range(n_tiles):
         c0 = t * phases * nn - lh + 1
         lo = -c0 - (kc - 1 + phases * (nn - 1))
@@ -64,7 +66,15 @@ def k2_live_chunks(ts, lh, kc=64, nn=256, phases=16):
         hi = ts - 1 - c0
         hi = -1 if hi < 0 else hi // kc
         hi = min(hi, n_chunks - 1)
-        tot += max(hi - lo + 1, 0)
+        for i, ch in enumerate(range(lo, hi + 1)):
+            width = nn
+            if i > 0:
+                base = c0 + kc * ch
+                nl = max(-((63 + base) >> 4), 0)
+                nh = min((ts - 1 - base) >> 4, nn - 1)
+                if nl <= nh:
+                    width = ((nh | 31) + 1) - (nl & ~31)
+            tot += width / nn
     return tot
 
 
@@ -595,8 +605,9 @@ def run_ours(args, ws, rank):
 
     # K2 alone (no noise), timed back to back: split-BF16 needs at least the
     # three products hi.hi, hi.lo, lo.hi of 2 Ts Lh flops per mic; the kernel
-    # executes those three, as 12 MMAs of 128 x 256 x 16 per live 64-tap
-    # chunk of a 4096-output tile (the padding at the tile edges is the rest)
+    # executes those three, as 12 MMAs of 128 x N x 16 per live 64-tap chunk
+    # of a 4096-output tile (N = 256, or the live columns where the source's
+    # edge cuts the chunk; the padding at the tile edges is the rest)
     jobs_clean, _ = ism.conv_jobs([N_MICS] * n_rooms, [LH] * n_rooms, [TS] * n_rooms)
     k2_ms = None
     if precision == ism.BF16X3:
@@ -649,8 +660,9 @@ def run_ours(args, ws, rank):
             "executed_frac": k2_exec / (k2_ms * 1e-3) / bf16_peak, "ms": k2_ms,
             "traffic": K2_TRAFFIC_PER_ROOM * n_rooms,
             "traffic_note": "dram read+write of a 256-room ncu capture, scaled by rooms",
-            "work": "3 x 2 Ts Lh per mic (split-BF16 minimum); executed: 12 MMAs 128x256x16 "
-                    "per live 64-tap chunk per 4096-output tile",
+            "work": "3 x 2 Ts Lh per mic (split-BF16 minimum); executed: 12 MMAs 128xNx16 "
+                    "per live 64-tap chunk per 4096-output tile (N = 256 or the chunk's live "
+                    "columns)",
             "peak_note": f"dense bf16, {pk_kind} burst (kernel timed alone)"},
         "e2e": {"value": ws * taps / (e2e_ms * 1e-3), "unit": "taps/s",
                 "h2d_bytes_per_step": int(src_host.numel() * 4),

@@ -504,7 +504,7 @@ k_conv_tc(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles,
 // 128 x 256 FP32 accumulator, so no hi / lo rows are merged in the epilogue.
 //
 // One CTA per SM walks its tiles (blockIdx.x, + gridDim.x, ...).  Warps 0-7
-// build the A operands of 64-tap chunks into three TMEM stages of 64
+// build the A operands of 64-tap chunks into four TMEM stages of 64
 // columns (warps 0-3 the hi parts, 4-7 the lo parts) and, a slice per chunk,
 // convert the next tile's source window into the other of two window
 // buffers (the slice's source values are loaded one chunk before they are
@@ -518,7 +518,7 @@ constexpr int P_PH = 16;                 // output phases per row set
 constexpr int P_TT = P_PH * NN;          // outputs per tile (4096)
 static_assert(P_TT == 2 * kConvTT, "a tile covers two noise-partial slots");
 constexpr int P_KC = 64;                 // k values per chunk: 32 per parity
-constexpr int P_NS = 3;                  // operand stages (in TMEM)
+constexpr int P_NS = 4;                  // operand stages (in TMEM)
 constexpr int P_ACOL = 256;              // TMEM column of stage 0 (after the accumulator)
 constexpr int P_SCOL = 64;               // TMEM columns per stage: [parity][hi / lo][32 kappa / 2]
 constexpr int P_STG = 8 * 80;            // raw RIR per chunk: 8 mics x 80 values
