@@ -456,8 +456,8 @@ def run_frames(ism, n_frames, y, n_rooms, T, stream, hbm_gbs, pk_kind):
 def run_paper_dataset(ism, wl, n_sources, dev, stream):
     """RIR throughput on the paper's own dataset geometry: the 7 x 10 x 3.7 m
     classroom at RT 0.5 s, UMA-8 array, torus sources, 44.1 kHz, delay-limited
-    image sets; the benchmark spec 81-tap Hann sinc and the paper's 8-tap
-    Lagrange filter.  Projects the time of one room's 336000 RIRs."""
+    image sets; the 81-tap Hann sinc of the main workload and the paper's
+    8-tap Lagrange filter.  Projects the time of one room's 336000 RIRs."""
     import torch
     out = {"workload": f"{n_sources} torus sources x 7 mics, room 7x10x3.7 m, RT 0.5 s "
                        "(Sabine), 44.1 kHz, RIR 22050, order auto"}

@@ -1,7 +1,8 @@
 """The paper's own dataset workload on the GPU (Sec. II.A / III.A): the
 7 x 10 x 3.7 m classroom and the 5 x 5 x 4 m room at RT 0.5 s, UMA-8 array,
-torus sources, 44.1 kHz, delay-limited image sets, with the benchmark spec Hann
-sinc and the paper's 8-tap Lagrange filter; RIRs against the FP64 oracle."""
+torus sources, 44.1 kHz, delay-limited image sets, with the 81-tap Hann
+sinc of the main workload and the paper's 8-tap Lagrange filter; RIRs
+against the FP64 oracle."""
 import numpy as np
 import pytest
 
