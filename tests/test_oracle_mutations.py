@@ -23,6 +23,7 @@ MUTATIONS = {
     "dropped_term": ("double d2 = dx * dx + dy * dy;", "double d2 = dx * dx + dy * dx;"),
     "spreading": ("g / (4.0 * ORACLE_PI * im.d)", "g / (ORACLE_PI * im.d)"),
     "split_floor": ("double k = rint(im.tau);", "double k = floor(im.tau);"),
+    "window_width": ("cos(ORACLE_PI * t / (double)(H + 1))", "cos(ORACLE_PI * t / (double)H)"),
     "conv_index": ("acc += h[k] * s[t - k];\n        y[t] = acc;",
                    "acc += h[k] * s[t - k + (k > 0)];\n        y[t] = acc;"),
     "noise_branch": ("return (t & 1) ? r * sin(2.0 * ORACLE_PI * u2) : r * cos(2.0 * ORACLE_PI * u2);",

@@ -138,6 +138,32 @@ def test_hann_sinc_mirror_symmetry():
     np.testing.assert_allclose(a, b[::-1], rtol=0, atol=1e-16)
 
 
+def test_hann_sinc_three_taps_closed_form():
+    """The window's width and centring (reading D2: w(t) = (1 + cos(pi t /
+    (H + 1))) / 2 on t = j - f) in closed form.  Three taps (H = 1) at the
+    half-sample delay f = 1/2 sit at t = -3/2, -1/2, 1/2, where sin(pi t) =
+    1, -1, 1, cos(pi t / 2) = -sqrt(2)/2, sqrt(2)/2, sqrt(2)/2, so the taps
+    are -(1 - sqrt(2)/2) / (3 pi), (1 + sqrt(2)/2) / pi, (1 + sqrt(2)/2) / pi.
+    A window of width H instead of H + 1 would give 1/pi and -1/(3 pi)."""
+    r2 = math.sqrt(2.0) / 2.0
+    ref = np.array([-(1.0 - r2) / (3.0 * math.pi), (1.0 + r2) / math.pi,
+                    (1.0 + r2) / math.pi])
+    np.testing.assert_allclose(ref, [-0.0310769357, 0.5433889652, 0.5433889652], atol=1e-10)
+    np.testing.assert_allclose(oracle.hann_sinc_taps(0.5, 3), ref, rtol=0, atol=1e-15)
+
+
+def test_hann_sinc_81_taps_by_hand():
+    """Two taps of the 81-tap filter (H = 40) at f = 1/2, written out from
+    the reading's formula: the centre tap j = 0 (t = -1/2, sinc = 2/pi) is
+    (1 + cos(pi / 82)) / pi, the last tap j = 40 (t = 79/2, sin(pi t) = -1)
+    is -(1 + cos(79 pi / 82)) / (79 pi)."""
+    taps = oracle.hann_sinc_taps(0.5, 81)
+    centre = (1.0 + math.cos(math.pi / 82.0)) / math.pi
+    last = -(1.0 + math.cos(79.0 * math.pi / 82.0)) / (79.0 * math.pi)
+    assert abs(taps[40] - centre) <= 1e-13 * abs(centre)
+    assert abs(taps[80] - last) <= 1e-12 * abs(last)
+
+
 def test_hann_sinc_short_filter_window_positive():
     """Window 0.5(1+cos(pi t/(H+1))) stays positive on every tap, so every
     tap has the sign of the sinc."""
