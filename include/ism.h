@@ -194,8 +194,11 @@ int ism_rir_filter_terms(int32_t fd_kind, int32_t n_taps, int32_t *n_terms);
  *  - all calls share the array, which keeps the last call's contents; each
  *    call clears what must start at zero, but calls that overlap on the GPU
  *    (on different streams) race on it, so serialise them;
- *  - job tables are copied from a host stack buffer with pageable copies,
- *    which may make the call wait for earlier work on the stream. */
+ *  - the job table reaches the device as the arguments of small kernels
+ *    enqueued on `stream` (up to 128 RIRs each), so the call never waits for
+ *    the stream and reads no host memory after it returns;
+ *  - a negative offset in h_offsets returns ISM_ERR_INVALID_ARG before
+ *    anything is launched. */
 int ism_rir_batch_noalloc(const ism_room *rooms, int64_t n_rooms, float *h_dev,
                           const int64_t *h_offsets, void *stream);
 

@@ -214,16 +214,46 @@ def rir_batch(rooms, h=None, h_offsets=None, window=0, per_room=False, stats=Non
     return h
 
 
+def _rir_extent(rooms, offs):
+    """Elements of h a RIR batch writes: the packed length, or with explicit
+    offsets the end of the farthest RIR."""
+    if isinstance(rooms, PreparedRooms):
+        if offs is None:
+            return rooms.h_len
+        lens = [int(rooms.arr[i].rir_len) for i in range(rooms.n)
+                for _ in range(int(rooms.arr[i].n_mics))]
+    else:
+        if offs is None:
+            return rir_batch_size(rooms)[1]
+        lens = [int(r["rir_len"]) for r in rooms
+                for _ in range(np.asarray(r["mics"]).reshape(-1, 3).shape[0])]
+    if len(offs) != len(lens):
+        raise ValueError(f"h_offsets has {len(offs)} entries for {len(lens)} RIRs")
+    return max((int(o) + L for o, L in zip(offs, lens)), default=0)
+
+
 def rir_batch_noalloc(rooms, h, h_offsets=None, stream=None):
-    """ism_rir_batch_noalloc: as rir_batch into an existing float32 CUDA
-    tensor h, through the entry point that allocates nothing."""
+    """ism_rir_batch_noalloc: as rir_batch (room dicts or PreparedRooms) into
+    an existing contiguous float32 CUDA tensor h that holds every RIR,
+    through the entry point that allocates nothing."""
+    import torch
     lib = load()
-    arr, keep = make_rooms(rooms)
+    if isinstance(rooms, PreparedRooms):
+        arr, keep, n = rooms.arr, [rooms.keep], rooms.n
+    else:
+        arr, keep = make_rooms(rooms)
+        n = len(rooms)
+    if not (isinstance(h, torch.Tensor) and h.dtype == torch.float32 and h.is_cuda
+            and h.is_contiguous()):
+        raise ValueError("h must be a contiguous float32 CUDA tensor")
     offs = None
     if h_offsets is not None:
         offs = np.ascontiguousarray(h_offsets, np.int64)
         keep.append(offs)
-    check(lib.ism_rir_batch_noalloc(arr, len(rooms), c_vp(h.data_ptr()),
+    need = _rir_extent(rooms, offs)
+    if h.numel() < need:
+        raise ValueError(f"h holds {h.numel()} floats, the batch writes {need}")
+    check(lib.ism_rir_batch_noalloc(arr, n, c_vp(h.data_ptr()),
                                     offs.ctypes.data if offs is not None else None,
                                     _stream_ptr(stream)))
     return h

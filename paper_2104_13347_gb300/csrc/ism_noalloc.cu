@@ -8,9 +8,10 @@
 // acceptable.  This entry point runs the same image-source kernel as
 // ism_rir_batch, but its scratch (the per-RIR job table and the work
 // counters) lives in the fixed device array below instead of a stream-ordered
-// allocation, and the job table is copied from a stack buffer instead of a
-// pinned staging block.  It calls no cudaMalloc, cudaFree, cudaHostAlloc or
-// other allocating routine.
+// allocation, and the job table reaches the device as the kernel arguments of
+// small store kernels (chunks of kChunk jobs, by value) instead of through a
+// pinned staging block, so no host memory is read after the call returns.  It
+// calls no cudaMalloc, cudaFree, cudaHostAlloc or other allocating routine.
 //
 // The array is a file-scope __device__ symbol: every GPU that loads this
 // library holds its 2 MiB until the process exits.  In host code its name is
@@ -62,7 +63,23 @@ int scratch_address(unsigned char **out) {
     return ISM_OK;
 }
 
-constexpr int kChunk = 128;  // jobs per host-to-device copy (stack buffer)
+constexpr int kChunk = 128;  // jobs per store kernel (18 KB of kernel arguments)
+
+// One chunk of the job table, passed by value as a kernel argument.
+struct JobChunk {
+    RirJob job[kChunk];
+};
+static_assert(sizeof(JobChunk) + 64 <= 32764, "kernel argument limit");
+
+// Writes n jobs of a chunk to dst; the first chunk of a launch also clears
+// the work counter of the image-source kernel that follows.
+__global__ void __launch_bounds__(kChunk)
+k_store_jobs(RirJob *__restrict__ dst, const __grid_constant__ JobChunk chunk, int n,
+             unsigned int *__restrict__ counter) {
+    const int i = threadIdx.x;
+    if (i < n) dst[i] = chunk.job[i];
+    if (counter && i == 0) *counter = 0u;
+}
 
 }  // namespace
 
@@ -96,27 +113,41 @@ extern "C" int ism_rir_batch_noalloc(const ism_room *rooms, int64_t n_rooms, flo
         if (count[k] && rir_smem_bytes(W, max_order[k], max_taps[k]) > kMaxDynSmem)
             return fail(ISM_ERR_INVALID_ARG, "window/order/taps need too much shared memory");
 
+    if (h_offsets) {  // checked before anything is launched
+        const int64_t n_rirs = count[0] + count[1];
+        for (int64_t j = 0; j < n_rirs; ++j)
+            if (h_offsets[j] < 0) return fail(ISM_ERR_INVALID_ARG, "negative h offset");
+    }
+
     unsigned char *base = nullptr;
     if (int st = scratch_address(&base)) return st;
     RirJob *jobs_dev[2] = {(RirJob *)(base + kCounterBytes),
                            (RirJob *)(base + kCounterBytes) + count[0]};
     unsigned int *counter_dev[2] = {(unsigned int *)base, (unsigned int *)(base + 16)};
 
-    // job tables, copied chunk by chunk from the stack (pageable copies are
-    // staged by the driver before cudaMemcpyAsync returns)
-    RirJob buf[kChunk];
+    // job tables, chunk by chunk as kernel arguments (the counter of kind k
+    // is cleared by its first chunk)
+    JobChunk buf;
     for (int k = 0; k < 2; ++k) {
         if (!count[k]) continue;
         int64_t j = 0, packed = 0, done = 0;
         int nb = 0;
+        auto store = [&]() -> int {
+            k_store_jobs<<<1, kChunk, 0, stream>>>(jobs_dev[k] + done, buf, nb,
+                                                    done == 0 ? counter_dev[k] : nullptr);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return cuda_fail(e, "launch k_store_jobs");
+            done += nb;
+            nb = 0;
+            return ISM_OK;
+        };
         for (int64_t r = 0; r < n_rooms; ++r) {
             const ism_room &R = rooms[r];
             for (int m = 0; m < R.n_mics; ++m, ++j) {
                 const int64_t off = h_offsets ? h_offsets[j] : packed;
                 packed += R.rir_len;
                 if (R.fd_kind != k) continue;
-                if (off < 0) return fail(ISM_ERR_INVALID_ARG, "negative h offset");
-                RirJob &J = buf[nb++];
+                RirJob &J = buf.job[nb++];
                 memset(&J, 0, sizeof(J));
                 for (int a = 0; a < 3; ++a) {
                     J.src[a] = R.src[a];
@@ -132,22 +163,12 @@ extern "C" int ism_rir_batch_noalloc(const ism_room *rooms, int64_t n_rooms, flo
                 J.n_windows = (int32_t)((R.rir_len + W - 1) / W);
                 J.h_offset = off;
                 J.stat_index = j;
-                if (nb == kChunk) {
-                    cudaError_t e = cudaMemcpyAsync(jobs_dev[k] + done, buf, nb * sizeof(RirJob),
-                                                    cudaMemcpyHostToDevice, stream);
-                    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(jobs)");
-                    done += nb;
-                    nb = 0;
-                }
+                if (nb == kChunk)
+                    if (int st = store()) return st;
             }
         }
-        if (nb) {
-            cudaError_t e = cudaMemcpyAsync(jobs_dev[k] + done, buf, nb * sizeof(RirJob),
-                                            cudaMemcpyHostToDevice, stream);
-            if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(jobs)");
-        }
-        cudaError_t e = cudaMemsetAsync(counter_dev[k], 0, sizeof(unsigned int), stream);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(counter)");
+        if (nb)
+            if (int st = store()) return st;
         RirLaunch L{jobs_dev[k], (int)count[k], wmax[k], W, max_order[k], max_taps[k], k,
                     h_dev, nullptr, counter_dev[k], nullptr, 0};
         if (int st = launch_rir(L, stream)) return st;

@@ -55,12 +55,46 @@ def test_noalloc_matches_allocating_entry_point(ism):
         assert o == hl
 
 
+def test_noalloc_explicit_offsets_through_the_binding(ism):
+    """Per-RIR offsets (RIRs in reverse order, gaps between them) through the
+    Python wrapper, against the allocating entry point given the same
+    offsets; the gaps keep the caller's NaN fill."""
+    import torch
+
+    rooms = wl.room_batch(3, seed=80, order=5, rir_len=1500, n_mics=3)
+    n_rirs, _ = ism.rir_batch_size(rooms)
+    L, gap = 1500, 37
+    offs = [(n_rirs - 1 - j) * (L + gap) + gap for j in range(n_rirs)]
+    total = n_rirs * (L + gap) + gap
+    ref = torch.full((total,), float("nan"), dtype=torch.float32, device="cuda")
+    ism.rir_batch(rooms, h=ref, h_offsets=offs)
+    prep = ism.PreparedRooms(rooms)
+    for call in range(2):
+        got = torch.full((total,), float("nan"), dtype=torch.float32, device="cuda")
+        ism.rir_batch_noalloc(prep if call else rooms, got, h_offsets=offs)
+        torch.cuda.synchronize()
+        g, r = got.cpu().numpy().astype(np.float64), ref.cpu().numpy().astype(np.float64)
+        filled = np.zeros(total, bool)
+        for o in offs:
+            filled[o:o + L] = True
+            assert rel_l2(g[o:o + L], r[o:o + L]) <= TOL, f"call {call}, RIR at {o}"
+        assert np.isnan(g[~filled]).all()
+    with pytest.raises(ValueError):
+        ism.rir_batch_noalloc(rooms, torch.empty(total - 1, device="cuda"), h_offsets=offs)
+
+
 def test_noalloc_rejects_more_rirs_than_its_scratch(ism):
+    import torch
     from paper_2104_13347_gb300 import _lib
 
     room = wl.room_batch(1, seed=79, order=1, rir_len=64,
                          n_mics=14561)[0]
     arr, keep = _lib.make_rooms([room])
-    st = _lib.load().ism_rir_batch_noalloc(arr, 1, ctypes.c_void_p(0x1000), None, None)
+    # a real buffer that holds the whole batch: a regression of the size
+    # check shows up as a wrong status, not as writes to a bad address
+    h = torch.zeros(14561 * 64, dtype=torch.float32, device="cuda")
+    st = _lib.load().ism_rir_batch_noalloc(arr, 1, ctypes.c_void_p(h.data_ptr()), None, None)
+    torch.cuda.synchronize()
     assert st == _lib.ISM_ERR_INVALID_ARG
     assert "14560" in _lib.last_error()
+    assert not h.any().item()
