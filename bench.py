@@ -648,10 +648,20 @@ def run_ours(args, ws, rank):
                      "binding": K1_BINDING,
                      "taps_per_s": taps / (rir_med * 1e-3),
                      "direct_formulation_bound_taps_per_s": direct_bound,
-                     "shared_atomics": {"achieved_per_s": atom_rate, "peak_per_s": atom_peak,
-                                        "frac": atom_rate / atom_peak,
-                                        "peak_note": "random-address u32 shared atomics, "
-                                                     "9.1 per clock per SM, measured"}},
+                     "k1_ms": rir_med,
+                     # the binding resource of K1: shared-memory atomics
+                     "shared_atomics_per_s": atom_rate, "shared_atomics_peak_per_s": atom_peak,
+                     "shared_atomics_frac": atom_rate / atom_peak,
+                     # K2 (tensor-core convolution, timed alone), scalars so
+                     # that every reader of the line keeps them
+                     "k2_kernel": "k_conv_tcp",
+                     "k2_ms": k2_ms,
+                     "k2_achieved_tflops": None if k2_ms is None else k2_alg / (k2_ms * 1e-3) / 1e12,
+                     "k2_peak_tflops": bf16_peak / 1e12,
+                     "k2_frac": None if k2_ms is None else k2_alg / (k2_ms * 1e-3) / bf16_peak,
+                     "k2_executed_frac": None if k2_ms is None else
+                     k2_exec / (k2_ms * 1e-3) / bf16_peak,
+                     "k2_traffic": K2_TRAFFIC_PER_ROOM * n_rooms},
         "roofline_k2": None if k2_ms is None else {
             "bound": "tensor", "kernel": "k_conv_tcp", "achieved": k2_alg / (k2_ms * 1e-3) / 1e12,
             "peak": bf16_peak / 1e12, "unit": "TFLOP/s",

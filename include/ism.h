@@ -418,6 +418,34 @@ int ism_serve_stats_get(ism_server *server, ism_serve_stats *out);
  * server memory; outstanding results become invalid. */
 int ism_serve_destroy(ism_server *server);
 
+/* ------------------------------------------------------------------------
+ * Kernel-reported errors.  The split-BF16 tensor-core convolution kernels
+ * bound every wait inside them (2 s): if one runs out, the kernel stops,
+ * writes zeros for the outputs it did not finish and records the failure in
+ * the call's status cell.  Batch calls return before their kernels run, so
+ * the failure is reported once the call's work has completed, as
+ * ISM_ERR_INTERNAL: by ism_stream_status on the call's stream, by the next
+ * ism_convolve_batch on that stream (which then launches nothing), by
+ * ism_dataset_batch (which waits for its work), and by ism_serve_poll /
+ * ism_serve_wait for the requests of a served batch.
+ * ------------------------------------------------------------------------ */
+
+/* Waits for every earlier call on `stream` (current device) that holds a
+ * status cell, then returns ISM_ERR_INTERNAL if any call on the stream
+ * reported a kernel error since the last report (the report clears it),
+ * ISM_OK otherwise. */
+int ism_stream_status(void *stream);
+
+/* Fault injection for tests of the error path (no counterpart in the paper).
+ * ISM_INJECT_CONV_WAIT: the next split-BF16 convolution launch (any thread)
+ * makes each of its CTAs' MMA issuer wait, before issuing anything, on a
+ * barrier that nothing arrives at, with every wait of that launch limited to
+ * 20 ms; the launch then stops as after a real timeout and its call reports
+ * ISM_ERR_INTERNAL.  0 cancels a pending injection.  Nothing faults or hangs:
+ * the waits are bounded and the kernels return. */
+#define ISM_INJECT_CONV_WAIT 1
+int ism_debug_inject(int32_t what);
+
 /* Message of the last error on the calling thread ("" if none). */
 const char *ism_last_error_string(void);
 

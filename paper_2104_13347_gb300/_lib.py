@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(HERE, "libism.so")
 ISM_OK, ISM_PENDING = 0, 1
 ISM_ERR_INVALID_ARG, ISM_ERR_OUT_OF_MEMORY, ISM_ERR_BUSY = 2, 3, 4
 ISM_ERR_TIMEOUT, ISM_ERR_CUDA, ISM_ERR_INTERNAL, ISM_ERR_UNKNOWN_TICKET = 5, 6, 7, 8
+INJECT_CONV_WAIT = 1
 FD_HANN_SINC, FD_LAGRANGE = 0, 1
 RIR_SPARSE, RIR_DIRECT = 0, 1
 F32, BF16X3 = 0, 1
@@ -91,6 +92,8 @@ SIGNATURES = {
     "ism_serve_copy": (c_i32, [c_vp, c_u64, c_vp, c_vp, c_vp]),
     "ism_serve_stats_get": (c_i32, [c_vp, c_vp]),
     "ism_serve_destroy": (c_i32, [c_vp]),
+    "ism_stream_status": (c_i32, [c_vp]),
+    "ism_debug_inject": (c_i32, [c_i32]),
     "ism_last_error_string": (ctypes.c_char_p, []),
     "ism_version": (ctypes.c_char_p, []),
 }
@@ -257,6 +260,19 @@ def rir_batch_noalloc(rooms, h, h_offsets=None, stream=None):
                                     offs.ctypes.data if offs is not None else None,
                                     _stream_ptr(stream)))
     return h
+
+
+def stream_status(stream=None):
+    """ism_stream_status: waits for the stream's calls that hold a status
+    cell and raises IsmError (ISM_ERR_INTERNAL) if a kernel of one of them
+    reported an error since the last report."""
+    check(load().ism_stream_status(_stream_ptr(stream)))
+
+
+def debug_inject(what=INJECT_CONV_WAIT):
+    """ism_debug_inject: test aid that makes the next split-BF16 convolution
+    launch stop on a bounded wait nothing ends (0 cancels)."""
+    check(load().ism_debug_inject(int(what)))
 
 
 def conv_jobs(rooms_mics, rir_lens, src_lens, snr_db=None, noise_ids=None, h_offsets=None,

@@ -592,6 +592,8 @@ int ism::convolve_batch(const ism_conv_job *jobs, int64_t n_jobs, const float *h
         c.part_offset = n_part;
         n_part += conv_partials_per_job(J.n_mics, c.y_len);
     }
+    // a kernel of an earlier call on this stream reported an error
+    if (int st = status_collect(stream, false)) return st;
     const size_t jb = cj.size() * sizeof(ConvJob);
     const size_t pb = any_noise ? (size_t)n_part * sizeof(double) : 0;
     void *scr = nullptr;
@@ -609,12 +611,24 @@ int ism::convolve_batch(const ism_conv_job *jobs, int64_t n_jobs, const float *h
     L.any_noise = any_noise;
     L.noise_partials_dev = any_noise ? (double *)((char *)scr + jb + 256) : nullptr;
     L.per_tile = per_tile ? 1 : 0;
-    int st = upload_async(scr, cj.data(), jb, stream);
+    StatusTicket tk;
+    int st = ISM_OK;
+    if (precision == ISM_BF16X3) {
+        // the tensor-core kernels' bounded waits report through a status cell
+        st = status_begin(&tk);
+        L.err_dev = tk.dev;
+        L.inject = st ? 0 : take_injection();
+    }
+    if (!st) st = upload_async(scr, cj.data(), jb, stream);
     if (!st) {
         if (precision == ISM_BF16X3) st = launch_conv_bf16x3(L, stream);
         else st = launch_conv_f32(L, stream);
     }
     if (!st) st = launch_noise(L, stream);
+    if (tk.cell >= 0) {
+        const int se = status_end(tk, stream, st == ISM_OK);
+        if (!st) st = se;
+    }
     scratch_free(scr, stream);
     return st;
 }

@@ -41,8 +41,9 @@
 // permutes.  Chunks whose source window is all zero padding are skipped.
 // Stages hand over through mbarriers (full: producer arrivals; empty:
 // tcgen05.commit).  Every wait is bounded: on timeout the kernel records an
-// error, stops issuing, waits (bounded) for its own MMAs, frees TMEM and
-// returns.
+// error in the call's status cell (host-mapped memory the host reads once the
+// call has completed), stops issuing, writes zeros for the outputs it did not
+// finish, waits (bounded) for its own MMAs, frees TMEM and returns.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -54,8 +55,6 @@
 #include "ism_internal.h"
 
 namespace ism {
-
-__device__ int g_conv_tc_error;  // set to 1 by a timed-out wait
 
 namespace {
 
@@ -98,14 +97,25 @@ __device__ __forceinline__ uint64_t make_desc(uint32_t addr, uint32_t lbo, uint3
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NN >> 3) << 17) |
                             ((128u >> 4) << 24);
 
+// Bounded waits of one launch: the call's status cell (host-mapped int,
+// set to 1 when a wait runs out; may be null), the limit of every wait, and
+// the test aid that makes the MMA issuer wait once on a barrier nothing
+// arrives at (ism_debug_inject).
+struct WaitCtl {
+    int *err;
+    unsigned long long limit_ns;
+    int inject;
+};
+
 __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
 
-// Waits for the given phase parity of an mbarrier, at most kWaitNs.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// Waits for the given phase parity of an mbarrier, at most w.limit_ns; on
+// timeout sets the call's status cell (host-mapped) and returns false.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const WaitCtl &w) {
     const unsigned long long t0 = global_ns();
     while (true) {
         uint32_t ok;
@@ -116,9 +126,12 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
             : "r"(bar), "r"(parity)
             : "memory");
         if (ok) return true;
-        if (global_ns() - t0 > kWaitNs) break;
+        if (global_ns() - t0 > w.limit_ns) break;
     }
-    atomicExch(&g_conv_tc_error, 1);
+    if (w.err) {
+        *reinterpret_cast<volatile int *>(w.err) = 1;
+        __threadfence_system();
+    }
     return false;
 }
 
@@ -204,9 +217,9 @@ template <bool WHOLE_B>
 __global__ void __launch_bounds__(NTHR, 1)
 k_conv_tc(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles,
           const float *__restrict__ h, const float *__restrict__ src, float *__restrict__ y,
-          double *__restrict__ part) {
+          double *__restrict__ part, const WaitCtl wc) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ __align__(8) uint64_t bar_full[NS], bar_empty[NS], bar_done;
+    __shared__ __align__(8) uint64_t bar_full[NS], bar_empty[NS], bar_done, bar_never;
     __shared__ double s_red[2];
     __shared__ uint32_t s_tmem;
     __shared__ volatile int s_abort;
@@ -237,6 +250,7 @@ k_conv_tc(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles,
                          "r"(1));
         }
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_done)), "r"(1));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_never)), "r"(1));
         asm volatile("fence.mbarrier_init.release.cluster;");
         s_abort = 0;
     }
@@ -292,7 +306,7 @@ k_conv_tc(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles,
         for (int i = 0; i < n_live; ++i) {
             const int ch = ch_lo + i, s = i % NS, u = i / NS, buf = i & 1;
             asm volatile("cp.async.wait_group 1;" ::: "memory");
-            const bool ok = (u == 0) || mbar_wait(smem_u32(&bar_empty[s]), (u - 1) & 1);
+            const bool ok = (u == 0) || mbar_wait(smem_u32(&bar_empty[s]), (u - 1) & 1, wc);
             if (producers_any(!ok || s_abort)) {  // uniform decision, also a barrier
                 s_abort = 1;
                 break;
@@ -359,9 +373,11 @@ k_conv_tc(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles,
         // MMA issuer
         // ------------------------------------------------------------------
         uint32_t acc = 0;
-        for (int i = 0; i < n_live; ++i) {
+        // test aid: a wait that nothing ends, before any MMA is issued
+        if (wc.inject && !mbar_wait(smem_u32(&bar_never), 0, wc)) s_abort = 1;
+        for (int i = 0; i < n_live && !s_abort; ++i) {
             const int ch = ch_lo + i, s = i % NS, u = i / NS;
-            if (!mbar_wait(smem_u32(&bar_full[s]), u & 1)) {
+            if (!mbar_wait(smem_u32(&bar_full[s]), u & 1, wc)) {
                 s_abort = 1;
                 break;
             }
@@ -406,7 +422,7 @@ k_conv_tc(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles,
     // goes through shared memory (the stage buffers are idle by then).
     // ----------------------------------------------------------------------
     bool ok = true;
-    if (warp < 4) ok = mbar_wait(smem_u32(&bar_done), 0);
+    if (warp < 4) ok = mbar_wait(smem_u32(&bar_done), 0, wc);
     asm volatile("tcgen05.fence::after_thread_sync;");
     __syncthreads();
     ok = ok && !s_abort && n_live > 0;
@@ -672,10 +688,11 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
 __global__ void __launch_bounds__(P_NT, 1)
 k_conv_tcp(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles, int n_tiles,
            int max_lh, const float *__restrict__ h, const float *__restrict__ src,
-           float *__restrict__ y, double *__restrict__ part, int h_aligned16) {
+           float *__restrict__ y, double *__restrict__ part, int h_aligned16,
+           const WaitCtl wc) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) uint64_t bar_full[P_NS], bar_empty[P_NS], bar_win[2], bar_accf[2],
-        bar_acce[2], bar_done;
+        bar_acce[2], bar_done, bar_never;
     __shared__ double s_red[2][4];
     __shared__ uint32_t s_tmem;
     __shared__ volatile int s_abort;
@@ -702,6 +719,7 @@ k_conv_tcp(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles, int
                          "r"(128));
         }
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_done)), "r"(1));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_never)), "r"(1));
         asm volatile("fence.mbarrier_init.release.cluster;");
         s_abort = 0;
     }
@@ -758,7 +776,8 @@ k_conv_tcp(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles, int
         };
         // the window buffer of tile lt is free once tile lt - 2's MMAs are done
         auto wait_window = [&](int lt) {
-            if (lt >= 2 && !mbar_wait(smem_u32(&bar_win[lt & 1]), ((lt >> 1) - 1) & 1)) s_abort = 1;
+            if (lt >= 2 && !mbar_wait(smem_u32(&bar_win[lt & 1]), ((lt >> 1) - 1) & 1, wc))
+                s_abort = 1;
         };
         if (n_my > 0) {
             const PTile T = p_tile(jobs, tiles, (int)blockIdx.x);
@@ -824,7 +843,7 @@ k_conv_tcp(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles, int
             for (int i = 0; i < T.n_live; ++i, ++gi) {
                 const int ch = T.ch_lo + i, s = gi % P_NS, u = gi / P_NS, buf = i % P_PB;
                 asm volatile("cp.async.wait_group %0;" ::"n"(P_PD - 1) : "memory");
-                const bool ok = (u == 0) || mbar_wait(smem_u32(&bar_empty[s]), (u - 1) & 1);
+                const bool ok = (u == 0) || mbar_wait(smem_u32(&bar_empty[s]), (u - 1) & 1, wc);
                 // the chunk as bf16 pairs (the pairs this thread staged), into
                 // the converted buffer that chunk gi - 2 read (every producer
                 // passed chunk gi - 1's barrier after its reads)
@@ -898,11 +917,13 @@ k_conv_tcp(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles, int
         // ------------------------------------------------------------------
         if (lane == 0) {
             int gi = 0;
+            // test aid: a wait that nothing ends, before any MMA is issued
+            if (wc.inject && !mbar_wait(smem_u32(&bar_never), 0, wc)) s_abort = 1;
             for (int lt = 0; lt < n_my && !s_abort; ++lt) {
                 const PTile T = p_tile(jobs, tiles, (int)blockIdx.x + lt * (int)gridDim.x);
                 const int wb = lt & 1;
                 // one accumulator: the previous tile's epilogue has drained it
-                if (lt >= 1 && !mbar_wait(smem_u32(&bar_acce[0]), (lt - 1) & 1)) {
+                if (lt >= 1 && !mbar_wait(smem_u32(&bar_acce[0]), (lt - 1) & 1, wc)) {
                     s_abort = 1;
                     break;
                 }
@@ -914,7 +935,7 @@ k_conv_tcp(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles, int
                 bool aborted = false;
                 for (int i = 0; i < T.n_live; ++i, ++gi) {
                     const int ch = T.ch_lo + i, s = gi % P_NS, u = gi / P_NS;
-                    if (!mbar_wait(smem_u32(&bar_full[s]), u & 1)) {
+                    if (!mbar_wait(smem_u32(&bar_full[s]), u & 1, wc)) {
                         s_abort = 1;
                         aborted = true;
                         break;
@@ -978,8 +999,14 @@ k_conv_tcp(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles, int
             const PTile T = p_tile(jobs, tiles, (int)blockIdx.x + lt * (int)gridDim.x);
             const ConvJob &J = jobs[T.tl.job];
             const int ab = lt & 1;  // s_red buffer
-            // after an abort the remaining tiles are written as zeros at once
-            bool ok = !s_abort && mbar_wait(smem_u32(&bar_accf[0]), lt & 1);
+            // after an abort the remaining tiles are written as zeros at once;
+            // a wait of its own that runs out aborts the CTA (its later
+            // accumulator phases would no longer match)
+            bool ok = !s_abort;
+            if (ok && !mbar_wait(smem_u32(&bar_accf[0]), lt & 1, wc)) {
+                s_abort = 1;
+                ok = false;
+            }
             asm volatile("tcgen05.fence::after_thread_sync;");
             ok = ok && !s_abort && T.n_live > 0;
             const int64_t ylen = J.y_len;
@@ -1037,7 +1064,7 @@ k_conv_tcp(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles, int
     __syncthreads();
     if (warp == 8) {
         // every issued MMA has completed before the columns are freed
-        mbar_wait(smem_u32(&bar_done), 0);
+        mbar_wait(smem_u32(&bar_done), 0, wc);
         asm volatile("tcgen05.fence::after_thread_sync;");
         __syncwarp();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
@@ -1107,6 +1134,11 @@ int launch_conv_bf16x3(const ConvLaunch &L, cudaStream_t stream) {
     all.insert(all.end(), ptiles.begin(), ptiles.end());
     st = upload_async(d_tiles, all.data(), n_tiles * sizeof(Tile), stream);
     if (st) { scratch_free(d_tiles, stream); return st; }
+    WaitCtl wc{L.err_dev, kWaitNs, 0};
+    if (L.inject) {
+        wc.inject = 1;
+        wc.limit_ns = 20000000ull;  // 20 ms: the injected wait and the aborts it causes
+    }
     cudaError_t e = cudaSuccess;
     if (!ptiles.empty()) {
         const size_t smem = p_layout(p_max_lh).total;
@@ -1116,7 +1148,7 @@ int launch_conv_bf16x3(const ConvLaunch &L, cudaStream_t stream) {
             k_conv_tcp<<<grid, P_NT, smem, stream>>>(
                 L.jobs_dev, (const Tile *)d_tiles + tiles[1].size() + tiles[0].size(),
                 (int)ptiles.size(), (int)p_max_lh, L.h_dev, L.src_dev, L.y_dev,
-                L.noise_partials_dev, (int)(((uintptr_t)L.h_dev & 15) == 0));
+                L.noise_partials_dev, (int)(((uintptr_t)L.h_dev & 15) == 0), wc);
     }
     if (e == cudaSuccess && !tiles[1].empty()) {
         const size_t smem = tc_layout(true, max_chunks).total;
@@ -1124,7 +1156,7 @@ int launch_conv_bf16x3(const ConvLaunch &L, cudaStream_t stream) {
         if (e == cudaSuccess)
             k_conv_tc<true><<<(unsigned)tiles[1].size(), NTHR, smem, stream>>>(
                 L.jobs_dev, (const Tile *)d_tiles, L.h_dev, L.src_dev, L.y_dev,
-                L.noise_partials_dev);
+                L.noise_partials_dev, wc);
     }
     if (e == cudaSuccess && !tiles[0].empty()) {
         const size_t smem = tc_layout(false, 0).total;
@@ -1132,7 +1164,7 @@ int launch_conv_bf16x3(const ConvLaunch &L, cudaStream_t stream) {
         if (e == cudaSuccess)
             k_conv_tc<false><<<(unsigned)tiles[0].size(), NTHR, smem, stream>>>(
                 L.jobs_dev, (const Tile *)d_tiles + tiles[1].size(), L.h_dev, L.src_dev, L.y_dev,
-                L.noise_partials_dev);
+                L.noise_partials_dev, wc);
     }
     if (e == cudaSuccess) e = cudaGetLastError();
     scratch_free(d_tiles, stream);

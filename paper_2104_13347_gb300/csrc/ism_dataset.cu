@@ -278,5 +278,10 @@ extern "C" int ism_dataset_batch(const ism_room *rooms, int64_t n_rooms, const f
     if (!st && e2 != cudaSuccess) st = cuda_fail(e2, "dataset download");
     if (!st && e3 != cudaSuccess) st = cuda_fail(e3, "dataset kernels");
     if (!st && e4 != cudaSuccess) st = cuda_fail(e4, "dataset kernels");
+    // kernel errors of the chunks' convolutions (the streams are drained)
+    for (int s = 0; s < 2; ++s) {
+        const int ks = status_collect(P.comp[s], false);
+        if (!st) st = ks;
+    }
     return st;
 }

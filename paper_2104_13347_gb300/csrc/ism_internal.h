@@ -156,6 +156,10 @@ struct ConvLaunch {
     // split-BF16 only: per-tile kernels for every RIR (small latency-bound
     // batches) instead of the persistent kernel
     int per_tile;
+    // split-BF16 only: the call's status cell (host-mapped; a kernel whose
+    // bounded wait runs out sets it), and the test aid of ism_debug_inject
+    int *err_dev;
+    int inject;
 };
 // Tile shape shared by both convolution kernels (and the noise partials).
 constexpr int kConvMG = 8;     // mics per tile
@@ -201,6 +205,28 @@ __device__ __forceinline__ double warp_sum_f64(double x) {
     return x;
 }
 #endif
+
+// Kernel status of a call (ism_status.cu).  A call whose kernels contain
+// bounded waits takes a status cell -- an int in page-locked, device-mapped
+// host memory, zeroed by the host -- and passes its device address to them;
+// a wait that runs out sets it.  After enqueueing, the call records an event
+// on its stream; once the event has completed, the host reads the cell.
+struct StatusTicket {
+    int device = -1;
+    int cell = -1;
+    int *dev = nullptr;
+};
+int status_begin(StatusTicket *t);
+// Records the ticket's completion event on `stream` (or, with ok = false,
+// gives the cell back at once: nothing was enqueued).
+int status_end(const StatusTicket &t, cudaStream_t stream, bool ok);
+// ISM_ERR_INTERNAL (with the message set) if a call on `stream` (current
+// device) whose kernels have completed reported an internal error since the
+// last report; ISM_OK otherwise.  wait: first wait for every call on the
+// stream that holds a status cell.
+int status_collect(cudaStream_t stream, bool wait);
+// Test aid (ism_debug_inject): returns and clears the pending injection.
+int take_injection();
 
 // SplitMix64 (Steele, Lea and Flood 2014): output i of the stream with
 // state x is mix(x + (i+1) * gamma).

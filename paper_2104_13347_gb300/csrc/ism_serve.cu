@@ -349,9 +349,21 @@ void ism_server::finish_batches() {
         cudaError_t e = cudaEventQuery(b->done);
         if (e == cudaErrorNotReady) continue;
         const auto now = Clock::now();
+        // kernel errors of the batch's convolution (its status cell; the
+        // slot's stream runs one batch at a time)
+        int kst = ISM_OK;
+        std::string kmsg;
+        if (e == cudaSuccess) {
+            kst = status_collect(streams[b->slot], false);
+            if (kst) kmsg = std::string("batch failed: ") + ism_last_error_string();
+        }
         for (auto &r : b->reqs) {
-            if (e == cudaSuccess) {
+            if (e == cudaSuccess && kst == ISM_OK) {
                 r->state = DONE;
+            } else if (e == cudaSuccess) {
+                r->state = FAILED;
+                r->status = kst;
+                r->error = kmsg;
             } else {
                 r->state = FAILED;
                 r->status = ISM_ERR_CUDA;
@@ -359,7 +371,7 @@ void ism_server::finish_batches() {
             }
             r->t_done = now;
         }
-        if (e == cudaSuccess) {
+        if (e == cudaSuccess && kst == ISM_OK) {
             for (int64_t i = 0; i < b->n_rirs; ++i) st.taps += b->stats_host[2 * i + 1];
             st.mic_samples += b->mic_samples;
         }

@@ -260,3 +260,13 @@ def test_dataset_batch_argument_errors(lib):
     arr2, keep2 = lib.make_rooms([good_room(src=[9.0, 1.0, 1.0])])
     assert call(rooms=arr2) == lib.ISM_ERR_INVALID_ARG
     assert lib.last_error()
+
+
+def test_debug_inject_arguments(lib):
+    """The fault-injection switch is host state only: unknown kinds are
+    rejected, 0 cancels a pending injection."""
+    L = lib.load()
+    assert L.ism_debug_inject(99) == lib.ISM_ERR_INVALID_ARG
+    assert "unknown injection" in lib.last_error()
+    assert L.ism_debug_inject(lib.INJECT_CONV_WAIT) == lib.ISM_OK
+    assert L.ism_debug_inject(0) == lib.ISM_OK

@@ -93,9 +93,13 @@ def test_serve_mix_matches_batch_api_and_alone(ism, precision):
         assert rel_l2(mixed[k][1], yd) < 1e-5
 
 
-def test_serve_parity_with_oracle(ism):
+@pytest.mark.parametrize("precision", [0, 1])
+def test_serve_parity_with_oracle(ism, precision):
+    """Served RIRs and signals against the FP64 oracle: the FP32 convolution
+    and the split-BF16 per-tile tensor-core kernel that every served
+    request takes."""
     reqs = requests(4, seed=5)
-    with ism.Server(precision=0) as srv:
+    with ism.Server(precision=precision) as srv:
         tickets = [srv.submit(r, s) for r, s, _, _ in reqs]  # no noise
         for t, (r, s, _, _) in zip(tickets, reqs):
             h, y, res = fetch(ism, srv, t, r, s)
@@ -122,3 +126,29 @@ def test_serve_hbm_admission_queues_requests(ism):
         assert st["completed"] == len(reqs)
         assert 0 < st["bytes_peak"] <= budget
         assert st["taps"] > 0 and st["mic_samples"] > 0
+
+
+def test_serve_split_bf16_short_rirs_against_oracle(ism):
+    """The server's split-BF16 convolution runs the per-tile kernel with the
+    tile's whole source window converted once; RIRs from a few hundred
+    samples to ~8.7k (two CTAs per SM) and partial 8-mic groups, each
+    (request, mic) against the oracle's convolution of the served RIR and
+    the served RIR against the oracle's RIR (1e-5 rel-L2 each)."""
+    rng = np.random.default_rng(41)
+    shapes = [(1, 200, 3000), (5, 1000, 700), (8, 2048, 4100), (12, 4097, 2500),
+              (3, 8700, 1500), (9, 333, 9000)]
+    reqs = []
+    for i, (M, L, T) in enumerate(shapes):
+        room = wl.room_batch(1, seed=4100 + i, order=int(rng.integers(2, 6)), rir_len=L,
+                             n_mics=M)[0]
+        reqs.append((room, rng.standard_normal(T).astype(np.float32)))
+    with ism.Server(precision=1, max_batch=3, n_streams=2) as srv:
+        tickets = [srv.submit(r, s) for r, s in reqs]
+        for t, (r, s) in zip(tickets, reqs):
+            h, y, _ = fetch(ism, srv, t, r, s)
+            href, _ = oracle.rir_batch([r])
+            yref = oracle.convolve_batch([h], [s.astype(np.float64)])[0]
+            for m in range(h.shape[0]):
+                assert rel_l2(h[m], href[0][m]) <= 1e-5, (r["rir_len"], m)
+                assert rel_l2(y[m], yref[m]) <= 1e-5, (r["rir_len"], m)
+            srv.release(t)
