@@ -112,15 +112,29 @@ typedef struct ism_room {
  *    formula and accumulated in a fixed order (bitwise reproducible). */
 typedef enum ism_rir_variant { ISM_RIR_SPARSE = 0, ISM_RIR_DIRECT = 1 } ism_rir_variant;
 
+/* ism_rir_opts.window = ISM_WINDOW_TUNE: the window the library's autotuner
+ * found fastest for the call's bucket -- the filter (kinds and tap counts),
+ * the largest lattice order, the sampling rate, the RIR length (power-of-two
+ * class), the number of RIRs (power-of-two class) and the variant.  The first
+ * call of a bucket tunes it: it runs the call once per candidate window (64
+ * to 2048 samples), timing each on `stream` with the host waiting, and
+ * finishes with the fastest, whose outputs it leaves; it returns
+ * ISM_ERR_INVALID_ARG if the stream is being captured then.  Choices are kept
+ * for the process and, if the environment variable ISM_TUNE_CACHE names a
+ * file, appended to it and read by later processes, so a tuned bucket keeps
+ * its window (and its RIRs stay bitwise reproducible).  Not with per_room. */
+#define ISM_WINDOW_TUNE (-1)
+
 /* Options of ism_rir_batch_ex (zero-initialise for defaults). */
 typedef struct ism_rir_opts {
     int32_t window;      /* output window per work item, samples (multiple of
                             32 in [32, 8192]); 0 = automatic: 1024, halved
                             down to 64 while the call has fewer than four
-                            work items per SM.  The automatic window depends
-                            on the whole call, so pass a fixed window when a
-                            RIR must be bitwise equal across calls of
-                            different sizes */
+                            work items per SM; ISM_WINDOW_TUNE = autotuned
+                            (above).  The automatic window depends on the
+                            whole call, so pass a fixed window when a RIR
+                            must be bitwise equal across calls of different
+                            sizes */
     int32_t per_room;    /* 1 = one plain launch per room (the unbatched path) */
     int64_t *stats_dev;  /* optional device int64[2 * n_rirs]: per RIR, the
                             images with a tap in [0, Lh) and the taps that
@@ -154,6 +168,13 @@ int ism_rir_batch(const ism_room *rooms, int64_t n_rooms, float *h_dev,
 /* As ism_rir_batch, with options (NULL = defaults). */
 int ism_rir_batch_ex(const ism_room *rooms, int64_t n_rooms, float *h_dev,
                      const int64_t *h_offsets, const ism_rir_opts *opts, void *stream);
+
+/* The window ISM_WINDOW_TUNE would use for this call (same rooms and
+ * options), or 0 if its bucket is not tuned yet (host only: reads the
+ * ISM_TUNE_CACHE file if set, runs nothing).  Errors: ISM_ERR_INVALID_ARG for
+ * invalid rooms or a NULL window. */
+int ism_rir_tuned_window(const ism_room *rooms, int64_t n_rooms, const ism_rir_opts *opts,
+                         int32_t *window);
 
 /* Number of RIRs (sum of n_mics) and packed h length of a batch, for sizing
  * buffers; host only. */

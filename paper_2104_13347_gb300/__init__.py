@@ -15,9 +15,10 @@ from ._lib import (BF16X3, F32, FD_HANN_SINC, FD_LAGRANGE, INJECT_CONV_WAIT, RIR
                    RIR_SPARSE, IsmError, PreparedRooms, check, conv_jobs, convolve_batch,
                    dataset_batch, debug_inject, frame_jobs, frames_batch, last_error, load,
                    make_rooms, rir_batch, rir_batch_noalloc, rir_batch_size, rir_filter_terms,
-                   Server, stream_status)
+                   rir_tuned_window, Server, stream_status, WINDOW_TUNE)
 
 __all__ = ["load", "rir_batch", "rir_batch_size", "rir_batch_noalloc", "convolve_batch",
            "conv_jobs", "dataset_batch", "frame_jobs", "frames_batch", "IsmError", "F32", "BF16X3", "FD_HANN_SINC", "FD_LAGRANGE", "RIR_SPARSE",
            "RIR_DIRECT", "last_error", "check", "make_rooms", "PreparedRooms", "rir_filter_terms", "Server",
-           "stream_status", "debug_inject", "INJECT_CONV_WAIT"]
+           "stream_status", "debug_inject", "INJECT_CONV_WAIT", "rir_tuned_window",
+           "WINDOW_TUNE"]

@@ -21,6 +21,7 @@ ISM_OK, ISM_PENDING = 0, 1
 ISM_ERR_INVALID_ARG, ISM_ERR_OUT_OF_MEMORY, ISM_ERR_BUSY = 2, 3, 4
 ISM_ERR_TIMEOUT, ISM_ERR_CUDA, ISM_ERR_INTERNAL, ISM_ERR_UNKNOWN_TICKET = 5, 6, 7, 8
 INJECT_CONV_WAIT = 1
+WINDOW_TUNE = -1
 FD_HANN_SINC, FD_LAGRANGE = 0, 1
 RIR_SPARSE, RIR_DIRECT = 0, 1
 F32, BF16X3 = 0, 1
@@ -80,6 +81,7 @@ SIGNATURES = {
     "ism_rir_batch_size": (c_i32, [c_vp, c_i64, c_vp, c_vp]),
     "ism_rir_batch_noalloc": (c_i32, [c_vp, c_i64, c_vp, c_vp, c_vp]),
     "ism_rir_filter_terms": (c_i32, [c_i32, c_i32, c_vp]),
+    "ism_rir_tuned_window": (c_i32, [c_vp, c_i64, c_vp, c_vp]),
     "ism_convolve_batch": (c_i32, [c_vp, c_i64, c_vp, c_vp, c_vp, c_u64, c_i32, c_vp]),
     "ism_frames_batch": (c_i32, [c_vp, c_i64, c_i32, c_vp, c_vp, c_u64, c_vp]),
     "ism_dataset_batch": (c_i32, [c_vp, c_i64, c_vp, c_vp, c_vp, c_vp, c_u64, c_u64, c_i32, c_vp,
@@ -171,6 +173,20 @@ def rir_batch_size(rooms):
     nr, hl = c_i64(), c_i64()
     check(load().ism_rir_batch_size(arr, len(rooms), ctypes.byref(nr), ctypes.byref(hl)))
     return nr.value, hl.value
+
+
+def rir_tuned_window(rooms, variant=RIR_SPARSE):
+    """The window rir_batch(..., window=WINDOW_TUNE) uses for these rooms,
+    or 0 if their bucket is not tuned yet (host only)."""
+    if isinstance(rooms, PreparedRooms):
+        arr, n = rooms.arr, rooms.n
+    else:
+        arr, keep = make_rooms(rooms)
+        n = len(rooms)
+    opts = RirOpts(0, 0, None, int(variant), 0)
+    w = c_i32()
+    check(load().ism_rir_tuned_window(arr, n, ctypes.byref(opts), ctypes.byref(w)))
+    return w.value
 
 
 def rir_filter_terms(fd_kind, n_taps):

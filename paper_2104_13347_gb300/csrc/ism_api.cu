@@ -343,12 +343,17 @@ int ism_rir_batch_ex(const ism_room *rooms, int64_t n_rooms, float *h_dev,
     ism_rir_opts o;
     memset(&o, 0, sizeof(o));
     if (opts) o = *opts;
-    if (o.window != 0 && (o.window % 32 != 0 || o.window < 32 || o.window > 8192))
-        return fail(ISM_ERR_INVALID_ARG, "window must be a multiple of 32 in [32, 8192]");
+    if (o.window != 0 && o.window != ISM_WINDOW_TUNE &&
+        (o.window % 32 != 0 || o.window < 32 || o.window > 8192))
+        return fail(ISM_ERR_INVALID_ARG,
+                    "window must be a multiple of 32 in [32, 8192], 0 or ISM_WINDOW_TUNE");
     if (o.variant != ISM_RIR_SPARSE && o.variant != ISM_RIR_DIRECT)
         return fail(ISM_ERR_INVALID_ARG, "unknown variant");
+    if (o.per_room && o.window == ISM_WINDOW_TUNE)
+        return fail(ISM_ERR_INVALID_ARG, "ISM_WINDOW_TUNE is for batched launches");
     for (int64_t r = 0; r < n_rooms; ++r)
         if (int st = validate_room(rooms[r], r)) return st;
+    if (o.window == ISM_WINDOW_TUNE) return rir_batch_tuned(rooms, n_rooms, h_dev, h_offsets, o, stream);
     const int W = o.window > 0 ? o.window : auto_window(rooms, n_rooms);
 
     // jobs, one per RIR; grouped by filter kind (one launch per kind)

@@ -81,6 +81,11 @@ int validate_room(const ism_room &r, int64_t idx);
 
 // The default output window of a K1 call (see ism_api.cu).
 int auto_window(const ism_room *rooms, int64_t n_rooms);
+// Window autotuner (ism_tune.cu): the tuned window of a call's bucket (0 if
+// not tuned yet), and ism_rir_batch_ex with window = ISM_WINDOW_TUNE.
+int rir_window_tuned(const ism_room *rooms, int64_t n_rooms, int variant);
+int rir_batch_tuned(const ism_room *rooms, int64_t n_rooms, float *h_dev,
+                    const int64_t *h_offsets, const ism_rir_opts &opts, cudaStream_t stream);
 
 // K1: image-source taps.  jobs_dev has n_rirs jobs; every job's windows are
 // processed; wmax = max n_windows.  counter_dev: one zeroed uint32 work

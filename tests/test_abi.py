@@ -270,3 +270,28 @@ def test_debug_inject_arguments(lib):
     assert "unknown injection" in lib.last_error()
     assert L.ism_debug_inject(lib.INJECT_CONV_WAIT) == lib.ISM_OK
     assert L.ism_debug_inject(0) == lib.ISM_OK
+
+
+def test_tuned_window_reads_the_cache_file(lib, tmp_path, monkeypatch):
+    """The autotuner's cache file (host only): a bucket that is not tuned
+    reads as window 0; a line for the call's bucket -- variant, filter kinds
+    (bit mask), Hann and Lagrange tap counts, largest order, sampling rate,
+    ceil(log2 longest RIR), floor(log2 RIR count) -- gives its window."""
+    L = lib.load()
+    room = good_room(rir_len=1000, order=3)
+    arr, keep = lib.make_rooms([room])
+    w = ctypes.c_int32(-5)
+    path = tmp_path / "tune.txt"
+    monkeypatch.setenv("ISM_TUNE_CACHE", str(path))
+    assert L.ism_rir_tuned_window(arr, 1, None, ctypes.byref(w)) == lib.ISM_OK
+    assert w.value == 0
+    path2 = tmp_path / "tune2.txt"
+    path2.write_text("ism-tune 1 0 1 81 0 3 16000 10 0 768 0.5\n"
+                     "garbage line\n"
+                     "ism-tune 1 0 1 81 0 3 16000 10 1 512 0.5\n")
+    monkeypatch.setenv("ISM_TUNE_CACHE", str(path2))
+    assert L.ism_rir_tuned_window(arr, 1, None, ctypes.byref(w)) == lib.ISM_OK
+    assert w.value == 768
+    bad = dict(room, beta=[2.0] * 6)
+    arr2, keep2 = lib.make_rooms([bad])
+    assert L.ism_rir_tuned_window(arr2, 1, None, ctypes.byref(w)) == lib.ISM_ERR_INVALID_ARG
