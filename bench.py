@@ -248,7 +248,9 @@ def run_single_room(ism, wl, dev, stream, reps=200):
     e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     out = {"workload": "5x4x3 m, beta 0.8, order 10 (74088 images), 81 taps, RIR 4096 @ 16 kHz, "
                        "1 source, 1 mic", "taps": taps}
+    plan = ism.Plan(prep, h)  # automatic window, as the sparse eager call
     for name, fn in (("sparse", lambda: ism.rir_batch(prep, h=h)),
+                     ("sparse_graph", lambda: plan.run(prep)),
                      ("direct", lambda: ism.rir_batch(prep, h=h, variant=ism.RIR_DIRECT)),
                      ("noalloc", lambda: ism.rir_batch_noalloc(rooms, h))):
         for _ in range(5):
@@ -262,6 +264,18 @@ def run_single_room(ism, wl, dev, stream, reps=200):
         torch.cuda.synchronize()
         out[name] = {"device_us": 1e3 * e[0].elapsed_time(e[1]) / reps,
                      "wall_us": 1e6 * (time.perf_counter() - t0) / reps}
+        # one call alone: host work + device time until the result is ready
+        lat = []
+        for _ in range(20):
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            lat.append(1e6 * (time.perf_counter() - t1))
+        out[name]["isolated_call_us"] = float(np.median(lat))
+    plan.close()
+    out["sparse_graph"]["note"] = ("ism_plan_run: the same kernels replayed from a CUDA graph "
+                                   "with the room's descriptors copied in")
     # FP32-pipe fraction of the sparse call, on the same algorithmic count as
     # the batch roofline (FIR per output, delay split and terms per image)
     P = ism.rir_filter_terms(0, 81)
@@ -293,17 +307,21 @@ def run_plain_path(ism, prep, h, jobs, src, y, stream, ms_step, taps):
             "speedup_of_the_step": (rir_ms + conv_ms) / ms_step}
 
 
-def run_ragged(ism, wl, n_requests, dev, stream, n_cmp=128):
+def run_ragged(ism, wl, n_requests, dev, stream, n_cmp=128, seconds=1.0):
     """The ragged batch (RT60 U[0.1, 1.0] s, fs 16/48 kHz, 4-16 mics, Sabine
-    walls, order from the length) as one launch, and its first n_cmp
-    requests both batched and one launch per room (the plain path)."""
+    walls, order from the length): RIRs as one launch at the autotuned
+    window; the whole step (RIRs, convolution of a `seconds`-long white
+    source per request, noise) eagerly and replayed from a CUDA graph
+    (ism_plan_run); the convolution alone (mic-samples/s); and the first
+    n_cmp requests' RIRs batched and one launch per room (the plain path)."""
     import torch
     rooms = wl.ragged_batch(n_requests, seed=1005)
     prep = ism.PreparedRooms(rooms)
     n_rirs, hl = ism.rir_batch_size(rooms)
     h = torch.empty(hl, device=dev)
     stats = torch.zeros(2 * n_rirs, dtype=torch.int64, device=dev)
-    ism.rir_batch(rooms, h=h, stats=stats)
+    ism.rir_batch(rooms, h=h, stats=stats, window=ism.WINDOW_TUNE)  # tunes the bucket
+    W = ism.rir_tuned_window(prep)
     e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
 
     def timed(fn, reps):
@@ -316,17 +334,49 @@ def run_ragged(ism, wl, n_requests, dev, stream, n_cmp=128):
         torch.cuda.synchronize()
         return e[0].elapsed_time(e[1]) / reps
 
-    ms = timed(lambda: ism.rir_batch(prep, h=h), 2)
+    ms = timed(lambda: ism.rir_batch(prep, h=h, window=ism.WINDOW_TUNE), 2)
+    ms_auto = timed(lambda: ism.rir_batch(prep, h=h), 2)
     taps = int(stats.view(-1, 2)[:, 1].sum().item())
+    # the whole step: sources, convolution (split BF16), noise
+    srcs = wl.sources(rooms, seconds, seed=1008)
+    lens = [len(x) for x in srcs]
+    mics = [len(r["mics"]) for r in rooms]
+    src = torch.from_numpy(np.concatenate(srcs)).to(dev)
+    snr = wl.snrs(n_requests, seed=1009)
+    jobs, ylen = ism.conv_jobs(mics, [r["rir_len"] for r in rooms], lens, snr_db=snr)
+    y = torch.empty(ylen, device=dev)
+    mic_samples = int(sum(M * (T + r["rir_len"] - 1) for M, T, r in zip(mics, lens, rooms)))
+
+    def eager():
+        ism.rir_batch(prep, h=h, window=W)
+        ism.convolve_batch(jobs, h, src, y, seed=7, precision=ism.BF16X3)
+
+    ms_conv = timed(lambda: ism.convolve_batch(jobs, h, src, y, seed=7, precision=ism.BF16X3), 2)
+    ms_eager = timed(eager, 2)
+    y_eager = y.clone()
+    plan = ism.Plan(prep, h, src, y, src_lens=lens, precision=ism.BF16X3, window=W, seed=7)
+    ms_graph = timed(lambda: plan.run(prep, snr_db=snr), 2)
+    same = bool(torch.equal(y, y_eager))
+    plan.close()
+    del y_eager, y, src
     sub = ism.PreparedRooms(rooms[:n_cmp])
     hs = torch.empty(sub.h_len, device=dev)
     ms_b = timed(lambda: ism.rir_batch(sub, h=hs), 3)
     ms_r = timed(lambda: ism.rir_batch(sub, h=hs, per_room=True), 1)
     del h, hs
     return {"requests": n_requests, "rirs": n_rirs, "samples": hl, "ms": ms,
+            "window": W, "window_rule": "autotuned", "ms_automatic_window": ms_auto,
             "taps_per_s": taps / (ms * 1e-3), "rirs_per_s": n_rirs / (ms * 1e-3),
             "workload": "RT60 U[0.1,1.0] s (Sabine walls), fs 16/48 kHz, 4-16 mics, RIR "
-                        "ceil(RT60 fs), order from the length, 81-tap Hann sinc",
+                        "ceil(RT60 fs), order from the length, 81-tap Hann sinc; "
+                        f"{seconds:g} s white sources, SNR U[0,30] dB",
+            "step": {"mic_samples": mic_samples, "conv_ms": ms_conv,
+                     "mic_samples_per_s_convolution": mic_samples / (ms_conv * 1e-3),
+                     "eager_ms": ms_eager, "graph_ms": ms_graph,
+                     "mic_samples_per_s": mic_samples / (ms_graph * 1e-3),
+                     "graph_output_bitwise_equal_to_eager": same,
+                     "graph": "ism_plan_run: RIRs + split-BF16 convolution + noise of the batch "
+                              "replayed from a CUDA graph"},
             "first_requests_batched_vs_per_room": {"requests": n_cmp, "batched_ms": ms_b,
                                                    "per_room_ms": ms_r,
                                                    "speedup": ms_r / ms_b}}
@@ -477,8 +527,19 @@ def run_paper_dataset(ism, wl, n_sources, dev, stream):
         e[1].record(stream)
         torch.cuda.synchronize()
         ms = e[0].elapsed_time(e[1]) / 3
+        # the same batch at the autotuned window (tuned on its first call)
+        ism.rir_batch(prep, h=h, window=ism.WINDOW_TUNE)
+        torch.cuda.synchronize()
+        e[0].record(stream)
+        for _ in range(3):
+            ism.rir_batch(prep, h=h, window=ism.WINDOW_TUNE)
+        e[1].record(stream)
+        torch.cuda.synchronize()
+        ms_t = e[0].elapsed_time(e[1]) / 3
         st = stats.view(-1, 2)
         out[name] = {"ms": ms, "rirs": n_rirs, "rirs_per_s": n_rirs / (ms * 1e-3),
+                     "window_automatic": 1024, "tuned_window": ism.rir_tuned_window(prep),
+                     "tuned_ms": ms_t, "s_per_336000_rirs_tuned": 336000 / (n_rirs / (ms_t * 1e-3)),
                      "taps_per_s": int(st[:, 1].sum().item()) / (ms * 1e-3),
                      "contributing_images_per_rir": int(st[:, 0].sum().item()) / n_rirs,
                      "s_per_336000_rirs": 336000 / (n_rirs / (ms * 1e-3))}
@@ -630,7 +691,10 @@ def run_ours(args, ws, rank):
         "data": "synthetic",
         "config": {"workload": WORKLOAD if n_rooms == N_ROOMS else
                    WORKLOAD.replace(f"{N_ROOMS} rooms", f"{n_rooms} rooms"), "rooms": n_rooms, "mics": N_MICS, "order": ORDER,
-                   "rir_len": LH, "src_len": TS, "n_taps": 81, "window": args.window or 1024,
+                   "rir_len": LH, "src_len": TS, "n_taps": 81,
+                   "window": (ism.rir_tuned_window(prep, variant) if args.window < 0 else
+                              args.window or 1024),
+                   "window_rule": {-1: "autotuned", 0: "automatic"}.get(args.window, "fixed"),
                    "precision": args.precision, "parallelism": f"replicas x{ws}",
                    "l2": f"inputs larger than L2 (h {hl * 4 / 1e6:.0f} MB, y {ylen * 4 / 1e6:.0f} MB "
                          "per step), no flush"},
@@ -712,7 +776,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="bf16x3", choices=["f32", "bf16x3"],
                     help="convolution arithmetic (both meet 1e-5 rel-L2 on this workload)")
-    ap.add_argument("--window", type=int, default=0)
+    ap.add_argument("--window", type=int, default=-1,
+                    help="K1 window: -1 = the library's autotuner (default), 0 = automatic "
+                         "rule, or a multiple of 32")
     ap.add_argument("--rir-variant", default="sparse", choices=["sparse", "direct"],
                     help="K1 kernel: sparse Chebyshev arrays (default) or the direct per-tap one")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -301,6 +301,61 @@ int ism_dataset_batch(const ism_room *rooms, int64_t n_rooms, const float *src_h
                       float *h_host, const int64_t *h_offsets, int64_t chunk_rooms);
 
 /* ------------------------------------------------------------------------
+ * Plans: the dataset step of Sec. II.A (RIRs, convolution) with the noise of
+ * Sec. III.A, for a batch of fixed shape, captured once into CUDA graphs and
+ * replayed.  A run costs the host one descriptor build and one graph launch
+ * instead of the batch entry points' validation, staging and launches, and
+ * its outputs are bitwise those of ism_rir_batch_ex (with the plan's window)
+ * followed by ism_convolve_batch on the same rooms.
+ * ------------------------------------------------------------------------ */
+typedef struct ism_plan ism_plan;
+
+typedef struct ism_plan_config {
+    int32_t precision;   /* ISM_F32 or ISM_BF16X3 (convolution) */
+    int32_t window;      /* K1 window: 0 = automatic for the creation rooms, a
+                            multiple of 32 in [32, 8192], or ISM_WINDOW_TUNE
+                            (the bucket's tuned window if it is tuned,
+                            automatic otherwise; plans never tune) */
+    int32_t max_order;   /* lattice-order capacity of every RIR: 0 = each
+                            RIR's order at creation (ISM_ORDER_AUTO rooms of
+                            later runs may need more: give it here); never
+                            below a RIR's order at creation */
+    int32_t variant;     /* ism_rir_variant */
+    uint64_t seed;       /* noise seed (see ism_convolve_batch) */
+} ism_plan_config;
+
+/* Creates a plan for batches shaped like `rooms`: the same number of rooms,
+ * and per room the same n_mics, rir_len, n_taps and fd_kind (geometry,
+ * walls, fs, c and order -- up to the capacity -- may change per run).
+ * h_dev: device output, packed RIRs (as ism_rir_batch with NULL offsets).
+ * src_lens: host, source length per room, or NULL for a plan of RIRs only;
+ * src_dev: device sources packed in room order; y_dev: device output, room
+ * i's n_mics x (src_lens[i] + rir_len - 1) samples, packed.  The buffers are
+ * the caller's and must outlive the plan; the plan keeps its own device
+ * block (descriptors and scratch) and two page-locked staging buffers, and
+ * captures its graphs on a private stream (call it before capturing any
+ * stream of your own).  Errors: ISM_ERR_INVALID_ARG (rooms, config),
+ * ISM_ERR_OUT_OF_MEMORY, ISM_ERR_CUDA. */
+int ism_plan_create(const ism_room *rooms, int64_t n_rooms, const int64_t *src_lens,
+                    const ism_plan_config *config, float *h_dev, const float *src_dev,
+                    float *y_dev, ism_plan **out);
+
+/* Runs the plan on `stream` for `rooms` (same shape as at creation; the
+ * current device must be the plan's): RIRs into h_dev and, for a plan with
+ * sources, the signals into y_dev with room i's noise at snr_db[i] (host
+ * array, NaN = none, or NULL = no noise) and noise id noise_id_base + i.
+ * Enqueues and returns; the two staging buffers alternate, so a run waits
+ * for the run before the previous one to finish before it overwrites its
+ * staging buffer.  Errors: ISM_ERR_INVALID_ARG (a room of another shape, an
+ * order above the capacity), ISM_ERR_INTERNAL (an earlier call on the stream
+ * reported a kernel error, see ism_stream_status), ISM_ERR_CUDA. */
+int ism_plan_run(ism_plan *plan, const ism_room *rooms, const float *snr_db,
+                 uint64_t noise_id_base, void *stream);
+
+/* Waits for the plan's runs, then frees it. */
+int ism_plan_destroy(ism_plan *plan);
+
+/* ------------------------------------------------------------------------
  * Training frames: the network of the paper reads multichannel windows of
  * 1024 samples (23.2 ms at 44.1 kHz) of the convolved signals, with
  * measurement noise added at a chosen SNR as data augmentation
@@ -465,6 +520,12 @@ int ism_stream_status(void *stream);
  * ISM_ERR_INTERNAL.  0 cancels a pending injection.  Nothing faults or hangs:
  * the waits are bounded and the kernels return. */
 #define ISM_INJECT_CONV_WAIT 1
+/* ISM_INJECT_SERVE_ALLOC: the next batch a server launches finds its device
+ * allocation failing (the allocator is not called): the batch's requests
+ * fail with ISM_ERR_OUT_OF_MEMORY, their memory budget is returned when they
+ * are released, and later batches run normally.  Injections of different
+ * kinds may be pending together. */
+#define ISM_INJECT_SERVE_ALLOC 2
 int ism_debug_inject(int32_t what);
 
 /* Message of the last error on the calling thread ("" if none). */

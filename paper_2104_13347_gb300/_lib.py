@@ -21,6 +21,7 @@ ISM_OK, ISM_PENDING = 0, 1
 ISM_ERR_INVALID_ARG, ISM_ERR_OUT_OF_MEMORY, ISM_ERR_BUSY = 2, 3, 4
 ISM_ERR_TIMEOUT, ISM_ERR_CUDA, ISM_ERR_INTERNAL, ISM_ERR_UNKNOWN_TICKET = 5, 6, 7, 8
 INJECT_CONV_WAIT = 1
+INJECT_SERVE_ALLOC = 2
 WINDOW_TUNE = -1
 FD_HANN_SINC, FD_LAGRANGE = 0, 1
 RIR_SPARSE, RIR_DIRECT = 0, 1
@@ -68,6 +69,11 @@ class Result(ctypes.Structure):
                 ("rir_len", c_i64), ("y_len", c_i64), ("queue_s", c_f64), ("latency_s", c_f64)]
 
 
+class PlanConfig(ctypes.Structure):
+    _fields_ = [("precision", c_i32), ("window", c_i32), ("max_order", c_i32),
+                ("variant", c_i32), ("seed", c_u64)]
+
+
 class ServeStats(ctypes.Structure):
     _fields_ = [(n, c_i64) for n in ("submitted", "completed", "rejected_busy", "batches",
                                      "queued", "in_flight", "bytes_in_use", "bytes_peak", "taps",
@@ -86,6 +92,9 @@ SIGNATURES = {
     "ism_frames_batch": (c_i32, [c_vp, c_i64, c_i32, c_vp, c_vp, c_u64, c_vp]),
     "ism_dataset_batch": (c_i32, [c_vp, c_i64, c_vp, c_vp, c_vp, c_vp, c_u64, c_u64, c_i32, c_vp,
                                   c_vp, c_vp, c_vp, c_i64]),
+    "ism_plan_create": (c_i32, [c_vp, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "ism_plan_run": (c_i32, [c_vp, c_vp, c_vp, c_u64, c_vp]),
+    "ism_plan_destroy": (c_i32, [c_vp]),
     "ism_serve_create": (c_i32, [c_vp, c_vp]),
     "ism_serve_submit": (c_i32, [c_vp, c_vp, c_vp]),
     "ism_serve_poll": (c_i32, [c_vp, c_u64, c_vp]),
@@ -380,6 +389,53 @@ def dataset_batch(rooms, src_host, src_lens, y_host, snr_db=None, seed=0, noise_
                                 c_u64(noise_id_base), int(precision), ptr(y_host), None,
                                 ptr(h_host), None, int(chunk_rooms)))
     return y_host
+
+
+class Plan:
+    """ism_plan_*: the dataset step of a fixed batch shape captured into CUDA
+    graphs and replayed (argument marshalling only).  h, src, y: the
+    caller's float32 CUDA tensors (packed; src and y None for a plan of RIRs
+    only), kept alive by the plan."""
+
+    def __init__(self, rooms, h, src=None, y=None, src_lens=None, precision=BF16X3, window=0,
+                 max_order=0, variant=RIR_SPARSE, seed=0):
+        self._lib = load()
+        arr, keep = (rooms.arr, [rooms.keep]) if isinstance(rooms, PreparedRooms) else \
+            make_rooms(rooms)
+        n = len(arr)
+        for t in (h, src, y):
+            if t is not None:
+                assert t.dtype.is_floating_point and t.is_cuda and t.is_contiguous()
+        lens = None
+        if src_lens is not None:
+            lens = np.ascontiguousarray(np.asarray(src_lens, np.int64))
+            assert src is not None and y is not None and len(lens) == n
+        cfg = PlanConfig(int(precision), int(window), int(max_order), int(variant), int(seed))
+        self._h = c_vp()
+        self._bufs = (h, src, y)
+        check(self._lib.ism_plan_create(arr, n, None if lens is None else c_vp(lens.ctypes.data),
+                                        ctypes.byref(cfg), c_vp(h.data_ptr()),
+                                        None if src is None else c_vp(src.data_ptr()),
+                                        None if y is None else c_vp(y.data_ptr()),
+                                        ctypes.byref(self._h)))
+
+    def run(self, rooms, snr_db=None, noise_id_base=0, stream=None):
+        arr, keep = (rooms.arr, [rooms.keep]) if isinstance(rooms, PreparedRooms) else \
+            make_rooms(rooms)
+        snr = None if snr_db is None else np.ascontiguousarray(np.asarray(snr_db, np.float32))
+        check(self._lib.ism_plan_run(self._h, arr, None if snr is None else c_vp(snr.ctypes.data),
+                                     c_u64(noise_id_base), _stream_ptr(stream)))
+
+    def close(self):
+        if self._h:
+            check(self._lib.ism_plan_destroy(self._h))
+            self._h = c_vp()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 class PreparedRequest:

@@ -306,6 +306,189 @@ const ChebTable &cheb_table(int fd_kind, int n_taps) {
     return *t;
 }
 
+// ---------------------------------------------------------------------------
+// K1 calls: host preparation and launches
+// ---------------------------------------------------------------------------
+int rir_prepare(const ism_room *rooms, int64_t n_rooms, const int64_t *h_offsets,
+                const ism_rir_opts &o, int W, const int *order_caps, RirPrep *out) {
+    RirPrep &P = *out;
+    P.W = W;
+    // jobs, one per RIR; grouped by filter kind (one launch per kind)
+    std::vector<int64_t> room_of[2];
+    int64_t j = 0, packed = 0;
+    for (int kind = 0; kind < 2; ++kind) {
+        P.k[kind] = RirKindPrep();
+        P.k[kind].kind = kind;
+    }
+    for (int64_t r = 0; r < n_rooms; ++r) {
+        const ism_room &R = rooms[r];
+        const int kind = R.fd_kind;
+        RirKindPrep &K = P.k[kind];
+        for (int m = 0; m < R.n_mics; ++m, ++j) {
+            RirJob J;
+            memset(&J, 0, sizeof(J));
+            for (int a = 0; a < 3; ++a) {
+                J.src[a] = R.src[a];
+                J.mic[a] = R.mics[3 * m + a];
+                J.dims[a] = R.dims[a];
+            }
+            J.q = R.fs / R.c;
+            for (int w = 0; w < 6; ++w) J.beta[w] = (float)R.beta[w];
+            J.order = room_order(R, m);
+            J.n_taps = R.n_taps;
+            J.fd_kind = (int16_t)kind;
+            J.rir_len = R.rir_len;
+            J.n_windows = (int32_t)((R.rir_len + W - 1) / W);
+            J.h_offset = h_offsets ? h_offsets[j] : packed;
+            J.stat_index = (int32_t)j;  // statistics slot: RIR index in the caller's order
+            packed += R.rir_len;
+            if (J.h_offset < 0) return fail(ISM_ERR_INVALID_ARG, "negative h offset");
+            const int cap = order_caps ? order_caps[j] : J.order;
+            if (J.order > cap)
+                return fail(ISM_ERR_INVALID_ARG, "RIR " + std::to_string(j) +
+                                                     ": lattice order above the plan's capacity");
+            K.jobs.push_back(J);
+            K.caps.push_back(cap);
+            room_of[kind].push_back(r);
+            K.max_order = std::max(K.max_order, cap);
+            K.max_taps = std::max(K.max_taps, R.n_taps);
+            K.wmax = std::max(K.wmax, J.n_windows);
+        }
+    }
+    if (j > 0x3fffffff) return fail(ISM_ERR_INVALID_ARG, "too many RIRs");
+
+    for (int kind = 0; kind < 2; ++kind) {
+        RirKindPrep &K = P.k[kind];
+        auto &jv = K.jobs;
+        if (jv.empty()) continue;
+        // sparse path: one Chebyshev table per distinct filter length
+        K.sparse = o.variant == ISM_RIR_SPARSE;
+        K.max_cheb = 0;
+        K.min_cheb = kMaxCheb;
+        if (K.sparse) {
+            std::vector<std::pair<int, int>> seen;  // (n_taps, offset)
+            for (auto &J : jv) {
+                int off = -1;
+                for (auto &pr : seen)
+                    if (pr.first == J.n_taps) off = pr.second;
+                const ChebTable &ct = cheb_table(kind, J.n_taps);
+                if (ct.n_cheb == 0) { K.sparse = false; break; }
+                if (off < 0) {
+                    // rows padded with zeros to a multiple of 4 taps (the
+                    // kernel reads them as 16-byte vectors)
+                    off = (int)K.tabs.size();
+                    const int tp = (J.n_taps + 3) & ~3;
+                    K.tabs.resize(K.tabs.size() + (size_t)ct.n_cheb * tp, 0.f);
+                    for (int p = 0; p < ct.n_cheb; ++p)
+                        for (int jj = 0; jj < J.n_taps; ++jj)
+                            K.tabs[off + (size_t)p * tp + jj] = ct.coef[(size_t)p * J.n_taps + jj];
+                    seen.push_back({J.n_taps, off});
+                }
+                J.tab_offset = off;
+                J.n_cheb = (int16_t)ct.n_cheb;
+                K.max_cheb = std::max(K.max_cheb, ct.n_cheb);
+                K.min_cheb = std::min(K.min_cheb, ct.n_cheb);
+            }
+            if (K.sparse && rir_sparse_smem_bytes(W, K.max_order, K.max_taps, K.max_cheb) >
+                                kMaxDynSmem)
+                K.sparse = false;
+            if (!K.sparse) {
+                K.tabs.clear();
+                K.max_cheb = 0;
+                K.min_cheb = kMaxCheb;
+            }
+        }
+        if (!K.sparse && rir_smem_bytes(W, K.max_order, K.max_taps) > kMaxDynSmem)
+            return fail(ISM_ERR_INVALID_ARG, "window/order/taps need too much shared memory");
+        // launches: one per room on the unbatched path; otherwise the whole
+        // kind, cut where the sparse kernel's sorted column lists would pass
+        // kColBudget entries
+        {
+            size_t b = 0;
+            long long acc = 0;
+            for (size_t k = 0; k < jv.size(); ++k) {
+                const long long ce = K.sparse ? rir_col_entries(K.caps[k]) : 0;
+                const bool cut = o.per_room ? room_of[kind][k] != room_of[kind][b]
+                                            : (k > b && acc + ce > kColBudget);
+                if (cut) {
+                    K.chunks.push_back({b, k});
+                    b = k;
+                    acc = 0;
+                }
+                acc += ce;
+            }
+            K.chunks.push_back({b, jv.size()});
+        }
+        // per RIR: column-list and window-range offsets, relative to its
+        // launch; the lists are sized for the RIR's order capacity
+        long long max_cols = 0, max_wins = 0;
+        if (K.sparse) {
+            K.offs.resize(2 * jv.size());
+            for (auto &c : K.chunks) {
+                long long co = 0, wo = 0;
+                for (size_t k = c.first; k < c.second; ++k) {
+                    K.offs[2 * k] = co;
+                    K.offs[2 * k + 1] = wo;
+                    co += rir_col_entries(K.caps[k]);
+                    wo += jv[k].n_windows;
+                }
+                max_cols = std::max(max_cols, co);
+                max_wins = std::max(max_wins, wo);
+            }
+        }
+        size_t max_chunk = 0;
+        for (auto &c : K.chunks) max_chunk = std::max(max_chunk, c.second - c.first);
+        auto al = [](size_t n) { return (n + 255) & ~(size_t)255; };
+        K.jb = al(jv.size() * sizeof(RirJob));
+        K.tb = al(K.sparse ? K.tabs.size() * sizeof(float) : 0);
+        K.ob = al(K.offs.size() * sizeof(long long));
+        K.up_bytes = K.jb + 256 + K.tb + K.ob;
+        K.cb = al((size_t)max_cols * sizeof(uint32_t));
+        K.wb = al((size_t)max_wins * sizeof(int2));
+        K.gb = K.sparse ? al(rir_tables_bytes((long long)max_chunk, K.max_order)) : 0;
+        K.blob.assign(K.up_bytes, 0);
+        memcpy(K.blob.data(), jv.data(), jv.size() * sizeof(RirJob));
+        if (K.sparse) {
+            memcpy(K.blob.data() + K.jb + 256, K.tabs.data(), K.tabs.size() * sizeof(float));
+            memcpy(K.blob.data() + K.jb + 256 + K.tb, K.offs.data(),
+                   K.offs.size() * sizeof(long long));
+        }
+    }
+    return ISM_OK;
+}
+
+int rir_enqueue(const RirKindPrep &K, char *sp, int W, float *h_dev, long long *stats,
+                int *err_dev, cudaStream_t stream) {
+    (void)err_dev;  // the image-source kernels have no waits
+    RirJob *d_jobs = (RirJob *)sp;
+    unsigned int *d_counter = (unsigned int *)(sp + K.jb);
+    const float *d_tabs = (const float *)(sp + K.jb + 256);
+    long long *d_offs = (long long *)(sp + K.jb + 256 + K.tb);
+    uint32_t *d_cols = (uint32_t *)(sp + K.up_bytes);
+    int2 *d_wr = (int2 *)(sp + K.up_bytes + K.cb);
+    void *d_tables = K.sparse ? (void *)(sp + K.up_bytes + K.cb + K.wb) : nullptr;
+    int st = ISM_OK;
+    for (size_t ci = 0; !st && ci < K.chunks.size(); ++ci) {
+        const size_t b = K.chunks[ci].first, n = K.chunks[ci].second - b;
+        int wm = 0;
+        for (size_t k = b; k < b + n; ++k) wm = std::max(wm, K.jobs[k].n_windows);
+        if (ci > 0) {
+            cudaError_t e = cudaMemsetAsync(d_counter, 0, sizeof(unsigned int), stream);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(counter)");
+        }
+        RirLaunch L{d_jobs + b, (int)n, wm, W, K.max_order, K.max_taps, K.kind, h_dev,
+                    stats, d_counter, nullptr, 0, d_tabs, K.max_cheb, K.min_cheb};
+        if (K.sparse) {
+            L.cols_dev = d_cols;
+            L.wr_dev = d_wr;
+            L.offs_dev = d_offs + 2 * b;
+            L.tables_dev = d_tables;
+        }
+        st = K.sparse ? launch_rir_sparse(L, stream) : launch_rir(L, stream);
+    }
+    return st;
+}
+
 }  // namespace ism
 
 using namespace ism;
@@ -355,171 +538,22 @@ int ism_rir_batch_ex(const ism_room *rooms, int64_t n_rooms, float *h_dev,
         if (int st = validate_room(rooms[r], r)) return st;
     if (o.window == ISM_WINDOW_TUNE) return rir_batch_tuned(rooms, n_rooms, h_dev, h_offsets, o, stream);
     const int W = o.window > 0 ? o.window : auto_window(rooms, n_rooms);
-
-    // jobs, one per RIR; grouped by filter kind (one launch per kind)
-    std::vector<RirJob> jobs[2];
-    std::vector<int64_t> room_of[2];
-    int max_order[2] = {0, 0}, max_taps[2] = {1, 1}, wmax[2] = {0, 0};
-    int64_t j = 0, packed = 0;
-    for (int64_t r = 0; r < n_rooms; ++r) {
-        const ism_room &R = rooms[r];
-        if (int st = validate_room(R, r)) return st;
-        const int kind = R.fd_kind;
-        for (int m = 0; m < R.n_mics; ++m, ++j) {
-            RirJob J;
-            memset(&J, 0, sizeof(J));
-            for (int a = 0; a < 3; ++a) {
-                J.src[a] = R.src[a];
-                J.mic[a] = R.mics[3 * m + a];
-                J.dims[a] = R.dims[a];
-            }
-            J.q = R.fs / R.c;
-            for (int w = 0; w < 6; ++w) J.beta[w] = (float)R.beta[w];
-            J.order = room_order(R, m);
-            J.n_taps = R.n_taps;
-            J.fd_kind = (int16_t)kind;
-            J.rir_len = R.rir_len;
-            J.n_windows = (int32_t)((R.rir_len + W - 1) / W);
-            J.h_offset = h_offsets ? h_offsets[j] : packed;
-            J.stat_index = (int32_t)j;  // statistics slot: RIR index in the caller's order
-            packed += R.rir_len;
-            if (J.h_offset < 0) return fail(ISM_ERR_INVALID_ARG, "negative h offset");
-            jobs[kind].push_back(J);
-            room_of[kind].push_back(r);
-            max_order[kind] = std::max(max_order[kind], J.order);
-            max_taps[kind] = std::max(max_taps[kind], R.n_taps);
-            wmax[kind] = std::max(wmax[kind], J.n_windows);
-        }
+    RirPrep P;
+    {
+        NvtxRange r("ism.rir.plan");
+        if (int st = rir_prepare(rooms, n_rooms, h_offsets, o, W, nullptr, &P)) return st;
     }
-    const int64_t n_rirs = j;
-    if (n_rirs > 0x3fffffff) return fail(ISM_ERR_INVALID_ARG, "too many RIRs");
-
+    NvtxRange r("ism.rir.K1");
     for (int kind = 0; kind < 2; ++kind) {
-        auto &jv = jobs[kind];
-        if (jv.empty()) continue;
-        // sparse path: one Chebyshev table per distinct filter length
-        bool sparse = o.variant == ISM_RIR_SPARSE;
-        std::vector<float> tabs;
-        int max_cheb = 0, min_cheb = kMaxCheb;
-        if (sparse) {
-            std::vector<std::pair<int, int>> seen;  // (n_taps, offset)
-            for (auto &J : jv) {
-                int off = -1;
-                for (auto &pr : seen)
-                    if (pr.first == J.n_taps) off = pr.second;
-                const ChebTable &ct = cheb_table(kind, J.n_taps);
-                if (ct.n_cheb == 0) { sparse = false; break; }
-                if (off < 0) {
-                    // rows padded with zeros to a multiple of 4 taps (the
-                    // kernel reads them as 16-byte vectors)
-                    off = (int)tabs.size();
-                    const int tp = (J.n_taps + 3) & ~3;
-                    tabs.resize(tabs.size() + (size_t)ct.n_cheb * tp, 0.f);
-                    for (int p = 0; p < ct.n_cheb; ++p)
-                        for (int jj = 0; jj < J.n_taps; ++jj)
-                            tabs[off + (size_t)p * tp + jj] = ct.coef[(size_t)p * J.n_taps + jj];
-                    seen.push_back({J.n_taps, off});
-                }
-                J.tab_offset = off;
-                J.n_cheb = (int16_t)ct.n_cheb;
-                max_cheb = std::max(max_cheb, ct.n_cheb);
-                min_cheb = std::min(min_cheb, ct.n_cheb);
-            }
-            if (sparse && rir_sparse_smem_bytes(W, max_order[kind], max_taps[kind], max_cheb) >
-                              kMaxDynSmem)
-                sparse = false;
-        }
-        if (!sparse && rir_smem_bytes(W, max_order[kind], max_taps[kind]) > kMaxDynSmem)
-            return fail(ISM_ERR_INVALID_ARG, "window/order/taps need too much shared memory");
-        // launches: one per room on the unbatched path; otherwise the whole
-        // kind, cut where the sparse kernel's sorted column lists would pass
-        // kColBudget entries
-        std::vector<std::pair<size_t, size_t>> chunks;
-        {
-            size_t b = 0;
-            long long acc = 0;
-            for (size_t k = 0; k < jv.size(); ++k) {
-                const long long ce = sparse ? rir_col_entries(jv[k].order) : 0;
-                const bool cut = o.per_room ? room_of[kind][k] != room_of[kind][b]
-                                            : (k > b && acc + ce > kColBudget);
-                if (cut) {
-                    chunks.push_back({b, k});
-                    b = k;
-                    acc = 0;
-                }
-                acc += ce;
-            }
-            chunks.push_back({b, jv.size()});
-        }
-        // per RIR: column-list and window-range offsets, relative to its launch
-        std::vector<long long> offs;
-        long long max_cols = 0, max_wins = 0;
-        if (sparse) {
-            offs.resize(2 * jv.size());
-            for (auto &c : chunks) {
-                long long co = 0, wo = 0;
-                for (size_t k = c.first; k < c.second; ++k) {
-                    offs[2 * k] = co;
-                    offs[2 * k + 1] = wo;
-                    co += rir_col_entries(jv[k].order);
-                    wo += jv[k].n_windows;
-                }
-                max_cols = std::max(max_cols, co);
-                max_wins = std::max(max_wins, wo);
-            }
-        }
+        const RirKindPrep &K = P.k[kind];
+        if (K.jobs.empty()) continue;
         // one scratch block and one upload: [jobs | counter | filter tables |
         // offsets] copied from the host, then the column lists, window
         // ranges and per-RIR tables the kernels fill
-        size_t max_chunk = 0;
-        for (auto &c : chunks) max_chunk = std::max(max_chunk, c.second - c.first);
-        auto al = [](size_t n) { return (n + 255) & ~(size_t)255; };
-        const size_t jb = al(jv.size() * sizeof(RirJob));
-        const size_t tb = al(sparse ? tabs.size() * sizeof(float) : 0);
-        const size_t ob = al(offs.size() * sizeof(long long));
-        const size_t up_bytes = jb + 256 + tb + ob;
-        const size_t cb = al((size_t)max_cols * sizeof(uint32_t));
-        const size_t wb = al((size_t)max_wins * sizeof(int2));
-        const size_t gb = sparse ? al(rir_tables_bytes((long long)max_chunk, max_order[kind])) : 0;
-        std::vector<unsigned char> blob(up_bytes, 0);
-        memcpy(blob.data(), jv.data(), jv.size() * sizeof(RirJob));
-        if (sparse) {
-            memcpy(blob.data() + jb + 256, tabs.data(), tabs.size() * sizeof(float));
-            memcpy(blob.data() + jb + 256 + tb, offs.data(), offs.size() * sizeof(long long));
-        }
         void *scr = nullptr;
-        if (int st = scratch_alloc(&scr, up_bytes + cb + wb + gb, stream)) return st;
-        char *sp = (char *)scr;
-        RirJob *d_jobs = (RirJob *)sp;
-        unsigned int *d_counter = (unsigned int *)(sp + jb);
-        const float *d_tabs = (const float *)(sp + jb + 256);
-        long long *d_offs = (long long *)(sp + jb + 256 + tb);
-        uint32_t *d_cols = (uint32_t *)(sp + up_bytes);
-        int2 *d_wr = (int2 *)(sp + up_bytes + cb);
-        void *d_tables = sparse ? (void *)(sp + up_bytes + cb + wb) : nullptr;
-        long long *d_stats = (long long *)o.stats_dev;
-        int st = upload_async(scr, blob.data(), up_bytes, stream);  // counter uploaded as 0
-        for (size_t ci = 0; !st && ci < chunks.size(); ++ci) {
-            const size_t b = chunks[ci].first, n = chunks[ci].second - b;
-            int wm = 0;
-            for (size_t k = b; k < b + n; ++k) wm = std::max(wm, jv[k].n_windows);
-            if (ci > 0) {
-                cudaError_t e = cudaMemsetAsync(d_counter, 0, sizeof(unsigned int), stream);
-                if (e != cudaSuccess) {
-                    st = cuda_fail(e, "cudaMemsetAsync(counter)");
-                    break;
-                }
-            }
-            RirLaunch L{d_jobs + b, (int)n, wm, W, max_order[kind], max_taps[kind], kind, h_dev,
-                        d_stats, d_counter, nullptr, 0, d_tabs, max_cheb, min_cheb};
-            if (sparse) {
-                L.cols_dev = d_cols;
-                L.wr_dev = d_wr;
-                L.offs_dev = d_offs + 2 * b;
-                L.tables_dev = d_tables;
-            }
-            st = sparse ? launch_rir_sparse(L, stream) : launch_rir(L, stream);
-        }
+        if (int st = scratch_alloc(&scr, K.total(), stream)) return st;
+        int st = upload_async(scr, K.blob.data(), K.up_bytes, stream);  // counter uploaded as 0
+        if (!st) st = rir_enqueue(K, (char *)scr, W, h_dev, (long long *)o.stats_dev, nullptr, stream);
         scratch_free(scr, stream);
         if (st) return st;
     }
@@ -567,6 +601,7 @@ int ism::convolve_batch(const ism_conv_job *jobs, int64_t n_jobs, const float *h
         return fail(ISM_ERR_INVALID_ARG, "unknown precision");
     if (n_jobs > 0x7fffffff) return fail(ISM_ERR_INVALID_ARG, "too many jobs");
     cudaStream_t stream = (cudaStream_t)stream_v;
+    NvtxRange nr("ism.conv");
     std::vector<ConvJob> cj(n_jobs);
     bool any_noise = false;
     int64_t n_part = 0;
@@ -622,14 +657,18 @@ int ism::convolve_batch(const ism_conv_job *jobs, int64_t n_jobs, const float *h
         // the tensor-core kernels' bounded waits report through a status cell
         st = status_begin(&tk);
         L.err_dev = tk.dev;
-        L.inject = st ? 0 : take_injection();
+        L.inject = st ? 0 : take_injection(ISM_INJECT_CONV_WAIT);
     }
     if (!st) st = upload_async(scr, cj.data(), jb, stream);
     if (!st) {
+        NvtxRange r("ism.conv.K2");
         if (precision == ISM_BF16X3) st = launch_conv_bf16x3(L, stream);
         else st = launch_conv_f32(L, stream);
     }
-    if (!st) st = launch_noise(L, stream);
+    if (!st) {
+        NvtxRange r("ism.conv.noise");
+        st = launch_noise(L, stream);
+    }
     if (tk.cell >= 0) {
         const int se = status_end(tk, stream, st == ISM_OK);
         if (!st) st = se;

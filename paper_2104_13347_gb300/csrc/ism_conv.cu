@@ -35,11 +35,7 @@ constexpr int MG = 8;            // mics per CTA
 constexpr int KC = 256;          // taps per shared-memory chunk
 static_assert(TT == kConvTT && MG == kConvMG, "tile shape of the noise partials");
 
-struct Tile {
-    int job;
-    int mic0;
-    int64_t t0;
-};
+using Tile = ConvTile;
 
 __global__ void __launch_bounds__(CT, 2)
 k_conv_f32(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles,
@@ -212,27 +208,41 @@ k_noise(const ConvJob *__restrict__ jobs, float *__restrict__ y, const double *_
 
 }  // namespace
 
-int launch_conv_f32(const ConvLaunch &L, cudaStream_t stream) {
-    std::vector<Tile> tiles;
+int conv_f32_plan(const ConvLaunch &L, ConvPlan *P) {
+    P->precision = ISM_F32;
+    P->tiles.clear();
     for (int j = 0; j < L.n_jobs; ++j) {
         const ConvJob &J = L.jobs_host[j];
         for (int m0 = 0; m0 < J.n_mics; m0 += MG)
-            for (int64_t t0 = 0; t0 < J.y_len; t0 += TT) tiles.push_back(Tile{j, m0, t0});
+            for (int64_t t0 = 0; t0 < J.y_len; t0 += TT) P->tiles.push_back(Tile{j, m0, t0});
     }
-    if (tiles.empty()) return ISM_OK;
-    if (tiles.size() > 0x7fffffffULL) return fail(ISM_ERR_INVALID_ARG, "too many tiles");
-    void *d_tiles = nullptr;
-    int st = scratch_alloc(&d_tiles, tiles.size() * sizeof(Tile), stream);
-    if (st) return st;
-    st = upload_async(d_tiles, tiles.data(), tiles.size() * sizeof(Tile), stream);
-    if (st) { scratch_free(d_tiles, stream); return st; }
-    k_conv_f32<<<(unsigned)tiles.size(), CT, 0, stream>>>(L.jobs_dev, (const Tile *)d_tiles,
-                                                           L.h_dev, L.src_dev, L.y_dev,
-                                                           L.noise_partials_dev);
+    if (P->tiles.size() > 0x7fffffffULL) return fail(ISM_ERR_INVALID_ARG, "too many tiles");
+    P->n_a = P->tiles.size();
+    P->n_b = P->n_c = 0;
+    return ISM_OK;
+}
+
+int conv_f32_enqueue(const ConvLaunch &L, const ConvPlan &P, const ConvTile *d_tiles,
+                     cudaStream_t stream) {
+    if (P.n_a == 0) return ISM_OK;
+    k_conv_f32<<<(unsigned)P.n_a, CT, 0, stream>>>(L.jobs_dev, d_tiles, L.h_dev, L.src_dev,
+                                                    L.y_dev, L.noise_partials_dev);
     cudaError_t e = cudaGetLastError();
-    scratch_free(d_tiles, stream);
     if (e != cudaSuccess) return cuda_fail(e, "launch k_conv_f32");
     return ISM_OK;
+}
+
+int launch_conv_f32(const ConvLaunch &L, cudaStream_t stream) {
+    ConvPlan P;
+    if (int st = conv_f32_plan(L, &P)) return st;
+    if (P.tiles.empty()) return ISM_OK;
+    void *d_tiles = nullptr;
+    int st = scratch_alloc(&d_tiles, P.tiles.size() * sizeof(Tile), stream);
+    if (st) return st;
+    st = upload_async(d_tiles, P.tiles.data(), P.tiles.size() * sizeof(Tile), stream);
+    if (!st) st = conv_f32_enqueue(L, P, (const Tile *)d_tiles, stream);
+    scratch_free(d_tiles, stream);
+    return st;
 }
 
 int launch_noise(const ConvLaunch &L, cudaStream_t stream) {
@@ -256,6 +266,16 @@ int launch_noise(const ConvLaunch &L, cudaStream_t stream) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "launch k_noise");
     return ISM_OK;
+}
+
+int conv_plan(const ConvLaunch &L, ConvPlan *P) {
+    return L.precision == ISM_BF16X3 ? conv_bf16x3_plan(L, P) : conv_f32_plan(L, P);
+}
+
+int conv_enqueue(const ConvLaunch &L, const ConvPlan &P, const ConvTile *d_tiles,
+                 cudaStream_t stream) {
+    return P.precision == ISM_BF16X3 ? conv_bf16x3_enqueue(L, P, d_tiles, stream)
+                                     : conv_f32_enqueue(L, P, d_tiles, stream);
 }
 
 }  // namespace ism

@@ -71,11 +71,7 @@ constexpr int NPROD = 128;             // producer threads (warps 0-3)
 constexpr int NTHR = 160;
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s bound on any mbarrier wait
 
-struct Tile {
-    int job;
-    int mic0;
-    int64_t t0;
-};
+using Tile = ConvTile;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -1096,16 +1092,16 @@ int64_t conv_bf16x3_persistent_tiles(int n_mics, int64_t rir_len, int64_t y_len)
     return (int64_t)((n_mics + MG - 1) / MG) * ((y_len + P_TT - 1) / P_TT);
 }
 
-int launch_conv_bf16x3(const ConvLaunch &L, cudaStream_t stream) {
-    // one launch per kernel: the persistent three-product kernel for every
-    // RIR whose two tile windows fit beside its stages; the per-tile kernel
-    // for longer RIRs, with the tile's whole source window converted once
-    // where it fits and per chunk beyond.  L.per_tile (the server's small
-    // latency-bound batches) takes the per-tile kernel for every RIR: its
-    // 2048-output tiles give twice the CTAs, two per SM, so a batch below
-    // one round of the persistent kernel's tiles finishes sooner.  The choice
-    // depends on the call's kind and the RIR length only, never on the rest
-    // of the batch, so a job's result is the same in any batch of its kind.
+int conv_bf16x3_plan(const ConvLaunch &L, ConvPlan *P) {
+    // the persistent three-product kernel for every RIR whose two tile
+    // windows fit beside its stages; the per-tile kernel for longer RIRs,
+    // with the tile's whole source window converted once where it fits and
+    // per chunk beyond.  L.per_tile (the server's small latency-bound
+    // batches) takes the per-tile kernel for every RIR: its 2048-output
+    // tiles give twice the CTAs, two per SM, so a batch below one round of
+    // the persistent kernel's tiles finishes sooner.  The choice depends on
+    // the call's kind and the RIR length only, never on the rest of the
+    // batch, so a job's result is the same in any batch of its kind.
     std::vector<Tile> tiles[2], ptiles;
     int max_chunks = 0;
     int64_t p_max_lh = 0;
@@ -1124,52 +1120,68 @@ int launch_conv_bf16x3(const ConvLaunch &L, cudaStream_t stream) {
             for (int64_t t0 = 0; t0 < J.y_len; t0 += TT) tiles[whole].push_back(Tile{j, m0, t0});
     }
     const size_t n_tiles = tiles[0].size() + tiles[1].size() + ptiles.size();
-    if (n_tiles == 0) return ISM_OK;
     if (n_tiles > 0x7fffffffULL) return fail(ISM_ERR_INVALID_ARG, "too many tiles");
-    void *d_tiles = nullptr;
-    int st = scratch_alloc(&d_tiles, n_tiles * sizeof(Tile), stream);
-    if (st) return st;
-    std::vector<Tile> all(tiles[1]);
-    all.insert(all.end(), tiles[0].begin(), tiles[0].end());
-    all.insert(all.end(), ptiles.begin(), ptiles.end());
-    st = upload_async(d_tiles, all.data(), n_tiles * sizeof(Tile), stream);
-    if (st) { scratch_free(d_tiles, stream); return st; }
+    P->precision = ISM_BF16X3;
+    P->tiles.assign(tiles[1].begin(), tiles[1].end());
+    P->tiles.insert(P->tiles.end(), tiles[0].begin(), tiles[0].end());
+    P->tiles.insert(P->tiles.end(), ptiles.begin(), ptiles.end());
+    P->n_a = tiles[1].size();
+    P->n_b = tiles[0].size();
+    P->n_c = ptiles.size();
+    P->max_chunks = max_chunks;
+    P->p_max_lh = p_max_lh;
+    return ISM_OK;
+}
+
+int conv_bf16x3_enqueue(const ConvLaunch &L, const ConvPlan &P, const ConvTile *d_tiles,
+                        cudaStream_t stream) {
     WaitCtl wc{L.err_dev, kWaitNs, 0};
     if (L.inject) {
         wc.inject = 1;
         wc.limit_ns = 20000000ull;  // 20 ms: the injected wait and the aborts it causes
     }
     cudaError_t e = cudaSuccess;
-    if (!ptiles.empty()) {
-        const size_t smem = p_layout(p_max_lh).total;
+    if (P.n_c) {
+        const size_t smem = p_layout(P.p_max_lh).total;
         e = ensure_smem(k_conv_tcp, g_smem_persistent, g_smem_mu, smem);
-        const int grid = (int)std::min<size_t>(ptiles.size(), (size_t)device_sm_count());
+        const int grid = (int)std::min<size_t>(P.n_c, (size_t)device_sm_count());
         if (e == cudaSuccess)
             k_conv_tcp<<<grid, P_NT, smem, stream>>>(
-                L.jobs_dev, (const Tile *)d_tiles + tiles[1].size() + tiles[0].size(),
-                (int)ptiles.size(), (int)p_max_lh, L.h_dev, L.src_dev, L.y_dev,
-                L.noise_partials_dev, (int)(((uintptr_t)L.h_dev & 15) == 0), wc);
+                L.jobs_dev, d_tiles + P.n_a + P.n_b, (int)P.n_c, (int)P.p_max_lh, L.h_dev,
+                L.src_dev, L.y_dev, L.noise_partials_dev,
+                (int)(((uintptr_t)L.h_dev & 15) == 0), wc);
     }
-    if (e == cudaSuccess && !tiles[1].empty()) {
-        const size_t smem = tc_layout(true, max_chunks).total;
+    if (e == cudaSuccess && P.n_a) {
+        const size_t smem = tc_layout(true, P.max_chunks).total;
         e = ensure_smem(k_conv_tc<true>, g_smem_whole, g_smem_mu, smem);
         if (e == cudaSuccess)
-            k_conv_tc<true><<<(unsigned)tiles[1].size(), NTHR, smem, stream>>>(
-                L.jobs_dev, (const Tile *)d_tiles, L.h_dev, L.src_dev, L.y_dev,
-                L.noise_partials_dev, wc);
+            k_conv_tc<true><<<(unsigned)P.n_a, NTHR, smem, stream>>>(
+                L.jobs_dev, d_tiles, L.h_dev, L.src_dev, L.y_dev, L.noise_partials_dev, wc);
     }
-    if (e == cudaSuccess && !tiles[0].empty()) {
+    if (e == cudaSuccess && P.n_b) {
         const size_t smem = tc_layout(false, 0).total;
         e = ensure_smem(k_conv_tc<false>, g_smem_chunked, g_smem_mu, smem);
         if (e == cudaSuccess)
-            k_conv_tc<false><<<(unsigned)tiles[0].size(), NTHR, smem, stream>>>(
-                L.jobs_dev, (const Tile *)d_tiles + tiles[1].size(), L.h_dev, L.src_dev, L.y_dev,
-                L.noise_partials_dev, wc);
+            k_conv_tc<false><<<(unsigned)P.n_b, NTHR, smem, stream>>>(
+                L.jobs_dev, d_tiles + P.n_a, L.h_dev, L.src_dev, L.y_dev, L.noise_partials_dev,
+                wc);
     }
     if (e == cudaSuccess) e = cudaGetLastError();
-    scratch_free(d_tiles, stream);
     if (e != cudaSuccess) return cuda_fail(e, "launch k_conv_tc");
     return ISM_OK;
+}
+
+int launch_conv_bf16x3(const ConvLaunch &L, cudaStream_t stream) {
+    ConvPlan P;
+    if (int st = conv_bf16x3_plan(L, &P)) return st;
+    if (P.tiles.empty()) return ISM_OK;
+    void *d_tiles = nullptr;
+    int st = scratch_alloc(&d_tiles, P.tiles.size() * sizeof(Tile), stream);
+    if (st) return st;
+    st = upload_async(d_tiles, P.tiles.data(), P.tiles.size() * sizeof(Tile), stream);
+    if (!st) st = conv_bf16x3_enqueue(L, P, (const Tile *)d_tiles, stream);
+    scratch_free(d_tiles, stream);
+    return st;
 }
 
 }  // namespace ism

@@ -197,7 +197,9 @@ extern "C" int ism_dataset_batch(const ism_room *rooms, int64_t n_rooms, const f
 
     int st = ISM_OK;
     std::vector<ism_conv_job> jobs;
+    NvtxRange nr("ism.dataset");
     for (int c = 0; c < n_chunks && !st; ++c) {
+        NvtxRange cr("ism.dataset.chunk");
         const int s = c & 1;
         const int64_t r0 = cb[c], r1 = cb[c + 1];
         // sources of the chunk, packed in src_d[s]

@@ -8,9 +8,21 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/ism.h"
 
 namespace ism {
+
+// NVTX range on the calling thread for the scope of the object (a profiler
+// shows the library's host phases -- plan, K1, K2, noise, serve batches --
+// on its timeline; without a profiler attached a range costs a branch).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // One RIR = (room, microphone) as the ISM kernel sees it.  FP64 geometry so
 // that the per-axis image offsets round exactly as the definition
@@ -125,6 +137,39 @@ inline long long rir_col_entries(int order) {
     const long long te = 2 * (2 * (long long)order + 1);
     return te * te;
 }
+// One K1 call prepared on the host, per filter kind: the jobs, the sparse
+// path's Chebyshev tables and per-RIR offsets, its launches (chunks of the
+// job list), and its device block: [jobs | counter | tables | offsets]
+// (blob, uploaded) then [column lists | window ranges | per-RIR tables]
+// (filled by the kernels).
+struct RirKindPrep {
+    int kind = 0;
+    bool sparse = false;
+    std::vector<RirJob> jobs;
+    std::vector<int> caps;  // per job: the lattice order its layout is sized for
+    std::vector<float> tabs;
+    std::vector<long long> offs;
+    std::vector<std::pair<size_t, size_t>> chunks;
+    int max_order = 0, max_taps = 1, wmax = 0, max_cheb = 0, min_cheb = 0;
+    size_t jb = 0, tb = 0, ob = 0, up_bytes = 0, cb = 0, wb = 0, gb = 0;
+    std::vector<unsigned char> blob;
+    size_t total() const { return up_bytes + cb + wb + gb; }
+};
+struct RirPrep {
+    int W = 0;
+    RirKindPrep k[2];
+};
+// Host preparation of a K1 call at window W (rooms validated by the
+// caller).  order_caps (nullable, one per RIR in the caller's order): the
+// lattice order each RIR's layout and launch are sized for (a RIR above its
+// capacity is an error), so that calls with other rooms of the same shape
+// get the same launches; NULL = each RIR's own order.
+int rir_prepare(const ism_room *rooms, int64_t n_rooms, const int64_t *h_offsets,
+                const ism_rir_opts &o, int W, const int *order_caps, RirPrep *out);
+// The launches of one kind, its device block at sp (blob already there).
+int rir_enqueue(const RirKindPrep &K, char *sp, int W, float *h_dev, long long *stats,
+                int *err_dev, cudaStream_t stream);
+
 // Direct per-tap kernel (bitwise reproducible).
 int launch_rir(const RirLaunch &L, cudaStream_t stream);
 size_t rir_smem_bytes(int window, int max_order, int max_taps);
@@ -182,6 +227,32 @@ int convolve_batch(const ism_conv_job *jobs, int64_t n_jobs, const float *h_dev,
                    void *stream, bool per_tile);
 int launch_conv_f32(const ConvLaunch &L, cudaStream_t stream);
 int launch_conv_bf16x3(const ConvLaunch &L, cudaStream_t stream);
+// One convolution tile: mics [mic0, mic0 + 8) of job `job`, outputs from t0.
+struct ConvTile {
+    int job;
+    int mic0;
+    int64_t t0;
+};
+// The tiles of a convolution call and its launch shapes (host), then its
+// launches given the tiles in device memory (launch_conv_* = both, with the
+// tiles uploaded through the staging blocks).  Split-BF16: tiles are
+// [whole-window per-tile | chunked per-tile | persistent]; FP32: all n_a.
+struct ConvPlan {
+    int precision = ISM_F32;
+    std::vector<ConvTile> tiles;
+    size_t n_a = 0, n_b = 0, n_c = 0;
+    int max_chunks = 0;
+    int64_t p_max_lh = 0;
+};
+int conv_plan(const ConvLaunch &L, ConvPlan *P);
+int conv_f32_plan(const ConvLaunch &L, ConvPlan *P);
+int conv_bf16x3_plan(const ConvLaunch &L, ConvPlan *P);
+int conv_f32_enqueue(const ConvLaunch &L, const ConvPlan &P, const ConvTile *d_tiles,
+                     cudaStream_t stream);
+int conv_bf16x3_enqueue(const ConvLaunch &L, const ConvPlan &P, const ConvTile *d_tiles,
+                        cudaStream_t stream);
+int conv_enqueue(const ConvLaunch &L, const ConvPlan &P, const ConvTile *d_tiles,
+                 cudaStream_t stream);
 // Tiles the persistent split-BF16 kernel makes of a room (n_mics mics,
 // RIRs of rir_len samples, signals of y_len = src_len + rir_len - 1), or -1
 // when its RIRs are too long for that kernel.
@@ -223,15 +294,18 @@ struct StatusTicket {
 };
 int status_begin(StatusTicket *t);
 // Records the ticket's completion event on `stream` (or, with ok = false,
-// gives the cell back at once: nothing was enqueued).
-int status_end(const StatusTicket &t, cudaStream_t stream, bool ok);
+// gives the cell back at once: nothing was enqueued).  owned: the cell stays
+// with its owner (a plan, whose launches all use it) until status_release.
+int status_end(const StatusTicket &t, cudaStream_t stream, bool ok, bool owned = false);
+void status_release(const StatusTicket &t);
 // ISM_ERR_INTERNAL (with the message set) if a call on `stream` (current
 // device) whose kernels have completed reported an internal error since the
 // last report; ISM_OK otherwise.  wait: first wait for every call on the
 // stream that holds a status cell.
 int status_collect(cudaStream_t stream, bool wait);
-// Test aid (ism_debug_inject): returns and clears the pending injection.
-int take_injection();
+// Test aid (ism_debug_inject): 1 if injection `what` is pending (and
+// clears it), else 0.
+int take_injection(int what);
 
 // SplitMix64 (Steele, Lea and Flood 2014): output i of the stream with
 // state x is mix(x + (i+1) * gamma).

@@ -210,6 +210,7 @@ static int64_t req_bytes(const ism_request &r) {
 
 void ism_server::launch(std::vector<std::shared_ptr<Req>> &take) {
     // called with mu held; drops it around CUDA work
+    NvtxRange nr("ism.serve.batch");
     int slot = -1;
     for (size_t i = 0; i < slot_busy.size(); ++i)
         if (!slot_busy[i]) { slot = (int)i; break; }
@@ -254,7 +255,10 @@ void ism_server::launch(std::vector<std::shared_ptr<Req>> &take) {
         }
     };
     void *blk = nullptr;
-    if (int st2 = scratch_alloc(&blk, (size_t)off * 4, s)) {
+    if (take_injection(ISM_INJECT_SERVE_ALLOC)) {  // test aid: the allocator fails
+        status = ISM_ERR_OUT_OF_MEMORY;
+        err = "device block of the batch (injected allocation failure)";
+    } else if (int st2 = scratch_alloc(&blk, (size_t)off * 4, s)) {
         status = st2;
         err = ism_last_error_string();
     }

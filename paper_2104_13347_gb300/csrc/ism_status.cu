@@ -33,6 +33,7 @@ struct Pending {
     cudaStream_t stream;
     int cell;
     cudaEvent_t ev;
+    bool owned;  // the cell belongs to a plan: read and cleared, not freed
 };
 
 std::mutex g_mu;
@@ -63,7 +64,7 @@ void reap_locked() {
         volatile int *c = host_cell(p.device, p.cell);
         if (*c) g_failed[{p.device, p.stream}]++;
         *c = 0;
-        g_free[p.device].push_back(p.cell);
+        if (!p.owned) g_free[p.device].push_back(p.cell);
         g_events[p.device].push_back(p.ev);
         g_pending[i] = g_pending.back();
         g_pending.pop_back();
@@ -110,11 +111,11 @@ int status_begin(StatusTicket *t) {
     return ISM_OK;
 }
 
-int status_end(const StatusTicket &t, cudaStream_t stream, bool ok) {
+int status_end(const StatusTicket &t, cudaStream_t stream, bool ok, bool owned) {
     if (t.cell < 0) return ISM_OK;
     std::lock_guard<std::mutex> lk(g_mu);
     if (!ok) {  // nothing was enqueued with this cell
-        g_free[t.device].push_back(t.cell);
+        if (!owned) g_free[t.device].push_back(t.cell);
         return ISM_OK;
     }
     cudaEvent_t ev = nullptr;
@@ -134,8 +135,19 @@ int status_end(const StatusTicket &t, cudaStream_t stream, bool ok) {
         g_events[t.device].push_back(ev);
         return cuda_fail(e, "cudaEventRecord(status)");
     }
-    g_pending.push_back(Pending{t.device, stream, t.cell, ev});
+    g_pending.push_back(Pending{t.device, stream, t.cell, ev, owned});
     return ISM_OK;
+}
+
+void status_release(const StatusTicket &t) {
+    if (t.cell < 0) return;
+    std::lock_guard<std::mutex> lk(g_mu);
+    // the owner has waited for its work: reap its entries, then free the cell
+    for (auto &p : g_pending)
+        if (p.device == t.device && p.cell == t.cell && cudaEventSynchronize(p.ev) != cudaSuccess)
+            cudaGetLastError();
+    reap_locked();
+    g_free[t.device].push_back(t.cell);
 }
 
 int status_collect(cudaStream_t stream, bool wait) {
@@ -163,7 +175,12 @@ int status_collect(cudaStream_t stream, bool wait) {
                 "convolution kernel after a wait ran out; their outputs are incomplete");
 }
 
-int take_injection() { return g_inject.exchange(0); }
+int take_injection(int what) {
+    int cur = g_inject.load();
+    while (cur & what)
+        if (g_inject.compare_exchange_weak(cur, cur & ~what)) return 1;
+    return 0;
+}
 
 }  // namespace ism
 
@@ -174,8 +191,9 @@ extern "C" int ism_stream_status(void *stream) {
 
 extern "C" int ism_debug_inject(int32_t what) {
     ism::set_error("");
-    if (what != 0 && what != ISM_INJECT_CONV_WAIT)
+    if (what != 0 && what != ISM_INJECT_CONV_WAIT && what != ISM_INJECT_SERVE_ALLOC)
         return ism::fail(ISM_ERR_INVALID_ARG, "unknown injection");
-    ism::g_inject.store(what);
+    if (what == 0) ism::g_inject.store(0);
+    else ism::g_inject.fetch_or(what);
     return ISM_OK;
 }

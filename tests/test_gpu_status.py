@@ -99,3 +99,32 @@ def test_served_batch_reports_it(ism):
         res = srv.wait(t2, 60.0)
         assert res.n_mics == 2
         srv.release(t2)
+
+
+def test_served_batch_allocation_failure(ism):
+    """A failing device allocation in the server's admission path (injected:
+    the allocator is not called) fails that batch's requests with
+    ISM_ERR_OUT_OF_MEMORY and returns their budget; later requests run."""
+    import time
+    room = wl.room_batch(1, seed=65, order=3, rir_len=900, n_mics=3)[0]
+    src = np.random.default_rng(66).standard_normal(1500).astype(np.float32)
+    with ism.Server(precision=ism.F32, n_streams=1, max_batch=4) as srv:
+        t0 = srv.submit(room, src)
+        srv.wait(t0, 60.0)
+        srv.release(t0)
+        ism.debug_inject(ism.INJECT_SERVE_ALLOC)
+        t = srv.submit(room, src)
+        with pytest.raises(ism.IsmError) as ei:
+            srv.wait(t, 60.0)
+        assert ei.value.status == 3  # ISM_ERR_OUT_OF_MEMORY
+        srv.release(t)
+        t2 = srv.submit(room, src)
+        res = srv.wait(t2, 60.0)
+        assert res.n_mics == 3
+        srv.release(t2)
+        for _ in range(100):  # the server thread frees released batches
+            if srv.stats()["bytes_in_use"] == 0:
+                break
+            time.sleep(0.01)
+        st = srv.stats()
+        assert st["bytes_in_use"] == 0 and st["completed"] >= 2

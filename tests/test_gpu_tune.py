@@ -36,7 +36,7 @@ def test_tuned_window_parity_and_stability(ism, tmp_path, kind, taps):
         assert W % 32 == 0 and 64 <= W <= 2048
         lines = cache.read_text().splitlines()
         assert len(lines) == 1 and lines[0].startswith("ism-tune 1 ")
-        assert int(lines[0].split()[11]) == W
+        assert int(lines[0].split()[10]) == W
         h2 = ism.rir_batch(rooms, window=ism.WINDOW_TUNE)
         h3 = ism.rir_batch(rooms, window=W)
         torch.cuda.synchronize()
