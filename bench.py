@@ -468,6 +468,8 @@ def run_served(ism, wl, rate, seconds, precision, seed=1006):
             "p99_ms": float(np.percentile(lat_ms, 99)), "completed_req_s": n / wall,
             "taps_per_s": st["taps"] / wall, "mic_samples_per_s": st["mic_samples"] / wall,
             "batches": st["batches"], "busy_retries": rejected[0],
+            "host_launch_us_per_batch": st["launch_host_ns"] / 1e3 / max(st["batches"], 1),
+            "device_us_per_batch": st["batch_device_ns"] / 1e3 / max(st["batches"], 1),
             "hbm_peak_bytes": st.get("bytes_peak"), "hbm_limit_bytes": 32 << 30,
             "workload": "Poisson arrivals; rooms U[3,20]^3 m, 4-32 mics, fs 16/48 kHz, "
                         "RT60 U[0.1,0.6] s (Sabine), sources 0.5-4 s, SNR U[0,30] dB"}

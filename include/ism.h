@@ -452,6 +452,10 @@ typedef struct ism_serve_stats {
     int64_t bytes_in_use, bytes_peak;
     int64_t taps;            /* image-source taps that landed in the RIRs */
     int64_t mic_samples;     /* convolution outputs written */
+    int64_t launch_host_ns;  /* host time the server thread spent launching
+                                batches (allocation, uploads, launches) */
+    int64_t batch_device_ns; /* device time of the finished batches, first
+                                kernel to completion (CUDA events) */
 } ism_serve_stats;
 
 /* Creates a server on config->device.  Besides at most max_hbm_bytes of
@@ -527,6 +531,16 @@ int ism_stream_status(void *stream);
  * kinds may be pending together. */
 #define ISM_INJECT_SERVE_ALLOC 2
 int ism_debug_inject(int32_t what);
+
+/* Bounds-checked build (libism_checked.so, compiled with ISM_BOUNDS_CHECK):
+ * the kernels test every index they compute from data (table entries,
+ * sparse-array positions, FIR reads, column-list slots, window words,
+ * operand extents, noise-partial slots); an index out of range sets a flag
+ * bit and its access is skipped, never trapped.  ism_debug_bounds waits for
+ * the device, returns the bits set since the last call in *flags and clears
+ * them (no counterpart in the paper; a debugging aid).  In the normal build
+ * it returns ISM_ERR_INVALID_ARG. */
+int ism_debug_bounds(uint32_t *flags);
 
 /* Message of the last error on the calling thread ("" if none). */
 const char *ism_last_error_string(void);

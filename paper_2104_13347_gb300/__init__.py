@@ -13,12 +13,12 @@ include/ism.h; this package is its Python binding.
 """
 from ._lib import (BF16X3, F32, FD_HANN_SINC, FD_LAGRANGE, INJECT_CONV_WAIT, INJECT_SERVE_ALLOC, RIR_DIRECT,  # noqa
                    RIR_SPARSE, IsmError, PreparedRooms, check, conv_jobs, convolve_batch,
-                   dataset_batch, debug_inject, frame_jobs, frames_batch, last_error, load,
+                   dataset_batch, debug_bounds, debug_inject, frame_jobs, frames_batch, last_error, load,
                    make_rooms, Plan, rir_batch, rir_batch_noalloc, rir_batch_size, rir_filter_terms,
                    rir_tuned_window, Server, stream_status, WINDOW_TUNE)
 
 __all__ = ["load", "rir_batch", "rir_batch_size", "rir_batch_noalloc", "convolve_batch",
            "conv_jobs", "dataset_batch", "frame_jobs", "frames_batch", "IsmError", "F32", "BF16X3", "FD_HANN_SINC", "FD_LAGRANGE", "RIR_SPARSE",
            "RIR_DIRECT", "last_error", "check", "make_rooms", "PreparedRooms", "rir_filter_terms", "Server",
-           "stream_status", "debug_inject", "INJECT_CONV_WAIT", "INJECT_SERVE_ALLOC", "rir_tuned_window",
+           "stream_status", "debug_inject", "debug_bounds", "INJECT_CONV_WAIT", "INJECT_SERVE_ALLOC", "rir_tuned_window",
            "WINDOW_TUNE", "Plan"]

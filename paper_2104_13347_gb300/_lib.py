@@ -15,7 +15,9 @@ import threading
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libism.so")
+# ISM_LIB selects another build of the library, e.g. the bounds-checked
+# libism_checked.so (a file name is taken relative to this package)
+LIB_PATH = os.path.join(HERE, os.environ.get("ISM_LIB", "libism.so"))
 
 ISM_OK, ISM_PENDING = 0, 1
 ISM_ERR_INVALID_ARG, ISM_ERR_OUT_OF_MEMORY, ISM_ERR_BUSY = 2, 3, 4
@@ -77,7 +79,7 @@ class PlanConfig(ctypes.Structure):
 class ServeStats(ctypes.Structure):
     _fields_ = [(n, c_i64) for n in ("submitted", "completed", "rejected_busy", "batches",
                                      "queued", "in_flight", "bytes_in_use", "bytes_peak", "taps",
-                                     "mic_samples")]
+                                     "mic_samples", "launch_host_ns", "batch_device_ns")]
 
 
 # every symbol include/ism.h declares, with its ctypes signature
@@ -105,6 +107,7 @@ SIGNATURES = {
     "ism_serve_destroy": (c_i32, [c_vp]),
     "ism_stream_status": (c_i32, [c_vp]),
     "ism_debug_inject": (c_i32, [c_i32]),
+    "ism_debug_bounds": (c_i32, [c_vp]),
     "ism_last_error_string": (ctypes.c_char_p, []),
     "ism_version": (ctypes.c_char_p, []),
 }
@@ -292,6 +295,18 @@ def stream_status(stream=None):
     cell and raises IsmError (ISM_ERR_INTERNAL) if a kernel of one of them
     reported an error since the last report."""
     check(load().ism_stream_status(_stream_ptr(stream)))
+
+
+def debug_bounds():
+    """ism_debug_bounds: the out-of-range bits the kernels of a bounds-checked
+    build recorded since the last call (cleared), or None for the normal
+    build."""
+    f = ctypes.c_uint32()
+    st = load().ism_debug_bounds(ctypes.byref(f))
+    if st == ISM_ERR_INVALID_ARG:
+        return None
+    check(st)
+    return f.value
 
 
 def debug_inject(what=INJECT_CONV_WAIT):

@@ -3,7 +3,10 @@
 Every translation unit under csrc/ is compiled by nvcc for sm_103a only, in
 parallel, then linked into paper_2104_13347_gb300/libism.so with the static
 CUDA runtime.  Rebuilds only what changed (by modification time).
-Usage: python -m paper_2104_13347_gb300.build  [--force] [--verbose]
+--bounds-check builds libism_checked.so instead (ISM_BOUNDS_CHECK: kernels
+record out-of-range indices, see ism_debug_bounds); select it at run time
+with ISM_LIB=libism_checked.so.
+Usage: python -m paper_2104_13347_gb300.build  [--force] [--verbose] [--bounds-check]
 """
 from __future__ import annotations
 
@@ -19,6 +22,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libism.so")
+BUILD_CHECKED = os.path.join(HERE, "_build_checked")
+LIB_CHECKED = os.path.join(HERE, "libism_checked.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -29,9 +34,11 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libism.so")
 
 
-def _flags(verbose: bool):
+def _flags(verbose: bool, bounds_check: bool = False):
     f = ["-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC",
          "-I", os.path.join(ROOT, "include"), "--expt-relaxed-constexpr"]
+    if bounds_check:
+        f += ["-DISM_BOUNDS_CHECK"]
     if verbose:
         f += ["-Xptxas", "-v"]
     return f
@@ -43,7 +50,9 @@ def _headers_mtime() -> float:
     return max(os.path.getmtime(h) for h in hs if os.path.exists(h))
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
+def build(force: bool = False, verbose: bool = False, bounds_check: bool = False) -> str:
+    BUILD = BUILD_CHECKED if bounds_check else globals()["BUILD"]
+    LIB = LIB_CHECKED if bounds_check else globals()["LIB"]
     os.makedirs(BUILD, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     hm = _headers_mtime()
@@ -58,7 +67,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def compile_one(so):
         s, o = so
-        cmd = [exe, *_flags(verbose), "-c", s, "-o", o + ".tmp"]
+        cmd = [exe, *_flags(verbose, bounds_check), "-c", s, "-o", o + ".tmp"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {os.path.basename(s)}:\n{r.stderr}")
@@ -82,4 +91,5 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="--verbose" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="--verbose" in sys.argv,
+                bounds_check="--bounds-check" in sys.argv))

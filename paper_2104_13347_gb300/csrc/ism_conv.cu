@@ -126,7 +126,9 @@ k_conv_f32(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles,
         if (tid == 0) {
             double t = 0.0;
             for (int w = 0; w < CT / 32; ++w) t += s_red[w];
-            part[J.part_offset + conv_partial_slot(tl.mic0, t0, ylen)] = t;
+            const int s0 = conv_partial_slot(tl.mic0, t0, ylen);
+            if (ISM_IN_RANGE(s0 >= 0 && s0 < conv_partials_per_job(J.n_mics, ylen), kOobConvF32))
+                part[J.part_offset + s0] = t;
         }
     }
 }
@@ -207,6 +209,8 @@ k_noise(const ConvJob *__restrict__ jobs, float *__restrict__ y, const double *_
 }
 
 }  // namespace
+
+ISM_OOB_READER(conv)
 
 int conv_f32_plan(const ConvLaunch &L, ConvPlan *P) {
     P->precision = ISM_F32;

@@ -380,6 +380,13 @@ k_conv_tc(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles,
             asm volatile("tcgen05.fence::after_thread_sync;");
             const uint32_t a0 = smem_u32(smem + (size_t)s * Lay.a_stride);
             uint32_t bh0, bl0;
+            if (!ISM_IN_RANGE((WHOLE_B ? ch * KC : 0) + 48 + 15 + 8 * (NN - 1) < Lay.bl,
+                              kOobTcOperand)) {
+                asm volatile(
+                    "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                        smem_u32(&bar_empty[s])));
+                continue;
+            }
             if (WHOLE_B) {
                 bh0 = smem_u32(smem + Lay.bhi) + 2u * (uint32_t)(ch * KC);
                 bl0 = smem_u32(smem + Lay.blo) + 2u * (uint32_t)(ch * KC);
@@ -493,8 +500,11 @@ k_conv_tc(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles,
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-    if (part && tid == 0)
-        part[J.part_offset + conv_partial_slot(tl.mic0, T0, J.y_len)] = s_red[0] + s_red[1];
+    if (part && tid == 0) {
+        const int s0 = conv_partial_slot(tl.mic0, T0, J.y_len);
+        if (ISM_IN_RANGE(s0 >= 0 && s0 < conv_partials_per_job(J.n_mics, J.y_len), kOobTcPartial))
+            part[J.part_offset + s0] = s_red[0] + s_red[1];
+    }
     if (warp == 4) {
         __syncwarp();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
@@ -891,7 +901,8 @@ k_conv_tcp(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles, int
                         next_waited = true;
                     }
                     const int e2 = next_pos + tid;
-                    if (e2 < next_words) store_split4(wn + e2, bl / 2, px);
+                    if (e2 < next_words && ISM_IN_RANGE(e2 < bl / 2, kOobTcpWindow))
+                        store_split4(wn + e2, bl / 2, px);
                     next_pos += P_NPROD;
                     if (e2 + P_NPROD < next_words)
                         load_source4(px, sbn, Tn.c0 + 4 * (int64_t)(e2 + P_NPROD), Tn.Ts);
@@ -956,6 +967,11 @@ k_conv_tcp(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles, int
                     }
                     const uint32_t idesc = (kIdesc & ~(0x3Fu << 17)) | ((uint32_t)(nw >> 3) << 17);
                     const uint32_t dn = d + (uint32_t)n0;
+                    // the last source element the chunk's MMAs read (per parity array)
+                    if (!ISM_IN_RANGE(32 * ch + 16 + 15 + 8 * (n0 + nw - 1) < bl, kOobTcpOperand)) {
+                        mma_commit(smem_u32(&bar_empty[s]));
+                        continue;
+                    }
 #pragma unroll
                     for (int kk = 0; kk < 2; ++kk) {
 #pragma unroll
@@ -1050,10 +1066,16 @@ k_conv_tcp(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles, int
             if (et == 0 && part) {
                 // the tile spans two slots of the noise-partial grid: its sum
                 // in the first, zero in the second
-                part[J.part_offset + conv_partial_slot(T.tl.mic0, T.T0, ylen)] =
-                    (s_red[ab][0] + s_red[ab][1]) + (s_red[ab][2] + s_red[ab][3]);
-                if (T.T0 + kConvTT < ylen)
-                    part[J.part_offset + conv_partial_slot(T.tl.mic0, T.T0 + kConvTT, ylen)] = 0.0;
+                const int np = conv_partials_per_job(J.n_mics, ylen);
+                const int s0 = conv_partial_slot(T.tl.mic0, T.T0, ylen);
+                if (ISM_IN_RANGE(s0 >= 0 && s0 < np, kOobTcpPartial))
+                    part[J.part_offset + s0] =
+                        (s_red[ab][0] + s_red[ab][1]) + (s_red[ab][2] + s_red[ab][3]);
+                if (T.T0 + kConvTT < ylen) {
+                    const int s1 = conv_partial_slot(T.tl.mic0, T.T0 + kConvTT, ylen);
+                    if (ISM_IN_RANGE(s1 >= 0 && s1 < np, kOobTcpPartial))
+                        part[J.part_offset + s1] = 0.0;
+                }
             }
         }
     }
@@ -1086,6 +1108,8 @@ std::mutex g_smem_mu;
 int g_smem_whole[64], g_smem_chunked[64], g_smem_persistent[64];
 
 }  // namespace
+
+ISM_OOB_READER(conv_tc)
 
 int64_t conv_bf16x3_persistent_tiles(int n_mics, int64_t rir_len, int64_t y_len) {
     if (p_layout(rir_len).total > kMaxDynSmem) return -1;

@@ -259,7 +259,65 @@ int conv_enqueue(const ConvLaunch &L, const ConvPlan &P, const ConvTile *d_tiles
 int64_t conv_bf16x3_persistent_tiles(int n_mics, int64_t rir_len, int64_t y_len);
 int launch_noise(const ConvLaunch &L, cudaStream_t stream);
 
+// Bounds-checked build (-DISM_BOUNDS_CHECK, libism_checked.so): the kernels
+// test the indices they compute from data -- table entries, sparse-array
+// positions, FIR reads, column-list slots, window words, operand extents,
+// output samples, noise slots -- and an index out of its range is recorded
+// as a bit in the translation unit's device flag word and its access
+// skipped (never a trap).  ism_debug_bounds reads and clears the flags.  In
+// the normal build ISM_IN_RANGE is the constant true and costs nothing.
+enum OobBit : unsigned {
+    kOobTableIndex = 1u << 0,     // K1 sparse: z table entry of a candidate
+    kOobSparsePos = 1u << 1,      // K1 sparse: sparse-array position
+    kOobFirRead = 1u << 2,        // K1 sparse: FIR read of a sparse array
+    kOobDeltaRead = 1u << 3,      // K1 sparse: integer-delay array read
+    kOobColumnSlot = 1u << 4,     // K1 tables: sorted column-list slot
+    kOobColumnEntry = 1u << 5,    // K1 sparse: column-list entry
+    kOobDirectRow = 1u << 6,      // K1 direct: window row index
+    kOobTcpWindow = 1u << 8,      // K2 persistent: source-window word
+    kOobTcpOperand = 1u << 9,     // K2 persistent: B operand extent
+    kOobTcpOutput = 1u << 10,     // K2 persistent: output sample
+    kOobTcpPartial = 1u << 11,    // K2 persistent: noise-partial slot
+    kOobTcWindow = 1u << 12,      // K2 per-tile: source-window word
+    kOobTcOperand = 1u << 13,     // K2 per-tile: B operand extent
+    kOobTcOutput = 1u << 14,      // K2 per-tile: output sample
+    kOobTcPartial = 1u << 15,     // K2 per-tile: noise-partial slot
+    kOobNoise = 1u << 16,         // noise: output sample
+    kOobConvF32 = 1u << 17,       // FP32 convolution: output sample or partial
+};
+// Per translation unit (no relocatable device code): reads and clears its
+// flag word; ISM_ERR_INVALID_ARG in the normal build.
+int oob_read_rir(unsigned int *flags);
+int oob_read_conv(unsigned int *flags);
+int oob_read_conv_tc(unsigned int *flags);
+
 #ifdef __CUDACC__
+#ifdef ISM_BOUNDS_CHECK
+static __device__ unsigned int g_ism_oob;
+__device__ __forceinline__ bool ism_oob_record(unsigned int bit) {
+    atomicOr(&g_ism_oob, bit);
+    return false;
+}
+#define ISM_IN_RANGE(cond, bit) ((cond) || ::ism::ism_oob_record(bit))
+#define ISM_OOB_READER(name)                                                              \
+    int oob_read_##name(unsigned int *flags) {                                            \
+        unsigned int v = 0u;                                                              \
+        cudaError_t e = cudaDeviceSynchronize();                                          \
+        if (e == cudaSuccess) e = cudaMemcpyFromSymbol(&v, g_ism_oob, sizeof(v));         \
+        const unsigned int z = 0u;                                                        \
+        if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_ism_oob, &z, sizeof(z));           \
+        if (e != cudaSuccess) return cuda_fail(e, "bounds flags");                        \
+        *flags |= v;                                                                      \
+        return ISM_OK;                                                                    \
+    }
+#else
+#define ISM_IN_RANGE(cond, bit) true
+#define ISM_OOB_READER(name)                                                              \
+    int oob_read_##name(unsigned int *) {                                                 \
+        return fail(ISM_ERR_INVALID_ARG, "not a bounds-checked build");                   \
+    }
+#endif
+
 // s + e += v^2 in float-float: the square's rounding error from an FMA, the
 // sum's from a two-sum (error-free transformations; the pair keeps ~2^-44
 // relative accuracy over thousands of terms).

@@ -490,7 +490,8 @@ k_ism_tables(const RirJob *__restrict__ jobs, int n_rirs, int TE, int W,
             const float r2 = col_rho2(s_x[ix], s_y[iy]);
             if (r2 <= R2) {
                 const unsigned pos = atomicAdd(&s_bin[rho2_bin(r2, sc)], 1u);
-                out[pos] = (uint32_t)ix | ((uint32_t)iy << 16);
+                if (ISM_IN_RANGE(pos < (unsigned)n_cols, kOobColumnSlot))
+                    out[pos] = (uint32_t)ix | ((uint32_t)iy << 16);
             }
         }
         __syncthreads();
@@ -663,8 +664,9 @@ __device__ __forceinline__ void sorted_sweep(const Tables &T, int TE, const Item
             iy = (int)(e >> 16);
             // (entries are < TEj by construction; the guard keeps a bad
             // entry from indexing past the tables)
-            const Col col = (ix < it.TEj && iy < it.TEj) ? column_solve_xy(T, TE, it, ix, iy, c & 1)
-                                                         : Col{1, 0, 1, 0, 0, 0, 0};
+            const bool ok_e = ISM_IN_RANGE(ix < it.TEj && iy < it.TEj, kOobColumnEntry);
+            const Col col = ok_e ? column_solve_xy(T, TE, it, ix, iy, c & 1)
+                                 : Col{1, 0, 1, 0, 0, 0, 0};
             na = max(col.hi_a - col.lo_a + 1, 0);
             nb = max(col.hi_b - col.lo_b + 1, 0);
             if (na + nb > 0) {
@@ -719,6 +721,7 @@ __device__ __forceinline__ bool eval_expanded(const Tables &T, int TE, const Ite
                                               float Rl, float gxy, int iz, int ix, int iy, int &kb,
                                               float &f, float &a, unsigned &my_taps,
                                               unsigned &my_contrib) {
+    if (!ISM_IN_RANGE(iz >= 2 * TE && iz < 2 * TE + it.TEj, kOobTableIndex)) return false;
     const float4 Z = T.hlg[iz];
     float Th, Tl;
     ff_add(Rh, Rl, Z.x, Z.y, Th, Tl);
@@ -870,7 +873,10 @@ k_ism_taps(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int max
                     const float vz = __shfl_sync(0xffffffffu, v.z, src);
                     const float vw = __shfl_sync(0xffffffffu, v.w, src);
                     // row index of tap index n is n - w0 + HALO, in [0, RL)
-                    float *p = rowp + (kbs - w0 + HALO);
+                    const int ri = kbs - w0 + HALO;
+                    if (!ISM_IN_RANGE(ri >= 0 && ri + it.n_taps - 1 < RL, kOobDirectRow))
+                        continue;
+                    float *p = rowp + ri;
                     if (KIND == ISM_FD_HANN_SINC) {
                         if (vw == 0.f) {
                             if (lane == 0) p[H] += vx;
@@ -1070,6 +1076,7 @@ k_ism_sparse(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int m
                                             my_contrib))
                 return;
             const int pos = kb + POS0;
+            if (!ISM_IN_RANGE(pos >= 0 && pos < CL, kOobSparsePos)) return;
             const float as = a * S4;  // a S, with a = prod(beta^hits) / (4 pi d)
                                       // (a = g / tau here, S4 = S q / (4 pi))
             const uint32_t q0 = __float2uint_rn(as);
@@ -1155,8 +1162,11 @@ k_ism_sparse(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int m
                         float R[12];
 #pragma unroll
                         for (int v = 0; v < 3; ++v) {
+                            const int fi = base - 4 + 4 * v;
                             const float4 w4 =
-                                *reinterpret_cast<const float4 *>(cp + base - 4 + 4 * v);
+                                ISM_IN_RANGE(fi >= 0 && fi + 3 < CL, kOobFirRead)
+                                    ? *reinterpret_cast<const float4 *>(cp + fi)
+                                    : make_float4(0.f, 0.f, 0.f, 0.f);
                             R[4 * v] = w4.x; R[4 * v + 1] = w4.y;
                             R[4 * v + 2] = w4.z; R[4 * v + 3] = w4.w;
                         }
@@ -1170,8 +1180,11 @@ k_ism_sparse(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int m
                                 for (int q = 0; q < 8; ++q)
                                     acc[q] = fmaf(bv[jj], R[(4 + q - jj - 4 * S + 12) % 12], acc[q]);
                             if (jb + 4 * S + 4 < TPj) {
-                                const float4 w4 = *reinterpret_cast<const float4 *>(
-                                    cp + base - jb - 4 * S - 8);
+                                const int fi = base - jb - 4 * S - 8;
+                                const float4 w4 =
+                                    ISM_IN_RANGE(fi >= 0 && fi + 3 < CL, kOobFirRead)
+                                        ? *reinterpret_cast<const float4 *>(cp + fi)
+                                        : make_float4(0.f, 0.f, 0.f, 0.f);
                                 constexpr int d = (12 - 4 * (S + 1) % 12) % 12;
                                 R[d] = w4.x; R[d + 1] = w4.y; R[d + 2] = w4.z; R[d + 3] = w4.w;
                             }
@@ -1201,7 +1214,9 @@ k_ism_sparse(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int m
         float *hout = h + J.h_offset;
         for (int i = tid; i < W; i += NT) {
             const long long n = (long long)it.w0 + i;
-            const float v = s_part[i] + s_delta[i + n_taps - 1 - jdelta + OFF + PADL];
+            const int di = i + n_taps - 1 - jdelta + OFF + PADL;
+            const float v =
+                s_part[i] + (ISM_IN_RANGE(di >= 0 && di < CL, kOobDeltaRead) ? s_delta[di] : 0.f);
             if (n < it.Lh) hout[n] = v;
         }
         __syncthreads();
@@ -1305,6 +1320,8 @@ int launch_sparse_t(const RirLaunch &L, cudaStream_t stream) {
 }
 
 }  // namespace
+
+ISM_OOB_READER(rir)
 
 size_t rir_smem_bytes(int window, int max_order, int max_taps) {
     return make_layout(false, window, max_order, max_taps, 0).total;

@@ -138,6 +138,7 @@ struct Batch {
     char *block = nullptr;
     int64_t bytes = 0;
     cudaEvent_t done = nullptr;
+    cudaEvent_t start = nullptr;      // timing: recorded before the batch's first copy
     long long *stats_host = nullptr;  // stats_block.ptr
     PinnedPool::Block stats_block;
     int64_t n_rirs = 0;
@@ -171,6 +172,7 @@ struct ism_server {
     int64_t bytes_in_use = 0;
     PinnedPool pool;                     // sources and statistics readbacks
     std::vector<cudaEvent_t> free_events;  // completion events for reuse (mu)
+    std::vector<cudaEvent_t> free_timing;  // timing events for reuse (mu)
 
     void loop();
     bool setup_device();
@@ -211,6 +213,7 @@ static int64_t req_bytes(const ism_request &r) {
 void ism_server::launch(std::vector<std::shared_ptr<Req>> &take) {
     // called with mu held; drops it around CUDA work
     NvtxRange nr("ism.serve.batch");
+    const auto t_host0 = Clock::now();
     int slot = -1;
     for (size_t i = 0; i < slot_busy.size(); ++i)
         if (!slot_busy[i]) { slot = (int)i; break; }
@@ -280,7 +283,17 @@ void ism_server::launch(std::vector<std::shared_ptr<Req>> &take) {
                 free_events.pop_back();
             }
         }
-        if (!bp->done) cerr(cudaEventCreateWithFlags(&bp->done, cudaEventDisableTiming), "event");
+        if (!bp->done) cerr(cudaEventCreateWithFlags(&bp->done, 0), "event");
+        {
+            std::lock_guard<std::mutex> lk2(mu);
+            if (!free_timing.empty()) {
+                bp->start = free_timing.back();
+                free_timing.pop_back();
+            }
+        }
+        if (!bp->start && status == ISM_OK)
+            cerr(cudaEventCreateWithFlags(&bp->start, 0), "event");
+        if (status == ISM_OK) cerr(cudaEventRecord(bp->start, s), "event record");
     }
     if (status == ISM_OK) {
         for (auto &r : take)
@@ -328,6 +341,8 @@ void ism_server::launch(std::vector<std::shared_ptr<Req>> &take) {
         cerr(cudaEventRecord(bp->done, s), "event record");
     }
     mu.lock();
+    st.launch_host_ns +=
+        std::chrono::duration_cast<std::chrono::nanoseconds>(Clock::now() - t_host0).count();
     if (status != ISM_OK) {
         // the batch failed to launch: its requests fail, its memory is freed
         // once every launched operation on the stream has finished
@@ -378,6 +393,9 @@ void ism_server::finish_batches() {
         if (e == cudaSuccess && kst == ISM_OK) {
             for (int64_t i = 0; i < b->n_rirs; ++i) st.taps += b->stats_host[2 * i + 1];
             st.mic_samples += b->mic_samples;
+            float ms = 0.f;
+            if (b->start && cudaEventElapsedTime(&ms, b->start, b->done) == cudaSuccess)
+                st.batch_device_ns += (int64_t)(1e6 * (double)ms);
         }
         cudaGetLastError();
         b->complete = true;
@@ -397,6 +415,7 @@ void ism_server::free_released() {
             if (b->block) scratch_free(b->block, streams[b->slot]);
             pool.put(b->stats_block);
             if (b->done) free_events.push_back(b->done);
+            if (b->start) free_timing.push_back(b->start);
             bytes_in_use -= b->bytes;
             st.bytes_in_use = bytes_in_use;
             batches.erase(batches.begin() + i);
@@ -639,12 +658,14 @@ int ism_serve_destroy(ism_server *s) {
         if (b->block) scratch_free(b->block, s->streams[b->slot]);
         s->pool.put(b->stats_block);
         if (b->done) cudaEventDestroy(b->done);
+        if (b->start) cudaEventDestroy(b->start);
     }
     for (auto st : s->streams) {
         cudaStreamSynchronize(st);
         cudaStreamDestroy(st);
     }
     for (cudaEvent_t e : s->free_events) cudaEventDestroy(e);
+    for (cudaEvent_t e : s->free_timing) cudaEventDestroy(e);
     for (auto &kv : s->reqs) s->pool.put(kv.second->src_block);
     delete s;  // frees the cached page-locked blocks
     return ISM_OK;

@@ -189,6 +189,17 @@ extern "C" int ism_stream_status(void *stream) {
     return ism::status_collect((cudaStream_t)stream, true);
 }
 
+extern "C" int ism_debug_bounds(uint32_t *flags) {
+    ism::set_error("");
+    if (!flags) return ism::fail(ISM_ERR_INVALID_ARG, "NULL flags");
+    unsigned int f = 0u;
+    if (int st = ism::oob_read_rir(&f)) return st;
+    if (int st = ism::oob_read_conv(&f)) return st;
+    if (int st = ism::oob_read_conv_tc(&f)) return st;
+    *flags = f;
+    return ISM_OK;
+}
+
 extern "C" int ism_debug_inject(int32_t what) {
     ism::set_error("");
     if (what != 0 && what != ISM_INJECT_CONV_WAIT && what != ISM_INJECT_SERVE_ALLOC)

@@ -29,3 +29,19 @@ def ism():
     import paper_2104_13347_gb300 as pkg
     pkg.load()
     return pkg
+
+
+@pytest.fixture(scope="session", autouse=True)
+def bounds_checked_build_reports_nothing():
+    """With the bounds-checked library (ISM_LIB=libism_checked.so), the
+    kernels of the whole session must have recorded no out-of-range index."""
+    yield
+    if "checked" not in os.environ.get("ISM_LIB", ""):
+        return
+    import torch
+    if not torch.cuda.is_available():
+        return
+    from paper_2104_13347_gb300 import _lib
+    flags = _lib.debug_bounds()
+    assert flags is not None, "ISM_LIB names a library that is not bounds-checked"
+    assert flags == 0, f"kernels recorded out-of-range indices: flags {flags:#x}"

@@ -295,3 +295,14 @@ def test_tuned_window_reads_the_cache_file(lib, tmp_path, monkeypatch):
     bad = dict(room, beta=[2.0] * 6)
     arr2, keep2 = lib.make_rooms([bad])
     assert L.ism_rir_tuned_window(arr2, 1, None, ctypes.byref(w)) == lib.ISM_ERR_INVALID_ARG
+
+
+def test_bounds_flags_need_the_checked_build(lib):
+    """ism_debug_bounds answers only in the bounds-checked build (host-side
+    in the normal one: no device call)."""
+    import os as _os
+    if "checked" in _os.environ.get("ISM_LIB", ""):
+        pytest.skip("bounds-checked library loaded")
+    f = ctypes.c_uint32(7)
+    assert lib.load().ism_debug_bounds(ctypes.byref(f)) == lib.ISM_ERR_INVALID_ARG
+    assert "bounds-checked" in lib.last_error()
