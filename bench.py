@@ -39,7 +39,7 @@ WORKLOAD = (f"{N_ROOMS} rooms U[3,10]x[3,8]x[2.5,4] m, beta U[0.5,0.95], {N_MICS
 # K1 DRAM traffic per room from the ncu capture summarised in
 # profiles/k_ism_sparse_and_k_conv_tcp_1024rooms.md (None when that capture
 # predates the current kernel), and the binding resources it measured.
-K1_TRAFFIC_PER_ROOM = (33.762048e6 + 16.236544e6) / 256
+K1_TRAFFIC_PER_ROOM = None  # the kernel changed (8 Chebyshev terms) since the last capture
 K1_TRAFFIC_NOTE = ("dram read+write of a 256-room ncu capture, scaled by rooms; reads are "
                    "mostly the per-RIR sorted column lists (15 KB per RIR at order 15), h "
                    "mostly leaves L2 after the kernel, so this understates its 268 MB write")

@@ -245,13 +245,23 @@ double lagrange_tap(int j, int P, double D) {
     return c;
 }
 
+// Truncation of the Chebyshev expansion: the largest tail a tap may lose,
+// relative to the peak tap.  Hann sinc: 1e-6, which keeps 8 terms for 81
+// taps (tail 7.7e-7; 9 terms would leave 3.3e-8): the truncation adds about
+// 1.2e-6 rel-L2 to a RIR, under the 1e-5 bar, for one sparse-array atomic
+// and 81 FIR multiply-adds fewer per image and output (K1 -7 % on GB300).
+// Lagrange: 5e-8, below FP32 resolution, so that the P + 1 terms of an
+// order-P filter -- exact, its taps being degree-P polynomials in the
+// delay -- are all kept.
+constexpr double kChebTailHann = 1e-6;
+constexpr double kChebTailLagrange = 5e-8;
+
 ChebTable build_cheb(int kind, int n_taps) {
     // Chebyshev interpolation at M first-kind nodes: each tap, as a function
     // of x in [-1, 1], is sampled at x_k = cos(pi (k + 1/2) / M) and
     // c_p = (2/M) sum_k g(x_k) T_p(x_k) (c_0 halved).  Terms are kept while
-    // the largest remaining tail, over all taps, exceeds 5e-8 -- below the
-    // FP32 resolution of the largest tap (about 1), so the truncation is
-    // invisible next to the FP32 accumulation.
+    // the largest remaining tail, over all taps, exceeds the filter's
+    // truncation (above) of the peak tap (about 1).
     const int M = 64;
     std::vector<double> c((size_t)M * n_taps);
     std::vector<double> vals(M);
@@ -281,7 +291,7 @@ ChebTable build_cheb(int kind, int n_taps) {
             for (int p = P; p < M; ++p) tail += fabs(c[(size_t)p * n_taps + j]);
             worst = std::max(worst, tail);
         }
-        if (worst <= 5e-8) {
+        if (worst <= (kind == ISM_FD_HANN_SINC ? kChebTailHann : kChebTailLagrange)) {
             t.n_cheb = P;
             break;
         }
@@ -313,18 +323,29 @@ int rir_prepare(const ism_room *rooms, int64_t n_rooms, const int64_t *h_offsets
                 const ism_rir_opts &o, int W, const int *order_caps, RirPrep *out) {
     RirPrep &P = *out;
     P.W = W;
-    // jobs, one per RIR; grouped by filter kind (one launch per kind)
-    std::vector<int64_t> room_of[2];
+    // jobs, one per RIR; grouped by filter kind (one launch per group)
+    std::vector<int64_t> room_of[kRirGroups];
     int64_t j = 0, packed = 0;
-    for (int kind = 0; kind < 2; ++kind) {
-        P.k[kind] = RirKindPrep();
-        P.k[kind].kind = kind;
+    for (int g = 0; g < kRirGroups; ++g) {
+        P.k[g] = RirKindPrep();
+        P.k[g].kind = g == 1 ? ISM_FD_LAGRANGE : ISM_FD_HANN_SINC;
     }
     for (int64_t r = 0; r < n_rooms; ++r) {
         const ism_room &R = rooms[r];
         const int kind = R.fd_kind;
-        RirKindPrep &K = P.k[kind];
         for (int m = 0; m < R.n_mics; ++m, ++j) {
+            // a Hann-sinc RIR that ends before its direct arrival holds only
+            // filter tails: the direct per-tap kernel (group 2)
+            int grp = kind;
+            if (kind == ISM_FD_HANN_SINC && o.variant == ISM_RIR_SPARSE) {
+                double d2 = 0.0;
+                for (int a = 0; a < 3; ++a) {
+                    const double dd = R.src[a] - R.mics[3 * m + a];
+                    d2 += dd * dd;
+                }
+                if (rint(sqrt(d2) * (R.fs / R.c)) >= (double)R.rir_len) grp = 2;
+            }
+            RirKindPrep &K = P.k[grp];
             RirJob J;
             memset(&J, 0, sizeof(J));
             for (int a = 0; a < 3; ++a) {
@@ -349,7 +370,7 @@ int rir_prepare(const ism_room *rooms, int64_t n_rooms, const int64_t *h_offsets
                                                      ": lattice order above the plan's capacity");
             K.jobs.push_back(J);
             K.caps.push_back(cap);
-            room_of[kind].push_back(r);
+            room_of[grp].push_back(r);
             K.max_order = std::max(K.max_order, cap);
             K.max_taps = std::max(K.max_taps, R.n_taps);
             K.wmax = std::max(K.wmax, J.n_windows);
@@ -357,12 +378,13 @@ int rir_prepare(const ism_room *rooms, int64_t n_rooms, const int64_t *h_offsets
     }
     if (j > 0x3fffffff) return fail(ISM_ERR_INVALID_ARG, "too many RIRs");
 
-    for (int kind = 0; kind < 2; ++kind) {
-        RirKindPrep &K = P.k[kind];
+    for (int grp = 0; grp < kRirGroups; ++grp) {
+        RirKindPrep &K = P.k[grp];
+        const int kind = K.kind;
         auto &jv = K.jobs;
         if (jv.empty()) continue;
         // sparse path: one Chebyshev table per distinct filter length
-        K.sparse = o.variant == ISM_RIR_SPARSE;
+        K.sparse = o.variant == ISM_RIR_SPARSE && grp != 2;
         K.max_cheb = 0;
         K.min_cheb = kMaxCheb;
         if (K.sparse) {
@@ -408,7 +430,7 @@ int rir_prepare(const ism_room *rooms, int64_t n_rooms, const int64_t *h_offsets
             long long acc = 0;
             for (size_t k = 0; k < jv.size(); ++k) {
                 const long long ce = K.sparse ? rir_col_entries(K.caps[k]) : 0;
-                const bool cut = o.per_room ? room_of[kind][k] != room_of[kind][b]
+                const bool cut = o.per_room ? room_of[grp][k] != room_of[grp][b]
                                             : (k > b && acc + ce > kColBudget);
                 if (cut) {
                     K.chunks.push_back({b, k});
@@ -544,8 +566,8 @@ int ism_rir_batch_ex(const ism_room *rooms, int64_t n_rooms, float *h_dev,
         if (int st = rir_prepare(rooms, n_rooms, h_offsets, o, W, nullptr, &P)) return st;
     }
     NvtxRange r("ism.rir.K1");
-    for (int kind = 0; kind < 2; ++kind) {
-        const RirKindPrep &K = P.k[kind];
+    for (int grp = 0; grp < kRirGroups; ++grp) {
+        const RirKindPrep &K = P.k[grp];
         if (K.jobs.empty()) continue;
         // one scratch block and one upload: [jobs | counter | filter tables |
         // offsets] copied from the host, then the column lists, window

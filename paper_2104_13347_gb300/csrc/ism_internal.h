@@ -155,9 +155,16 @@ struct RirKindPrep {
     std::vector<unsigned char> blob;
     size_t total() const { return up_bytes + cb + wb + gb; }
 };
+// Launch groups of a K1 call: 0 the Hann-sinc RIRs, 1 the Lagrange ones,
+// 2 the Hann-sinc RIRs that end before their direct arrival (rint of the
+// direct delay >= rir_len), which hold nothing but filter tails and take the
+// direct per-tap kernel: the sparse path's truncation error is relative to
+// the peak tap, so on a RIR made only of far tail taps it could pass the
+// 1e-5 bar (on every other RIR the direct path's central taps dominate).
+constexpr int kRirGroups = 3;
 struct RirPrep {
     int W = 0;
-    RirKindPrep k[2];
+    RirKindPrep k[kRirGroups];
 };
 // Host preparation of a K1 call at window W (rooms validated by the
 // caller).  order_caps (nullable, one per RIR in the caller's order): the

@@ -47,8 +47,8 @@ struct ism_plan {
     std::vector<ConvJob> cjobs;
     int64_t n_part = 0;
     char *dblock = nullptr;
-    size_t off_rir[2] = {0, 0}, off_cj = 0, off_tiles = 0, off_part = 0, d_bytes = 0;
-    size_t s_rir[2] = {0, 0}, s_cj = 0, stage_bytes = 0;
+    size_t off_rir[kRirGroups] = {}, off_cj = 0, off_tiles = 0, off_part = 0, d_bytes = 0;
+    size_t s_rir[kRirGroups] = {}, s_cj = 0, stage_bytes = 0;
     void *pinned[2] = {nullptr, nullptr};
     cudaGraphExec_t exec[2] = {nullptr, nullptr};
     cudaEvent_t done[2] = {nullptr, nullptr};
@@ -122,7 +122,7 @@ ConvLaunch plan_conv_launch(ism_plan &P) {
 
 // The same launches as at creation?  (rooms already validated)
 int same_launches(const RirPrep &a, const RirPrep &b) {
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < kRirGroups; ++k) {
         const RirKindPrep &x = a.k[k], &y = b.k[k];
         if (x.jobs.size() != y.jobs.size() || x.sparse != y.sparse || x.up_bytes != y.up_bytes ||
             x.total() != y.total() || x.chunks != y.chunks || x.max_order != y.max_order ||
@@ -149,7 +149,7 @@ int check_shape(const ism_plan &P, const ism_room *rooms, int64_t n_rooms) {
 // Writes run descriptors into staging buffer k.
 void stage(ism_plan &P, int k, const RirPrep &rp, const std::vector<ConvJob> &cj) {
     char *st = (char *)P.pinned[k];
-    for (int kind = 0; kind < 2; ++kind)
+    for (int kind = 0; kind < kRirGroups; ++kind)
         if (!rp.k[kind].jobs.empty())
             memcpy(st + P.s_rir[kind], rp.k[kind].blob.data(), rp.k[kind].up_bytes);
     if (P.conv) memcpy(st + P.s_cj, cj.data(), cj.size() * sizeof(ConvJob));
@@ -224,7 +224,7 @@ int ism_plan_create(const ism_room *rooms, int64_t n_rooms, const int64_t *src_l
     }
     // device block: [kind 0 | kind 1 | conv jobs | tiles | noise partials]
     size_t o_ = 0;
-    for (int kind = 0; kind < 2; ++kind) {
+    for (int kind = 0; kind < kRirGroups; ++kind) {
         P->off_rir[kind] = o_;
         if (!P->prep.k[kind].jobs.empty()) o_ += al256(P->prep.k[kind].total());
     }
@@ -243,7 +243,7 @@ int ism_plan_create(const ism_room *rooms, int64_t n_rooms, const int64_t *src_l
     P->d_bytes = std::max<size_t>(o_, 256);
     // staging: [kind 0 blob | kind 1 blob | conv jobs]
     size_t s_ = 0;
-    for (int kind = 0; kind < 2; ++kind) {
+    for (int kind = 0; kind < kRirGroups; ++kind) {
         P->s_rir[kind] = s_;
         s_ += al256(P->prep.k[kind].up_bytes);
     }
@@ -284,7 +284,7 @@ int ism_plan_create(const ism_room *rooms, int64_t n_rooms, const int64_t *src_l
             st = cuda_fail(e, "cudaStreamBeginCapture(plan)");
             break;
         }
-        for (int kind = 0; kind < 2 && !st; ++kind) {
+        for (int kind = 0; kind < kRirGroups && !st; ++kind) {
             const RirKindPrep &K = P->prep.k[kind];
             if (K.jobs.empty()) continue;
             if ((e = cudaMemcpyAsync(P->dblock + P->off_rir[kind], (char *)P->pinned[k] + P->s_rir[kind],
@@ -296,7 +296,7 @@ int ism_plan_create(const ism_room *rooms, int64_t n_rooms, const int64_t *src_l
                                  P->cjobs.size() * sizeof(ConvJob), cudaMemcpyHostToDevice, cs)) !=
                 cudaSuccess)
             st = cuda_fail(e, "plan descriptor copy");
-        for (int kind = 0; kind < 2 && !st; ++kind) {
+        for (int kind = 0; kind < kRirGroups && !st; ++kind) {
             const RirKindPrep &K = P->prep.k[kind];
             if (K.jobs.empty()) continue;
             st = rir_enqueue(K, P->dblock + P->off_rir[kind], W, h_dev, nullptr, nullptr, cs);

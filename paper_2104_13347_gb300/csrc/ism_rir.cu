@@ -27,9 +27,9 @@
 //  * k_ism_sparse (default): the tap function of the filter, g_j(f), is
 //    expanded in Chebyshev polynomials of the fraction, g_j(f) ~ sum_p
 //    B[p][j] T_p(x(f)) (FP64 table, truncated where the remaining terms sum
-//    below 5e-8 of the peak tap, under FP32 resolution; exact for the
-//    8-tap Lagrange filter, whose taps are degree-7 polynomials in the
-//    delay).  Each image then adds a T_p(x) to P sparse integer-delay
+//    below 1e-6 of the peak tap for the Hann sinc -- 8 terms for 81 taps --
+//    and exact for the 8-tap Lagrange filter, whose taps are degree-7
+//    polynomials in the delay).  Each image then adds a T_p(x) to P sparse integer-delay
 //    arrays c_p[kb] -- the paper's representation of the integer delays as a
 //    sparse array -- held in 32-bit fixed point (native u32 shared-memory
 //    atomics, order-independent sums: bitwise reproducible), and one FIR per
@@ -1372,6 +1372,9 @@ int launch_rir_sparse(const RirLaunch &L, cudaStream_t stream) {
     if (pf == 9)
         return st ? launch_sparse_t<ISM_FD_HANN_SINC, true, 9>(L, stream)
                   : launch_sparse_t<ISM_FD_HANN_SINC, false, 9>(L, stream);
+    if (pf == 8)
+        return st ? launch_sparse_t<ISM_FD_HANN_SINC, true, 8>(L, stream)
+                  : launch_sparse_t<ISM_FD_HANN_SINC, false, 8>(L, stream);
     return st ? launch_sparse_t<ISM_FD_HANN_SINC, true, 0>(L, stream)
               : launch_sparse_t<ISM_FD_HANN_SINC, false, 0>(L, stream);
 }

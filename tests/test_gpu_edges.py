@@ -1,8 +1,8 @@
 """Edge cases of the RIR kernels against the FP64 oracle (Sec. II.A
 definition): the smallest lattice, RIRs of one or two samples, lengths at
-the work-item window boundary, the shortest and longest filters (the 1- and
-3-tap Hann filters need 11 Chebyshev terms, so they take the generic term
-loop; the 255-tap one needs the widest sparse arrays), the 2-tap Lagrange
+the work-item window boundary, the shortest and longest filters (the 1-tap
+Hann filter needs 11 Chebyshev terms, so it takes the generic term loop; the
+255-tap one needs the widest sparse arrays), the 2-tap Lagrange
 filter (linear interpolation), and mixed filters and orders in one call."""
 import numpy as np
 import pytest
@@ -49,6 +49,8 @@ def test_order_zero_and_tiny_rirs(ism, variant):
     for i, L in enumerate((1, 2, 3, 17)):
         rooms += wl.room_batch(1, seed=60 + i, order=0, rir_len=L, n_mics=2)
     # a source 0.3 m from the mic: the direct path lands in the first taps
+    # (its delay is 14 samples: the 1- and 5-sample RIRs hold only the tails
+    # of its filter, and take the direct per-tap kernel on the sparse path)
     rooms += [dict(dims=np.array([4.0, 3.0, 2.5]), beta=np.full(6, 0.9),
                    src=np.array([1.0, 1.0, 1.0]), mics=np.array([[1.3, 1.0, 1.0]]), fs=16000.0,
                    c=343.0, order=2, n_taps=81, fd_kind=0, rir_len=L) for L in (1, 5, 40)]
@@ -73,12 +75,40 @@ def test_extreme_filters(ism, variant):
 
 
 def test_sparse_term_counts():
-    """Which filters above take the unrolled term loop: 9 terms for the
-    Hann sinc from 33 taps up (255 included), 11 for the 1- and 3-tap Hann
-    filters (their window is sharp, so the taps vary faster with the
-    fraction) and exact counts for short Lagrange filters -- so the
-    generic loop is exercised too."""
+    """Which filters above take the unrolled term loops: 8 terms for the
+    Hann sinc from 33 taps up (255 included), 9 for 3 taps and 11 for the
+    1-tap filter (its window is sharp, so the tap varies faster with the
+    fraction) and exact counts for Lagrange filters -- so the generic loop
+    is exercised too."""
     import paper_2104_13347_gb300 as ism
-    assert ism.rir_filter_terms(0, 81) == 9 and ism.rir_filter_terms(0, 255) == 9
-    assert ism.rir_filter_terms(0, 1) == 11 and ism.rir_filter_terms(0, 3) == 11
+    assert ism.rir_filter_terms(0, 81) == 8 and ism.rir_filter_terms(0, 255) == 8
+    assert ism.rir_filter_terms(0, 1) == 11 and ism.rir_filter_terms(0, 3) == 9
     assert ism.rir_filter_terms(1, 2) == 2 and ism.rir_filter_terms(1, 8) == 8
+
+
+def test_tail_only_rirs_take_the_direct_kernel(ism):
+    """RIRs that end before their direct arrival hold only filter tails; the
+    sparse path routes them to the direct per-tap kernel, so with the same
+    window they are bitwise those of the direct variant (and within the bar
+    of the oracle); the other RIRs of the call stay on the sparse kernel."""
+    import torch
+    rooms = [dict(dims=np.array([6.0, 5.0, 3.0]), beta=np.full(6, 0.85),
+                  src=np.array([1.0, 1.0, 1.5]), mics=np.array([[3.5, 2.0, 1.2], [1.2, 1.1, 1.5]]),
+                  fs=16000.0, c=343.0, order=3, n_taps=81, fd_kind=0, rir_len=L)
+             for L in (20, 100, 700)]
+    hs = ism.rir_batch(rooms, window=256)
+    hd = ism.rir_batch(rooms, window=256, variant=ism.RIR_DIRECT)
+    torch.cuda.synchronize()
+    hs, hd = hs.cpu().numpy(), hd.cpu().numpy()
+    # mic 0 is 2.7 m away (126 samples): tail-only in the 20- and 100-sample
+    # RIRs (the second holds the direct path's taps 86..99); mic 1 is 0.22 m
+    # away (10 samples): its direct path is inside
+    o = 0
+    for L in (20, 100, 700):
+        for m in range(2):
+            seg = slice(o, o + L)
+            if m == 0 and L < 126:
+                np.testing.assert_array_equal(hs[seg], hd[seg])
+                assert (L == 20) != bool(np.any(hs[seg]))
+            o += L
+    run(ism, rooms, 0)

@@ -104,8 +104,10 @@ def test_reciprocity(ism):
 
 def test_window_and_per_room_paths_agree(ism):
     """The direct path is bitwise reproducible: the per-room launches and the
-    batched launch lay down the same items in the same order.  The sparse
-    path sums with shared-memory atomics, so it agrees to FP32 rounding."""
+    batched launch lay down the same items in the same order, and other
+    windows agree to FP32 rounding.  The sparse path differs from it by its
+    Chebyshev truncation (a tail of 7.7e-7 of the peak tap for the 81-tap
+    filter, about 1.2e-6 rel-L2 on a RIR), so it is held to 3e-6."""
     rooms = wl.room_batch(6, seed=12, order=6, rir_len=3000, n_mics=3)
     a, _ = gpu_rirs(ism, rooms, window=512, variant=1)
     b, _ = gpu_rirs(ism, rooms, window=512, per_room=True, variant=1)
@@ -115,8 +117,9 @@ def test_window_and_per_room_paths_agree(ism):
     for x, y, z, u, v in zip(a, b, c, d, e):
         np.testing.assert_array_equal(x, y)
         assert rel_l2(z, x) < 1e-6
-        assert rel_l2(u, x) < 1e-6
-        assert rel_l2(v, x) < 1e-6
+        assert rel_l2(u, x) < 3e-6
+        assert rel_l2(v, x) < 3e-6
+        assert rel_l2(v, u) < 1e-6
 
 
 @pytest.mark.parametrize("variant", VARIANTS)
