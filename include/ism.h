@@ -352,6 +352,8 @@ int ism_plan_create(const ism_room *rooms, int64_t n_rooms, const int64_t *src_l
 int ism_plan_run(ism_plan *plan, const ism_room *rooms, const float *snr_db,
                  uint64_t noise_id_base, void *stream);
 
+/* A plan is not thread-safe: run it from one thread at a time. */
+
 /* Waits for the plan's runs, then frees it. */
 int ism_plan_destroy(ism_plan *plan);
 

@@ -89,3 +89,47 @@ def test_plan_of_rirs_only_and_shape_checks(ism):
         with pytest.raises(ism.IsmError) as ei:
             plan.run(deep)
         assert ei.value.status == 2
+
+
+def test_plan_with_every_launch_group(ism):
+    """A plan whose batch holds Hann-sinc RIRs, Lagrange RIRs and Hann RIRs
+    that end before their direct arrival (the three launch groups of a RIR
+    call, the last on the direct kernel), delay-limited orders with a
+    capacity, and FP32 convolution: runs with new geometry match the batch
+    entry points bit for bit."""
+    import torch
+
+    def batch(seed):
+        rng = np.random.default_rng(seed)
+        out = []
+        for i in range(4):
+            kind = i % 2
+            r = wl.room_batch(1, seed=seed * 10 + i, order=-1, rir_len=700 + 300 * i, n_mics=3,
+                              n_taps=8 if kind else 81, fd_kind=kind)[0]
+            out.append(r)
+        # a 24-sample RIR of mics about 1 m from the source (direct delay
+        # ~47 samples): only the direct path's filter tail lands in it
+        dx = 0.01 * rng.random()
+        out.append(dict(dims=np.array([6.0, 5.0, 3.0]), beta=np.full(6, 0.8),
+                        src=np.array([1.0 + dx, 1.0, 1.5]),
+                        mics=np.array([[2.0, 1.0, 1.5], [1.0, 2.1, 1.5]]), fs=16000.0,
+                        c=343.0, order=3, n_taps=81, fd_kind=0, rir_len=24))
+        return out
+
+    sets = [batch(500 + k) for k in range(3)]
+    srcs = wl.sources(sets[0], 0.05, seed=510)
+    lens = [len(s) for s in srcs]
+    src = torch.from_numpy(np.concatenate(srcs)).cuda()
+    _, hl = ism.rir_batch_size(sets[0])
+    M = [len(r["mics"]) for r in sets[0]]
+    ylen = sum(m * (T + r["rir_len"] - 1) for m, T, r in zip(M, lens, sets[0]))
+    h = torch.empty(hl, device="cuda")
+    y = torch.empty(ylen, device="cuda")
+    with ism.Plan(sets[0], h, src, y, src_lens=lens, precision=ism.F32, window=256,
+                  max_order=40, seed=3) as plan:
+        for k, rooms in enumerate(sets):
+            plan.run(rooms, snr_db=[10.0] * len(rooms), noise_id_base=7 * k)
+            torch.cuda.synchronize()
+            hd, yd = direct_step(ism, rooms, srcs, [10.0] * len(rooms), 7 * k, 3, ism.F32, 256)
+            assert torch.equal(h, hd), k
+            assert torch.equal(y, yd), k

@@ -63,3 +63,21 @@ def test_tuned_window_statistics_counted_once(ism):
     ism.rir_batch(rooms, stats=s2)
     torch.cuda.synchronize()
     assert torch.equal(s1, s2)
+
+
+def test_tuned_window_mixed_call(ism, tmp_path):
+    """A call mixing both filters and RIR lengths tunes one window for the
+    call; its RIRs are those of that window given explicitly."""
+    import torch
+    os.environ["ISM_TUNE_CACHE"] = str(tmp_path / "t.txt")
+    try:
+        rooms = (wl.room_batch(20, seed=97, order=5, rir_len=2500, n_mics=3)
+                 + wl.room_batch(20, seed=98, order=4, rir_len=1200, n_mics=2, n_taps=8,
+                                 fd_kind=wl.FD_LAGRANGE))
+        h1 = ism.rir_batch(rooms, window=ism.WINDOW_TUNE)
+        W = ism.rir_tuned_window(rooms)
+        h2 = ism.rir_batch(rooms, window=W)
+        torch.cuda.synchronize()
+        assert W > 0 and torch.equal(h1, h2)
+    finally:
+        os.environ.pop("ISM_TUNE_CACHE", None)
