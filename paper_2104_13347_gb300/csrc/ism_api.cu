@@ -373,6 +373,7 @@ int rir_prepare(const ism_room *rooms, int64_t n_rooms, const int64_t *h_offsets
             room_of[grp].push_back(r);
             K.max_order = std::max(K.max_order, cap);
             K.max_taps = std::max(K.max_taps, R.n_taps);
+            K.min_taps = std::min(K.min_taps, R.n_taps);
             K.wmax = std::max(K.wmax, J.n_windows);
         }
     }
@@ -499,7 +500,7 @@ int rir_enqueue(const RirKindPrep &K, char *sp, int W, float *h_dev, long long *
             if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(counter)");
         }
         RirLaunch L{d_jobs + b, (int)n, wm, W, K.max_order, K.max_taps, K.kind, h_dev,
-                    stats, d_counter, nullptr, 0, d_tabs, K.max_cheb, K.min_cheb};
+                    stats, d_counter, nullptr, 0, d_tabs, K.max_cheb, K.min_cheb, K.min_taps};
         if (K.sparse) {
             L.cols_dev = d_cols;
             L.wr_dev = d_wr;

@@ -118,6 +118,7 @@ struct RirLaunch {
     const float *tabs_dev;  // sparse kernel: Chebyshev tables [p][n_taps]
     int max_cheb;           // sparse kernel: largest n_cheb of the jobs
     int min_cheb;           // sparse kernel: smallest n_cheb of the jobs
+    int min_taps = 0;       // sparse kernel: smallest n_taps of the jobs
     // sparse kernel scratch: per RIR j, offs_dev[2 j] is the offset of its
     // sorted column list in cols_dev (room for TEj^2 entries, TEj = 2 (2 N_j
     // + 1)) and offs_dev[2 j + 1] the offset of its per-window rank ranges
@@ -150,7 +151,7 @@ struct RirKindPrep {
     std::vector<float> tabs;
     std::vector<long long> offs;
     std::vector<std::pair<size_t, size_t>> chunks;
-    int max_order = 0, max_taps = 1, wmax = 0, max_cheb = 0, min_cheb = 0;
+    int max_order = 0, max_taps = 1, min_taps = 1 << 30, wmax = 0, max_cheb = 0, min_cheb = 0;
     size_t jb = 0, tb = 0, ob = 0, up_bytes = 0, cb = 0, wb = 0, gb = 0;
     std::vector<unsigned char> blob;
     size_t total() const { return up_bytes + cb + wb + gb; }

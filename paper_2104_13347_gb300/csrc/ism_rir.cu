@@ -979,19 +979,28 @@ constexpr double kFix0 = 16777216.0;           // 2^24
 constexpr uint32_t kFixLimit = 0x7e000000u;    // 2^31 - 2^25
 
 // PFIX > 0: every job of the launch has PFIX Chebyshev terms (the term loop
-// is unrolled); 0: per-job count.
-template <int KIND, bool STATS, int PFIX>
+// is unrolled); 0: per-job count.  SPEC = 1: the launch's window is
+// kSpecW and every job has kSpecTaps taps (the dataset's configuration), so
+// the sparse arrays' stride, the FIR's tap loop and the window loop are
+// compile-time constants (the term atomics address their arrays with
+// immediate offsets).
+constexpr int kSpecW = 1024, kSpecTaps = 81;
+
+template <int KIND, bool STATS, int PFIX, int SPEC>
 __global__ void __launch_bounds__(NT, 4)
-k_ism_sparse(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int max_order,
-             int max_taps, int max_cheb, const float *__restrict__ tabs, float *__restrict__ h,
+k_ism_sparse(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W_arg, int max_order,
+             int max_taps_arg, int max_cheb, const float *__restrict__ tabs, float *__restrict__ h,
              long long *__restrict__ stats, unsigned int *__restrict__ counter,
              const double *__restrict__ g_sq, const float4 *__restrict__ g_hlg,
              const float *__restrict__ g_dl, const JobConst *__restrict__ g_jc,
              const uint32_t *__restrict__ g_cols, const int2 *__restrict__ g_wr,
              const long long *__restrict__ g_offs) {
     extern __shared__ __align__(16) unsigned char smem[];
+    const int W = SPEC ? kSpecW : W_arg;
+    const int max_taps = SPEC ? kSpecTaps : max_taps_arg;
     const Layout Lay = make_layout(true, W, max_order, max_taps, max_cheb);
-    const int TE = Lay.TE, CL = Lay.CL;
+    const int TE = Lay.TE;
+    const int CL = SPEC ? round4(kSpecW + kSpecTaps + 12 + PADL) : Lay.CL;
     Tables T;
     T.sq = nullptr;  // per item: the RIR's FP64 table in global memory (exact path only)
     T.hlg = (float4 *)(smem + Lay.off_hlg);
@@ -1058,7 +1067,7 @@ k_ism_sparse(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int m
                          0.5f * (float)kFixLimit * 12.566370614359172f * d_floor / n_bound);
         };
         const int Pc = J.n_cheb;
-        const int n_taps = it.n_taps;
+        const int n_taps = SPEC ? kSpecTaps : it.n_taps;
         // this window's ranks in the RIR's sorted column list
         const int2 wr = g_wr[g_offs[2 * jr + 1] + wi];
         const uint32_t *cols = g_cols + g_offs[2 * jr];
@@ -1282,10 +1291,10 @@ int launch_direct_t(const RirLaunch &L, cudaStream_t stream) {
     return ISM_OK;
 }
 
-template <int KIND, bool STATS, int PFIX>
+template <int KIND, bool STATS, int PFIX, int SPEC = 0>
 int launch_sparse_t(const RirLaunch &L, cudaStream_t stream) {
     const Layout Lay = make_layout(true, L.window, L.max_order, L.max_taps, L.max_cheb);
-    auto kern = k_ism_sparse<KIND, STATS, PFIX>;
+    auto kern = k_ism_sparse<KIND, STATS, PFIX, SPEC>;
     static KernelCache cache;
     int grid = 0;
     if (int st = prepare_launch(kern, cache, Lay.total, "k_ism_sparse", &grid)) return st;
@@ -1372,6 +1381,9 @@ int launch_rir_sparse(const RirLaunch &L, cudaStream_t stream) {
     if (pf == 9)
         return st ? launch_sparse_t<ISM_FD_HANN_SINC, true, 9>(L, stream)
                   : launch_sparse_t<ISM_FD_HANN_SINC, false, 9>(L, stream);
+    if (pf == 8 && L.window == kSpecW && L.max_taps == kSpecTaps && L.min_taps == kSpecTaps)
+        return st ? launch_sparse_t<ISM_FD_HANN_SINC, true, 8, 1>(L, stream)
+                  : launch_sparse_t<ISM_FD_HANN_SINC, false, 8, 1>(L, stream);
     if (pf == 8)
         return st ? launch_sparse_t<ISM_FD_HANN_SINC, true, 8>(L, stream)
                   : launch_sparse_t<ISM_FD_HANN_SINC, false, 8>(L, stream);
