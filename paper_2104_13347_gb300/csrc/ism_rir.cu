@@ -1050,6 +1050,11 @@ k_ism_sparse(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W_arg, i
         float tau_lo, tau_hi;
         const JobConst jc = g_jc[jr];
         item_setup_f32<KIND>(J, jc, W, wi, it, tau_lo, tau_hi);
+        if (SPEC) {  // the same values, known to the compiler
+            it.n_taps = kSpecTaps;
+            it.H = (kSpecTaps - 1) / 2;
+            it.W = kSpecW;
+        }
         // fixed-point scales (see kFix0): d_floor bounds from below the
         // distance of every image whose taps reach this window; one delay
         // bucket holds at most n_bound images
