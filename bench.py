@@ -407,7 +407,7 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
-def run_served(ism, wl, rate, seconds, precision, seed=1006):
+def run_served(ism, wl, rate, seconds, precision, seed=1006, n_streams=16):
     """Serving stream: Poisson arrivals at `rate` req/s for `seconds`; rooms
     U[3,20] m per side, 4-32 mics, fs 16/48 kHz, RT60 U[0.1,0.6] s, sources
     0.5-4 s.  Requests are submitted at their arrival times while earlier
@@ -417,7 +417,7 @@ def run_served(ism, wl, rate, seconds, precision, seed=1006):
     arrivals, rooms, srcs, snrs = wl.serve_stream(n, rate_hz=rate, seed=seed)
     lat, tickets, rejected = [], [], [0]
     done = threading.Event()
-    with ism.Server(precision=precision, seed=seed, max_batch=64, n_streams=4,
+    with ism.Server(precision=precision, seed=seed, max_batch=64, n_streams=n_streams,
                     max_hbm_bytes=32 << 30, max_queue=1 << 16) as srv:
         # warm the kernels and tables outside the measurement
         for i in range(4):
@@ -467,7 +467,7 @@ def run_served(ism, wl, rate, seconds, precision, seed=1006):
     return {"rate_req_s": rate, "requests": n, "p50_ms": float(np.percentile(lat_ms, 50)),
             "p99_ms": float(np.percentile(lat_ms, 99)), "completed_req_s": n / wall,
             "taps_per_s": st["taps"] / wall, "mic_samples_per_s": st["mic_samples"] / wall,
-            "batches": st["batches"], "busy_retries": rejected[0],
+            "batches": st["batches"], "busy_retries": rejected[0], "streams": n_streams,
             "host_launch_us_per_batch": st["launch_host_ns"] / 1e3 / max(st["batches"], 1),
             "device_us_per_batch": st["batch_device_ns"] / 1e3 / max(st["batches"], 1),
             "hbm_peak_bytes": st.get("bytes_peak"), "hbm_limit_bytes": 32 << 30,
@@ -760,7 +760,8 @@ def run_ours(args, ws, rank):
         line["ragged"] = run_ragged(ism, wl, args.ragged, dev, stream)
     rates = [float(r) for r in args.serve_rates.split(",") if r] if args.serve_rate > 0 else []
     if rates:
-        line["served"] = [run_served(ism, wl, r, args.serve_seconds, precision) for r in rates]
+        line["served"] = [run_served(ism, wl, r, args.serve_seconds, precision,
+                                     n_streams=args.serve_streams) for r in rates]
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cb = cpu_sample(rooms, srcs)
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample",
@@ -787,6 +788,8 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=1.0,
                     help="0 skips the served streams (their rates: --serve-rates)")
     ap.add_argument("--serve-seconds", type=float, default=2.0)
+    ap.add_argument("--serve-streams", type=int, default=16,
+                    help="streams of the server (batches in flight at once)")
     ap.add_argument("--serve-rates", default="200,1000,5000",
                     help="Poisson rates (req/s) of the served streams, comma-separated")
     ap.add_argument("--plain-path", type=int, default=1,
