@@ -100,6 +100,17 @@ __device__ __forceinline__ int block_scan(int v, int *s_w, int &total) {
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 __host__ __device__ inline int round4(int x) { return (x + 3) & ~3; }
+__host__ __device__ inline int round64(int x) { return (x + 63) & ~63; }
+
+// Storage order of the sparse arrays: word x is kept at x ^ (bit 5 of x ->
+// bit 2), i.e. the 16-byte groups of every odd 32-word line are swapped in
+// pairs.  The FIR reads 128-bit words at a stride of 8 words per lane, which
+// in plain order hits only 4 of the 8 16-byte bank groups per 8-lane phase
+// (2-way conflicts); swizzled, any 8 consecutive lanes cover all 8, for every
+// alignment.  The map permutes each 32-word line in place, keeps 16-byte
+// groups whole and, with the row length a multiple of 64 words, commutes
+// with the row offsets.
+__device__ __forceinline__ int swz(int x) { return x ^ ((x >> 3) & 4); }
 
 struct Tables {
     const double *sq;  // [3][TE] squared axis offsets (FP64, definition rounding)
@@ -123,7 +134,7 @@ __host__ __device__ inline Layout make_layout(bool sparse, int window, int max_o
     Layout L;
     L.TE = 2 * (2 * max_order + 1);
     L.RL = round4(window + 2 * (max_taps - 1));
-    L.CL = round4(window + max_taps + 12 + PADL);
+    L.CL = sparse ? round64(window + max_taps + 12 + PADL) : round4(window + max_taps + 12 + PADL);
     size_t o = 0;
     // the sparse kernel reads the FP64 squares (exact path only) from the
     // per-RIR tables in global memory
@@ -1000,7 +1011,7 @@ k_ism_sparse(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W_arg, i
     const int max_taps = SPEC ? kSpecTaps : max_taps_arg;
     const Layout Lay = make_layout(true, W, max_order, max_taps, max_cheb);
     const int TE = Lay.TE;
-    const int CL = SPEC ? round4(kSpecW + kSpecTaps + 12 + PADL) : Lay.CL;
+    const int CL = SPEC ? round64(kSpecW + kSpecTaps + 12 + PADL) : Lay.CL;
     Tables T;
     T.sq = nullptr;  // per item: the RIR's FP64 table in global memory (exact path only)
     T.hlg = (float4 *)(smem + Lay.off_hlg);
@@ -1014,7 +1025,7 @@ k_ism_sparse(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W_arg, i
     const int tid = threadIdx.x;
     uint32_t *s_cq = (uint32_t *)s_c;      // the same words before conversion
     uint32_t *s_dq = (uint32_t *)s_delta;
-    // CL is a multiple of 4 and both arrays start on 16-byte boundaries
+    // CL is a multiple of 64 and both arrays start on 16-byte boundaries
     zero_words4(s_cq, max_cheb * CL / 4);
     zero_words4(s_dq, CL / 4);
     if (tid == 0) s_ovf = 0;
@@ -1091,18 +1102,19 @@ k_ism_sparse(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W_arg, i
                 return;
             const int pos = kb + POS0;
             if (!ISM_IN_RANGE(pos >= 0 && pos < CL, kOobSparsePos)) return;
+            const int sp = swz(pos);
             const float as = a * S4;  // a S, with a = prod(beta^hits) / (4 pi d)
                                       // (a = g / tau here, S4 = S q / (4 pi))
             const uint32_t q0 = __float2uint_rn(as);
             uint32_t *c0 = (f == 0.f) ? s_dq : s_cq;  // integer delay: exact Kronecker delta
-            const uint32_t old = atomicAdd(&c0[pos], q0);
+            const uint32_t old = atomicAdd(&c0[sp], q0);
             if (f != 0.f) {
                 // u_p = a S T_p(x) by the Chebyshev recurrence on the scaled
                 // values, u_{p+1} = 2 x u_p - u_{p-1}: one FMA, one conversion
                 // and one atomic per term
                 const float x = (KIND == ISM_FD_HANN_SINC) ? 2.f * f : 2.f * f - 1.f;
                 const float x2 = 2.f * x;
-                uint32_t *cp = s_cq + pos;
+                uint32_t *cp = s_cq + sp;
                 float u0 = as, u1 = as * x;
                 if (PFIX > 0) {
                     atomicAdd(cp + CL, (uint32_t)__float2int_rn(u1));
@@ -1179,7 +1191,7 @@ k_ism_sparse(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W_arg, i
                             const int fi = base - 4 + 4 * v;
                             const float4 w4 =
                                 ISM_IN_RANGE(fi >= 0 && fi + 3 < CL, kOobFirRead)
-                                    ? *reinterpret_cast<const float4 *>(cp + fi)
+                                    ? *reinterpret_cast<const float4 *>(cp + swz(fi))
                                     : make_float4(0.f, 0.f, 0.f, 0.f);
                             R[4 * v] = w4.x; R[4 * v + 1] = w4.y;
                             R[4 * v + 2] = w4.z; R[4 * v + 3] = w4.w;
@@ -1197,7 +1209,7 @@ k_ism_sparse(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W_arg, i
                                 const int fi = base - jb - 4 * S - 8;
                                 const float4 w4 =
                                     ISM_IN_RANGE(fi >= 0 && fi + 3 < CL, kOobFirRead)
-                                        ? *reinterpret_cast<const float4 *>(cp + fi)
+                                        ? *reinterpret_cast<const float4 *>(cp + swz(fi))
                                         : make_float4(0.f, 0.f, 0.f, 0.f);
                                 constexpr int d = (12 - 4 * (S + 1) % 12) % 12;
                                 R[d] = w4.x; R[d + 1] = w4.y; R[d + 2] = w4.z; R[d + 3] = w4.w;
@@ -1230,7 +1242,7 @@ k_ism_sparse(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W_arg, i
             const long long n = (long long)it.w0 + i;
             const int di = i + n_taps - 1 - jdelta + OFF + PADL;
             const float v =
-                s_part[i] + (ISM_IN_RANGE(di >= 0 && di < CL, kOobDeltaRead) ? s_delta[di] : 0.f);
+                s_part[i] + (ISM_IN_RANGE(di >= 0 && di < CL, kOobDeltaRead) ? s_delta[swz(di)] : 0.f);
             if (n < it.Lh) hout[n] = v;
         }
         __syncthreads();
