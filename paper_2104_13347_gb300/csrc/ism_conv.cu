@@ -140,7 +140,7 @@ k_conv_f32(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles,
 // r cos(2 pi u2) and r sin(2 pi u2) (both Box--Muller branches).  Block x of
 // job y covers pair indices [x NCH, (x+1) NCH) of the job's (mic, pair)
 // sequence; each thread walks its pairs with stride 256, carrying (mic, k)
-// and the mic's stream key.
+// and the pair's SplitMix64 input.  The pair math is box_muller().
 constexpr int NCH = 32768;  // pairs per block
 __global__ void __launch_bounds__(256)
 k_noise(const ConvJob *__restrict__ jobs, float *__restrict__ y, const double *__restrict__ part,
@@ -168,42 +168,41 @@ k_noise(const ConvJob *__restrict__ jobs, float *__restrict__ y, const double *_
     if (i >= e) return;
     uint64_t m = (uint64_t)(i / npr);
     int64_t k = i - (int64_t)m * npr;
-    uint64_t key = sm64_out(seed, J.noise_id * 65536ull + m);
+    // SplitMix64 input of pair k of mic m: key(m) + (k + 1) gamma, advanced
+    // by 256 gamma per pair of this thread (recomputed when k wraps)
+    uint64_t zs = sm64_out(seed, J.noise_id * 65536ull + m) + ((uint64_t)k + 1) * kSm64Gamma;
+    constexpr uint64_t kStep = 256ull * kSm64Gamma;
     // U pairs per round: their loads are all issued before any is used, so
     // each thread keeps U read-modify-writes in flight
     constexpr int U = 4;
     while (i < e) {
         float *ptr[U];
         float v0[U], v1[U];
-        uint64_t kk[U], keys[U];
+        uint64_t zz[U];
         bool ok[U], ok1[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             ok[u] = i < e;
             ok1[u] = ok[u] && 2 * k + 1 < ylen;
-            kk[u] = (uint64_t)k;
-            keys[u] = key;
+            zz[u] = zs;
             ptr[u] = yb + (int64_t)m * ylen + 2 * k;
             v0[u] = ok[u] ? ptr[u][0] : 0.f;
             v1[u] = ok1[u] ? ptr[u][1] : 0.f;
             i += 256;
             k += 256;
+            zs += kStep;
             if (k >= npr) {
                 while (k >= npr) { k -= npr; ++m; }
-                key = sm64_out(seed, J.noise_id * 65536ull + m);
+                zs = sm64_out(seed, J.noise_id * 65536ull + m) + ((uint64_t)k + 1) * kSm64Gamma;
             }
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             if (!ok[u]) continue;
-            const uint64_t bits = sm64_out(keys[u], kk[u]);
-            const float u1 = ((float)(bits >> 40) + 0.5f) * (1.0f / 16777216.0f);
-            const float u2 = (float)((bits >> 16) & 0xFFFFFFull) * (1.0f / 16777216.0f);
-            const float r = sigma * sqrtf(-2.f * logf(u1));
-            float sn, cs;
-            sincospif(2.f * u2, &sn, &cs);
-            ptr[u][0] = v0[u] + r * cs;
-            if (ok1[u]) ptr[u][1] = v1[u] + r * sn;
+            float z0, z1;
+            box_muller(sm64_mix(zz[u]), sigma, z0, z1);
+            ptr[u][0] = v0[u] + z0;
+            if (ok1[u]) ptr[u][1] = v1[u] + z1;
         }
     }
 }

@@ -74,22 +74,21 @@ k_frames(const FrameJob *__restrict__ jobs, int frame_len, const float *__restri
     for (int m = 0; m < J.n_mics; ++m) {
         const float *ym = yb + (int64_t)m * J.y_len;
         float *om = ob + (int64_t)m * frame_len;
-        const uint64_t key = noisy ? sm64_out(seed, J.noise_id * 65536ull + (uint64_t)m) : 0ull;
-        // samples 2k, 2k+1 of the frame share counter output k
-        for (int k = tid; 2 * k < frame_len; k += FT) {
+        // samples 2k, 2k+1 of the frame share counter output k, whose
+        // SplitMix64 input key(m) + (k + 1) gamma advances by FT gamma per step
+        uint64_t zs = noisy ? sm64_out(seed, J.noise_id * 65536ull + (uint64_t)m) +
+                                  ((uint64_t)tid + 1) * kSm64Gamma
+                            : 0ull;
+        for (int k = tid; 2 * k < frame_len; k += FT, zs += (uint64_t)FT * kSm64Gamma) {
             const int i = 2 * k;
             const int64_t t = J.t0 + i;
             float v0 = (t >= 0 && t < J.y_len) ? ym[t] : 0.f;
             float v1 = (t + 1 >= 0 && t + 1 < J.y_len) ? ym[t + 1] : 0.f;
             if (noisy) {
-                const uint64_t bits = sm64_out(key, (uint64_t)k);
-                const float u1 = ((float)(bits >> 40) + 0.5f) * (1.0f / 16777216.0f);
-                const float u2 = (float)((bits >> 16) & 0xFFFFFFull) * (1.0f / 16777216.0f);
-                const float r = sigma * sqrtf(-2.f * logf(u1));
-                float sn, cs;
-                sincospif(2.f * u2, &sn, &cs);
-                v0 += r * cs;
-                v1 += r * sn;
+                float z0, z1;
+                box_muller(sm64_mix(zs), sigma, z0, z1);
+                v0 += z0;
+                v1 += z1;
             }
             om[i] = v0;
             if (i + 1 < frame_len) om[i + 1] = v1;

@@ -380,8 +380,51 @@ __host__ __device__ inline uint64_t sm64_mix(uint64_t z) {
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
     return z ^ (z >> 31);
 }
+constexpr uint64_t kSm64Gamma = 0x9E3779B97F4A7C15ULL;
 __host__ __device__ inline uint64_t sm64_out(uint64_t state, uint64_t i) {
-    return sm64_mix(state + (i + 1) * 0x9E3779B97F4A7C15ULL);
+    return sm64_mix(state + (i + 1) * kSm64Gamma);
 }
+
+#ifdef __CUDACC__
+// Box--Muller pair (Sec. III.A measurement noise) from one SplitMix64 output
+// `bits`: u1 = (bits 63..40 + 1/2) 2^-24, u2 = (bits 39..16) 2^-24,
+// r = scale sqrt(-2 ln u1), z0 = r cos(2 pi u2), z1 = r sin(2 pi u2).
+//  -ln u1 = -ln(1 - t) with t = 1 - u1, exact in FP32 (a 24-bit integer
+//   plus 1/2, scaled).  For t < 2^-6 the Taylor series t + t^2/2 + ... +
+//   t^5/5 (remainder below 2e-10 relative); above, the hardware base-2
+//   logarithm times ln 2, whose small absolute error is then far below
+//   -ln u1 >= 0.0157 (r moves by under 1e-6).
+//  cos, sin: the octant of the angle comes from the top 3 bits of u2; within
+//   it, the distance x in [0, pi/4] to the nearest multiple of pi/2 (the
+//   octant offset, reflected in odd octants, exactly, in integers) goes
+//   through the Taylor series of sin to x^9 and of cos to x^8 (within 2e-9
+//   and 3e-8), which the octant then swaps and negates.
+__device__ __forceinline__ void box_muller(uint64_t bits, float scale, float &z0, float &z1) {
+    const uint32_t k1 = (uint32_t)(bits >> 40);
+    const uint32_t k2 = (uint32_t)(bits >> 16) & 0xFFFFFFu;
+    const float u1 = ((float)k1 + 0.5f) * (1.0f / 16777216.0f);
+    const float t = ((float)(0xFFFFFFu - k1) + 0.5f) * (1.0f / 16777216.0f);
+    const float ser =
+        t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 0.2f, 0.25f), 0.33333333f), 0.5f), 1.f);
+    const float lg = -__log2f(u1) * 0.69314718f;
+    const float r2 = 2.f * (t < 0.015625f ? ser : lg);
+    const float r = scale * (r2 * rsqrtf(r2));
+    const uint32_t o = k2 >> 21, rem = k2 & 0x1FFFFFu;
+    const uint32_t rr = (o & 1u) ? 0x200000u - rem : rem;
+    const float x = (float)rr * (0.78539816f / 2097152.0f);
+    const float x2 = x * x;
+    const float sx = fmaf(x * x2,
+                          fmaf(x2, fmaf(x2, fmaf(x2, 1.f / 362880.f, -1.f / 5040.f), 1.f / 120.f),
+                               -1.f / 6.f),
+                          x);
+    const float cx =
+        fmaf(x2, fmaf(x2, fmaf(x2, fmaf(x2, 1.f / 40320.f, -1.f / 720.f), 1.f / 24.f), -0.5f),
+             1.f);
+    const bool swap = ((o + 1u) >> 1) & 1u;
+    const float c = swap ? sx : cx, s = swap ? cx : sx;
+    z0 = r * __uint_as_float(__float_as_uint(c) ^ ((((o + 2u) >> 2) & 1u) << 31));
+    z1 = r * __uint_as_float(__float_as_uint(s) ^ ((o >> 2) << 31));
+}
+#endif
 
 }  // namespace ism
