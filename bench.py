@@ -39,13 +39,13 @@ WORKLOAD = (f"{N_ROOMS} rooms U[3,10]x[3,8]x[2.5,4] m, beta U[0.5,0.95], {N_MICS
 # K1 DRAM traffic per room from the ncu capture summarised in
 # profiles/k_ism_sparse_and_k_conv_tcp_1024rooms.md (None when that capture
 # predates the current kernel), and the binding resources it measured.
-K1_TRAFFIC_PER_ROOM = (33.701376e6 + 15.680768e6) / 256
+K1_TRAFFIC_PER_ROOM = (33.706752e6 + 15.508480e6) / 256
 K1_TRAFFIC_NOTE = ("dram read+write of a 256-room ncu capture, scaled by rooms; reads are "
                    "mostly the per-RIR sorted column lists (15 KB per RIR at order 15), h "
                    "mostly leaves L2 after the kernel, so this understates its 268 MB write")
-K1_BINDING = {"issue_active_pct": 74.6, "smem_wavefronts_pct_of_peak": 86.9,
-              "fma_pipe_pct": 39.3, "alu_pipe_pct": 28.3, "xu_pipe_pct": 47.8,
-              "fp64_pipe_pct": 2.9, "shared_atomic_wavefronts_per_instruction": 3.62,
+K1_BINDING = {"issue_active_pct": 78.0, "smem_wavefronts_pct_of_peak": 80.9,
+              "fma_pipe_pct": 35.3, "alu_pipe_pct": 42.8, "xu_pipe_pct": 48.9,
+              "fp64_pipe_pct": 3.1, "shared_atomic_wavefronts_per_instruction": 3.64,
               "source": "ncu --set full, 256-room case"}
 K2_TRAFFIC_PER_ROOM = (83.967744e6 + 139.09248e6) / 256
 
