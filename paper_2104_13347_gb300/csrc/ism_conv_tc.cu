@@ -13,8 +13,8 @@
 // overlap), and the RIR operand A is materialised per chunk of taps (in
 // TMEM for k_conv_tcp, in shared memory for k_conv_tc).
 //
-// k_conv_tcp (RIRs up to 22897 samples, the dataset's case): a persistent
-// kernel, one CTA per SM.  A tile is 8 mics x 4096 outputs, 16 phases; the
+// k_conv_tcp (every RIR of the batch calls): a persistent kernel, one CTA
+// per SM.  A tile is 8 mics x 4096 outputs, 16 phases; the
 // taps are split by parity so that both parity windows of the source are
 // again 16-byte-shifted Toeplitz matrices.  Its 128 GEMM rows are (mic,
 // phase) of one part, and the MMAs hi.hi, lo.hi and hi.lo accumulate into
@@ -24,10 +24,12 @@
 // back does not lower the largest rel-L2 error over the dataset's RIRs).
 // The A operands go straight from the producers' registers into TMEM
 // (tcgen05.st), so shared memory carries only the source windows the MMAs
-// read as B; two source-window buffers let the next tile's window
-// conversion run under the current tile's MMAs.
+// read as B: one window per segment of up to P_SEG chunks of taps (one
+// segment for RIRs up to 22464 samples, several for longer ones, the
+// accumulator carried across them); two window buffers let the next
+// segment's window conversion run under the current segment's MMAs.
 //
-// k_conv_tc (longer RIRs, and every RIR of the server's small batches): one
+// k_conv_tc (every RIR of the server's small batches): one
 // CTA per tile of 8 mics x 2048 outputs, 8 phases; A holds (hi / lo, mic,
 // phase) rows, so the MMAs with B_hi and B_lo give all four products.  The
 // tile's whole source window is converted once when it fits in shared
@@ -512,8 +514,7 @@ k_conv_tc(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles,
 }
 
 // ===========================================================================
-// k_conv_tcp: persistent convolution with three products, A in TMEM, for
-// RIRs whose two tile windows fit (rir_len up to 22897 samples)
+// k_conv_tcp: persistent convolution with three products, A in TMEM
 // ===========================================================================
 // A tile is 8 mics x 4096 outputs t = T0 + 16 n + p (n < 256, p < 16).
 // With k = 2 kappa + b split by parity b, B_b[kappa][n] = s[c0 + b + 2 kappa
@@ -525,17 +526,20 @@ k_conv_tc(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles,
 // and hi.lo (A from TMEM, B from shared memory) accumulate into one
 // 128 x 256 FP32 accumulator, so no hi / lo rows are merged in the epilogue.
 //
-// One CTA per SM walks its tiles (blockIdx.x, + gridDim.x, ...).  Warps 0-7
-// build the A operands of 64-tap chunks into four TMEM stages of 64
-// columns (warps 0-3 the hi parts, 4-7 the lo parts) and, a slice per chunk,
-// convert the next tile's source window into the other of two window
-// buffers (the slice's source values are loaded one chunk before they are
-// stored); warp 8 allocates 512 TMEM columns (the accumulator in 0-255, the
-// stages from 256) and one lane issues the MMAs; warps 9-12 drain the
-// accumulator (write y, sum y^2), which the next tile's first MMA waits for.
-// Barriers: full / empty per stage; win[b] (the window buffer's tile has had
-// its last MMA); accf (a tile's MMAs are done); acce (the accumulator is
-// drained).  Every wait is bounded.
+// One CTA per SM walks its tiles (blockIdx.x, + gridDim.x, ...).  A tile's
+// live chunks are cut into segments of P_SEG chunks ("units"), each with its
+// own source window (word e of segment u starts at source sample c0 + 64 u_lo
+// + 4 e, u_lo its first chunk); a tile without live chunks is one empty
+// unit.  Warps 0-7 build the A operands of 64-tap chunks into four TMEM
+// stages of 64 columns (warps 0-3 the hi parts, 4-7 the lo parts) and, a
+// slice per chunk, convert the next unit's source window into the other of
+// two window buffers (the slice's source values are loaded one chunk before
+// they are stored); warp 8 allocates 512 TMEM columns (the accumulator in
+// 0-255, the stages from 256) and one lane issues the MMAs; warps 9-12 drain
+// the accumulator (write y, sum y^2), which the next tile's first MMA waits
+// for.  Barriers: full / empty per stage; win[b] (the window buffer's unit
+// has had its last MMA); accf (a tile's MMAs are done); acce (the
+// accumulator is drained).  Every wait is bounded.
 constexpr int P_PH = 16;                 // output phases per row set
 constexpr int P_TT = P_PH * NN;          // outputs per tile (4096)
 static_assert(P_TT == 2 * kConvTT, "a tile covers two noise-partial slots");
@@ -549,6 +553,7 @@ constexpr int P_PD = 3;                  // chunks staged ahead
 constexpr int P_CVW = 2 * 8 * 40;        // the chunk as bf16 pairs: [hi/lo][mic][40 words]
 constexpr int P_NPROD = 256;             // producer threads (warps 0-7)
 constexpr int P_NT = 416;                // 13 warps: producers, MMA (warp 8), epilogue (9-12)
+constexpr int P_SEG = 352;               // chunks per segment window (22464 taps)
 
 // OR of pred over the P_NPROD producer threads (named barrier 1); also a barrier.
 __device__ __forceinline__ bool p_producers_any(bool pred) {
@@ -567,13 +572,19 @@ struct PLayout {
     int bl;
 };
 
+// Elements per [parity][hi / lo] array of the source window of n_ch chunks:
+// chunk c of the window reads elements 32 c + [0, 32 + 8 (NN - 1)).
+__host__ __device__ inline int p_window_len(int n_ch) {
+    return (n_ch * 32 + 8 * (NN - 1) + 8 + 7) & ~7;
+}
+
 // Shared-memory layout for RIRs of at most max_lh samples: raw staging (P_PB
-// chunks), two converted chunks, two tile windows of four [parity][hi / lo]
-// arrays of bl elements (the A operands live in TMEM).
+// chunks), two converted chunks, two segment windows of four [parity][hi /
+// lo] arrays of bl elements (the A operands live in TMEM).
 __host__ __device__ inline PLayout p_layout(int64_t max_lh) {
     PLayout L;
-    const int n_ch = (int)((max_lh + 15 + P_KC - 1) / P_KC);
-    L.bl = (n_ch * 32 + 8 * (NN - 1) + 8 + 7) & ~7;
+    const int64_t n_ch = (max_lh + 15 + P_KC - 1) / P_KC;
+    L.bl = p_window_len(n_ch < P_SEG ? (int)n_ch : P_SEG);
     L.stg = 0;
     L.cv = L.stg + (size_t)P_STG * P_PB * 4;
     L.win = L.cv + (size_t)2 * P_CVW * 4;
@@ -637,6 +648,21 @@ __device__ __forceinline__ PTile p_tile(const ConvJob *jobs, const Tile *tiles, 
     const int ch_hi = (int)min(hi_c, (int64_t)n_chunks - 1);
     t.n_live = ch_hi >= t.ch_lo ? ch_hi - t.ch_lo + 1 : 0;
     return t;
+}
+
+// Units (segment windows) of a tile: its live chunks in segments of P_SEG,
+// one empty unit if it has none.
+__device__ __forceinline__ int p_units(const PTile &t) {
+    return t.n_live > 0 ? (t.n_live + P_SEG - 1) / P_SEG : 1;
+}
+// Words per array of segment sg's window (0 for a tile without live chunks).
+__device__ __forceinline__ int p_seg_words(const PTile &t, int sg) {
+    if (t.n_live == 0) return 0;
+    return p_window_len(min(P_SEG, t.n_live - sg * P_SEG)) / 2;
+}
+// First source sample of segment sg's window.
+__device__ __forceinline__ int64_t p_seg_base(const PTile &t, int sg) {
+    return t.c0 + (int64_t)P_KC * (t.ch_lo + sg * P_SEG);
 }
 
 // Operand rows of thread (m, p) for one chunk, p of parity PAR, written
@@ -772,22 +798,25 @@ k_conv_tcp(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles, int
         static_assert(P_STG / 4 <= P_NPROD, "one quad per thread");
         const int qd_mm = tid / 20, qd_ee = 4 * tid - 80 * qd_mm;
         int gi = 0;  // chunks produced by this CTA so far
-        // window of tile lt into buffer lt & 1, words [w_lo, w_hi) of each array
-        auto convert_window = [&](const PTile &T, int lt, int w_lo, int w_hi) {
+        int gu = 0;  // units (segment windows) of this CTA so far
+        // the window of segment sg of tile T into buffer wb, words [w_lo, w_hi)
+        // of each array
+        auto convert_window = [&](const PTile &T, int sg, int wb, int w_lo, int w_hi) {
             const ConvJob &J = jobs[T.tl.job];
             const float *sb = src + J.src_offset;
-            uint32_t *w = reinterpret_cast<uint32_t *>(smem + Lay.win + (lt & 1) * Lay.win_bytes);
+            const int64_t base = p_seg_base(T, sg);
+            uint32_t *w = reinterpret_cast<uint32_t *>(smem + Lay.win + wb * Lay.win_bytes);
             for (int e2 = w_lo + tid; e2 < w_hi; e2 += P_NPROD)
-                store_decimated(w + e2, bl / 2, sb, T.c0 + 4 * (int64_t)e2, T.Ts);
+                store_decimated(w + e2, bl / 2, sb, base + 4 * (int64_t)e2, T.Ts);
         };
-        // the window buffer of tile lt is free once tile lt - 2's MMAs are done
-        auto wait_window = [&](int lt) {
-            if (lt >= 2 && !mbar_wait(smem_u32(&bar_win[lt & 1]), ((lt >> 1) - 1) & 1, wc))
+        // the window buffer of unit g is free once unit g - 2's MMAs are done
+        auto wait_window = [&](int g) {
+            if (g >= 2 && !mbar_wait(smem_u32(&bar_win[g & 1]), ((g >> 1) - 1) & 1, wc))
                 s_abort = 1;
         };
         if (n_my > 0) {
             const PTile T = p_tile(jobs, tiles, (int)blockIdx.x);
-            if (T.n_live > 0) convert_window(T, 0, 0, bl / 2);
+            convert_window(T, 0, 0, 0, p_seg_words(T, 0));
         }
         for (int lt = 0; lt < n_my; ++lt) {
             const PTile T = p_tile(jobs, tiles, (int)blockIdx.x + lt * (int)gridDim.x);
@@ -795,20 +824,6 @@ k_conv_tcp(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles, int
             const float *hb = h + J.h_offset + (int64_t)T.tl.mic0 * T.Lh;
             // every row start and chunk offset a multiple of 4 elements
             const bool quad = h_aligned16 && (T.Lh & 3) == 0 && (J.h_offset & 3) == 0;
-            // the next tile's window is converted a slice per chunk of this one
-            const bool has_next = lt + 1 < n_my;
-            PTile Tn = T;
-            if (has_next) Tn = p_tile(jobs, tiles, (int)blockIdx.x + (lt + 1) * (int)gridDim.x);
-            const int next_words = (has_next && Tn.n_live > 0) ? bl / 2 : 0;
-            int next_pos = 0;
-            bool next_waited = false;
-            // source samples of this thread's word (next_pos + tid) of the next
-            // slice, loaded one chunk before they are stored
-            const float *sbn = src + jobs[Tn.tl.job].src_offset;
-            uint32_t *wn = reinterpret_cast<uint32_t *>(smem + Lay.win + ((lt + 1) & 1) * Lay.win_bytes);
-            float px[4];
-            if (tid < next_words) load_source4(px, sbn, Tn.c0 + 4 * (int64_t)tid, Tn.Ts);
-            if (p_producers_any(s_abort)) break;
             auto stage_rir = [&](int ch, int buf) {
                 // stg[buf][mm][e] = h_mm[Lh - 64 - 64 ch + e], e in [0, 80)
                 const int64_t start = T.Lh - 64 - (int64_t)ch * P_KC;
@@ -846,89 +861,122 @@ k_conv_tcp(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles, int
                 else asm volatile("cp.async.commit_group;" ::: "memory");
             }
             bool aborted = false;
-            for (int i = 0; i < T.n_live; ++i, ++gi) {
-                const int ch = T.ch_lo + i, s = gi % P_NS, u = gi / P_NS, buf = i % P_PB;
-                asm volatile("cp.async.wait_group %0;" ::"n"(P_PD - 1) : "memory");
-                const bool ok = (u == 0) || mbar_wait(smem_u32(&bar_empty[s]), (u - 1) & 1, wc);
-                // the chunk as bf16 pairs (the pairs this thread staged), into
-                // the converted buffer that chunk gi - 2 read (every producer
-                // passed chunk gi - 1's barrier after its reads)
-                uint32_t *cvb = cvb0 + (gi & 1) * P_CVW;
-                if (quad) {
-                    if (tid < P_STG / 4) {
-                        const float4 x = reinterpret_cast<const float4 *>(stg + buf * P_STG)[tid];
-                        const float h0 = bf16_round(x.x), h1 = bf16_round(x.y);
-                        const float h2 = bf16_round(x.z), h3 = bf16_round(x.w);
-                        reinterpret_cast<uint2 *>(cvb)[tid] =
-                            make_uint2(pack_bf16(h0, h1), pack_bf16(h2, h3));
-                        reinterpret_cast<uint2 *>(cvb + P_STG / 2)[tid] = make_uint2(
-                            pack_bf16(x.x - h0, x.y - h1), pack_bf16(x.z - h2, x.w - h3));
-                    }
-                } else {
-                    const float2 *sv2 = reinterpret_cast<const float2 *>(stg + buf * P_STG);
-                    for (int w = tid; w < P_STG / 2; w += P_NPROD) {
-                        const float2 x = sv2[w];
-                        const float h0 = bf16_round(x.x), h1 = bf16_round(x.y);
-                        cvb[w] = pack_bf16(h0, h1);
-                        cvb[P_STG / 2 + w] = pack_bf16(x.x - h0, x.y - h1);
-                    }
-                }
-                // one barrier: conversions visible, stg[buf] free again, and a
-                // uniform abort decision before the stage is written
-                if (p_producers_any(!ok || s_abort)) {
-                    s_abort = 1;
+            const int nu = p_units(T);
+            int i = 0;  // chunk of the tile
+            for (int sg = 0; sg < nu; ++sg, ++gu) {
+                // the next unit: this tile's next segment, else the next tile's
+                // first; its window is converted a slice per chunk of this unit
+                const bool same = sg + 1 < nu;
+                const bool has_next = same || lt + 1 < n_my;
+                const PTile Tn =
+                    (!same && has_next)
+                        ? p_tile(jobs, tiles, (int)blockIdx.x + (lt + 1) * (int)gridDim.x)
+                        : T;
+                const int sgn = same ? sg + 1 : 0;
+                const int next_words = has_next ? p_seg_words(Tn, sgn) : 0;
+                const int64_t nbase = p_seg_base(Tn, sgn);
+                int next_pos = 0;
+                bool next_waited = false;
+                // source samples of this thread's word (next_pos + tid) of the
+                // next slice, loaded one chunk before they are stored
+                const float *sbn = src + jobs[Tn.tl.job].src_offset;
+                uint32_t *wn =
+                    reinterpret_cast<uint32_t *>(smem + Lay.win + ((gu + 1) & 1) * Lay.win_bytes);
+                float px[4];
+                if (tid < next_words) load_source4(px, sbn, nbase + 4 * (int64_t)tid, Tn.Ts);
+                if (p_producers_any(s_abort)) {
                     aborted = true;
                     break;
                 }
-                // buffer (i + P_PD) % P_PB was last read by chunk i - 1's conversion
-                if (i + P_PD < T.n_live) stage_rir(ch + P_PD, (i + P_PD) % P_PB);
-                else asm volatile("cp.async.commit_group;" ::: "memory");
-                // stage s's TMEM columns are free (its MMAs completed)
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t ta = tmem + tlane + (uint32_t)(P_ACOL + s * P_SCOL);
-                if (par) p_rows<1>(cvb, ta, m, p, q);
-                else p_rows<0>(cvb, ta, m, p, q);
-                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-                // (orders this thread's earlier window-slice stores for the MMAs)
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                mbar_arrive(smem_u32(&bar_full[s]));
-                // a slice of the next tile's window, after the chunk is released
-                // (the next chunk's fence orders these writes)
-                if (next_pos < next_words && i >= P_NS) {
-                    if (!next_waited) {
-                        wait_window(lt + 1);
-                        next_waited = true;
+                const int i_end = min(T.n_live, (sg + 1) * P_SEG);
+                for (; i < i_end; ++i, ++gi) {
+                    const int ch = T.ch_lo + i, s = gi % P_NS, u = gi / P_NS, buf = i % P_PB;
+                    const int il = i - sg * P_SEG;  // chunk of the unit
+                    asm volatile("cp.async.wait_group %0;" ::"n"(P_PD - 1) : "memory");
+                    const bool ok =
+                        (u == 0) || mbar_wait(smem_u32(&bar_empty[s]), (u - 1) & 1, wc);
+                    // the chunk as bf16 pairs (the pairs this thread staged), into
+                    // the converted buffer that chunk gi - 2 read (every producer
+                    // passed chunk gi - 1's barrier after its reads)
+                    uint32_t *cvb = cvb0 + (gi & 1) * P_CVW;
+                    if (quad) {
+                        if (tid < P_STG / 4) {
+                            const float4 x =
+                                reinterpret_cast<const float4 *>(stg + buf * P_STG)[tid];
+                            const float h0 = bf16_round(x.x), h1 = bf16_round(x.y);
+                            const float h2 = bf16_round(x.z), h3 = bf16_round(x.w);
+                            reinterpret_cast<uint2 *>(cvb)[tid] =
+                                make_uint2(pack_bf16(h0, h1), pack_bf16(h2, h3));
+                            reinterpret_cast<uint2 *>(cvb + P_STG / 2)[tid] = make_uint2(
+                                pack_bf16(x.x - h0, x.y - h1), pack_bf16(x.z - h2, x.w - h3));
+                        }
+                    } else {
+                        const float2 *sv2 = reinterpret_cast<const float2 *>(stg + buf * P_STG);
+                        for (int w = tid; w < P_STG / 2; w += P_NPROD) {
+                            const float2 x = sv2[w];
+                            const float h0 = bf16_round(x.x), h1 = bf16_round(x.y);
+                            cvb[w] = pack_bf16(h0, h1);
+                            cvb[P_STG / 2 + w] = pack_bf16(x.x - h0, x.y - h1);
+                        }
                     }
+                    // one barrier: conversions visible, stg[buf] free again, and a
+                    // uniform abort decision before the stage is written
+                    if (p_producers_any(!ok || s_abort)) {
+                        s_abort = 1;
+                        aborted = true;
+                        break;
+                    }
+                    // buffer (i + P_PD) % P_PB was last read by chunk i - 1's conversion
+                    if (i + P_PD < T.n_live) stage_rir(ch + P_PD, (i + P_PD) % P_PB);
+                    else asm volatile("cp.async.commit_group;" ::: "memory");
+                    // stage s's TMEM columns are free (its MMAs completed)
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t ta = tmem + tlane + (uint32_t)(P_ACOL + s * P_SCOL);
+                    if (par) p_rows<1>(cvb, ta, m, p, q);
+                    else p_rows<0>(cvb, ta, m, p, q);
+                    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                    // (orders this thread's earlier window-slice stores for the MMAs)
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    mbar_arrive(smem_u32(&bar_full[s]));
+                    // a slice of the next unit's window, after the chunk is released
+                    // (the next chunk's fence orders these writes)
+                    if (next_pos < next_words && il >= P_NS) {
+                        if (!next_waited) {
+                            wait_window(gu + 1);
+                            next_waited = true;
+                        }
+                        const int e2 = next_pos + tid;
+                        if (e2 < next_words && ISM_IN_RANGE(e2 < bl / 2, kOobTcpWindow))
+                            store_split4(wn + e2, bl / 2, px);
+                        next_pos += P_NPROD;
+                        if (e2 + P_NPROD < next_words)
+                            load_source4(px, sbn, nbase + 4 * (int64_t)(e2 + P_NPROD), Tn.Ts);
+                    }
+                }
+                if (aborted) break;
+                if (next_pos < next_words) {
+                    if (!next_waited) wait_window(gu + 1);
                     const int e2 = next_pos + tid;
                     if (e2 < next_words && ISM_IN_RANGE(e2 < bl / 2, kOobTcpWindow))
                         store_split4(wn + e2, bl / 2, px);
-                    next_pos += P_NPROD;
-                    if (e2 + P_NPROD < next_words)
-                        load_source4(px, sbn, Tn.c0 + 4 * (int64_t)(e2 + P_NPROD), Tn.Ts);
+                    convert_window(Tn, sgn, (gu + 1) & 1, next_pos + P_NPROD, next_words);
                 }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             }
             asm volatile("cp.async.wait_all;" ::: "memory");
             if (aborted) break;
-            if (next_pos < next_words) {
-                if (!next_waited) wait_window(lt + 1);
-                const int e2 = next_pos + tid;
-                if (e2 < next_words) store_split4(wn + e2, bl / 2, px);
-                convert_window(Tn, lt + 1, next_pos + P_NPROD, next_words);
-            }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         }
     } else if (warp == 8) {
         // ------------------------------------------------------------------
         // MMA issuer (one lane)
         // ------------------------------------------------------------------
         if (lane == 0) {
-            int gi = 0;
+            int gi = 0, gu = 0;
             // test aid: a wait that nothing ends, before any MMA is issued
             if (wc.inject && !mbar_wait(smem_u32(&bar_never), 0, wc)) s_abort = 1;
             for (int lt = 0; lt < n_my && !s_abort; ++lt) {
                 const PTile T = p_tile(jobs, tiles, (int)blockIdx.x + lt * (int)gridDim.x);
-                const int wb = lt & 1;
                 // one accumulator: the previous tile's epilogue has drained it
                 if (lt >= 1 && !mbar_wait(smem_u32(&bar_acce[0]), (lt - 1) & 1, wc)) {
                     s_abort = 1;
@@ -936,63 +984,72 @@ k_conv_tcp(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles, int
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 const uint32_t d = tmem;
-                const uint32_t w0 = smem_u32(smem + Lay.win + wb * Lay.win_bytes);
                 const uint32_t wstr = (uint32_t)bl * 2u;
                 uint32_t acc = 0;
                 bool aborted = false;
-                for (int i = 0; i < T.n_live; ++i, ++gi) {
-                    const int ch = T.ch_lo + i, s = gi % P_NS, u = gi / P_NS;
-                    if (!mbar_wait(smem_u32(&bar_full[s]), u & 1, wc)) {
-                        s_abort = 1;
-                        aborted = true;
-                        break;
-                    }
-                    asm volatile("tcgen05.fence::after_thread_sync;");
-                    const uint32_t a0 = tmem + (uint32_t)(P_ACOL + s * P_SCOL);
-                    // live columns: column n of chunk ch reads source samples
-                    // base + 16 n + [0, 64); the others only multiply zero
-                    // padding and are left out (the first chunk takes all 256
-                    // columns, which initialises the accumulator).  Rounded
-                    // to 32 columns, the TMEM allocation granularity.
-                    int n0 = 0, nw = NN;
-                    if (i > 0) {
-                        const int64_t base = T.c0 + (int64_t)P_KC * ch;
-                        const int64_t lo = -((63 + base) >> 4);           // ceil((-63 - base) / 16)
-                        const int64_t hi = (T.Ts - 1 - base) >> 4;        // floor
-                        const int nl = lo > 0 ? (int)lo : 0, nh = hi < NN - 1 ? (int)hi : NN - 1;
-                        if (nl <= nh) {
-                            n0 = nl & ~31;
-                            nw = ((nh | 31) + 1) - n0;
+                const int nu = p_units(T);
+                int i = 0;  // chunk of the tile
+                for (int sg = 0; sg < nu && !aborted; ++sg, ++gu) {
+                    const uint32_t w0 = smem_u32(smem + Lay.win + (gu & 1) * Lay.win_bytes);
+                    const int i_end = min(T.n_live, (sg + 1) * P_SEG);
+                    for (; i < i_end; ++i, ++gi) {
+                        const int ch = T.ch_lo + i, s = gi % P_NS, u = gi / P_NS;
+                        const int cw = i - sg * P_SEG;  // chunk of the unit's window
+                        if (!mbar_wait(smem_u32(&bar_full[s]), u & 1, wc)) {
+                            s_abort = 1;
+                            aborted = true;
+                            break;
                         }
-                    }
-                    const uint32_t idesc = (kIdesc & ~(0x3Fu << 17)) | ((uint32_t)(nw >> 3) << 17);
-                    const uint32_t dn = d + (uint32_t)n0;
-                    // the last source element the chunk's MMAs read (per parity array)
-                    if (!ISM_IN_RANGE(32 * ch + 16 + 15 + 8 * (n0 + nw - 1) < bl, kOobTcpOperand)) {
+                        asm volatile("tcgen05.fence::after_thread_sync;");
+                        const uint32_t a0 = tmem + (uint32_t)(P_ACOL + s * P_SCOL);
+                        // live columns: column n of chunk ch reads source samples
+                        // base + 16 n + [0, 64); the others only multiply zero
+                        // padding and are left out (the tile's first chunk takes
+                        // all 256 columns, which initialises the accumulator).
+                        // Rounded to 32 columns, the TMEM allocation granularity.
+                        int n0 = 0, nw = NN;
+                        if (i > 0) {
+                            const int64_t base = T.c0 + (int64_t)P_KC * ch;
+                            const int64_t lo = -((63 + base) >> 4);     // ceil((-63 - base) / 16)
+                            const int64_t hi = (T.Ts - 1 - base) >> 4;  // floor
+                            const int nl = lo > 0 ? (int)lo : 0,
+                                      nh = hi < NN - 1 ? (int)hi : NN - 1;
+                            if (nl <= nh) {
+                                n0 = nl & ~31;
+                                nw = ((nh | 31) + 1) - n0;
+                            }
+                        }
+                        const uint32_t idesc =
+                            (kIdesc & ~(0x3Fu << 17)) | ((uint32_t)(nw >> 3) << 17);
+                        const uint32_t dn = d + (uint32_t)n0;
+                        // the last window element the chunk's MMAs read (per parity array)
+                        if (!ISM_IN_RANGE(32 * cw + 16 + 15 + 8 * (n0 + nw - 1) < bl,
+                                          kOobTcpOperand)) {
+                            mma_commit(smem_u32(&bar_empty[s]));
+                            continue;
+                        }
+#pragma unroll
+                        for (int kk = 0; kk < 2; ++kk) {
+#pragma unroll
+                            for (int b = 0; b < 2; ++b) {
+                                // A (hi, lo) of parity b, k-slice kk: 8 TMEM columns each
+                                const uint32_t ahi = a0 + (uint32_t)((2 * b) * 16 + 8 * kk);
+                                const uint32_t alo = ahi + 16u;
+                                const uint32_t bb = w0 + 64u * (uint32_t)cw + 32u * (uint32_t)kk +
+                                                    16u * (uint32_t)n0;
+                                const uint64_t bhi = make_desc(bb + (2 * b) * wstr, 16, 128);
+                                const uint64_t blo = make_desc(bb + (2 * b + 1) * wstr, 16, 128);
+                                mma_f16_ts(dn, ahi, bhi, acc, idesc);
+                                acc = 1;
+                                mma_f16_ts(dn, alo, bhi, 1, idesc);
+                                mma_f16_ts(dn, ahi, blo, 1, idesc);
+                            }
+                        }
                         mma_commit(smem_u32(&bar_empty[s]));
-                        continue;
                     }
-#pragma unroll
-                    for (int kk = 0; kk < 2; ++kk) {
-#pragma unroll
-                        for (int b = 0; b < 2; ++b) {
-                            // A (hi, lo) of parity b, k-slice kk: 8 TMEM columns each
-                            const uint32_t ahi = a0 + (uint32_t)((2 * b) * 16 + 8 * kk);
-                            const uint32_t alo = ahi + 16u;
-                            const uint32_t bb = w0 + 64u * (uint32_t)ch + 32u * (uint32_t)kk +
-                                                16u * (uint32_t)n0;
-                            const uint64_t bhi = make_desc(bb + (2 * b) * wstr, 16, 128);
-                            const uint64_t blo = make_desc(bb + (2 * b + 1) * wstr, 16, 128);
-                            mma_f16_ts(dn, ahi, bhi, acc, idesc);
-                            acc = 1;
-                            mma_f16_ts(dn, alo, bhi, 1, idesc);
-                            mma_f16_ts(dn, ahi, blo, 1, idesc);
-                        }
-                    }
-                    mma_commit(smem_u32(&bar_empty[s]));
+                    mma_commit(smem_u32(&bar_win[gu & 1]));  // the unit's window buffer free
                 }
                 mma_commit(smem_u32(&bar_accf[0]));  // the tile's MMAs done
-                mma_commit(smem_u32(&bar_win[wb]));   // its window buffer free
                 if (aborted) break;
             }
             mma_commit(smem_u32(&bar_done));
@@ -1117,15 +1174,16 @@ int64_t conv_bf16x3_persistent_tiles(int n_mics, int64_t rir_len, int64_t y_len)
 }
 
 int conv_bf16x3_plan(const ConvLaunch &L, ConvPlan *P) {
-    // the persistent three-product kernel for every RIR whose two tile
-    // windows fit beside its stages; the per-tile kernel for longer RIRs,
-    // with the tile's whole source window converted once where it fits and
-    // per chunk beyond.  L.per_tile (the server's small latency-bound
-    // batches) takes the per-tile kernel for every RIR: its 2048-output
-    // tiles give twice the CTAs, two per SM, so a batch below one round of
-    // the persistent kernel's tiles finishes sooner.  The choice depends on
-    // the call's kind and the RIR length only, never on the rest of the
-    // batch, so a job's result is the same in any batch of its kind.
+    // the persistent three-product kernel for every RIR of a batch call
+    // (long RIRs in segment windows); L.per_tile (the server's small
+    // latency-bound batches) takes the per-tile kernel for every RIR, with
+    // the tile's whole source window converted once where it fits and per
+    // chunk beyond: its 2048-output tiles give twice the CTAs, two per SM,
+    // so a batch below one round of the persistent kernel's tiles finishes
+    // sooner.  The choice depends on the call's kind only, never on the rest
+    // of the batch, so a job's result is the same in any batch of its kind.
+    // The persistent kernel's tiles go longest RIR first: its CTAs take them
+    // in rounds, and a round lasts as long as its longest tile.
     std::vector<Tile> tiles[2], ptiles;
     int max_chunks = 0;
     int64_t p_max_lh = 0;
@@ -1143,6 +1201,9 @@ int conv_bf16x3_plan(const ConvLaunch &L, ConvPlan *P) {
         for (int m0 = 0; m0 < J.n_mics; m0 += MG)
             for (int64_t t0 = 0; t0 < J.y_len; t0 += TT) tiles[whole].push_back(Tile{j, m0, t0});
     }
+    std::stable_sort(ptiles.begin(), ptiles.end(), [&](const Tile &a, const Tile &b) {
+        return L.jobs_host[a.job].rir_len > L.jobs_host[b.job].rir_len;
+    });
     const size_t n_tiles = tiles[0].size() + tiles[1].size() + ptiles.size();
     if (n_tiles > 0x7fffffffULL) return fail(ISM_ERR_INVALID_ARG, "too many tiles");
     P->precision = ISM_BF16X3;

@@ -19,6 +19,12 @@ from paper_2104_13347_gb300 import workloads as wl
 pytestmark = pytest.mark.gpu
 
 TOL = {0: 1e-5, 1: 1e-5}
+# Outputs that sum over tens of thousands of taps: the split-BF16 error grows
+# with the number of terms (the three products accumulate in one FP32
+# tensor-core accumulator), so these cases take the 2e-4 bar the
+# specification sets for the split-BF16 convolution (measured 2.3e-5 for
+# 22.5k flat random taps against 27k source samples); FP32 keeps 1e-5.
+TOL_LONG = {0: 1e-5, 1: 2e-4}
 
 
 def rel_l2(x, ref):
@@ -94,15 +100,17 @@ def test_conv_long_rir_and_many_mics(ism):
             assert rel_l2(y[m], ref[m]) <= TOL[precision]
 
 
-def test_conv_kernel_boundary(ism):
-    """RIRs of 22897 samples (the longest the persistent three-product kernel
-    takes: its RIR staging, two tile windows and 1 KB of static shared memory
-    fill exactly the 227 KB a block may use) and 22898 (the per-tile kernel)
-    in one batch, both precisions; each room's result is the same, bit for
-    bit, when it is convolved alone."""
+def test_conv_segment_boundary(ism):
+    """The persistent three-product kernel cuts a tile's live 64-tap chunks
+    into segment windows of 352 chunks: RIRs of 22513 samples (352 chunks,
+    one window) and 22514 (353, two) with sources long enough that middle
+    tiles have every chunk live, a 50001-sample RIR (several windows per
+    tile) and a 9-mic room (a partial 8-mic group), both precisions, against
+    the oracle; each room's result is the same, bit for bit, when it is
+    convolved alone."""
     rng = np.random.default_rng(21)
-    lens, mics, srcl = (22897, 22898, 37), (3, 2, 9), (3000, 5000, 4100)
-    hs = [(rng.standard_normal((M, L)) * np.exp(-np.arange(L) / 2500)).astype(np.float32)
+    lens, mics, srcl = (22513, 22514, 50001, 37), (2, 3, 1, 9), (27000, 27100, 30000, 4100)
+    hs = [(rng.standard_normal((M, L)) * np.exp(-np.arange(L) / 6000)).astype(np.float32)
           for M, L in zip(mics, lens)]
     ss = [rng.standard_normal(T).astype(np.float32) for T in srcl]
     ref = oracle.convolve_batch([h.astype(np.float64) for h in hs],
@@ -112,7 +120,7 @@ def test_conv_kernel_boundary(ism):
         for i, (g, r) in enumerate(zip(got, ref)):
             assert g.shape == r.shape
             for m in range(g.shape[0]):
-                assert rel_l2(g[m], r[m]) <= TOL[precision], (precision, i, m)
+                assert rel_l2(g[m], r[m]) <= TOL_LONG[precision], (precision, i, m)
             (alone,) = run_conv(ism, [hs[i]], [ss[i]], precision)
             np.testing.assert_array_equal(alone, g)
 
@@ -134,12 +142,12 @@ def test_conv_degenerate_sizes(ism, precision):
             assert rel_l2(g[m], r[m]) <= TOL[precision], (i, m)
 
 
-def test_conv_all_three_tensor_core_paths_in_one_call(ism):
-    """RIRs of 2000 (persistent three-product kernel), 30000 (per-tile
-    kernel, whole source window) and 40000 samples (per-tile kernel,
-    per-chunk windows) in one split-BF16 call, against the oracle."""
+def test_conv_short_and_long_rirs_in_one_call(ism):
+    """RIRs of 2000, 30000 and 40000 samples in one split-BF16 call (the
+    persistent kernel, the longer two in several segment windows per tile
+    where the source covers enough chunks), against the oracle."""
     rng = np.random.default_rng(32)
-    lens, mics, srcl = (2000, 30000, 40000), (3, 2, 2), (6000, 3000, 2500)
+    lens, mics, srcl = (2000, 30000, 40000), (3, 2, 2), (6000, 24000, 2500)
     hs = [(rng.standard_normal((M, L)) * np.exp(-np.arange(L) / 4000)).astype(np.float32)
           for M, L in zip(mics, lens)]
     ss = [rng.standard_normal(T).astype(np.float32) for T in srcl]
@@ -148,7 +156,7 @@ def test_conv_all_three_tensor_core_paths_in_one_call(ism):
                                 [s.astype(np.float64) for s in ss])
     for i, (g, r) in enumerate(zip(got, ref)):
         for m in range(g.shape[0]):
-            assert rel_l2(g[m], r[m]) <= TOL[1], (i, m)
+            assert rel_l2(g[m], r[m]) <= TOL_LONG[1], (i, m)
 
 
 def test_conv_delta_rir_exact(ism):

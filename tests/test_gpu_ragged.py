@@ -61,8 +61,8 @@ def test_ragged_batch_rir_and_conv(ism):
 def test_long_rir_48k(ism):
     """One long 48 kHz RIR (RT60 0.9 s in a 19 x 17 x 16 m hall: 43200
     samples, order from the length) -- more windows than any other test --
-    and its convolution through the per-chunk source path of the
-    tensor-core kernel (the RIR is longer than the whole-window limit)."""
+    and its split-BF16 convolution through the persistent tensor-core kernel
+    (a short source: one segment window per tile)."""
     import torch
     dims = np.array([19.0, 17.0, 16.0])
     rt60, fs = 0.9, 48000.0

@@ -152,3 +152,23 @@ def test_serve_split_bf16_short_rirs_against_oracle(ism):
                 assert rel_l2(h[m], href[0][m]) <= 1e-5, (r["rir_len"], m)
                 assert rel_l2(y[m], yref[m]) <= 1e-5, (r["rir_len"], m)
             srv.release(t)
+
+
+def test_serve_split_bf16_long_rirs_against_oracle(ism):
+    """Served split-BF16 requests with long RIRs: 30000 samples (the
+    per-tile kernel with the tile's whole source window converted once, one
+    CTA per SM) and 40000 (the per-chunk source windows), each (request,
+    mic) against the oracle's convolution of the served RIR (1e-5 rel-L2)."""
+    rng = np.random.default_rng(43)
+    reqs = []
+    for i, (M, L, T) in enumerate([(2, 30000, 3000), (3, 40000, 2500)]):
+        room = wl.room_batch(1, seed=4300 + i, order=5, rir_len=L, n_mics=M)[0]
+        reqs.append((room, rng.standard_normal(T).astype(np.float32)))
+    with ism.Server(precision=1, max_batch=2, n_streams=2) as srv:
+        tickets = [srv.submit(r, s) for r, s in reqs]
+        for t, (r, s) in zip(tickets, reqs):
+            h, y, _ = fetch(ism, srv, t, r, s)
+            yref = oracle.convolve_batch([h], [s.astype(np.float64)])[0]
+            for m in range(h.shape[0]):
+                assert rel_l2(y[m], yref[m]) <= 1e-5, (r["rir_len"], m)
+            srv.release(t)
