@@ -193,7 +193,8 @@ def test_noise_matches_oracle(ism):
 
 def test_noise_dense_against_oracle(ism):
     """Every sample of a long noisy 8-mic signal against the oracle's noise
-    (Sec. III.A), at the point-wise bar of the sampled test: 4.2e6 draws
+    (Sec. III.A): the deviates within 2e-6 (1 + |z|) of the oracle's
+    (measured 9.6e-7), plus the FP32 rounding of y + sigma z.  4.2e6 draws
     reach u1 within 2^-6 of 1 (the series branch of the logarithm) ~6e4
     times and every octant of the Box--Muller angle."""
     rng = np.random.default_rng(77)
@@ -205,7 +206,7 @@ def test_noise_dense_against_oracle(ism):
     ref, sigma = oracle.add_noise(clean.copy(), 12.5, 4321, 4242)
     z = (ref - clean) / sigma
     err = np.abs(noisy - ref)
-    bar = 1e-5 * sigma * (1 + np.abs(z)) + 2e-6 * np.abs(clean)
+    bar = 2e-6 * sigma * (1 + np.abs(z)) + 2.0 ** -22 * np.abs(clean)
     assert np.all(err <= bar), float(np.max(err / bar))
 
 
