@@ -56,10 +56,9 @@ typedef enum ism_fd_kind { ISM_FD_HANN_SINC = 0, ISM_FD_LAGRANGE = 1 } ism_fd_ki
  *  ISM_F32: FP32 direct convolution on the CUDA cores.
  *  ISM_BF16X3: tensor-core convolution with each operand split into
  *    bf16 hi + lo parts, the cross products accumulated in FP32: hi.hi,
- *    hi.lo and lo.hi in a persistent kernel (one CTA per SM) for every RIR
- *    of the batch calls (RIRs beyond 22464 samples in segments of that many
- *    taps, the accumulator carried across them); all four in a per-tile
- *    kernel for the server's requests (small batches).
+ *    hi.lo and lo.hi in a persistent kernel (one CTA per SM) for every RIR,
+ *    batch and served (RIRs beyond 22464 samples in segments of that many
+ *    taps, the accumulator carried across them).
  *    Rel-L2 error against FP64 below 1e-5 per (room, mic) on the dataset's
  *    rooms (8192-sample RIRs, 1 s sources at 16 kHz; the bf16 hi + lo split
  *    itself keeps about 16 bits of each operand).  The error grows with the
@@ -412,10 +411,10 @@ int ism_frames_batch(const ism_frame_job *jobs, int64_t n_frames, int32_t frame_
  * Each request's work items (RIR windows, convolution tiles, noise streams
  * keyed by its noise_id) are the same alone or mixed with others, bit for
  * bit (the sparse RIR path sums in fixed point, and the server always uses
- * 1024-sample RIR windows).  With ISM_BF16X3 the server convolves with the
- * per-tile tensor-core kernel (see ism_precision), whatever the mix, so its
- * signals match ism_convolve_batch's to within the split-BF16 error, not
- * bit for bit.
+ * 1024-sample RIR windows).  The server convolves with the kernels of
+ * ism_convolve_batch, whose work for a job does not depend on the rest of
+ * the batch: given the same RIRs, seed and noise ids its signals equal the
+ * batch call's bit for bit.
  * ------------------------------------------------------------------------ */
 typedef struct ism_server ism_server;
 

@@ -607,15 +607,14 @@ int ism_rir_batch(const ism_room *rooms, int64_t n_rooms, float *h_dev, const in
 int ism_convolve_batch(const ism_conv_job *jobs, int64_t n_jobs, const float *h_dev,
                        const float *src_dev, float *y_dev, uint64_t seed, int32_t precision,
                        void *stream_v) {
-    return ism::convolve_batch(jobs, n_jobs, h_dev, src_dev, y_dev, seed, precision, stream_v,
-                               false);
+    return ism::convolve_batch(jobs, n_jobs, h_dev, src_dev, y_dev, seed, precision, stream_v);
 }
 
 }  // extern "C"
 
 int ism::convolve_batch(const ism_conv_job *jobs, int64_t n_jobs, const float *h_dev,
                         const float *src_dev, float *y_dev, uint64_t seed, int32_t precision,
-                        void *stream_v, bool per_tile) {
+                        void *stream_v) {
     set_error("");
     if (n_jobs < 0) return fail(ISM_ERR_INVALID_ARG, "n_jobs < 0");
     if (n_jobs == 0) return ISM_OK;
@@ -673,7 +672,6 @@ int ism::convolve_batch(const ism_conv_job *jobs, int64_t n_jobs, const float *h
     L.seed = seed;
     L.any_noise = any_noise;
     L.noise_partials_dev = any_noise ? (double *)((char *)scr + jb + 256) : nullptr;
-    L.per_tile = per_tile ? 1 : 0;
     StatusTicket tk;
     int st = ISM_OK;
     if (precision == ISM_BF16X3) {

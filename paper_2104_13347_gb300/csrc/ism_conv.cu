@@ -220,16 +220,14 @@ int conv_f32_plan(const ConvLaunch &L, ConvPlan *P) {
             for (int64_t t0 = 0; t0 < J.y_len; t0 += TT) P->tiles.push_back(Tile{j, m0, t0});
     }
     if (P->tiles.size() > 0x7fffffffULL) return fail(ISM_ERR_INVALID_ARG, "too many tiles");
-    P->n_a = P->tiles.size();
-    P->n_b = P->n_c = 0;
     return ISM_OK;
 }
 
 int conv_f32_enqueue(const ConvLaunch &L, const ConvPlan &P, const ConvTile *d_tiles,
                      cudaStream_t stream) {
-    if (P.n_a == 0) return ISM_OK;
-    k_conv_f32<<<(unsigned)P.n_a, CT, 0, stream>>>(L.jobs_dev, d_tiles, L.h_dev, L.src_dev,
-                                                    L.y_dev, L.noise_partials_dev);
+    if (P.tiles.empty()) return ISM_OK;
+    k_conv_f32<<<(unsigned)P.tiles.size(), CT, 0, stream>>>(
+        L.jobs_dev, d_tiles, L.h_dev, L.src_dev, L.y_dev, L.noise_partials_dev);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "launch k_conv_f32");
     return ISM_OK;

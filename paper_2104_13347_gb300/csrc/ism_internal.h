@@ -211,28 +211,25 @@ struct ConvLaunch {
     // in slot part_offset(j) + g * ceil(y_len / kConvTT) + b, written by the
     // convolution kernels when non-null (noise requested)
     double *noise_partials_dev;
-    // split-BF16 only: per-tile kernels for every RIR (small latency-bound
-    // batches) instead of the persistent kernel
-    int per_tile;
     // split-BF16 only: the call's status cell (host-mapped; a kernel whose
     // bounded wait runs out sets it), and the test aid of ism_debug_inject
     int *err_dev;
     int inject;
 };
-// Tile shape shared by both convolution kernels (and the noise partials).
+// Noise-partial grid: one slot per 8 mics x 2048 outputs (the FP32
+// kernel's tile; a tile of the split-BF16 kernel spans two slots).
 constexpr int kConvMG = 8;     // mics per tile
-constexpr int kConvTT = 2048;  // outputs per tile
+constexpr int kConvTT = 2048;  // outputs per slot
 __host__ __device__ inline int conv_partials_per_job(int n_mics, int64_t y_len) {
     return (int)((n_mics + kConvMG - 1) / kConvMG * ((y_len + kConvTT - 1) / kConvTT));
 }
 __host__ __device__ inline int conv_partial_slot(int mic0, int64_t t0, int64_t y_len) {
     return (int)(mic0 / kConvMG * ((y_len + kConvTT - 1) / kConvTT) + t0 / kConvTT);
 }
-// ism_convolve_batch with the kernel choice of ConvLaunch::per_tile (the
-// server passes true).
+// ism_convolve_batch (also called by the server's worker).
 int convolve_batch(const ism_conv_job *jobs, int64_t n_jobs, const float *h_dev,
                    const float *src_dev, float *y_dev, uint64_t seed, int32_t precision,
-                   void *stream, bool per_tile);
+                   void *stream);
 int launch_conv_f32(const ConvLaunch &L, cudaStream_t stream);
 int launch_conv_bf16x3(const ConvLaunch &L, cudaStream_t stream);
 // One convolution tile: mics [mic0, mic0 + 8) of job `job`, outputs from t0.
@@ -248,9 +245,7 @@ struct ConvTile {
 struct ConvPlan {
     int precision = ISM_F32;
     std::vector<ConvTile> tiles;
-    size_t n_a = 0, n_b = 0, n_c = 0;
-    int max_chunks = 0;
-    int64_t p_max_lh = 0;
+    int64_t p_max_lh = 0;  // split-BF16: the longest RIR (shared-memory layout)
 };
 int conv_plan(const ConvLaunch &L, ConvPlan *P);
 int conv_f32_plan(const ConvLaunch &L, ConvPlan *P);
@@ -286,10 +281,6 @@ enum OobBit : unsigned {
     kOobTcpOperand = 1u << 9,     // K2 persistent: B operand extent
     kOobTcpOutput = 1u << 10,     // K2 persistent: output sample
     kOobTcpPartial = 1u << 11,    // K2 persistent: noise-partial slot
-    kOobTcWindow = 1u << 12,      // K2 per-tile: source-window word
-    kOobTcOperand = 1u << 13,     // K2 per-tile: B operand extent
-    kOobTcOutput = 1u << 14,      // K2 per-tile: output sample
-    kOobTcPartial = 1u << 15,     // K2 per-tile: noise-partial slot
     kOobNoise = 1u << 16,         // noise: output sample
     kOobConvF32 = 1u << 17,       // FP32 convolution: output sample or partial
 };

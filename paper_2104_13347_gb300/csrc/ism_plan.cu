@@ -114,7 +114,6 @@ ConvLaunch plan_conv_launch(ism_plan &P) {
     L.seed = P.cfg.seed;
     L.any_noise = 1;  // jobs without an SNR (NaN) skip the noise kernel's work
     L.noise_partials_dev = (double *)(P.dblock + P.off_part);
-    L.per_tile = 0;
     L.err_dev = P.cell.dev;
     L.inject = 0;
     return L;

@@ -329,7 +329,7 @@ void ism_server::launch(std::vector<std::shared_ptr<Req>> &take) {
         int rc = ism_rir_batch_ex(rooms.data(), (int64_t)rooms.size(), base, hoffs.data(), &o, s);
         if (rc == ISM_OK)
             rc = convolve_batch(jobs.data(), (int64_t)jobs.size(), base, base, base, cfg.seed,
-                                cfg.precision, s, true);
+                                cfg.precision, s);
         if (rc != ISM_OK) {
             status = rc;
             err = ism_last_error_string();

@@ -34,10 +34,10 @@ def conv_case(ism, L=2000, M=3, T=3000, seed=5):
             torch.full((ylen,), float("nan"), device="cuda"))
 
 
-@pytest.mark.parametrize("L", [2000, 30000])  # persistent kernel; per-tile kernel
-def test_injected_timeout_reported_then_clean_call(ism, L):
+@pytest.mark.parametrize("L,T", [(2000, 3000), (30000, 26000)])  # one / two segment windows
+def test_injected_timeout_reported_then_clean_call(ism, L, T):
     import torch
-    h, s, jobs, hd, sd, y = conv_case(ism, L=L)
+    h, s, jobs, hd, sd, y = conv_case(ism, L=L, T=T)
     stream = torch.cuda.current_stream()
     ism.debug_inject(ism.INJECT_CONV_WAIT)
     ism.convolve_batch(jobs, hd, sd, y, precision=ism.BF16X3)  # enqueued: OK
