@@ -102,16 +102,19 @@ extern "C" int ism_dataset_batch(const ism_room *rooms, int64_t n_rooms, const f
         hp += hlen[i];
         y_total += ylen[i];
     }
-    // chunks of consecutive rooms.  Automatic: K >= 6 chunks of about
-    // 128 MiB of signals each, balanced by signal length (ragged rooms).  With
-    // two compute streams the tails of consecutive chunks overlap; on the
-    // 1024-room step equal chunks beat chunks of decreasing size.  When every
-    // room goes to the persistent tensor-core convolution (one CTA per SM
-    // walking the chunk's tiles), chunks are instead cut at a whole number of
-    // rounds of tiles over the SMs -- as many rounds as still give K chunks --
-    // so that no chunk ends with a partly filled round (1024 8-mic rooms with
-    // 1 s sources and 8192-sample RIRs: chunks of 152 rooms, six rounds each,
-    // 2 % faster end to end than six equal chunks).
+    // chunks of consecutive rooms.  Automatic, split-BF16 (every room on the
+    // persistent tensor-core convolution, one CTA per SM walking the chunk's
+    // tiles): chunks cut at whole rounds of tiles over the SMs, so that no
+    // chunk but the last ends with a partly filled round -- main chunks of R
+    // rounds (R = rounds / 4.5, at most 9), then a chunk of R / 3 rounds and
+    // the rest, which keeps the last chunk's download (the one copy nothing
+    // hides) short.  1024 8-mic rooms with 1 s sources and 8192-sample RIRs
+    // (40.4 rounds): 228, 228, 228, 228, 76 and 36 rooms, 12.55 ms end to end
+    // against 13.3 ms (12.7-13.9 from call to call) for six chunks of six
+    // rounds and the rest; chunks of 12 rounds, or not cut at whole rounds,
+    // were slower still (13.2-13.6 ms).  FP32: K >= 6 chunks of about 128
+    // MiB of signals each, balanced by signal length (ragged rooms).  With
+    // two compute streams the tails of consecutive chunks overlap.
     std::vector<int64_t> cb;  // chunk boundaries
     const int64_t target = (128ll << 20) / 4;  // floats of signals per chunk
     const int64_t K = std::min<int64_t>(n_rooms,
@@ -127,14 +130,22 @@ extern "C" int ism_dataset_batch(const ism_room *rooms, int64_t n_rooms, const f
             else total += tiles[i];
         }
         const int64_t sms = device_sm_count();
-        const int64_t rounds = total / (K * sms);
-        if (!tiles.empty() && rounds >= 1) {
-            const int64_t cap = rounds * sms;
+        if (!tiles.empty() && sms > 0) {
+            const double rounds = (double)total / (double)sms;
+            const int64_t R = std::min<int64_t>(9, std::max<int64_t>(1, llround(rounds / 4.5)));
+            const int64_t Tr = std::max<int64_t>(1, R / 3);
+            const int64_t n_main = rounds > (double)R + 1.5 ? (int64_t)((rounds - 1.5) / R) : 0;
+            std::vector<int64_t> caps(n_main, R * sms);  // tiles per chunk
+            if (rounds - (double)(n_main * R) > (double)(Tr + 1)) caps.push_back(Tr * sms);
             int64_t acc = 0;
+            size_t ci = 0;
             for (int64_t r = 0; r < n_rooms; ++r) {
-                if (r == 0 || acc + tiles[r] > cap) {
+                if (r == 0) {
+                    cb.push_back(r);
+                } else if (ci < caps.size() && acc + tiles[r] > caps[ci]) {
                     cb.push_back(r);
                     acc = 0;
+                    ++ci;
                 }
                 acc += tiles[r];
             }
