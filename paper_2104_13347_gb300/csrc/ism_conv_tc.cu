@@ -446,6 +446,8 @@ k_conv_tcp(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles, int
         if (n_my > 0) {
             const PTile T = p_tile(jobs, tiles, (int)blockIdx.x);
             convert_window(T, 0, 0, 0, p_seg_words(T, 0));
+            // the window's stores before the first chunk's arrivals, for the MMAs
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         }
         for (int lt = 0; lt < n_my; ++lt) {
             const PTile T = p_tile(jobs, tiles, (int)blockIdx.x + lt * (int)gridDim.x);
@@ -565,11 +567,10 @@ k_conv_tcp(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles, int
                     else p_rows<0>(cvb, ta, m, p, q);
                     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-                    // (orders this thread's earlier window-slice stores for the MMAs)
-                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     mbar_arrive(smem_u32(&bar_full[s]));
                     // a slice of the next unit's window, after the chunk is released
-                    // (the next chunk's fence orders these writes)
+                    // (read by the MMAs of the next unit only: the proxy fence at the
+                    // end of this unit orders these writes before its arrivals)
                     if (next_pos < next_words && il >= P_NS) {
                         if (!next_waited) {
                             wait_window(gu + 1);
