@@ -734,15 +734,37 @@ k_conv_tcp(const ConvJob *__restrict__ jobs, const Tile *__restrict__ tiles, int
                     for (int j = 0; j < 32; ++j) r[j] = 0u;
                 }
                 if (m < T.nm) {
+                    // outputs t0 + 16 j of this row: one base address and
+                    // immediate offsets; the bounds test only on the block
+                    // that the signal's end cuts.  The block's squares are
+                    // summed in FP32 (four chains of eight positive terms,
+                    // within 5e-7), then added to the float-float sum.
+                    const int64_t t0 = T.T0 + P_PH * cb + p;
+                    float *yo = ym + t0;
+                    float q[4] = {0.f, 0.f, 0.f, 0.f};
+                    if (t0 + P_PH * 31 < ylen) {
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const int64_t t = T.T0 + P_PH * (cb + j) + p;
-                        const float v = __uint_as_float(r[j]);
-                        if (t < ylen) {
-                            ym[t] = v;
-                            ff_accumulate_sq(v, ss, se);
+                        for (int j = 0; j < 32; ++j) {
+                            const float v = __uint_as_float(r[j]);
+                            yo[P_PH * j] = v;
+                            q[j & 3] = __fmaf_rn(v, v, q[j & 3]);
+                        }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            const float v = __uint_as_float(r[j]);
+                            if (t0 + P_PH * j < ylen) {
+                                yo[P_PH * j] = v;
+                                q[j & 3] = __fmaf_rn(v, v, q[j & 3]);
+                            }
                         }
                     }
+                    // (ss, se) += the block's sum: two-sum, error into se
+                    const float x = __fadd_rn(__fadd_rn(q[0], q[1]), __fadd_rn(q[2], q[3]));
+                    const float t = __fadd_rn(ss, x);
+                    const float bb = __fsub_rn(t, ss);
+                    se = __fadd_rn(se, __fadd_rn(__fsub_rn(ss, __fsub_rn(t, bb)), __fsub_rn(x, bb)));
+                    ss = t;
                 }
             }
             asm volatile("tcgen05.fence::before_thread_sync;");
