@@ -47,7 +47,7 @@ K1_BINDING = {"issue_active_pct": 78.0, "smem_wavefronts_pct_of_peak": 80.9,
               "fma_pipe_pct": 35.3, "alu_pipe_pct": 42.8, "xu_pipe_pct": 48.9,
               "fp64_pipe_pct": 3.1, "shared_atomic_wavefronts_per_instruction": 3.64,
               "source": "ncu --set full, 256-room case"}
-K2_TRAFFIC_PER_ROOM = (84.119552e6 + 139.02208e6) / 256
+K2_TRAFFIC_PER_ROOM = (83.657984e6 + 138.841088e6) / 256
 
 
 def k2_live_chunks(ts, lh, kc=64, nn=256, phases=16):
