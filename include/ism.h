@@ -284,15 +284,16 @@ int ism_convolve_batch(const ism_conv_job *jobs, int64_t n_jobs, const float *h_
  *                 mic-major, at y_host + y_offsets[i] (NULL: packed).
  * h_host          nullable: the RIRs too, room i's n_mics x rir_len floats
  *                 at h_host + h_offsets[i] (NULL offsets: packed).
- * chunk_rooms     rooms per chunk, or 0: six or more chunks of about
- *                 128 MiB of signals each, balanced by signal length; with
- *                 ISM_BF16X3 and RIRs short enough for the persistent
- *                 tensor-core kernel (see ism_precision), chunks of
- *                 consecutive rooms whose tiles fill a whole number of
- *                 rounds over the SMs, as many rounds as still give six or
- *                 more chunks.  Consecutive chunks compute on two streams,
- *                 so one chunk's RIR kernel overlaps the previous chunk's
- *                 convolution.  The outputs do not depend on the chunking.
+ * chunk_rooms     rooms per chunk, or 0: with ISM_BF16X3, chunks of
+ *                 consecutive rooms whose convolution tiles fill whole
+ *                 rounds over the SMs -- main chunks of R rounds (R = the
+ *                 batch's rounds / 4.5, at most 9), then one of R / 3
+ *                 rounds and the rest, so that the last chunk's download is
+ *                 short; with ISM_F32, six or more chunks of about 128 MiB
+ *                 of signals each, balanced by signal length.  Consecutive
+ *                 chunks compute on two streams, so one chunk's RIR kernel
+ *                 overlaps the previous chunk's convolution.  The outputs
+ *                 do not depend on the chunking.
  * Returns when every output is in host memory.  Errors: those of
  * ism_rir_batch and ism_convolve_batch, ISM_ERR_INVALID_ARG for NULL
  * buffers or src_lens < 1, ISM_ERR_CUDA, ISM_ERR_OUT_OF_MEMORY. */
