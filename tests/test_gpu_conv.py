@@ -210,6 +210,30 @@ def test_noise_dense_against_oracle(ism):
     assert np.all(err <= bar), float(np.max(err / bar))
 
 
+def test_noise_split_bf16_against_oracle(ism):
+    """The noise level of the split-BF16 path comes from the y^2 sums of the
+    tensor-core kernel's epilogue (FP32 within a 32-column block, float-float
+    across blocks, FP64 across rows and tiles); sigma and every noise value
+    against the oracle's (Sec. III.A) on the kernel's own noise-free output:
+    ragged rooms, a 9-mic room (a partial 8-mic group) and a room of 7
+    output tiles whose last block the signal's end cuts."""
+    hs, ss = ragged_case(seed=19)
+    rng = np.random.default_rng(23)
+    hs.append((rng.standard_normal((9, 700)) * np.exp(-np.arange(700) / 200)).astype(np.float32))
+    ss.append(rng.standard_normal(2100).astype(np.float32))
+    hs.append((rng.standard_normal((8, 5000)) * np.exp(-np.arange(5000) / 900)).astype(np.float32))
+    ss.append(rng.standard_normal(20000).astype(np.float32))
+    snr = np.linspace(2, 28, len(hs)).astype(np.float32)
+    ids = [3000 + 11 * i for i in range(len(hs))]
+    clean = run_conv(ism, hs, ss, 1)
+    noisy = run_conv(ism, hs, ss, 1, snr=snr, seed=2468, noise_ids=ids)
+    for i, (c, n) in enumerate(zip(clean, noisy)):
+        ref, sigma = oracle.add_noise(c.copy(), float(snr[i]), 2468, ids[i])
+        z = (ref - c) / sigma
+        bar = 2e-6 * sigma * (1 + np.abs(z)) + 2.0 ** -22 * np.abs(c)
+        assert np.all(np.abs(n - ref) <= bar), (i, float(np.max(np.abs(n - ref) / bar)))
+
+
 def test_noise_same_in_any_batch(ism):
     hs, ss = ragged_case(seed=10)
     snr = np.full(len(hs), 10.0, np.float32)
