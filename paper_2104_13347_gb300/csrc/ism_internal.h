@@ -240,8 +240,9 @@ struct ConvTile {
 };
 // The tiles of a convolution call and its launch shapes (host), then its
 // launches given the tiles in device memory (launch_conv_* = both, with the
-// tiles uploaded through the staging blocks).  Split-BF16: tiles are
-// [whole-window per-tile | chunked per-tile | persistent]; FP32: all n_a.
+// tiles uploaded through the staging blocks).  Split-BF16: the persistent
+// kernel's 8-mic x 4096-output tiles, longest RIR first; FP32: 8-mic x
+// 2048-output tiles.
 struct ConvPlan {
     int precision = ISM_F32;
     std::vector<ConvTile> tiles;
