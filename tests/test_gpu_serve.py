@@ -172,3 +172,29 @@ def test_serve_split_bf16_long_rirs_against_oracle(ism):
             for m in range(h.shape[0]):
                 assert rel_l2(y[m], yref[m]) <= 1e-5, (r["rir_len"], m)
             srv.release(t)
+
+
+def test_serve_long_source_in_segment_windows(ism):
+    """A served split-BF16 request whose tiles need more than one source
+    window (RIR 30000 samples, source 26000): its signals equal the batch
+    call's on the served RIR bit for bit (the same kernel, a job's tiles do
+    not depend on the batch), and the oracle's convolution within the 2e-4
+    the specification sets for the split-BF16 convolution (tens of
+    thousands of terms per output)."""
+    import torch
+    rng = np.random.default_rng(47)
+    room = wl.room_batch(1, seed=4700, order=5, rir_len=30000, n_mics=3)[0]
+    src = rng.standard_normal(26000).astype(np.float32)
+    with ism.Server(precision=1) as srv:
+        t = srv.submit(room, src)
+        h, y, _ = fetch(ism, srv, t, room, src)
+        srv.release(t)
+    jobs, ylen = ism.conv_jobs([3], [30000], [len(src)])
+    yb = torch.empty(ylen, device="cuda")
+    ism.convolve_batch(jobs, torch.from_numpy(h.astype(np.float32).ravel()).cuda(),
+                       torch.from_numpy(src).cuda(), yb, precision=1)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(y, yb.cpu().numpy().astype(np.float64).reshape(y.shape))
+    yref = oracle.convolve_batch([h], [src.astype(np.float64)])[0]
+    for m in range(3):
+        assert rel_l2(y[m], yref[m]) <= 2e-4, m
