@@ -990,12 +990,12 @@ constexpr double kFix0 = 16777216.0;           // 2^24
 constexpr uint32_t kFixLimit = 0x7e000000u;    // 2^31 - 2^25
 
 // PFIX > 0: every job of the launch has PFIX Chebyshev terms (the term loop
-// is unrolled); 0: per-job count.  SPEC = 1: the launch's window is
-// kSpecW and every job has kSpecTaps taps (the dataset's configuration), so
-// the sparse arrays' stride, the FIR's tap loop and the window loop are
-// compile-time constants (the term atomics address their arrays with
-// immediate offsets).
-constexpr int kSpecW = 1024, kSpecTaps = 81;
+// is unrolled); 0: per-job count.  SPEC > 0: the launch's window is kSpecW
+// and every job has SPEC taps (the dataset's 81-tap Hann sinc, or the
+// paper's 8-tap Lagrange filter), so the sparse arrays' stride, the FIR's
+// tap loop and the window loop are compile-time constants (the term atomics
+// address their arrays with immediate offsets).
+constexpr int kSpecW = 1024;
 
 template <int KIND, bool STATS, int PFIX, int SPEC>
 __global__ void __launch_bounds__(NT, 4)
@@ -1008,10 +1008,10 @@ k_ism_sparse(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W_arg, i
              const long long *__restrict__ g_offs) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int W = SPEC ? kSpecW : W_arg;
-    const int max_taps = SPEC ? kSpecTaps : max_taps_arg;
+    const int max_taps = SPEC ? SPEC : max_taps_arg;
     const Layout Lay = make_layout(true, W, max_order, max_taps, max_cheb);
     const int TE = Lay.TE;
-    const int CL = SPEC ? round64(kSpecW + kSpecTaps + 12 + PADL) : Lay.CL;
+    const int CL = SPEC ? round64(kSpecW + SPEC + 12 + PADL) : Lay.CL;
     Tables T;
     T.sq = nullptr;  // per item: the RIR's FP64 table in global memory (exact path only)
     T.hlg = (float4 *)(smem + Lay.off_hlg);
@@ -1062,8 +1062,9 @@ k_ism_sparse(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W_arg, i
         const JobConst jc = g_jc[jr];
         item_setup_f32<KIND>(J, jc, W, wi, it, tau_lo, tau_hi);
         if (SPEC) {  // the same values, known to the compiler
-            it.n_taps = kSpecTaps;
-            it.H = (kSpecTaps - 1) / 2;
+            it.n_taps = SPEC;
+            it.H = (SPEC - 1) / 2;
+            it.P = SPEC - 1;
             it.W = kSpecW;
         }
         // fixed-point scales (see kFix0): d_floor bounds from below the
@@ -1083,7 +1084,7 @@ k_ism_sparse(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W_arg, i
                          0.5f * (float)kFixLimit * 12.566370614359172f * d_floor / n_bound);
         };
         const int Pc = J.n_cheb;
-        const int n_taps = SPEC ? kSpecTaps : it.n_taps;
+        const int n_taps = SPEC ? SPEC : it.n_taps;
         // this window's ranks in the RIR's sorted column list
         const int2 wr = g_wr[g_offs[2 * jr + 1] + wi];
         const uint32_t *cols = g_cols + g_offs[2 * jr];
@@ -1389,6 +1390,9 @@ int launch_rir_sparse(const RirLaunch &L, cudaStream_t stream) {
     const bool st = L.stats_dev != nullptr;  // statistics compiled out when not asked for
     const int pf = L.min_cheb == L.max_cheb ? L.max_cheb : 0;
     if (L.fd_kind == ISM_FD_LAGRANGE) {
+        if (pf == 8 && L.window == kSpecW && L.max_taps == 8 && L.min_taps == 8)
+            return st ? launch_sparse_t<ISM_FD_LAGRANGE, true, 8, 8>(L, stream)
+                      : launch_sparse_t<ISM_FD_LAGRANGE, false, 8, 8>(L, stream);
         if (pf == 8)
             return st ? launch_sparse_t<ISM_FD_LAGRANGE, true, 8>(L, stream)
                       : launch_sparse_t<ISM_FD_LAGRANGE, false, 8>(L, stream);
@@ -1398,9 +1402,9 @@ int launch_rir_sparse(const RirLaunch &L, cudaStream_t stream) {
     if (pf == 9)
         return st ? launch_sparse_t<ISM_FD_HANN_SINC, true, 9>(L, stream)
                   : launch_sparse_t<ISM_FD_HANN_SINC, false, 9>(L, stream);
-    if (pf == 8 && L.window == kSpecW && L.max_taps == kSpecTaps && L.min_taps == kSpecTaps)
-        return st ? launch_sparse_t<ISM_FD_HANN_SINC, true, 8, 1>(L, stream)
-                  : launch_sparse_t<ISM_FD_HANN_SINC, false, 8, 1>(L, stream);
+    if (pf == 8 && L.window == kSpecW && L.max_taps == 81 && L.min_taps == 81)
+        return st ? launch_sparse_t<ISM_FD_HANN_SINC, true, 8, 81>(L, stream)
+                  : launch_sparse_t<ISM_FD_HANN_SINC, false, 8, 81>(L, stream);
     if (pf == 8)
         return st ? launch_sparse_t<ISM_FD_HANN_SINC, true, 8>(L, stream)
                   : launch_sparse_t<ISM_FD_HANN_SINC, false, 8>(L, stream);
