@@ -91,6 +91,29 @@ def sabine_beta(dims, rt60):
     return math.sqrt(1.0 - alpha)
 
 
+def eyring_beta(dims, rt60):
+    """Wall reflection coefficient from a target RT60 through Eyring's
+    formula RT60 = 0.161 V / (-S ln(1 - alpha)): alpha = 1 - exp(-0.161 V /
+    (S RT60)), beta = sqrt(1 - alpha) = exp(-0.0805 V / (S RT60)).  Eyring's
+    law is the one a uniform image lattice obeys at first: its images cross
+    S / (4V) walls per metre on average, so with these walls the energy of
+    the image sum starts to decay at 60 dB per RT60.  Unlike Sabine's alpha
+    it never reaches 1, so any RT60 > 0 gives walls in (0, 1)."""
+    L = np.asarray(dims, float)
+    V = float(np.prod(L))
+    S = 2.0 * (L[0] * L[1] + L[0] * L[2] + L[1] * L[2])
+    return math.exp(-0.5 * 0.161 * V / (S * rt60))
+
+
+def wall_beta(dims, rt60, walls="sabine"):
+    """beta on all six walls for RT60 by `walls` = "sabine" or "eyring"."""
+    if walls == "sabine":
+        return sabine_beta(dims, rt60)
+    if walls == "eyring":
+        return eyring_beta(dims, rt60)
+    raise ValueError(f"walls must be 'sabine' or 'eyring', not {walls!r}")
+
+
 def order_for_length(dims, rir_len, fs, c, n_taps):
     """Smallest lattice order whose images cover every delay up to the RIR
     length plus the filter half-width, on every axis (plus one)."""
@@ -100,10 +123,11 @@ def order_for_length(dims, rir_len, fs, c, n_taps):
 
 
 def ragged_batch(n_requests=4096, seed=1005, rt_lo=0.1, rt_hi=1.0, n_taps=81,
-                 max_order=None):
+                 max_order=None, walls="sabine"):
     """Ragged requests: RT60 U[rt_lo, rt_hi] s, fs in {16, 48} kHz, RIR length
-    ceil(RT60 fs), beta from Sabine on all six walls, order from the length,
-    4..16 mics on a 5 cm circle, dims as in `room_batch`."""
+    ceil(RT60 fs), beta on all six walls from Sabine (or Eyring, `walls`),
+    order from the length, 4..16 mics on a 5 cm circle, dims as in
+    `room_batch`."""
     rng = np.random.default_rng(seed)
     rooms = []
     for _ in range(n_requests):
@@ -117,7 +141,7 @@ def ragged_batch(n_requests=4096, seed=1005, rt_lo=0.1, rt_hi=1.0, n_taps=81,
         order = order_for_length(dims, rir_len, fs, 343.0, n_taps)
         if max_order is not None:
             order = min(order, max_order)
-        rooms.append(dict(dims=dims, beta=np.full(6, sabine_beta(dims, rt60)), src=src,
+        rooms.append(dict(dims=dims, beta=np.full(6, wall_beta(dims, rt60, walls)), src=src,
                           mics=circular_array(ctr, n_mics, 0.05), fs=fs, c=343.0,
                           order=order, n_taps=n_taps, fd_kind=FD_HANN_SINC,
                           rir_len=rir_len, rt60=rt60))
@@ -125,10 +149,11 @@ def ragged_batch(n_requests=4096, seed=1005, rt_lo=0.1, rt_hi=1.0, n_taps=81,
 
 
 def serve_stream(n_requests=256, rate_hz=1000.0, seed=1006, rt_lo=0.1, rt_hi=0.6,
-                 src_lo=0.5, src_hi=4.0, mic_lo=4, mic_hi=32, max_order=None, n_taps=81):
+                 src_lo=0.5, src_hi=4.0, mic_lo=4, mic_hi=32, max_order=None, n_taps=81,
+                 walls="sabine"):
     """Poisson arrivals at `rate_hz`; rooms U[3,20] m per side; 4..32 mics;
-    fs 16/48 kHz; sources 0.5..4 s; RT60 as in `ragged_batch`.  Returns
-    (arrival times in s, rooms, sources, snrs)."""
+    fs 16/48 kHz; sources 0.5..4 s; RT60 and walls as in `ragged_batch`.
+    Returns (arrival times in s, rooms, sources, snrs)."""
     rng = np.random.default_rng(seed)
     t = np.cumsum(rng.exponential(1.0 / rate_hz, n_requests))
     rooms, srcs = [], []
@@ -143,7 +168,7 @@ def serve_stream(n_requests=256, rate_hz=1000.0, seed=1006, rt_lo=0.1, rt_hi=0.6
             order = min(order, max_order)
         src = _uniform_point(rng, dims, 0.5)
         ctr = _uniform_point(rng, dims, 0.55)
-        rooms.append(dict(dims=dims, beta=np.full(6, sabine_beta(dims, rt60)), src=src,
+        rooms.append(dict(dims=dims, beta=np.full(6, wall_beta(dims, rt60, walls)), src=src,
                           mics=circular_array(ctr, n_mics, 0.05), fs=fs, c=343.0,
                           order=order, n_taps=n_taps, fd_kind=FD_HANN_SINC, rir_len=rir_len))
         srcs.append(rng.standard_normal(int(rng.uniform(src_lo, src_hi) * fs)).astype(np.float32))
@@ -194,15 +219,17 @@ def torus_sources(n, center, dims, seed=1007, R=2.0, dR=0.5, dphi_deg=7.0, clear
     return out
 
 
-def paper_dataset(n_sources=1024, room=1, seed=1007, fd_kind=FD_HANN_SINC, n_taps=81, rt=None):
+def paper_dataset(n_sources=1024, room=1, seed=1007, fd_kind=FD_HANN_SINC, n_taps=81, rt=None,
+                  walls="sabine"):
     """One request per source position: the paper room `room` (1 or 2) at
-    RT 0.5 s (Sabine walls), the UMA-8 array, fs 44.1 kHz, RIR length RT fs,
+    RT 0.5 s (Sabine walls, or Eyring: `walls`), the UMA-8 array, fs 44.1
+    kHz, RIR length RT fs,
     and the delay-limited image set (order -1 = automatic).  fd_kind
     FD_LAGRANGE with n_taps 8 is the paper's own 7th-order filter."""
     dims, ctr = PAPER_ROOMS[room]
     rt = PAPER_RT if rt is None else rt
     mics = uma8_array(ctr)
-    beta = np.full(6, sabine_beta(dims, rt))
+    beta = np.full(6, wall_beta(dims, rt, walls))
     srcs = torus_sources(n_sources, ctr, dims, seed=seed)
     L = int(round(rt * PAPER_FS))
     return [dict(dims=dims, beta=beta, src=s, mics=mics, fs=PAPER_FS, c=343.0, order=-1,

@@ -430,6 +430,66 @@ def test_paper_room_images_within_rt():
 
 
 # ---------------------------------------------------------------------------
+# Energy decay of the image sum (Sec. II.A: each image carries the cumulated
+# damping of the walls it met) and the walls drawn from an RT60
+# ---------------------------------------------------------------------------
+
+DECAY_ROOMS = [((5.0, 4.0, 3.0), (1.2, 1.1, 1.3), (3.6, 2.7, 1.6), 0.25),
+               ((7.0, 10.0, 3.7), (2.0, 3.0, 1.2), (4.0, 6.0, 1.5), 0.5)]
+
+
+def schroeder_t20(h, fs):
+    """T20 of a RIR: the Schroeder backward-integrated energy fitted by a
+    line between -5 and -25 dB, extrapolated to 60 dB."""
+    e = np.cumsum((np.asarray(h, np.float64) ** 2)[::-1])[::-1]
+    lev = 10.0 * np.log10(e / e[0])
+    i5, i25 = int(np.argmax(lev <= -5.0)), int(np.argmax(lev <= -25.0))
+    t = np.arange(len(h)) / fs
+    return -60.0 / np.polyfit(t[i5:i25], lev[i5:i25], 1)[0]
+
+
+def test_lattice_damping_gives_eyring_initial_decay():
+    """A ray leaving the receiver along u meets the x walls |u_x| / Lx times
+    per metre (y, z likewise); over the sphere that averages to S / (4V), the
+    inverse mean free path.  The oracle's images in a shell well inside the
+    lattice carry beta^n / (4 pi d) with an integer n whose mean per metre is
+    that value, so with Eyring walls for RT60 the energy of the image sum
+    starts to fall at 60 dB per RT60."""
+    from paper_2104_13347_gb300 import workloads as wl
+    for dims, src, mic, rt in DECAY_ROOMS:
+        L = np.array(dims)
+        V, S = np.prod(L), 2 * (L[0] * L[1] + L[0] * L[2] + L[1] * L[2])
+        beta = wl.eyring_beta(dims, rt)
+        N = 14
+        im = oracle.images(dims, np.full(6, beta), src, mic, 8000.0, C, N)
+        d = im["d"]
+        shell = (d > 40.0) & (d < (2 * N - 1) * L.min())
+        assert shell.sum() > 10000
+        n = np.log(im["amp"][shell] * 4 * np.pi * d[shell]) / math.log(beta)
+        np.testing.assert_allclose(n, np.round(n), atol=1e-8)
+        rate = np.mean(n / d[shell])
+        assert abs(rate / (S / (4 * V)) - 1) < 3e-3
+        slope_db_per_s = 10 * math.log10(beta ** 2) * C * rate
+        assert abs(slope_db_per_s * rt / -60.0 - 1) < 3e-3
+
+
+def test_decay_time_scales_with_log_beta():
+    """For a fixed room and positions the image sum's energy depends on time
+    only through (-ln beta) t, so the decay times of RIRs with Sabine and
+    with Eyring walls for the same RT60 stand in the ratio ln beta_S /
+    ln beta_E (the Eyring walls reflect more)."""
+    from paper_2104_13347_gb300 import workloads as wl
+    fs = 8000.0
+    for dims, src, mic, rt in DECAY_ROOMS:
+        n = int(math.ceil(1.5 * rt * fs))
+        bs, be = wl.sabine_beta(dims, rt), wl.eyring_beta(dims, rt)
+        hs = oracle.rir(dims, np.full(6, bs), src, mic, fs, C, -1, rir_len=n)
+        he = oracle.rir(dims, np.full(6, be), src, mic, fs, C, -1, rir_len=n)
+        ratio = schroeder_t20(he, fs) / schroeder_t20(hs, fs)
+        assert abs(ratio / (math.log(bs) / math.log(be)) - 1) < 0.03
+
+
+# ---------------------------------------------------------------------------
 # Training frames (Sec. II.B: 1024-sample multichannel windows; Sec. III.A:
 # measurement noise at a drawn SNR)
 # ---------------------------------------------------------------------------

@@ -52,3 +52,28 @@ def test_paper_dataset_requests():
     assert abs(r["beta"][0] ** 2 - (1 - 0.161 * V / (S * 0.5))) < 1e-12
     lag = wl.paper_dataset(2, room=2, fd_kind=wl.FD_LAGRANGE, n_taps=8)
     assert lag[0]["fd_kind"] == 1 and lag[0]["n_taps"] == 8
+
+
+def test_eyring_walls():
+    """Eyring's alpha = 1 - exp(-0.161 V / (S RT60)) lies below Sabine's
+    0.161 V / (S RT60) (more reflective walls for the same RT60), tends to it
+    as the absorption vanishes, and stays inside (0, 1) where Sabine's
+    clamps; the generators take either law and keep Sabine by default."""
+    dims = np.array([5.0, 4.0, 3.0])
+    for rt in (0.1, 0.3, 1.0, 3.0):
+        be, bs = wl.eyring_beta(dims, rt), wl.sabine_beta(dims, rt)
+        assert 0.0 <= bs < be < 1.0
+    a = lambda b: 1.0 - b * b
+    assert abs(a(wl.eyring_beta(dims, 100.0)) / a(wl.sabine_beta(dims, 100.0)) - 1) < 2e-3
+    # RT60 so short that Sabine's alpha passes 1: Sabine gives beta 0, Eyring a wall
+    assert wl.sabine_beta(dims, 0.05) == 0.0 and 0.0 < wl.eyring_beta(dims, 0.05) < 1.0
+    assert wl.wall_beta(dims, 0.4, "eyring") == wl.eyring_beta(dims, 0.4)
+    with pytest.raises(ValueError):
+        wl.wall_beta(dims, 0.4, "lehmann")
+    r_s, r_e = wl.ragged_batch(8, seed=3), wl.ragged_batch(8, seed=3, walls="eyring")
+    for x, y in zip(r_s, r_e):
+        assert x["beta"][0] == wl.sabine_beta(x["dims"], x["rt60"])
+        assert y["beta"][0] == wl.eyring_beta(y["dims"], y["rt60"])
+        assert x["rir_len"] == y["rir_len"] and x["order"] == y["order"]
+    p = wl.paper_dataset(2, room=1, walls="eyring")
+    assert p[0]["beta"][0] == wl.eyring_beta(wl.PAPER_ROOMS[1][0], wl.PAPER_RT)
