@@ -234,6 +234,35 @@ def test_noise_split_bf16_against_oracle(ism):
         assert np.all(np.abs(n - ref) <= bar), (i, float(np.max(np.abs(n - ref) / bar)))
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_noise_degenerate_levels(ism, precision):
+    """Noise levels at the edges of Sec. III.A's augmentation, in one call:
+    a silent room (zero source: mean power 0, so sigma = 0 and the output
+    stays exactly zero -- u1 never reaches 0, so no deviate is infinite), a
+    room with SNR NaN (no noise: bitwise the noise-free output), noise 20 dB
+    above the signal, noise 80 dB below it, and an ordinary room with a
+    9-mic array; each against the oracle's noise on the kernel's own
+    noise-free output."""
+    rng = np.random.default_rng(91)
+    shapes = [(3, 900), (2, 400), (9, 1200), (4, 50), (8, 2000)]
+    hs = [(rng.standard_normal((M, L)) * np.exp(-np.arange(L) / 300)).astype(np.float32)
+          for M, L in shapes]
+    ss = [np.zeros(1500, np.float32)] + [rng.standard_normal(T).astype(np.float32)
+                                         for T in (700, 3000, 64, 5000)]
+    snr = np.array([10.0, np.nan, -20.0, 80.0, 7.5], np.float32)
+    ids = [901, 902, 903, 904, 905]
+    clean = run_conv(ism, hs, ss, precision)
+    noisy = run_conv(ism, hs, ss, precision, snr=snr, seed=97, noise_ids=ids)
+    assert not np.any(clean[0]) and not np.any(noisy[0])
+    np.testing.assert_array_equal(noisy[1], clean[1])
+    for i in (2, 3, 4):
+        ref, sigma = oracle.add_noise(clean[i].copy(), float(snr[i]), 97, ids[i])
+        assert sigma > 0
+        z = (ref - clean[i]) / sigma
+        bar = 2e-6 * sigma * (1 + np.abs(z)) + 2.0 ** -22 * np.abs(clean[i])
+        assert np.all(np.abs(noisy[i] - ref) <= bar), (i, float(np.max(np.abs(noisy[i] - ref) / bar)))
+
+
 def test_noise_same_in_any_batch(ism):
     hs, ss = ragged_case(seed=10)
     snr = np.full(len(hs), 10.0, np.float32)

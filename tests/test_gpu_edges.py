@@ -19,7 +19,9 @@ def rel_l2(x, ref):
     return float(np.linalg.norm(x - ref) / max(np.linalg.norm(ref), 1e-300))
 
 
-def run(ism, rooms, variant, tol=1e-5):
+def run(ism, rooms, variant, tol=1e-5, oracle_rooms=None):
+    """The GPU path on `rooms` against the oracle on `oracle_rooms` (the
+    same rooms unless given)."""
     import torch
     n_rirs, _ = ism.rir_batch_size(rooms)
     stats = torch.zeros(2 * n_rirs, dtype=torch.int64, device="cuda")
@@ -27,7 +29,7 @@ def run(ism, rooms, variant, tol=1e-5):
     torch.cuda.synchronize()
     h = h.cpu().numpy().astype(np.float64)
     st = stats.view(-1, 2).cpu().numpy()
-    ref, ost = oracle.rir_batch(rooms)
+    ref, ost = oracle.rir_batch(rooms if oracle_rooms is None else oracle_rooms)
     o = j = 0
     for r, rr in zip(rooms, ref):
         L = r["rir_len"]
@@ -112,3 +114,28 @@ def test_tail_only_rirs_take_the_direct_kernel(ism):
                 assert (L == 20) != bool(np.any(hs[seg]))
             o += L
     run(ism, rooms, 0)
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_largest_lattice_order(ism, variant):
+    """Order 200, the largest the ABI accepts (8 x 401^3 = 5.2e8 lattice
+    images per RIR: per-axis tables of 802 entries, 643204 columns to sort
+    per RIR), in rooms of about a metre with responses of 400 and 1600
+    samples, Hann and Lagrange filters.  The oracle runs the delay-limited
+    lattice instead, which holds every image able to reach the response
+    (its own pin: a larger lattice changes nothing), so RIRs and the counts
+    of contributing images and in-range taps must equal it."""
+    rooms = []
+    for i, (L, kind, taps) in enumerate([(400, 0, 81), (1600, 0, 81), (1600, 1, 8)]):
+        rng = np.random.default_rng(300 + i)
+        dims = np.array([1.0, 1.2, 0.9]) + rng.uniform(0, 0.2, 3)
+        rooms.append(dict(dims=dims, beta=rng.uniform(0.5, 0.95, 6),
+                          src=rng.uniform(0.2, 0.7, 3) * dims / dims.max(),
+                          mics=np.stack([rng.uniform(0.25, 0.75, 3) * dims for _ in range(3)]),
+                          fs=16000.0, c=343.0, order=200, n_taps=taps, fd_kind=kind,
+                          rir_len=L))
+    auto = [dict(r, order=-1) for r in rooms]  # ISM_ORDER_AUTO
+    for r in auto:
+        assert max(oracle.auto_order(r["dims"], r["src"], m, r["fs"], r["c"], r["n_taps"],
+                                     r["rir_len"]) for m in r["mics"]) < 200
+    run(ism, rooms, variant, oracle_rooms=auto)
