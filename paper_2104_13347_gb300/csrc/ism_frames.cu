@@ -14,7 +14,8 @@
 // One CTA per frame.  The frame's power is a float-float sum per thread and
 // an FP64 sum across threads in a fixed order, so results are bitwise
 // reproducible; the second pass re-reads the frame (L1/L2-resident) and
-// writes it.  HBM-bound: one read and one write of the frame.
+// writes it.  HBM work: one read and one write of the frame; the noise
+// generator's integer instructions set the pace.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -38,22 +39,27 @@ struct FrameJob {
 };
 static_assert(sizeof(FrameJob) == 48, "FrameJob layout");
 
-__global__ void __launch_bounds__(FT)
-k_frames(const FrameJob *__restrict__ jobs, int frame_len, const float *__restrict__ y,
-         float *__restrict__ out, uint64_t seed) {
-    const FrameJob J = jobs[blockIdx.x];
+// INSIDE: the frame lies within the signal ([t0, t0 + frame_len) inside
+// [0, y_len)), so no sample needs a range check.
+template <bool INSIDE>
+__device__ __forceinline__ void frame_body(const FrameJob &J, int frame_len,
+                                           const float *__restrict__ y, float *__restrict__ out,
+                                           uint64_t seed) {
     const float *yb = y + J.y_offset;
     float *ob = out + J.out_offset;
     const int tid = threadIdx.x;
     const bool noisy = !isnan(J.snr_db) && !isinf(J.snr_db);
     float sigma = 0.f;
     if (noisy) {
+        // 10^(snr/10) for thread 0, begun before the loads it waits behind
+        const double den = tid == 0 ? pow(10.0, (double)J.snr_db / 10.0) : 1.0;
         float ss = 0.f, se = 0.f;
         for (int m = 0; m < J.n_mics; ++m) {
             const float *ym = yb + (int64_t)m * J.y_len;
+#pragma unroll 4
             for (int i = tid; i < frame_len; i += FT) {
                 const int64_t t = J.t0 + i;
-                const float v = (t >= 0 && t < J.y_len) ? ym[t] : 0.f;
+                const float v = (INSIDE || (t >= 0 && t < J.y_len)) ? ym[t] : 0.f;
                 ff_accumulate_sq(v, ss, se);
             }
         }
@@ -66,7 +72,7 @@ k_frames(const FrameJob *__restrict__ jobs, int frame_len, const float *__restri
             double p = 0.0;
             for (int w = 0; w < FT / 32; ++w) p += s_red[w];
             p /= (double)J.n_mics * (double)frame_len;
-            s_sigma = (float)sqrt(p / pow(10.0, (double)J.snr_db / 10.0));
+            s_sigma = (float)sqrt(p / den);
         }
         __syncthreads();
         sigma = s_sigma;
@@ -82,8 +88,9 @@ k_frames(const FrameJob *__restrict__ jobs, int frame_len, const float *__restri
         for (int k = tid; 2 * k < frame_len; k += FT, zs += (uint64_t)FT * kSm64Gamma) {
             const int i = 2 * k;
             const int64_t t = J.t0 + i;
-            float v0 = (t >= 0 && t < J.y_len) ? ym[t] : 0.f;
-            float v1 = (t + 1 >= 0 && t + 1 < J.y_len) ? ym[t + 1] : 0.f;
+            float v0 = (INSIDE || (t >= 0 && t < J.y_len)) ? ym[t] : 0.f;
+            float v1 = (INSIDE ? i + 1 < frame_len : (t + 1 >= 0 && t + 1 < J.y_len)) ? ym[t + 1]
+                                                                                      : 0.f;
             if (noisy) {
                 float z0, z1;
                 box_muller(sm64_mix(zs), sigma, z0, z1);
@@ -94,6 +101,16 @@ k_frames(const FrameJob *__restrict__ jobs, int frame_len, const float *__restri
             if (i + 1 < frame_len) om[i + 1] = v1;
         }
     }
+}
+
+__global__ void __launch_bounds__(FT)
+k_frames(const FrameJob *__restrict__ jobs, int frame_len, const float *__restrict__ y,
+         float *__restrict__ out, uint64_t seed) {
+    const FrameJob J = jobs[blockIdx.x];
+    if (J.t0 >= 0 && J.t0 + frame_len <= J.y_len)
+        frame_body<true>(J, frame_len, y, out, seed);
+    else
+        frame_body<false>(J, frame_len, y, out, seed);
 }
 
 }  // namespace

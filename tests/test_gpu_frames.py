@@ -75,3 +75,38 @@ def test_frames_from_convolved_rooms(ism):
     for i in range(n):
         ref, sig = oracle.frame(yy[rr[i]], int(t0s[i]), 1024, float(snrs[i]), 5, i)
         assert np.max(np.abs(got[i] - ref)) <= 1e-5 * sig + 1e-6 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("frame_len,mics", [(333, 5), (1024, 8), (1023, 3), (1, 7),
+                                            (2000, 2), (512, 12)])
+def test_frames_shapes_and_alignments(ism, frame_len, mics):
+    """Frame lengths and mic counts on both kernels (frames of at most 1024
+    samples and 8 mics are held in registers between the two passes, longer
+    frames or more mics take the two-pass kernel), rows of odd length from an
+    odd offset and frames packed at odd offsets, so that 8-byte and 4-byte
+    accesses both occur, and frames reaching past either end of the signal;
+    against the oracle frame by frame."""
+    import torch
+    rng = np.random.default_rng(1000 * frame_len + mics)
+    T, base, n_rooms = 2501, 3, 3
+    ys = [rng.standard_normal((mics, T)) * rng.uniform(0.2, 3.0) for _ in range(n_rooms)]
+    buf = np.concatenate([np.zeros(base)] + [a.ravel() for a in ys]).astype(np.float32)
+    ys = [a.astype(np.float32).astype(np.float64) for a in ys]
+    y = torch.from_numpy(buf).cuda()
+    n = 40
+    rr = rng.integers(0, n_rooms, n)
+    t0s = rng.integers(-frame_len - 5, T + 5, n)
+    snrs = [[math.inf, math.nan, float(rng.uniform(-10, 40))][i % 3] for i in range(n)]
+    jobs, n_out = ism.frame_jobs([base + int(r) * mics * T for r in rr], [T] * n, [mics] * n,
+                                 t0s, frame_len, snr_db=snrs, noise_ids=[77 + i for i in range(n)])
+    out = torch.full((n_out,), float("nan"), device="cuda")
+    ism.frames_batch(jobs, frame_len, y, out, seed=31)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().astype(np.float64)
+    for i in range(n):
+        g = got[jobs[i].out_offset:jobs[i].out_offset + mics * frame_len].reshape(mics, frame_len)
+        ref, sig = oracle.frame(ys[rr[i]], int(t0s[i]), frame_len, snrs[i], 31, 77 + i)
+        if sig == 0.0:
+            np.testing.assert_array_equal(g, ref)
+        else:
+            assert np.max(np.abs(g - ref)) <= 1e-5 * sig + 1e-6 * np.max(np.abs(ref)), i
