@@ -26,7 +26,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 # reject it.
 _SRC = os.environ.get("ORACLE_SRC", os.path.join(_HERE, "ism_oracle.c"))
 _BUILD = os.environ.get("ORACLE_BUILD", os.path.join(_HERE, "_build"))
-_LIB_PATH = os.path.join(_BUILD, "libism_oracle.so")
+# ORACLE_SANITIZE=1: an AddressSanitizer + UndefinedBehaviorSanitizer build
+# (its own file; the process must preload the ASan runtime).
+_SANITIZE = os.environ.get("ORACLE_SANITIZE") == "1"
+_LIB_PATH = os.path.join(_BUILD, "libism_oracle_san.so" if _SANITIZE else "libism_oracle.so")
 
 FD_HANN_SINC = 0
 FD_LAGRANGE = 1
@@ -44,6 +47,9 @@ def build(force: bool = False) -> str:
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-ffp-contract=off",
            "-fno-fast-math", "-fopenmp", "-o", tmp, _SRC, "-lm"]
+    if _SANITIZE:
+        cmd[1:1] = ["-g", "-fsanitize=address,undefined", "-fno-omit-frame-pointer",
+                    "-fno-sanitize-recover=undefined"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH

@@ -5,8 +5,12 @@ parallel, then linked into paper_2104_13347_gb300/libism.so with the static
 CUDA runtime.  Rebuilds only what changed (by modification time).
 --bounds-check builds libism_checked.so instead (ISM_BOUNDS_CHECK: kernels
 record out-of-range indices, see ism_debug_bounds); select it at run time
-with ISM_LIB=libism_checked.so.
+with ISM_LIB=libism_checked.so.  --host-sanitize builds libism_san.so, whose
+host code (argument checks, planning, the serving layer) carries
+AddressSanitizer and UndefinedBehaviorSanitizer; a process that loads it
+must preload the ASan runtime.
 Usage: python -m paper_2104_13347_gb300.build  [--force] [--verbose] [--bounds-check]
+       [--host-sanitize]
 """
 from __future__ import annotations
 
@@ -24,6 +28,11 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libism.so")
 BUILD_CHECKED = os.path.join(HERE, "_build_checked")
 LIB_CHECKED = os.path.join(HERE, "libism_checked.so")
+BUILD_SAN = os.path.join(HERE, "_build_san")
+LIB_SAN = os.path.join(HERE, "libism_san.so")
+# (one flag per -Xcompiler: nvcc splits its argument at commas)
+SAN = ["-Xcompiler", "-fsanitize=address", "-Xcompiler", "-fsanitize=undefined",
+       "-Xcompiler", "-fno-omit-frame-pointer", "-Xcompiler", "-fno-sanitize-recover=undefined"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -34,11 +43,13 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libism.so")
 
 
-def _flags(verbose: bool, bounds_check: bool = False):
+def _flags(verbose: bool, bounds_check: bool = False, host_sanitize: bool = False):
     f = ["-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC",
          "-I", os.path.join(ROOT, "include"), "--expt-relaxed-constexpr"]
     if bounds_check:
         f += ["-DISM_BOUNDS_CHECK"]
+    if host_sanitize:
+        f += ["-g", *SAN]
     if verbose:
         f += ["-Xptxas", "-v"]
     return f
@@ -50,9 +61,13 @@ def _headers_mtime() -> float:
     return max(os.path.getmtime(h) for h in hs if os.path.exists(h))
 
 
-def build(force: bool = False, verbose: bool = False, bounds_check: bool = False) -> str:
-    BUILD = BUILD_CHECKED if bounds_check else globals()["BUILD"]
-    LIB = LIB_CHECKED if bounds_check else globals()["LIB"]
+def build(force: bool = False, verbose: bool = False, bounds_check: bool = False,
+          host_sanitize: bool = False) -> str:
+    if bounds_check and host_sanitize:
+        raise ValueError("choose one of bounds_check and host_sanitize")
+    BUILD = (BUILD_CHECKED if bounds_check else BUILD_SAN if host_sanitize
+             else globals()["BUILD"])
+    LIB = LIB_CHECKED if bounds_check else LIB_SAN if host_sanitize else globals()["LIB"]
     os.makedirs(BUILD, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     hm = _headers_mtime()
@@ -67,7 +82,7 @@ def build(force: bool = False, verbose: bool = False, bounds_check: bool = False
 
     def compile_one(so):
         s, o = so
-        cmd = [exe, *_flags(verbose, bounds_check), "-c", s, "-o", o + ".tmp"]
+        cmd = [exe, *_flags(verbose, bounds_check, host_sanitize), "-c", s, "-o", o + ".tmp"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {os.path.basename(s)}:\n{r.stderr}")
@@ -82,7 +97,8 @@ def build(force: bool = False, verbose: bool = False, bounds_check: bool = False
     if force or jobs or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(
             os.path.getmtime(o) for o in objs):
         tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [exe, "-shared", *ARCH, "-o", tmp, *objs, "-lpthread"]
+        cmd = [exe, "-shared", *ARCH, *(SAN if host_sanitize else []), "-o", tmp, *objs,
+               "-lpthread"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr}")
@@ -92,4 +108,5 @@ def build(force: bool = False, verbose: bool = False, bounds_check: bool = False
 
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose="--verbose" in sys.argv,
-                bounds_check="--bounds-check" in sys.argv))
+                bounds_check="--bounds-check" in sys.argv,
+                host_sanitize="--host-sanitize" in sys.argv))
