@@ -40,9 +40,10 @@
 //    that can reach it, one column per lane, each lane walking its own
 //    column's candidates (neighbouring columns have nearly equal counts).
 //  * k_ism_taps (direct): one warp per image, one lane per tap (81 taps -> 3
-//    rows of 32).  sin(pi (j-f)) = -(-1)^j sin(pi f) and the Hann term is
-//    expanded in cos/sin of pi j/(H+1) (per-lane constants) and of
-//    pi f/(H+1) (per image), leaving one reciprocal per tap.  Each warp
+//    rows of 32).  sin(pi (j-f)) = -(-1)^j sin(pi f), and the Hann window,
+//    written cos^2(pi (j-f) / (2(H+1))), is expanded in cos/sin of
+//    pi j/(2(H+1)) (per-lane constants) and of pi f/(2(H+1)) (per image),
+//    leaving one reciprocal per tap.  Each warp
 //    accumulates into its own shared-memory copy of the window (no atomics,
 //    fixed order, bitwise reproducible).
 #include <cuda_runtime.h>
@@ -827,7 +828,13 @@ k_ism_taps(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int max
                 const float sg = (j & 1) ? -1.f : 1.f;
                 cSJ[r] = sg * (float)j;
                 cMS[r] = -sg;
-                sincospif((float)j / (float)(H + 1), &cS[r], &cC[r]);
+                // half-angle constants cos, sin(pi j / (2 (H + 1))), from FP64
+                // so that the small cosines of the outer taps keep their
+                // relative precision
+                double sd, cd;
+                sincospi((double)j / (double)(2 * (H + 1)), &sd, &cd);
+                cS[r] = (float)sd;
+                cC[r] = (float)cd;
             } else {
                 const int j = lane + 32 * r;
                 cOK[r] = j <= P;
@@ -866,9 +873,10 @@ k_ism_taps(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int max
                         } else {
                             float sp, cp, sw, cw;
                             sincospif(f, &sp, &cp);
-                            sincospif(f / (float)(H + 1), &sw, &cw);
-                            const float A = -a * sp * 0.15915494309189535f;
-                            v = make_float4(A, A * cw, A * sw, f);
+                            sincospif(f / (float)(2 * (H + 1)), &sw, &cw);
+                            // a sinc(j - f) = A (-1)^j / (j - f), A = -a sin(pi f) / pi
+                            const float A = -a * sp * 0.3183098861837907f;
+                            v = make_float4(A, cw, sw, f);
                         }
                     } else {
                         v = make_float4(a, f + (float)((P - 1) / 2), 0.f, 0.f);
@@ -893,13 +901,17 @@ k_ism_taps(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int max
                             if (lane == 0) p[H] += vx;
                             continue;
                         }
+                        // Hann window w(t) = (1 + cos(pi t / (H + 1))) / 2 as
+                        // cos^2(pi t / (2 (H + 1))), t = j - f: the angle
+                        // difference's cosine cancels at most twofold, where
+                        // 1 + cos would lose most bits at the outer taps
 #pragma unroll
                         for (int r = 0; r < R; ++r) {
                             if (cOK[r]) {
                                 const float xs = fmaf(cMS[r], vw, cSJ[r]);
                                 const float rcp = rcp_approx(xs);
-                                const float nn = fmaf(cC[r], vy, fmaf(cS[r], vz, vx));
-                                p[32 * r] = fmaf(nn, rcp, p[32 * r]);
+                                const float d = fmaf(cC[r], vy, cS[r] * vz);
+                                p[32 * r] = fmaf(vx * d * d, rcp, p[32 * r]);
                             }
                         }
                     } else {

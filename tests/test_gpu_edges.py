@@ -139,3 +139,30 @@ def test_largest_lattice_order(ism, variant):
         assert max(oracle.auto_order(r["dims"], r["src"], m, r["fs"], r["c"], r["n_taps"],
                                      r["rir_len"]) for m in r["mics"]) < 200
     run(ism, rooms, variant, oracle_rooms=auto)
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_tail_only_rirs_of_wide_filters(ism, variant):
+    """255-tap Hann filters on RIRs that end before the direct arrival, so
+    that every sample is a far filter tail (both variants take the direct
+    per-tap kernel for them): the outer taps' window values are ~1e-4 of the
+    centre's, and must keep their relative precision (a window evaluated as
+    1 + cos cancels there).  Rooms from a randomized sweep against the
+    oracle: mics 1 mm from a wall, absorbing and rigid walls mixed."""
+    rooms = [
+        dict(dims=np.array([8.893839269383143, 10.506559043134592, 16.81623744945732]),
+             beta=np.array([0.0, 1.0, 0.0, 0.888459665457403, 0.0, 0.3110977831570719]),
+             src=np.array([6.450528485976667, 4.913054132597867, 10.390543488898375]),
+             mics=np.array([[0.001, 3.2381923758825675, 11.647781849740037],
+                            [4.580810968796418, 6.223670331673284, 16.815237449457317],
+                            [3.020822382567682, 0.001, 11.259194720355325]]),
+             fs=8000.0, c=343.0, order=-1, n_taps=255, fd_kind=0, rir_len=35),
+        dict(dims=np.array([6.46555925860823, 19.18357269018504, 0.7633025218621846]),
+             beta=np.array([0.4148920451030764, 0.7325607160274136, 0.0, 0.4594006983848494,
+                            0.5676990312042093, 0.0]),
+             src=np.array([3.802768292943413, 15.90782723262708, 0.5777257551062134]),
+             mics=np.array([[1.6813341875345282, 5.075864370062916, 0.5445760219183458],
+                            [3.625247770177144, 19.18257269018504, 0.05969707331769491]]),
+             fs=16000.0, c=343.0, order=-1, n_taps=255, fd_kind=0, rir_len=389),
+    ]
+    run(ism, rooms, variant)
