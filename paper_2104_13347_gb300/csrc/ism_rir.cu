@@ -818,7 +818,7 @@ k_ism_taps(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int max
         build_lists(T, TE, it, s_lx, s_ly, s_nl);
         const int H = it.H, P = it.P, w0 = it.w0;
         // per-lane tap constants
-        float cC[R], cS[R], cSJ[R], cMS[R];
+        float cC[R], cS[R], cQ[R], cSJ[R], cMS[R];
         bool cOK[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
@@ -828,13 +828,17 @@ k_ism_taps(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int max
                 const float sg = (j & 1) ? -1.f : 1.f;
                 cSJ[r] = sg * (float)j;
                 cMS[r] = -sg;
-                // half-angle constants cos, sin(pi j / (2 (H + 1))), from FP64
-                // so that the small cosines of the outer taps keep their
-                // relative precision
-                double sd, cd;
-                sincospi((double)j / (double)(2 * (H + 1)), &sd, &cd);
-                cS[r] = (float)sd;
-                cC[r] = (float)cd;
+                // ch, sh = cos, sin(pi j / (2 (H + 1))) from the
+                // complementary angle pi (H + 1 - |j|) / (2 (H + 1)), whose
+                // exact integer numerator keeps the small cosines of the
+                // outer taps at full relative precision
+                const int aj = j < 0 ? -j : j;
+                float sx, cx;
+                sincospif((float)(H + 1 - aj) / (float)(2 * (H + 1)), &sx, &cx);
+                const float ch = sx, sh = j < 0 ? -cx : cx;
+                cC[r] = ch * ch;
+                cS[r] = ch * sh;
+                cQ[r] = sh * sh;
             } else {
                 const int j = lane + 32 * r;
                 cOK[r] = j <= P;
@@ -842,7 +846,7 @@ k_ism_taps(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int max
                 for (int i = 0; i <= P; ++i)
                     if (i != j) den *= (float)(j - i);
                 cC[r] = cOK[r] ? 1.f / den : 0.f;
-                cS[r] = cSJ[r] = cMS[r] = 0.f;
+                cS[r] = cQ[r] = cSJ[r] = cMS[r] = 0.f;
             }
         }
         __syncthreads();
@@ -876,7 +880,7 @@ k_ism_taps(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int max
                             sincospif(f / (float)(2 * (H + 1)), &sw, &cw);
                             // a sinc(j - f) = A (-1)^j / (j - f), A = -a sin(pi f) / pi
                             const float A = -a * sp * 0.3183098861837907f;
-                            v = make_float4(A, cw, sw, f);
+                            v = make_float4(A * (cw * cw), A * (2.f * cw * sw), A * (sw * sw), f);
                         }
                     } else {
                         v = make_float4(a, f + (float)((P - 1) / 2), 0.f, 0.f);
@@ -902,16 +906,18 @@ k_ism_taps(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int max
                             continue;
                         }
                         // Hann window w(t) = (1 + cos(pi t / (H + 1))) / 2 as
-                        // cos^2(pi t / (2 (H + 1))), t = j - f: the angle
-                        // difference's cosine cancels at most twofold, where
-                        // 1 + cos would lose most bits at the outer taps
+                        // cos^2(pi t / (2 (H + 1))), t = j - f, the square of
+                        // ch cos(b) + sh sin(b) (b = pi f / (2 (H + 1)))
+                        // expanded over per-lane and per-image products: its
+                        // terms cancel at most a few-fold, where 1 + cos
+                        // would lose most bits at the outer taps
 #pragma unroll
                         for (int r = 0; r < R; ++r) {
                             if (cOK[r]) {
                                 const float xs = fmaf(cMS[r], vw, cSJ[r]);
                                 const float rcp = rcp_approx(xs);
-                                const float d = fmaf(cC[r], vy, cS[r] * vz);
-                                p[32 * r] = fmaf(vx * d * d, rcp, p[32 * r]);
+                                const float nn = fmaf(cC[r], vx, fmaf(cS[r], vy, cQ[r] * vz));
+                                p[32 * r] = fmaf(nn, rcp, p[32 * r]);
                             }
                         }
                     } else {
