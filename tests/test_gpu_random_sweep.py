@@ -10,7 +10,9 @@ path (RIRs within 1e-5 rel-L2 of the oracle, image and tap counts exact),
 then the convolution of the oracle's RIRs with random sources in both
 precisions (1e-5 and the split-BF16 bar of 2e-4) and its noise at random
 SNRs (NaN: none) against the oracle's noise on the kernel's own noise-free
-output."""
+output.  A second sweep sends random batches through the host-buffer
+dataset step and the server and compares them with the batch entry points
+bit for bit."""
 import math
 
 import numpy as np
@@ -129,3 +131,58 @@ def test_random_rooms_against_oracle(ism):
                     bar = 2e-6 * sigma * (1 + np.abs(z)) + 2.0 ** -22 * np.abs(c_)
                     assert np.all(np.abs(g - ref_n) <= bar), (b, prec, k)
                 o += x.shape[0] * T
+
+
+def test_random_batches_served_and_host_buffers_bitwise(ism):
+    """The same random rooms (RIRs up to 12000 samples) with random sources,
+    SNRs (NaN: none) and precision through the host-buffer dataset step at a
+    random chunking, and one by one through a server of random batch size
+    and stream count: every output equals the batch entry points' bit for
+    bit (the dataset step against the batch call, a served request against
+    the entry points at the server's 1024-sample window)."""
+    import torch
+    rng = np.random.default_rng(4)
+    done = 0
+    while done < 100:
+        rooms = [r for r in draw_rooms(rng) if r["rir_len"] <= 12000]
+        if not rooms:
+            continue
+        done += 1
+        srcs = [rng.standard_normal(int(rng.integers(1, 6000))).astype(np.float32) for _ in rooms]
+        snr = rng.uniform(-5, 40, len(rooms)).astype(np.float32)
+        snr[rng.random(len(rooms)) < 0.3] = np.nan
+        prec = int(rng.integers(0, 2))
+        seed = int(rng.integers(0, 1 << 30))
+        lens = [len(s) for s in srcs]
+        src_cat = np.concatenate(srcs)
+        h = ism.rir_batch(rooms)
+        jobs, ylen = ism.conv_jobs([len(r["mics"]) for r in rooms], [r["rir_len"] for r in rooms],
+                                   lens, snr_db=snr, noise_ids=np.arange(len(rooms)) + 100)
+        y = torch.empty(ylen, device="cuda")
+        ism.convolve_batch(jobs, h, torch.from_numpy(src_cat).cuda(), y, seed=seed, precision=prec)
+        torch.cuda.synchronize()
+        y_ref, h_ref = y.cpu(), h.cpu()
+        chunk = int(rng.choice([0, 1, 2, len(rooms)]))
+        y_host = torch.full((ylen,), float("nan")).pin_memory()
+        h_host = torch.full((h_ref.numel(),), float("nan")).pin_memory()
+        ism.dataset_batch(rooms, torch.from_numpy(src_cat).pin_memory(), lens, y_host,
+                          snr_db=snr, seed=seed, noise_id_base=100, precision=prec,
+                          h_host=h_host, chunk_rooms=chunk)
+        assert torch.equal(y_host, y_ref) and torch.equal(h_host, h_ref), (done, chunk, prec)
+        with ism.Server(precision=prec, seed=seed, max_batch=int(rng.integers(1, 9)),
+                        n_streams=int(rng.integers(1, 4))) as srv:
+            tickets = [srv.submit(r, s, float(sn), 100 + i)
+                       for i, (r, s, sn) in enumerate(zip(rooms, srcs, snr))]
+            for i, (t, r, s, sn) in enumerate(zip(tickets, rooms, srcs, snr)):
+                res = srv.wait(t, 60.0)
+                M, L, T = res.n_mics, res.rir_len, res.y_len
+                hs = torch.empty(M * L, device="cuda")
+                ys = torch.empty(M * T, device="cuda")
+                srv.copy(t, hs, ys)
+                srv.release(t)
+                hd = ism.rir_batch([r], window=1024)
+                jd, yl = ism.conv_jobs([M], [L], [len(s)], snr_db=[sn], noise_ids=[100 + i])
+                yd = torch.empty(yl, device="cuda")
+                ism.convolve_batch(jd, hd, torch.from_numpy(s).cuda(), yd, seed=seed, precision=prec)
+                torch.cuda.synchronize()
+                assert torch.equal(hs.cpu(), hd.cpu()) and torch.equal(ys.cpu(), yd.cpu()), (done, i)
