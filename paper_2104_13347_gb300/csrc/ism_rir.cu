@@ -774,8 +774,11 @@ __device__ __forceinline__ void flush_stats(long long *stats, const RirJob &J,
 // ===========================================================================
 // k_ism_taps: direct per-tap kernel
 // ===========================================================================
+// Three CTAs per SM (at most 85 registers; 80 are used, without spills):
+// bounded at two, the compiler took 114-124 registers and the kernel stayed
+// latency-bound at four warps per scheduler.
 template <int R, int KIND>
-__global__ void __launch_bounds__(NT, 2)
+__global__ void __launch_bounds__(NT, 3)
 k_ism_taps(const RirJob *__restrict__ jobs, int n_rirs, int wmax, int W, int max_order,
            int max_taps, float *__restrict__ h, long long *__restrict__ stats,
            unsigned int *__restrict__ counter) {
