@@ -160,10 +160,13 @@ typedef struct ism_rir_opts {
  * The image delay tau = d fs / c is split with the same FP64 rounding rule
  * as the definition (ties to even), so integer delays and window counts are
  * exact; taps are accumulated in FP32.
- * Errors: ISM_ERR_INVALID_ARG for a point outside the room, beta outside
- * [0,1], a tap count of the wrong parity for the filter, fs/c <= 0, order
- * < 0 or > 200, rir_len < 1, n_mics < 1, or a NULL pointer; ISM_ERR_CUDA if
- * a launch or scratch allocation fails. */
+ * Errors: ISM_ERR_INVALID_ARG for dims not finite and > 0, a source or mic
+ * not strictly inside the room, a mic on the source, beta outside [0,1],
+ * fs or c not finite and > 0, rir_len outside [1, 2^30], n_mics < 1, a tap
+ * count outside the filter's range (Hann sinc: odd, 1..255; Lagrange: even,
+ * 2..32), an unknown fd_kind, a lattice order above 200 (given, or that of
+ * the delay-limited set), lattice delays beyond 8e6 samples, or a NULL
+ * pointer; ISM_ERR_CUDA if a launch or scratch allocation fails. */
 int ism_rir_batch(const ism_room *rooms, int64_t n_rooms, float *h_dev,
                   const int64_t *h_offsets, void *stream);
 

@@ -74,15 +74,122 @@ BAD = {
 }
 
 
+BAD.update({
+    "hann taps above 255": dict(n_taps=257),
+    "lagrange taps above 32": dict(fd_kind=1, n_taps=34),
+    "rir above 2^30": dict(rir_len=(1 << 30) + 1),
+    "infinite fs": dict(fs=float("inf")),
+    "nan beta": dict(beta=[0.8] * 5 + [float("nan")]),
+    "nan mic": dict(mics=[[2.0, float("nan"), 2.0]]),
+    "lattice delays beyond 8e6 samples": dict(dims=[20.0, 20.0, 20.0], order=200, fs=192000.0),
+})
+
+
+def device_buffer(n):
+    """A real device buffer where a GPU is present (so that a regression in
+    the checks could never launch onto a stray pointer), else a pointer the
+    library must never dereference."""
+    import torch
+    if torch.cuda.is_available():
+        t = torch.zeros(n, device="cuda")
+        return t, ctypes.c_void_p(t.data_ptr())
+    return None, ctypes.c_void_p(0x1000)
+
+
 @pytest.mark.parametrize("case", sorted(BAD))
 def test_rir_batch_rejects_invalid_rooms(lib, case):
     L = lib.load()
     r = good_room(**BAD[case])
     arr, keep = lib.make_rooms([r])
-    fake = ctypes.c_void_p(0x1000)  # never dereferenced: validation comes first
-    st = L.ism_rir_batch(arr, 1, fake, None, None)
+    buf, ptr = device_buffer(1 << 16)
+    st = L.ism_rir_batch(arr, 1, ptr, None, None)
     assert st == lib.ISM_ERR_INVALID_ARG, (case, st, lib.last_error())
     assert lib.last_error()
+
+
+def documented_valid(r):
+    """The room rules include/ism.h states for ism_rir_batch, restated (the
+    delay-limited order by the header's formula; the 8e6-sample delay rule
+    cannot fire on the rooms drawn below)."""
+    d, b = np.asarray(r["dims"], float), np.asarray(r["beta"], float)
+    s, mics = np.asarray(r["src"], float), np.asarray(r["mics"], float).reshape(-1, 3)
+    if not np.all(np.isfinite(d) & (d > 0)) or not np.all((b >= 0) & (b <= 1)):
+        return False
+    inside = lambda p: bool(np.all((p > 0) & (p < d)))
+    if not inside(s) or len(mics) < 1:
+        return False
+    for m in mics:
+        if not inside(m) or float(np.sum((m - s) ** 2)) < 1e-12:
+            return False
+    fs, c, L, taps, kind = r["fs"], r["c"], r["rir_len"], r["n_taps"], r["fd_kind"]
+    if not (fs > 0 and math.isfinite(fs) and c > 0 and math.isfinite(c)) or not 1 <= L <= 1 << 30:
+        return False
+    if kind == 0:
+        if not (1 <= taps <= 255 and taps % 2 == 1):
+            return False
+    elif kind == 1:
+        if not (2 <= taps <= 32 and taps % 2 == 0):
+            return False
+    else:
+        return False
+    order = r["order"]
+    if order < 0:
+        reach = (L + taps) * c / fs
+        order = max(int(math.floor((reach + abs((1 - 2 * p) * s[a] - m[a])) / (2 * d[a])))
+                    for m in mics for a in range(3) for p in (0, 1))
+    return order <= 200
+
+
+def test_room_checks_follow_the_documented_rules(lib):
+    """Seeded random rooms, valid and invalid in every field (non-finite
+    values, points on or past a wall, tap counts at and past each filter's
+    limits, orders past 200, RIR lengths at 2^30): the library accepts
+    exactly the rooms the header's rules accept (host-only call)."""
+    L = lib.load()
+    rng = np.random.default_rng(77)
+    bad_f = [0.0, -1.0, float("nan"), float("inf")]
+    n_ok = 0
+    for _ in range(3000):
+        r = good_room()
+        pick = lambda p: rng.random() < p
+        r["dims"] = list(rng.uniform(1, 10, 3))
+        if pick(0.05):
+            r["dims"][int(rng.integers(3))] = float(rng.choice(bad_f))
+        r["beta"] = list(rng.uniform(0, 1, 6))
+        if pick(0.05):
+            r["beta"][int(rng.integers(6))] = float(rng.choice([-0.1, 1.1, float("nan")]))
+        dims = np.nan_to_num(np.abs(np.asarray(r["dims"], float)), posinf=1.0) + 1e-9
+
+        def point():
+            p = rng.uniform(0.01, 0.99, 3) * dims
+            if pick(0.05):
+                a = int(rng.integers(3))
+                p[a] = float(rng.choice([0.0, dims[a], -0.5, dims[a] + 0.5, float("nan")]))
+            return p
+
+        r["src"] = list(point())
+        r["mics"] = np.array([point() for _ in range(int(rng.integers(0, 4)))]).reshape(-1, 3)
+        if pick(0.03) and len(r["mics"]):
+            r["mics"][0] = r["src"]
+        r["fs"] = float(rng.uniform(8000, 48000)) if not pick(0.05) else float(rng.choice(bad_f))
+        r["c"] = float(rng.uniform(300, 400)) if not pick(0.05) else float(rng.choice(bad_f))
+        r["order"] = (int(rng.choice([-1, 0, 3, 15])) if not pick(0.2)
+                      else int(rng.choice([-5, 200, 201, 250])))
+        r["fd_kind"] = int(rng.choice([0, 1])) if not pick(0.05) else int(rng.choice([2, -1]))
+        valid_taps = [1, 3, 9, 33, 81, 255] if r["fd_kind"] == 0 else [2, 8, 32]
+        r["n_taps"] = (int(rng.choice(valid_taps)) if not pick(0.2)
+                       else int(rng.choice([-1, 0, 2, 3, 34, 80, 256, 257])))
+        r["rir_len"] = (int(rng.choice([1, 100, 5000])) if not pick(0.15)
+                        else int(rng.choice([-5, 0, 60000, 1 << 30, (1 << 30) + 1])))
+        if len(r["mics"]) == 0:
+            continue  # an empty mic array needs a NULL pointer: covered by BAD
+        arr, keep = lib.make_rooms([r])
+        w = ctypes.c_int32(-7)
+        st = L.ism_rir_tuned_window(arr, 1, None, ctypes.byref(w))
+        want = documented_valid(r)
+        assert st == (lib.ISM_OK if want else lib.ISM_ERR_INVALID_ARG), (r, st, lib.last_error())
+        n_ok += want
+    assert 500 < n_ok < 2500
 
 
 def test_rir_batch_argument_errors(lib):
