@@ -73,7 +73,8 @@ typedef enum ism_precision { ISM_F32 = 0, ISM_BF16X3 = 1 } ism_precision;
  *         a reflections on one wall is damped by beta^a (0^0 = 1).
  * src     source position (metres), strictly inside the room.
  * mics    host array of 3*n_mics doubles (x,y,z per mic), strictly inside
- *         the room and not on the source.
+ *         the room and not on the source; 1 <= n_mics <= 65536 (a room's
+ *         noise streams are keyed noise_id * 65536 + mic).
  * order   lattice order N >= 0: images (u,v,w,l,m,n), u,v,w in {0,1},
  *         l,m,n in [-N, N], 8 (2N+1)^3 in all.  ISM_ORDER_AUTO (any
  *         negative value): per microphone, the smallest N whose lattice
@@ -262,7 +263,9 @@ typedef struct ism_conv_job {
  *            SplitMix64 output k of that stream (u1 from bits 63..40, u2 from
  *            bits 39..16) and take the two Box--Muller branches.
  * precision  ISM_F32 or ISM_BF16X3.
- * Errors: ISM_ERR_INVALID_ARG (bad lengths, NULL pointers, unknown
+ * Errors: ISM_ERR_INVALID_ARG (n_mics outside [1, 65536], rir_len or
+ * src_len outside [1, 2^40], a negative offset, an SNR of +-inf, more than
+ * 2^30 - 1 tiles of 8 mics x 2048 outputs in a job, NULL pointers, an unknown
  * precision), ISM_ERR_CUDA, ISM_ERR_OUT_OF_MEMORY (scratch). */
 int ism_convolve_batch(const ism_conv_job *jobs, int64_t n_jobs, const float *h_dev,
                        const float *src_dev, float *y_dev, uint64_t seed,
@@ -299,7 +302,7 @@ int ism_convolve_batch(const ism_conv_job *jobs, int64_t n_jobs, const float *h_
  *                 do not depend on the chunking.
  * Returns when every output is in host memory.  Errors: those of
  * ism_rir_batch and ism_convolve_batch, ISM_ERR_INVALID_ARG for NULL
- * buffers or src_lens < 1, ISM_ERR_CUDA, ISM_ERR_OUT_OF_MEMORY. */
+ * buffers or src_lens outside [1, 2^40], ISM_ERR_CUDA, ISM_ERR_OUT_OF_MEMORY. */
 int ism_dataset_batch(const ism_room *rooms, int64_t n_rooms, const float *src_host,
                       const int64_t *src_lens, const int64_t *src_offsets,
                       const float *snr_db, uint64_t seed, uint64_t noise_id_base,
@@ -340,7 +343,8 @@ typedef struct ism_plan_config {
  * the caller's and must outlive the plan; the plan keeps its own device
  * block (descriptors and scratch) and two page-locked staging buffers, and
  * captures its graphs on a private stream (call it before capturing any
- * stream of your own).  Errors: ISM_ERR_INVALID_ARG (rooms, config),
+ * stream of your own).  Errors: ISM_ERR_INVALID_ARG (rooms, config,
+ * src_lens outside [1, 2^40]),
  * ISM_ERR_OUT_OF_MEMORY, ISM_ERR_CUDA. */
 int ism_plan_create(const ism_room *rooms, int64_t n_rooms, const int64_t *src_lens,
                     const ism_plan_config *config, float *h_dev, const float *src_dev,
@@ -401,7 +405,8 @@ typedef struct ism_frame_job {
 /* ism_frames_batch -- cut n_frames frames of frame_len samples and add their
  * noise.  jobs: host array; y_dev, frames_dev: device floats (must not
  * overlap).  Errors: ISM_ERR_INVALID_ARG (NULL pointers, frame_len < 1,
- * n_mics < 1, y_len < 1, negative offsets, SNR = -inf), ISM_ERR_CUDA,
+ * n_mics outside [1, 65536], y_len outside [1, 2^40], negative offsets,
+ * SNR = -inf), ISM_ERR_CUDA,
  * ISM_ERR_OUT_OF_MEMORY (scratch). */
 int ism_frames_batch(const ism_frame_job *jobs, int64_t n_frames, int32_t frame_len,
                      const float *y_dev, float *frames_dev, uint64_t seed, void *stream);
@@ -476,7 +481,8 @@ int ism_serve_create(const ism_serve_config *config, ism_server **out);
  * copied into a page-locked host block before the call returns, so the
  * caller's buffer may be reused at once.  ISM_ERR_BUSY if the queue is full
  * or the request alone needs more than max_hbm_bytes; ISM_ERR_INVALID_ARG
- * for an invalid room or source; ISM_ERR_OUT_OF_MEMORY if no host block
+ * for an invalid room or source (src_len outside [1, 2^40]);
+ * ISM_ERR_OUT_OF_MEMORY if no host block
  * can be had. */
 int ism_serve_submit(ism_server *server, const ism_request *request, uint64_t *ticket);
 

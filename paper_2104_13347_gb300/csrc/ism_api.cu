@@ -151,7 +151,7 @@ int validate_room(const ism_room &r, int64_t idx) {
     for (int w = 0; w < 6; ++w)
         if (!(r.beta[w] >= 0.0 && r.beta[w] <= 1.0)) return bad("beta must lie in [0, 1]");
     if (!inside(r.src, r.dims)) return bad("source not strictly inside the room");
-    if (r.n_mics < 1) return bad("n_mics must be >= 1");
+    if (r.n_mics < 1 || r.n_mics > kMaxMics) return bad("n_mics must lie in [1, 65536]");
     if (!r.mics) return bad("mics is NULL");
     for (int m = 0; m < r.n_mics; ++m) {
         const double *p = r.mics + 3 * m;
@@ -629,8 +629,9 @@ int ism::convolve_batch(const ism_conv_job *jobs, int64_t n_jobs, const float *h
     int64_t n_part = 0;
     for (int64_t i = 0; i < n_jobs; ++i) {
         const ism_conv_job &J = jobs[i];
-        if (J.n_mics < 1 || J.rir_len < 1 || J.src_len < 1 || J.h_offset < 0 ||
-            J.src_offset < 0 || J.y_offset < 0)
+        if (J.n_mics < 1 || J.n_mics > kMaxMics || J.rir_len < 1 || J.rir_len > kMaxSignal ||
+            J.src_len < 1 || J.src_len > kMaxSignal || J.h_offset < 0 || J.src_offset < 0 ||
+            J.y_offset < 0)
             return fail(ISM_ERR_INVALID_ARG, "job " + std::to_string(i) + ": bad sizes/offsets");
         ConvJob &c = cj[i];
         memset(&c, 0, sizeof(c));

@@ -89,7 +89,8 @@ extern "C" int ism_dataset_batch(const ism_room *rooms, int64_t n_rooms, const f
     for (int64_t i = 0; i < n_rooms; ++i) {
         const ism_room &R = rooms[i];
         if (int st = validate_room(R, i)) return st;
-        if (src_lens[i] < 1) return fail(ISM_ERR_INVALID_ARG, "room " + std::to_string(i) + ": src_len < 1");
+        if (src_lens[i] < 1 || src_lens[i] > kMaxSignal)
+            return fail(ISM_ERR_INVALID_ARG, "room " + std::to_string(i) + ": src_len must lie in [1, 2^40]");
         ylen[i] = (int64_t)R.n_mics * (src_lens[i] + R.rir_len - 1);
         hlen[i] = (int64_t)R.n_mics * R.rir_len;
         so[i] = src_offsets ? src_offsets[i] : sp;

@@ -130,7 +130,8 @@ extern "C" int ism_frames_batch(const ism_frame_job *jobs, int64_t n_frames, int
     std::vector<FrameJob> fj((size_t)n_frames);
     for (int64_t i = 0; i < n_frames; ++i) {
         const ism_frame_job &J = jobs[i];
-        if (J.n_mics < 1 || J.y_len < 1 || J.y_offset < 0 || J.out_offset < 0)
+        if (J.n_mics < 1 || J.n_mics > kMaxMics || J.y_len < 1 || J.y_len > kMaxSignal ||
+            J.y_offset < 0 || J.out_offset < 0)
             return fail(ISM_ERR_INVALID_ARG, "frame " + std::to_string(i) + ": bad sizes/offsets");
         if (isinf(J.snr_db) && J.snr_db < 0)
             return fail(ISM_ERR_INVALID_ARG, "frame " + std::to_string(i) + ": snr -inf");

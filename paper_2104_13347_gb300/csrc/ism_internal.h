@@ -218,6 +218,12 @@ struct ConvLaunch {
 };
 // Noise-partial grid: one slot per 8 mics x 2048 outputs (the FP32
 // kernel's tile; a tile of the split-BF16 kernel spans two slots).
+// Size limits of the entry points: signal lengths (sources, the RIRs a
+// convolution is given, a frame's source rows) up to 2^40 samples, and up
+// to 65536 mics per room (a room's noise streams are keyed noise_id * 65536
+// + mic).  Every size product the host forms then stays below 2^57.
+constexpr int64_t kMaxSignal = (int64_t)1 << 40;
+constexpr int kMaxMics = 65536;
 constexpr int kConvMG = 8;     // mics per tile
 constexpr int kConvTT = 2048;  // outputs per slot
 __host__ __device__ inline int conv_partials_per_job(int n_mics, int64_t y_len) {

@@ -182,8 +182,8 @@ int ism_plan_create(const ism_room *rooms, int64_t n_rooms, const int64_t *src_l
         return fail(ISM_ERR_INVALID_ARG, "max_order must lie in [0, 200]");
     for (int64_t i = 0; i < n_rooms; ++i) {
         if (int st = validate_room(rooms[i], i)) return st;
-        if (src_lens && src_lens[i] < 1)
-            return fail(ISM_ERR_INVALID_ARG, "room " + std::to_string(i) + ": src_len < 1");
+        if (src_lens && (src_lens[i] < 1 || src_lens[i] > kMaxSignal))
+            return fail(ISM_ERR_INVALID_ARG, "room " + std::to_string(i) + ": src_len must lie in [1, 2^40]");
     }
     std::unique_ptr<ism_plan> P(new ism_plan());
     cudaError_t e = cudaGetDevice(&P->device);

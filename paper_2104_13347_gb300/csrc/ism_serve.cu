@@ -503,6 +503,7 @@ int ism_serve_submit(ism_server *s, const ism_request *rq, uint64_t *ticket) {
     if (!s || !rq || !ticket) return fail(ISM_ERR_INVALID_ARG, "NULL argument");
     if (int st = validate_room(rq->room, 0)) return st;
     if (rq->src_len < 1 || !rq->src_host) return fail(ISM_ERR_INVALID_ARG, "empty source");
+    if (rq->src_len > kMaxSignal) return fail(ISM_ERR_INVALID_ARG, "src_len above 2^40");
     if (!isnan(rq->snr_db) && !isfinite(rq->snr_db))
         return fail(ISM_ERR_INVALID_ARG, "snr must be finite or NaN");
     const int64_t bytes = req_bytes(*rq);

@@ -82,6 +82,7 @@ BAD.update({
     "nan beta": dict(beta=[0.8] * 5 + [float("nan")]),
     "nan mic": dict(mics=[[2.0, float("nan"), 2.0]]),
     "lattice delays beyond 8e6 samples": dict(dims=[20.0, 20.0, 20.0], order=200, fs=192000.0),
+    "more than 65536 mics": dict(mics=np.tile([[2.0, 2.0, 2.0]], (65537, 1))),
 })
 
 
@@ -116,7 +117,7 @@ def documented_valid(r):
     if not np.all(np.isfinite(d) & (d > 0)) or not np.all((b >= 0) & (b <= 1)):
         return False
     inside = lambda p: bool(np.all((p > 0) & (p < d)))
-    if not inside(s) or len(mics) < 1:
+    if not inside(s) or not 1 <= len(mics) <= 65536:
         return False
     for m in mics:
         if not inside(m) or float(np.sum((m - s) ** 2)) < 1e-12:
@@ -219,6 +220,57 @@ def test_convolve_batch_argument_errors(lib):
     inf_snr, _ = lib.conv_jobs([1], [100], [50], snr_db=[float("inf")])
     assert L.ism_convolve_batch(inf_snr, 1, p, p, p, 0, 0, None) == lib.ISM_ERR_INVALID_ARG
     assert L.ism_convolve_batch(jobs, 0, p, p, p, 0, 0, None) == lib.ISM_OK
+
+
+def conv_job_valid(n_mics, rir_len, src_len, offs, snr):
+    """The job rules include/ism.h states for ism_convolve_batch, restated."""
+    if not (1 <= n_mics <= 65536 and 1 <= rir_len <= 1 << 40 and 1 <= src_len <= 1 << 40):
+        return False
+    if min(offs) < 0 or not (math.isnan(snr) or math.isfinite(snr)):
+        return False
+    tiles = -(-n_mics // 8) * -(-(src_len + rir_len - 1) // 2048)
+    return tiles <= (1 << 30) - 1
+
+
+def test_convolve_job_checks_follow_the_documented_rules(lib):
+    """Seeded random jobs at and past every documented limit (lengths up to
+    2^63 - 1, mic counts past 65536, negative offsets, infinite SNRs, tile
+    counts past 2^30): every job the rules reject is rejected before the
+    device is touched.  Jobs the rules accept are submitted only where no GPU
+    is present (the fake pointers are never dereferenced; the call then
+    fails on the device, not on its arguments)."""
+    import torch
+    L = lib.load()
+    gpu = torch.cuda.is_available()
+    p = ctypes.c_void_p(0x1000)
+    rng = np.random.default_rng(5)
+    big = [1, 7, 2048, 1 << 20, 1 << 40, (1 << 40) + 1, (1 << 62), (1 << 63) - 1, 0, -1]
+    n_valid = n_invalid = 0
+    for _ in range(2000):
+        n = int(rng.integers(1, 4))
+        fields = []
+        for _ in range(n):
+            fields.append((int(rng.choice([1, 8, 9, 33, 65536, 65537, 0, -3])),
+                           int(rng.choice(big)), int(rng.choice(big)),
+                           [int(rng.choice([0, 5, 1 << 40, -1])) if rng.random() < 0.1 else 0
+                            for _ in range(3)],
+                           float(rng.choice([np.nan, 0.0, 30.0, 1e30, np.inf, -np.inf]))))
+        jobs = (lib.ConvJob * n)()
+        for J, (m, lh, ls, offs, snr) in zip(jobs, fields):
+            J.n_mics, J.rir_len, J.src_len = m, lh, ls
+            J.h_offset, J.src_offset, J.y_offset = offs
+            J.snr_db = snr
+        want = all(conv_job_valid(*f) for f in fields)
+        if want and gpu:
+            continue
+        st = L.ism_convolve_batch(jobs, n, p, p, p, 0, int(rng.integers(0, 2)), None)
+        if want:
+            assert st != lib.ISM_ERR_INVALID_ARG, (fields, lib.last_error())
+            n_valid += 1
+        else:
+            assert st == lib.ISM_ERR_INVALID_ARG, fields
+            n_invalid += 1
+    assert n_invalid > 500 and (gpu or n_valid > 20)
 
 
 # --------------------------------------------------------------------------
