@@ -273,6 +273,39 @@ def test_convolve_job_checks_follow_the_documented_rules(lib):
     assert n_invalid > 500 and (gpu or n_valid > 20)
 
 
+def test_frame_job_checks_follow_the_documented_rules(lib):
+    """Seeded random frame jobs at and past the documented limits (mic
+    counts past 65536, row lengths past 2^40, negative offsets, SNR -inf,
+    frame lengths below 1): rejected exactly when the rules say so; jobs the
+    rules accept are submitted only where no GPU is present."""
+    import torch
+    L = lib.load()
+    gpu = torch.cuda.is_available()
+    p = ctypes.c_void_p(0x1000)
+    rng = np.random.default_rng(6)
+    n_invalid = 0
+    for _ in range(1000):
+        m = int(rng.choice([1, 8, 65536, 65537, 0, -1]))
+        yl = int(rng.choice([1, 1000, 1 << 40, (1 << 40) + 1, 0, -7]))
+        yo, oo = (int(rng.choice([0, 9, -1])) for _ in range(2))
+        snr = float(rng.choice([np.nan, 10.0, np.inf, -np.inf]))
+        fl = int(rng.choice([1, 1024, 0, -2]))
+        want = (1 <= m <= 65536 and 1 <= yl <= 1 << 40 and yo >= 0 and oo >= 0
+                and snr != -np.inf and fl >= 1)
+        if want and gpu:
+            continue
+        jobs = (lib.FrameJob * 1)()
+        J = jobs[0]
+        J.n_mics, J.y_len, J.y_offset, J.out_offset, J.t0, J.snr_db = m, yl, yo, oo, 0, snr
+        st = L.ism_frames_batch(jobs, 1, fl, p, p, 0, None)
+        if want:
+            assert st != lib.ISM_ERR_INVALID_ARG, (m, yl, yo, oo, snr, fl, lib.last_error())
+        else:
+            assert st == lib.ISM_ERR_INVALID_ARG, (m, yl, yo, oo, snr, fl)
+            n_invalid += 1
+    assert n_invalid > 300
+
+
 # --------------------------------------------------------------------------
 # serving: host-side failure paths
 # --------------------------------------------------------------------------
