@@ -325,10 +325,11 @@ typedef struct ism_plan_config {
                             multiple of 32 in [32, 8192], or ISM_WINDOW_TUNE
                             (the bucket's tuned window if it is tuned,
                             automatic otherwise; plans never tune) */
-    int32_t max_order;   /* lattice-order capacity of every RIR: 0 = each
-                            RIR's order at creation (ISM_ORDER_AUTO rooms of
-                            later runs may need more: give it here); never
-                            below a RIR's order at creation */
+    int32_t max_order;   /* lattice-order capacity of every RIR, in
+                            [0, 200]: 0 = each RIR's order at creation
+                            (ISM_ORDER_AUTO rooms of later runs may need
+                            more: give it here); never below a RIR's order
+                            at creation */
     int32_t variant;     /* ism_rir_variant */
     uint64_t seed;       /* noise seed (see ism_convolve_batch) */
 } ism_plan_config;
